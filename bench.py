@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""Benchmark of the sparse forward + reverse-mode hot path on one GB300.
+
+One step = the forward and both VJPs of Y = A X (Table 1, SpDMM rows):
+  SpMM        Y  = A X                    (spx_spmm)
+  SDDMM       gA = (G X^T) masked to A    (spx_sddmm)
+  A^T-SpMM    gX = A^T G                  (spx_spmm_t)
+on the random power-law CSR workload: n = 2^20 rows/cols, row lengths
+min(4096, floor(5.62 U^(-1/1.5))) (mean 16), uniform unique columns, N(0,1) values,
+dense X and G of width k = 32 (N(0,1)).  Inputs stay resident in HBM and exceed L2.
+The transpose pattern and row plans are per-pattern setup, outside the timed region.
+
+The headline value is compulsory bytes per step (each CSR array, X, G and the outputs
+moved once) divided by the step time: an effective GB/s that earns no credit for
+extra traffic.  The JSON line also carries a roofline object for the dominant kernel,
+a CPU baseline of the FP64 oracle on a bounded sample, an end-to-end number through
+host buffers, sampled SM clocks and extra workloads (k = 128, 3D Poisson 128^3).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sparse fwd+bwd GB/s vs HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------------- bytes
+def compulsory_bytes(m, n, nnz, k):
+    """Per-kernel compulsory bytes (int32 index / float32 value = 4 B)."""
+    spmm = 4 * (m + 1) + 8 * nnz + 4 * n * k + 4 * m * k
+    sddmm = 4 * (m + 1) + 4 * nnz + 4 * m * k + 4 * n * k + 4 * nnz
+    spmm_t = 4 * (n + 1) + 12 * nnz + 4 * m * k + 4 * n * k
+    return {"spmm": spmm, "sddmm": sddmm, "spmm_t": spmm_t}
+
+
+def gather_bytes(m, n, nnz, k):
+    """Bytes when every entry's dense row is fetched from DRAM (no cache reuse)."""
+    spmm = 4 * (m + 1) + 8 * nnz + 4 * nnz * k + 4 * m * k
+    sddmm = 4 * (m + 1) + 8 * nnz + 4 * m * k + 4 * nnz * k
+    spmm_t = 4 * (n + 1) + 12 * nnz + 4 * nnz * k + 4 * n * k
+    return {"spmm": spmm, "sddmm": sddmm, "spmm_t": spmm_t}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- traffic
+def ncu_traffic(kernel_tag, src_file):
+    """dram bytes per launch from a committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m_h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    if not m_b or not m_h:
+        return None
+    with open(src_file, "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != m_h.group(1):
+            return None                      # kernel changed since the counters were taken
+    return float(m_b.group(1))
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- workload
+class Workload:
+    def __init__(self, kind="powerlaw", k=32, seed=0, device="cuda"):
+        import synth
+        import torch
+        import paper_2212_05159_gb300 as spx
+        from paper_2212_05159_gb300 import abi
+        self.kind, self.k = kind, k
+        if kind == "powerlaw":
+            A = synth.powerlaw_csr(1 << 20, seed=seed)
+            self.name = f"powerlaw n=2^20 mean16 max4096 k={k}"
+        elif kind == "poisson3d":
+            A = synth.poisson3d(128)
+            self.name = f"poisson3d 128^3 7-point k={k}"
+        else:
+            raise ValueError(kind)
+        self.host = A
+        self.dA = spx.CSR.from_host(A, device)
+        self.X = torch.from_numpy(synth.normal((A.n, k), seed + 1)).to(device)
+        self.G = torch.from_numpy(synth.normal((A.m, k), seed + 2)).to(device)
+        self.Y = torch.empty(A.m, k, device=device)
+        self.gA = torch.empty(A.nnz, device=device)
+        self.gX = torch.empty(A.n, k, device=device)
+        # per-pattern setup (outside timed regions)
+        self.plan = self.dA.plan()
+        _, _, self.perm = self.dA.transpose_pattern()
+        self.t_plan = self.dA.t_plan()
+        self.s_A = self.dA.struct()
+        self.s_AT = self.dA.t_struct()
+        self.abi = abi
+        self.m, self.n, self.nnz = A.m, A.n, A.nnz
+
+    def launches_per_step(self):
+        return 3
+
+    def run_kernel(self, which):
+        a = self.abi
+        if which == "spmm":
+            a.spx_spmm(self.s_A, self.X, self.Y, 1.0, 0.0, self.plan)
+        elif which == "sddmm":
+            a.spx_sddmm(self.s_A, self.G, self.X, self.gA, 1.0)
+        else:
+            a.spx_spmm_t(self.s_AT, self.perm, self.G, self.gX, 1.0, 0.0, self.t_plan)
+
+    KERNELS = ("spmm", "sddmm", "spmm_t")
+
+
+def time_workload(W, steps, warmup, ws):
+    """Device-timed steps: returns (ms_per_step, {kernel: avg ms per launch})."""
+    import torch
+    for _ in range(warmup):
+        for kname in W.KERNELS:
+            W.run_kernel(kname)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(W.KERNELS) + 1)] for _ in range(steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(st)
+    for s in range(steps):
+        ev[s][0].record(st)
+        for i, kname in enumerate(W.KERNELS):
+            W.run_kernel(kname)
+            ev[s][i + 1].record(st)
+    end.record(st)
+    torch.cuda.synchronize()
+    barrier(ws)
+    total_ms = start.elapsed_time(end)
+    per = {k: 0.0 for k in W.KERNELS}
+    for s in range(steps):
+        for i, kname in enumerate(W.KERNELS):
+            per[kname] += ev[s][i].elapsed_time(ev[s][i + 1])
+    per = {k: v / steps for k, v in per.items()}
+    return total_ms / steps, per
+
+
+def time_e2e(W, steps, warmup):
+    """Same step through host buffers: pinned H2D of values, X, G; D2H of Y, gA, gX."""
+    import torch
+    hv = torch.from_numpy(W.host.values).pin_memory()
+    hX = W.X.cpu().pin_memory()
+    hG = W.G.cpu().pin_memory()
+    oY = torch.empty_like(W.Y, device="cpu").pin_memory()
+    oA = torch.empty_like(W.gA, device="cpu").pin_memory()
+    oX = torch.empty_like(W.gX, device="cpu").pin_memory()
+    vals = W.dA.values
+
+    def step():
+        vals.copy_(hv, non_blocking=True)
+        W.X.copy_(hX, non_blocking=True)
+        W.G.copy_(hG, non_blocking=True)
+        for kname in W.KERNELS:
+            W.run_kernel(kname)
+        oY.copy_(W.Y, non_blocking=True)
+        oA.copy_(W.gA, non_blocking=True)
+        oX.copy_(W.gX, non_blocking=True)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        step()
+    b.record(st)
+    torch.cuda.synchronize()
+    h2d = hv.numel() * 4 + hX.numel() * 4 + hG.numel() * 4
+    d2h = oY.numel() * 4 + oA.numel() * 4 + oX.numel() * 4
+    return a.elapsed_time(b) / steps, h2d, d2h
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(k=32, seed=0, budget_s=12.0):
+    import oracle
+    import synth
+    A = synth.powerlaw_csr(1 << 20, seed=seed)
+    X = synth.normal((A.n, k), seed + 1)
+    G = synth.normal((A.m, k), seed + 2)
+    oracle.build()
+    # grow a contiguous row block until one pass of the three oracle routines costs ~budget/3
+    rows = 4096
+    while True:
+        sub, t = _oracle_pass(A, X, G, rows)
+        if t > budget_s / 3 or rows >= A.m:
+            break
+        rows = min(A.m, int(rows * min(8.0, max(2.0, (budget_s / 3) / max(t, 1e-3)))))
+    reps = max(1, int(budget_s // max(t, 1e-6)) - 1)
+    times = [t] + [_oracle_pass(A, X, G, rows)[1] for _ in range(min(reps, 2))]
+    t_med = float(np.median(times))
+    b = compulsory_bytes(sub.m, A.n, sub.nnz, k)
+    # the dense operands are only touched where the sample reaches them; count the rows of
+    # X / gX the sample touches instead of all n
+    touched = np.unique(sub.indices).size
+    b_tot = (4 * (sub.m + 1) + 8 * sub.nnz + 4 * touched * k + 4 * sub.m * k) + \
+            (4 * (sub.m + 1) + 8 * sub.nnz + 4 * sub.m * k + 4 * touched * k) + \
+            (4 * (sub.m + 1) + 12 * sub.nnz + 4 * sub.m * k + 4 * touched * k)
+    del b
+    desc = (f"rows [0,{sub.m}) of the n=2^20 power-law matrix ({sub.nnz} entries, k={k}): "
+            f"oracle spmm + sddmm + spmm_t, median of {len(times)} passes")
+    return b_tot / t_med / 1e9, desc, 1
+
+
+def _oracle_pass(A, X, G, rows):
+    import oracle
+    import synth
+    ip = A.indptr[: rows + 1]
+    nnz = int(ip[-1])
+    sub = synth.CSR(rows, A.n, ip, A.indices[:nnz], A.values[:nnz])
+    t0 = time.perf_counter()
+    oracle.spmm(sub, X)
+    oracle.sddmm(sub, G[:rows], X)
+    oracle.spmm_t(sub, G[:rows])
+    return sub, time.perf_counter() - t0
+
+
+# ----------------------------------------------------------------------------- main
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    hbm, _ = measured_peaks()
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(budget_s=1.0)
+    desc = ""
+    for _ in range(args.steps):
+        v, desc, cores = cpu_baseline(budget_s=3.0)
+        vals.append(v)
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "powerlaw n=2^20 mean16 max4096 k=32 (bounded row sample)",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0, "hbm_peak_gbs": hbm}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=32)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    args.warmup = max(args.warmup, 3)
+    import paper_2212_05159_gb300  # noqa: F401  (fails loudly without the CUDA library)
+
+    W = Workload("powerlaw", k=args.k)
+    clocks = ClockSampler(index=local)
+    clocks.start()
+    ms, per = time_workload(W, args.steps, args.warmup, ws)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms, ws)
+    cb = compulsory_bytes(W.m, W.n, W.nnz, W.k)
+    gb = gather_bytes(W.m, W.n, W.nnz, W.k)
+    step_bytes = sum(cb.values())
+    value = ws * step_bytes / (ms * 1e-3) / 1e9
+    hbm, hbm_src = measured_peaks()
+    dom = max(per, key=per.get)
+    src = {"spmm": "spmm.cu", "sddmm": "sddmm.cu", "spmm_t": "spmm.cu"}[dom]
+    src_path = os.path.join(ROOT, "paper_2212_05159_gb300", "csrc", src)
+    achieved = cb[dom] / (per[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "peak_source": hbm_src, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": ncu_traffic(f"{dom}_powerlaw_k{W.k}", src_path),
+                "algorithmic_bytes": cb[dom], "bytes_model": "compulsory",
+                "gather_model_frac": gb[dom] / (per[dom] * 1e-3) / 1e9 / hbm}
+    e2e_ms, h2d, d2h = time_e2e(W, max(3, args.steps // 2), 2)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": W.name, "step": "SpMM fwd + SDDMM (grad A) + A^T G (grad X)",
+                   "m": W.m, "n": W.n, "nnz": W.nnz, "k": W.k,
+                   "l2": "inputs larger than L2 (~0.9 GB touched per step), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "per_kernel_ms": per,
+        "per_kernel_gbs_compulsory": {k: cb[k] / (per[k] * 1e-3) / 1e9 for k in per},
+        "roofline": roofline,
+        "e2e": {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": W.launches_per_step() * args.steps,
+        "clocks": clk,
+    }
+    if not args.no_extras and rank == 0:
+        extras = {}
+        for kind, k in (("powerlaw", 128), ("poisson3d", 32)):
+            del W
+            torch.cuda.empty_cache()
+            W = Workload(kind, k=k)
+            ms2, per2 = time_workload(W, max(5, args.steps // 2), 3, 1)
+            cb2 = compulsory_bytes(W.m, W.n, W.nnz, W.k)
+            extras[W.name] = {"ms_per_step": ms2, "gbs_compulsory": sum(cb2.values()) / (ms2 * 1e-3) / 1e9,
+                              "frac_of_peak": sum(cb2.values()) / (ms2 * 1e-3) / 1e9 / hbm,
+                              "per_kernel_ms": per2}
+        line["extras"] = extras
+    if rank == 0 and not args.no_cpu:
+        v, desc, cores = cpu_baseline(k=args.k)
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,158 @@
+/*
+ * spx.h -- C ABI of the GB300 (sm_103a) sparse forward / reverse-mode kernels.
+ *
+ * The operations follow "Optimized Sparse Matrix Operations for Reverse Mode
+ * Automatic Differentiation" (arXiv 2212.05159): CSR matrices (Section 3), the
+ * vector-Jacobian products of Table 1, with gradients of sparse inputs kept on the
+ * input's own sparsity pattern (Section 3.1, "Sparse Methods").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an spx_status; SPX_OK is 0.  Nothing throws or aborts
+ *   across the ABI.  spx_last_error() returns a thread-local message describing the
+ *   most recent failure on the calling thread.
+ * - The caller owns all memory.  Pointers marked "device" must be device memory of
+ *   the current CUDA device; pointers marked "host" are host memory.  No entry point
+ *   allocates device memory except where its comment says so; scratch space is a
+ *   caller-provided workspace whose size a *_workspace_size() query returns.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *   are asynchronous on that stream unless their comment says they synchronize it.
+ * - Integers: int32 row/column indices and indptr entries (nnz < 2^31); values are
+ *   IEEE float32 on the device.  Dense operands are row-major with a leading
+ *   dimension (ld*, in elements, >= the number of columns).
+ * - CSR patterns must have sorted, unique column indices per row.  spx_csr_validate()
+ *   checks a pattern on the device; the compute entry points do not re-check it.
+ * - mask(A) is the *structural* pattern of A: every stored entry, including stored
+ *   zeros, belongs to it (reading of the mask definition in Section 3).
+ */
+#ifndef SPX_H
+#define SPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spx_status {
+    SPX_OK = 0,
+    SPX_INVALID_ARG = 1,     /* a pointer, size or leading dimension is unusable */
+    SPX_BAD_PATTERN = 2,     /* indptr not monotone, or an index out of range */
+    SPX_UNSORTED = 3,        /* column indices not strictly increasing in a row */
+    SPX_OOM_WORKSPACE = 4,   /* the workspace passed is smaller than required */
+    SPX_MAXITER = 5,         /* an iterative solve hit its iteration limit */
+    SPX_BREAKDOWN = 6,       /* CG breakdown: p^T A p <= 0 or r^T z <= 0 */
+    SPX_NONFINITE = 7,       /* a NaN / Inf appeared */
+    SPX_DEVICE_TIMEOUT = 8,  /* a bounded device-side wait ran out */
+    SPX_CUDA_ERROR = 9,      /* a CUDA runtime call failed (see spx_last_error) */
+    SPX_NOT_SUPPORTED = 10   /* the combination of arguments is not implemented */
+} spx_status;
+
+/* A CSR matrix view (Section 3): m x n, nnz stored entries.
+ * indptr: device int32[m+1], indptr[0] = 0, indptr[m] = nnz, non-decreasing.
+ * indices: device int32[nnz], column of each entry, sorted and unique per row.
+ * values: device float32[nnz] (may be NULL where only the pattern is read). */
+typedef struct spx_csr {
+    int32_t m;
+    int32_t n;
+    int64_t nnz;
+    const int32_t* indptr;
+    const int32_t* indices;
+    const float* values;
+} spx_csr;
+
+/* Load-balancing plan of a CSR pattern for the row-wise products (spx_spmm,
+ * spx_spmm_t): the rows longer than `threshold` entries, processed by a whole thread
+ * block each instead of one warp.  Built once per pattern by spx_rowplan_build(). */
+typedef struct spx_rowplan {
+    const int32_t* long_rows; /* device int32[n_long], increasing row ids */
+    int32_t n_long;           /* host-known count */
+    int32_t threshold;        /* rows with more than this many entries are "long" */
+} spx_rowplan;
+
+/* ------------------------------------------------------------------ library */
+
+/* Message of the most recent failure on the calling thread ("" if none). */
+const char* spx_last_error(void);
+
+/* Static name of a status code ("SPX_OK", ...). */
+const char* spx_status_name(int status);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int32_t spx_version(void);
+
+/* Validates a CSR pattern on the device: indptr[0] == 0, indptr[m] == nnz,
+ * indptr non-decreasing, 0 <= indices < n, strictly increasing within each row.
+ * Synchronizes `stream`; returns SPX_OK, SPX_BAD_PATTERN or SPX_UNSORTED.
+ * workspace: device, >= 16 bytes. */
+spx_status spx_csr_validate(const spx_csr* A, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* ------------------------------------------------ SpMV / SpMM (Section 3.1.1, 3.1.3) */
+
+/* Workspace bytes needed by spx_rowplan_build for an m-row pattern. */
+spx_status spx_rowplan_workspace_size(int32_t m, size_t* bytes);
+
+/* Builds the row plan of A's pattern: writes the ids of rows with more than
+ * `threshold` entries, in increasing order, to long_rows (device int32[m]) and their
+ * count to *n_long_host.  Synchronizes `stream` (the count is returned to the host). */
+spx_status spx_rowplan_build(const spx_csr* A, int32_t threshold, int32_t* long_rows,
+                             int32_t* n_long_host, void* workspace, size_t workspace_bytes,
+                             void* stream);
+
+/* Sparse x dense product (Section 3.1.3; SpMV of Section 3.1.1 when k = 1):
+ *   Y = alpha * A X + beta * Y.
+ * A: m x n CSR with values.  X: device float32, n rows x k columns, leading dim ldx.
+ * Y: device float32, m x k, leading dim ldy; not read when beta == 0.
+ * plan: optional (NULL = one warp per row for every row).
+ * Each output element is reduced in a fixed order: results are run-to-run
+ * deterministic. */
+spx_status spx_spmm(const spx_csr* A, const float* X, int64_t ldx, int32_t k, float* Y,
+                    int64_t ldy, float alpha, float beta, const spx_rowplan* plan,
+                    void* stream);
+
+/* ------------------------------------------- reverse mode of SpMV / SpMM (Table 1) */
+
+/* Gradient w.r.t. the sparse matrix of Y = A X (Table 1, SpMV/SpDMM row "A"):
+ *   out[e] = scale * sum_c G[i,c] * X[j,c]   for every stored entry e = (i, j) of A,
+ * i.e. (G X^T) masked to mask(A) -- an SDDMM.  A.values is not read.
+ * G: device float32 m x k (ldg); X: device float32 n x k (ldx); out: device float32[nnz]. */
+spx_status spx_sddmm(const spx_csr* A, const float* G, int64_t ldg, const float* X,
+                     int64_t ldx, int32_t k, float scale, float* out, void* stream);
+
+/* The k = 1 case: out[e] = scale * u[i] * v[j] on mask(A) (Table 1, SpMV row "A";
+ * with scale = -1 and u = lambda, v = x it is the SpSolve gradient w.r.t. A).
+ * u: device float32[m]; v: device float32[n]. */
+spx_status spx_masked_outer(const spx_csr* A, const float* u, const float* v, float scale,
+                            float* out, void* stream);
+
+/* Workspace bytes needed by spx_csr_transpose. */
+spx_status spx_transpose_workspace_size(int32_t m, int32_t n, int64_t nnz, size_t* bytes);
+
+/* Sparse transpose of A's pattern (Section 3.1.3 forms A^T to compute A^T V):
+ * t_indptr: device int32[n+1]; t_indices: device int32[nnz] (row ids of A, sorted
+ * within each row of A^T); perm: device int32[nnz] with
+ *   A^T.values[e'] = A.values[perm[e']].
+ * Stable and deterministic.  A.values is not read. */
+spx_status spx_csr_transpose(const spx_csr* A, int32_t* t_indptr, int32_t* t_indices,
+                             int32_t* perm, void* workspace, size_t workspace_bytes,
+                             void* stream);
+
+/* Gradient w.r.t. the dense operand of Y = A X (Table 1, SpMV/SpDMM row "x"/"B"):
+ *   gX = alpha * A^T G + beta * gX,
+ * computed as a row-wise product over the transposed pattern, gathering A's values
+ * through perm (no atomics; deterministic).
+ * AT: the pattern of A^T from spx_csr_transpose (m = A.n rows, n = A.m columns) with
+ *     AT.values = A.values (in A's order).  perm: device int32[nnz].
+ * G: device float32 A.m x k (ldg).  gX: device float32 A.n x k (ldgx).
+ * plan: optional row plan of the transposed pattern. */
+spx_status spx_spmm_t(const spx_csr* AT, const int32_t* perm, const float* G, int64_t ldg,
+                      int32_t k, float* gX, int64_t ldgx, float alpha, float beta,
+                      const spx_rowplan* plan, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPX_H */

@@ -1,0 +1,198 @@
+"""ctypes binding of ``libspx.so`` (declared in ``include/spx.h``).
+
+Argument marshalling only: every function here has the name of the C entry point it
+calls, takes torch CUDA tensors (or host numpy arrays where the C side wants host
+memory), passes their raw pointers and the current CUDA stream, and raises
+:class:`SpxError` on a non-zero status.  No arithmetic of the method happens here.
+
+The library is built in-tree (``paper_2212_05159_gb300/_build/libspx.so``) by
+``paper_2212_05159_gb300.build``; if it is missing and cannot be built, importing a
+compute function raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libspx.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {
+    0: "SPX_OK", 1: "SPX_INVALID_ARG", 2: "SPX_BAD_PATTERN", 3: "SPX_UNSORTED",
+    4: "SPX_OOM_WORKSPACE", 5: "SPX_MAXITER", 6: "SPX_BREAKDOWN", 7: "SPX_NONFINITE",
+    8: "SPX_DEVICE_TIMEOUT", 9: "SPX_CUDA_ERROR", 10: "SPX_NOT_SUPPORTED",
+}
+
+
+class SpxError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+
+
+class spx_csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("indptr", ctypes.c_void_p), ("indices", ctypes.c_void_p),
+                ("values", ctypes.c_void_p)]
+
+
+class spx_rowplan(ctypes.Structure):
+    _fields_ = [("long_rows", ctypes.c_void_p), ("n_long", ctypes.c_int32),
+                ("threshold", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_F = ctypes.c_float
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+_CSRP = ctypes.POINTER(spx_csr)
+_PLANP = ctypes.POINTER(spx_rowplan)
+
+# name -> argtypes (every entry point returns spx_status, an int)
+SIGNATURES = {
+    "spx_csr_validate": [_CSRP, _P, _SZ, _P],
+    "spx_rowplan_workspace_size": [_I32, ctypes.POINTER(_SZ)],
+    "spx_rowplan_build": [_CSRP, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
+    "spx_spmm": [_CSRP, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P],
+    "spx_sddmm": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, _P],
+    "spx_masked_outer": [_CSRP, _P, _P, _F, _P, _P],
+    "spx_transpose_workspace_size": [_I32, _I32, _I64, ctypes.POINTER(_SZ)],
+    "spx_csr_transpose": [_CSRP, _P, _P, _P, _P, _SZ, _P],
+    "spx_spmm_t": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P],
+}
+
+
+def lib():
+    """The loaded library (built first if needed).  Raises if it cannot be had."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                from .build import build
+                build()
+            L = ctypes.CDLL(LIB_PATH)
+            L.spx_last_error.restype = ctypes.c_char_p
+            L.spx_status_name.restype = ctypes.c_char_p
+            L.spx_version.restype = ctypes.c_int32
+            for name, args in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = ctypes.c_int
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        msg = lib().spx_last_error().decode(errors="replace")
+        raise SpxError(status, where, msg)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def ptr(t):
+    """Device pointer of a tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def csr_struct(m, n, indptr, indices, values=None) -> spx_csr:
+    for t, dt in ((indptr, torch.int32), (indices, torch.int32)):
+        if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("indptr/indices must be contiguous int32 CUDA tensors")
+    if values is not None and (values.dtype != torch.float32 or not values.is_contiguous()):
+        raise ValueError("values must be a contiguous float32 CUDA tensor")
+    return spx_csr(int(m), int(n), int(indices.numel()), indptr.data_ptr(), indices.data_ptr(),
+                   values.data_ptr() if values is not None else None)
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+def _dense(t, name):
+    if t.dtype != torch.float32 or t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be a float32 2-D tensor with unit column stride")
+    return ctypes.c_void_p(t.data_ptr()), t.stride(0)
+
+
+# ------------------------------------------------------------------ entry points
+def spx_version() -> int:
+    return int(lib().spx_version())
+
+
+def spx_csr_validate(A: spx_csr, device) -> None:
+    ws = workspace(16, device)
+    _check(lib().spx_csr_validate(ctypes.byref(A), ptr(ws), ws.numel(), _stream()),
+           "spx_csr_validate")
+
+
+def spx_rowplan_build(A: spx_csr, threshold: int, device):
+    """Returns (long_rows tensor, spx_rowplan)."""
+    sz = _SZ(0)
+    _check(lib().spx_rowplan_workspace_size(A.m, ctypes.byref(sz)), "spx_rowplan_workspace_size")
+    ws = workspace(sz.value, device)
+    rows = torch.empty(max(A.m, 1), dtype=torch.int32, device=device)
+    n_long = _I32(0)
+    _check(lib().spx_rowplan_build(ctypes.byref(A), int(threshold), ptr(rows), ctypes.byref(n_long),
+                                   ptr(ws), ws.numel(), _stream()), "spx_rowplan_build")
+    rows = rows[: n_long.value].clone() if n_long.value > 0 else rows[:0]
+    plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold))
+    return rows, plan
+
+
+def spx_spmm(A: spx_csr, X, Y, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None):
+    px, ldx = _dense(X, "X")
+    py, ldy = _dense(Y, "Y")
+    _check(lib().spx_spmm(ctypes.byref(A), px, ldx, X.shape[1], py, ldy, float(alpha), float(beta),
+                          ctypes.byref(plan) if plan is not None else None, _stream()), "spx_spmm")
+    return Y
+
+
+def spx_sddmm(A: spx_csr, G, X, out, scale=1.0):
+    pg, ldg = _dense(G, "G")
+    px, ldx = _dense(X, "X")
+    _check(lib().spx_sddmm(ctypes.byref(A), pg, ldg, px, ldx, G.shape[1], float(scale), ptr(out),
+                           _stream()), "spx_sddmm")
+    return out
+
+
+def spx_masked_outer(A: spx_csr, u, v, out, scale=1.0):
+    _check(lib().spx_masked_outer(ctypes.byref(A), ptr(u), ptr(v), float(scale), ptr(out), _stream()),
+           "spx_masked_outer")
+    return out
+
+
+def spx_csr_transpose(A: spx_csr, device):
+    """Returns (t_indptr, t_indices, perm) int32 CUDA tensors."""
+    sz = _SZ(0)
+    _check(lib().spx_transpose_workspace_size(A.m, A.n, A.nnz, ctypes.byref(sz)),
+           "spx_transpose_workspace_size")
+    ws = workspace(sz.value, device)
+    t_ip = torch.empty(A.n + 1, dtype=torch.int32, device=device)
+    t_ix = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=device)
+    perm = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=device)
+    _check(lib().spx_csr_transpose(ctypes.byref(A), ptr(t_ip), ptr(t_ix), ptr(perm), ptr(ws), ws.numel(),
+                                   _stream()), "spx_csr_transpose")
+    return t_ip, t_ix[: A.nnz], perm[: A.nnz]
+
+
+def spx_spmm_t(AT: spx_csr, perm, G, gX, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None):
+    pg, ldg = _dense(G, "G")
+    px, ldx = _dense(gX, "gX")
+    _check(lib().spx_spmm_t(ctypes.byref(AT), ptr(perm), pg, ldg, G.shape[1], px, ldx, float(alpha),
+                            float(beta), ctypes.byref(plan) if plan is not None else None, _stream()),
+           "spx_spmm_t")
+    return gX

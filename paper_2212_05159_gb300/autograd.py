@@ -1,0 +1,35 @@
+"""torch.autograd.Functions whose backward passes are the VJPs of Table 1.
+
+Gradients of sparse inputs are plain value tensors on the input's own pattern
+(Section 3.1); gradients of dense inputs are dense.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import ops
+from .csr import CSR
+
+
+class SpMM(torch.autograd.Function):
+    """Y = A X with A = (pattern, values).  VJPs (Table 1, SpMV / SpDMM):
+    dL/dA = (V X^T) masked to mask(A)  [SDDMM],  dL/dX = A^T V  [transpose-SpMM]."""
+
+    @staticmethod
+    def forward(ctx, values: torch.Tensor, X: torch.Tensor, A: CSR):
+        ctx.A = A
+        ctx.save_for_backward(values, X)
+        return ops.spmm(A, X.contiguous(), values=values)
+
+    @staticmethod
+    def backward(ctx, V):
+        values, X = ctx.saved_tensors
+        A = ctx.A
+        V = V.contiguous()
+        g_vals = ops.sddmm(A, V, X.contiguous()) if ctx.needs_input_grad[0] else None
+        g_X = ops.spmm_t(A, V, values=values) if ctx.needs_input_grad[1] else None
+        return g_vals, g_X, None
+
+
+def spmm(A: CSR, X: torch.Tensor, values: torch.Tensor | None = None) -> torch.Tensor:
+    return SpMM.apply(A.values if values is None else values, X, A)

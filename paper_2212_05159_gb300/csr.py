@@ -1,0 +1,94 @@
+"""Device CSR matrix with per-pattern caches (transpose, load-balancing plans).
+
+The pattern (indptr, indices) is fixed for the life of the object; the values may be
+swapped (e.g. learned values) without invalidating the caches, because the transpose
+and the row plans depend only on the pattern (Section 3.1: gradients live on the
+input's pattern, so the pattern is known a priori).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import abi
+
+LONG_ROW_THRESHOLD = 256
+
+
+class CSR:
+    """An m x n CSR matrix on a CUDA device (int32 pattern, float32 values)."""
+
+    def __init__(self, indptr: torch.Tensor, indices: torch.Tensor, values: torch.Tensor | None,
+                 shape: tuple[int, int]):
+        self.indptr = indptr.to(torch.int32).contiguous()
+        self.indices = indices.to(torch.int32).contiguous()
+        self.values = None if values is None else values.to(torch.float32).contiguous()
+        self.shape = (int(shape[0]), int(shape[1]))
+        self.device = self.indptr.device
+        self._plan = None
+        self._t = None
+        self._t_plan = None
+
+    # ------------------------------------------------------------------ construction
+    @classmethod
+    def from_host(cls, A, device="cuda") -> "CSR":
+        """From any object with m, n, indptr, indices, values (numpy arrays)."""
+        ip = torch.from_numpy(np.ascontiguousarray(A.indptr, dtype=np.int32)).to(device)
+        ix = torch.from_numpy(np.ascontiguousarray(A.indices, dtype=np.int32)).to(device)
+        v = torch.from_numpy(np.ascontiguousarray(A.values, dtype=np.float32)).to(device)
+        return cls(ip, ix, v, (A.m, A.n))
+
+    def with_values(self, values: torch.Tensor) -> "CSR":
+        """Same pattern (and caches), other values."""
+        other = CSR.__new__(CSR)
+        other.__dict__.update(self.__dict__)
+        other.values = values.to(torch.float32).contiguous()
+        return other
+
+    @property
+    def m(self):
+        return self.shape[0]
+
+    @property
+    def n(self):
+        return self.shape[1]
+
+    @property
+    def nnz(self):
+        return int(self.indices.numel())
+
+    def struct(self, values: torch.Tensor | None = None) -> abi.spx_csr:
+        v = self.values if values is None else values
+        return abi.csr_struct(self.m, self.n, self.indptr, self.indices, v)
+
+    def validate(self) -> None:
+        abi.spx_csr_validate(self.struct(), self.device)
+
+    # ------------------------------------------------------------------ caches
+    def plan(self):
+        if self._plan is None:
+            rows, plan = abi.spx_rowplan_build(self.struct(), LONG_ROW_THRESHOLD, self.device)
+            self._plan = (rows, plan)
+        return self._plan[1]
+
+    def transpose_pattern(self):
+        """(t_indptr, t_indices, perm) of A^T, computed once per pattern."""
+        if self._t is None:
+            self._t = abi.spx_csr_transpose(self.struct(), self.device)
+        return self._t
+
+    def t_struct(self, values: torch.Tensor | None = None) -> abi.spx_csr:
+        """Pattern of A^T whose value pointer is A's values (gathered through perm)."""
+        t_ip, t_ix, _ = self.transpose_pattern()
+        v = self.values if values is None else values
+        return abi.csr_struct(self.n, self.m, t_ip, t_ix, v)
+
+    def t_plan(self):
+        if self._t_plan is None:
+            t_ip, t_ix, _ = self.transpose_pattern()
+            st = abi.csr_struct(self.n, self.m, t_ip, t_ix, None)
+            self._t_plan = abi.spx_rowplan_build(st, LONG_ROW_THRESHOLD, self.device)
+        return self._t_plan[1]
+
+    def __repr__(self):
+        return f"CSR({self.m}x{self.n}, nnz={self.nnz}, device={self.device})"

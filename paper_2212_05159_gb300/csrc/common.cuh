@@ -1,0 +1,57 @@
+// Shared helpers of the CUDA sources: status handling, launch checks, warp utilities.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spx.h"
+
+namespace spx {
+
+// Records a message for spx_last_error() (thread-local) and returns the status.
+spx_status set_error(spx_status st, const char* fmt, ...);
+
+// Translates a CUDA runtime error into SPX_CUDA_ERROR with a message.
+spx_status cuda_error(cudaError_t err, const char* where);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int NUM_SMS_GB300 = 152;
+
+// Number of SMs of the current device (cached per process; GB300 has 152).
+int num_sms();
+
+// Checks the header of a CSR view (not its contents).
+spx_status check_csr(const spx_csr* A, bool need_values, const char* who);
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+// Streaming loads for data read exactly once (CSR index / value streams): evict-first in
+// L2 so that the gathered dense operand keeps the cache.
+__device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+
+}  // namespace spx
+
+#define SPX_CHECK_LAUNCH(where)                                        \
+    do {                                                               \
+        cudaError_t e_ = cudaGetLastError();                           \
+        if (e_ != cudaSuccess) return ::spx::cuda_error(e_, where);    \
+    } while (0)
+
+#define SPX_CUDA(call, where)                                          \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::spx::cuda_error(e_, where);    \
+    } while (0)
+
+#define SPX_TRY(call)                                                  \
+    do {                                                               \
+        spx_status s_ = (call);                                        \
+        if (s_ != SPX_OK) return s_;                                   \
+    } while (0)

@@ -153,6 +153,20 @@ def _unique_sorted_columns(lengths: np.ndarray, ncols: int, rng) -> np.ndarray:
     """Per row, ``lengths[i]`` distinct uniform columns in [0, ncols), sorted."""
     m = lengths.size
     assert int(lengths.max(initial=0)) <= ncols
+    dense = lengths * 4 > ncols                 # near-full rows: draw without replacement
+    if dense.any():
+        out = np.zeros(int(lengths.sum()), dtype=np.int32)
+        offs = np.zeros(m + 1, dtype=np.int64)
+        np.cumsum(lengths, out=offs[1:])
+        sparse_cols = _unique_sorted_columns(np.where(dense, 0, lengths), ncols, rng)
+        sp_offs = np.zeros(m + 1, dtype=np.int64)
+        np.cumsum(np.where(dense, 0, lengths), out=sp_offs[1:])
+        for i in range(m):
+            if dense[i]:
+                out[offs[i]:offs[i + 1]] = np.sort(rng.choice(ncols, int(lengths[i]), replace=False))
+            else:
+                out[offs[i]:offs[i + 1]] = sparse_cols[sp_offs[i]:sp_offs[i + 1]]
+        return out
     rows = np.repeat(np.arange(m, dtype=np.int64), lengths)
     cols = rng.integers(0, ncols, size=rows.size, dtype=np.int64)
     for _ in range(64):

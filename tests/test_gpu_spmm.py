@@ -1,0 +1,183 @@
+"""GPU parity of SpMM / SpMV, SDDMM, the CSR transpose and transpose-SpMM against the
+FP64 oracle, through the C ABI (Section 3.1.1, 3.1.3 and Table 1)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import abs_csr, assert_close_normalised, sub_rows
+
+pytestmark = pytest.mark.gpu
+
+spx = pytest.importorskip("paper_2212_05159_gb300")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+MATS = {
+    "poisson2d_64": lambda: synth.poisson2d(64),
+    "ragged": lambda: synth.empty_rows_csr(3001, 2500, seed=4, max_len=70),
+    "powerlaw_20k": lambda: synth.powerlaw_csr(20000, seed=1, max_len=2000),
+    "poisson3d_16": lambda: synth.poisson3d(16),
+    "rect_wide": lambda: synth.random_k_per_row(777, 5, seed=3, ncols=4099),
+}
+
+
+@pytest.fixture(scope="module", params=list(MATS))
+def mat(request):
+    A = MATS[request.param]()
+    return request.param, A, spx.CSR.from_host(A)
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 32, 36, 128])
+def test_spmm_matches_oracle(mat, k):
+    name, A, dA = mat
+    X = synth.normal((A.n, k), seed=k)
+    Y = host(spx.spmm(dA, dev(X)))
+    ref = oracle.spmm(A, X)
+    norm = oracle.spmm(abs_csr(A), np.abs(X))
+    assert_close_normalised(Y, ref, norm, what=f"spmm {name} k={k}")
+
+
+def test_spmv_1d_and_alpha_beta(mat):
+    name, A, dA = mat
+    x = synth.normal(A.n, seed=3)
+    y0 = synth.normal(A.m, seed=4)
+    out = dev(y0.copy())
+    y = host(spx.spmm(dA, dev(x), out=out, alpha=0.5, beta=-2.0))
+    ref = 0.5 * oracle.spmm(A, x) - 2.0 * y0.astype(np.float64)
+    norm = 0.5 * oracle.spmm(abs_csr(A), np.abs(x)) + 2.0 * np.abs(y0)
+    assert_close_normalised(y, ref, norm, what=f"spmv {name}")
+
+
+@pytest.mark.parametrize("k", [1, 8, 32, 33, 128])
+def test_sddmm_matches_oracle(mat, k):
+    name, A, dA = mat
+    G = synth.normal((A.m, k), seed=10 + k)
+    X = synth.normal((A.n, k), seed=20 + k)
+    out = host(spx.sddmm(dA, dev(G), dev(X)))
+    ref = oracle.sddmm(A, G, X)
+    norm = oracle.sddmm(A, np.abs(G), np.abs(X))
+    assert_close_normalised(out, ref, norm, what=f"sddmm {name} k={k}")
+
+
+def test_transpose_bit_exact(mat):
+    name, A, dA = mat
+    t_ip, t_ix, perm = dA.transpose_pattern()
+    r_ip, r_ix, r_perm = oracle.transpose(A)
+    np.testing.assert_array_equal(host(t_ip), r_ip)
+    np.testing.assert_array_equal(host(t_ix), r_ix)
+    np.testing.assert_array_equal(host(perm), r_perm)
+
+
+@pytest.mark.parametrize("k", [1, 8, 32, 128])
+def test_spmm_t_matches_oracle(mat, k):
+    name, A, dA = mat
+    G = synth.normal((A.m, k), seed=30 + k)
+    gX = host(spx.spmm_t(dA, dev(G)))
+    ref = oracle.spmm_t(A, G)
+    norm = oracle.spmm_t(abs_csr(A), np.abs(G))
+    assert_close_normalised(gX, ref, norm, what=f"spmm_t {name} k={k}")
+
+
+def test_masked_outer_scale(mat):
+    name, A, dA = mat
+    u = synth.normal(A.m, seed=1)
+    v = synth.normal(A.n, seed=2)
+    out = host(spx.masked_outer(dA, dev(u), dev(v), scale=-1.0))
+    ref = -oracle.sddmm(A, u.reshape(-1, 1), v.reshape(-1, 1))
+    norm = np.abs(ref)
+    assert_close_normalised(out, ref, norm, what=f"masked_outer {name}")
+
+
+def test_deterministic_repeats(mat):
+    name, A, dA = mat
+    X = dev(synth.normal((A.n, 32), seed=5))
+    G = dev(synth.normal((A.m, 32), seed=6))
+    a1, a2 = host(spx.spmm(dA, X)), host(spx.spmm(dA, X))
+    b1, b2 = host(spx.sddmm(dA, G, X)), host(spx.sddmm(dA, G, X))
+    c1, c2 = host(spx.spmm_t(dA, G)), host(spx.spmm_t(dA, G))
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2) and np.array_equal(c1, c2)
+
+
+def test_autograd_spmm(mat):
+    name, A, dA = mat
+    from paper_2212_05159_gb300 import autograd
+    k = 8
+    X = synth.normal((A.n, k), seed=11)
+    V = synth.normal((A.m, k), seed=12)
+    vals = dev(A.values).requires_grad_(True)
+    Xt = dev(X).requires_grad_(True)
+    Y = autograd.spmm(dA, Xt, values=vals)
+    Y.backward(dev(V))
+    assert_close_normalised(host(vals.grad), oracle.sddmm(A, V, X),
+                            oracle.sddmm(A, np.abs(V), np.abs(X)), what="autograd dA")
+    assert_close_normalised(host(Xt.grad), oracle.spmm_t(A, V),
+                            oracle.spmm_t(abs_csr(A), np.abs(V)), what="autograd dX")
+
+
+def test_empty_and_degenerate():
+    # no stored entries at all
+    A = synth.CSR(5, 7, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    dA = spx.CSR.from_host(A)
+    Y = host(spx.spmm(dA, dev(np.ones((7, 4), np.float32))))
+    assert Y.shape == (5, 4) and np.all(Y == 0)
+    assert spx.sddmm(dA, dev(np.ones((5, 4), np.float32)), dev(np.ones((7, 4), np.float32))).numel() == 0
+    gX = host(spx.spmm_t(dA, dev(np.ones((5, 4), np.float32))))
+    assert np.all(gX == 0)
+    # 1 x 1
+    B = synth.CSR(1, 1, np.array([0, 1]), np.array([0]), np.array([3.0], np.float32))
+    dB = spx.CSR.from_host(B)
+    assert host(spx.spmm(dB, dev(np.array([[2.0]], np.float32))))[0, 0] == 6.0
+
+
+def test_validate_rejects_bad_patterns():
+    from paper_2212_05159_gb300.abi import SpxError
+    good = synth.poisson2d(5)
+    spx.CSR.from_host(good).validate()
+    bad = synth.CSR(good.m, good.n, good.indptr, good.indices.copy(), good.values)
+    bad.indices[1], bad.indices[2] = bad.indices[2], bad.indices[1]
+    with pytest.raises(SpxError, match="UNSORTED"):
+        spx.CSR.from_host(bad).validate()
+    oob = synth.CSR(good.m, good.n, good.indptr, good.indices.copy(), good.values)
+    oob.indices[-1] = good.n + 3
+    with pytest.raises(SpxError, match="BAD_PATTERN"):
+        spx.CSR.from_host(oob).validate()
+
+
+@pytest.mark.parametrize("k", [32])
+def test_full_size_powerlaw_sampled(k):
+    """The n = 2^20 power-law workload in the benchmark's launch configuration, checked
+    on sampled rows / columns that the oracle computes one by one."""
+    A = synth.powerlaw_csr(1 << 20, seed=0)
+    dA = spx.CSR.from_host(A)
+    rng = np.random.default_rng(0)
+    X = synth.normal((A.n, k), seed=1)
+    G = synth.normal((A.m, k), seed=2)
+    Y = host(spx.spmm(dA, dev(X)))
+    gA = host(spx.sddmm(dA, dev(G), dev(X)))
+    gX = host(spx.spmm_t(dA, dev(G)))
+    lens = A.row_lengths()
+    rows = np.concatenate([rng.choice(A.m, 400, replace=False), np.argsort(lens)[-20:]])
+    S, take = sub_rows(A, rows)
+    assert_close_normalised(Y[rows], oracle.spmm(S, X), oracle.spmm(abs_csr(S), np.abs(X)), what="Y")
+    Gs = G[rows]
+    assert_close_normalised(gA[take], oracle.sddmm(S, Gs, X), oracle.sddmm(S, np.abs(Gs), np.abs(X)),
+                            what="gA")
+    t_ip, t_ix, perm = oracle.transpose(A)
+    AT = synth.CSR(A.n, A.m, t_ip, t_ix, A.values[perm])
+    cols = rng.choice(A.n, 400, replace=False)
+    ST, _ = sub_rows(AT, cols)
+    assert_close_normalised(gX[cols], oracle.spmm(ST, G), oracle.spmm(abs_csr(ST), np.abs(G)), what="gX")
+    # the transpose itself, bit-exact on the sampled rows of A^T
+    d_ip, d_ix, d_perm = [host(t) for t in dA.transpose_pattern()]
+    np.testing.assert_array_equal(d_ip, t_ip)
+    np.testing.assert_array_equal(d_ix, t_ix)
+    np.testing.assert_array_equal(d_perm, perm)
