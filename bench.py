@@ -186,26 +186,39 @@ class Workload:
         self.Y = torch.empty(A.m, k, device=device)
         self.gA = torch.empty(A.nnz, device=device)
         self.gX = torch.empty(A.n, k, device=device)
-        # per-pattern setup (outside timed regions)
-        self.plan = self.dA.plan()
+        # per-pattern setup (outside timed regions): transpose, row plans, autotuning
+        from paper_2212_05159_gb300 import tune
         _, _, self.perm = self.dA.transpose_pattern()
-        self.t_plan = self.dA.t_plan()
+        self.plan = tune.tuned_plan(self.dA, k)
+        self.t_plan = tune.tuned_plan(self.dA, k, transposed=True)
+        self.sddmm_cb = tune.tune_sddmm(self.dA, k)
         self.s_A = self.dA.struct()
         self.s_AT = self.dA.t_struct()
+        ws = lambda nb: abi.workspace(nb, device) if nb > 0 else None  # noqa: E731
+        self.ws_spmm = ws(abi.spx_spmm_workspace_size(self.s_A, k, self.plan))
+        self.ws_sddmm = ws(abi.spx_sddmm_workspace_size(self.s_A, k, self.sddmm_cb))
+        self.ws_t = ws(abi.spx_spmm_t_workspace_size(self.s_AT, k, self.t_plan))
+        npass = lambda cb: -(-k // cb)  # noqa: E731
+        rp = lambda cb: 1 if cb < k else 0  # noqa: E731  (slab repack launch)
+        self.launches = (npass(self.plan.col_block) + rp(self.plan.col_block) + npass(self.sddmm_cb)
+                         + rp(self.sddmm_cb) + 1 + npass(self.t_plan.col_block) + rp(self.t_plan.col_block))
+        self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group],
+                       "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group],
+                       "sddmm_col_block": self.sddmm_cb}
         self.abi = abi
         self.m, self.n, self.nnz = A.m, A.n, A.nnz
 
     def launches_per_step(self):
-        return 3
+        return self.launches
 
     def run_kernel(self, which):
         a = self.abi
         if which == "spmm":
-            a.spx_spmm(self.s_A, self.X, self.Y, 1.0, 0.0, self.plan)
+            a.spx_spmm(self.s_A, self.X, self.Y, 1.0, 0.0, self.plan, self.ws_spmm)
         elif which == "sddmm":
-            a.spx_sddmm(self.s_A, self.G, self.X, self.gA, 1.0)
+            a.spx_sddmm(self.s_A, self.G, self.X, self.gA, 1.0, self.sddmm_cb, self.ws_sddmm)
         else:
-            a.spx_spmm_t(self.s_AT, self.perm, self.G, self.gX, 1.0, 0.0, self.t_plan)
+            a.spx_spmm_t(self.s_AT, self.perm, self.G, self.gX, 1.0, 0.0, self.t_plan, self.ws_t)
 
     KERNELS = ("spmm", "sddmm", "spmm_t")
 
@@ -398,6 +411,7 @@ def main():
                    "l2": "inputs larger than L2 (~0.9 GB touched per step), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "per_kernel_ms": per,
+        "tuning": W.tuning,
         "per_kernel_gbs_compulsory": {k: cb[k] / (per[k] * 1e-3) / 1e9 for k in per},
         "roofline": roofline,
         "e2e": {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
@@ -415,7 +429,7 @@ def main():
             cb2 = compulsory_bytes(W.m, W.n, W.nnz, W.k)
             extras[W.name] = {"ms_per_step": ms2, "gbs_compulsory": sum(cb2.values()) / (ms2 * 1e-3) / 1e9,
                               "frac_of_peak": sum(cb2.values()) / (ms2 * 1e-3) / 1e9 / hbm,
-                              "per_kernel_ms": per2}
+                              "per_kernel_ms": per2, "tuning": W.tuning}
         line["extras"] = extras
     if rank == 0 and not args.no_cpu:
         v, desc, cores = cpu_baseline(k=args.k)

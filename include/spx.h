@@ -69,6 +69,10 @@ typedef struct spx_rowplan {
     const int32_t* long_rows; /* device int32[n_long], increasing row ids */
     int32_t n_long;           /* host-known count */
     int32_t threshold;        /* rows with more than this many entries are "long" */
+    int32_t col_block;        /* dense columns per pass (0 = choose from the sizes); one
+                                 pass per block keeps the gathered slab of the dense
+                                 operand resident in L2 */
+    int32_t rows_per_group;   /* rows walked by one lane group (0 = default) */
 } spx_rowplan;
 
 /* ------------------------------------------------------------------ library */
@@ -101,25 +105,42 @@ spx_status spx_rowplan_build(const spx_csr* A, int32_t threshold, int32_t* long_
                              int32_t* n_long_host, void* workspace, size_t workspace_bytes,
                              void* stream);
 
+/* Workspace bytes with which spx_spmm repacks X into column-block slabs (0 when the
+ * gathered operand fits the L2 budget, or k is not a multiple of 4). */
+spx_status spx_spmm_workspace_size(const spx_csr* A, int32_t k, const spx_rowplan* plan,
+                                   size_t* bytes);
+
 /* Sparse x dense product (Section 3.1.3; SpMV of Section 3.1.1 when k = 1):
  *   Y = alpha * A X + beta * Y.
  * A: m x n CSR with values.  X: device float32, n rows x k columns, leading dim ldx.
  * Y: device float32, m x k, leading dim ldy; not read when beta == 0.
- * plan: optional (NULL = one warp per row for every row).
+ * plan: optional row plan (NULL = no long-row blocks, default column blocks).
+ * workspace: device scratch of spx_spmm_workspace_size() bytes, or NULL.  With it, X is
+ * first repacked into contiguous column-block slabs so that each pass's gathered slab
+ * fits in L2; without it the passes gather the strided X directly (same results).
+ * A non-NULL workspace smaller than required is an error (SPX_OOM_WORKSPACE).
  * Each output element is reduced in a fixed order: results are run-to-run
  * deterministic. */
 spx_status spx_spmm(const spx_csr* A, const float* X, int64_t ldx, int32_t k, float* Y,
                     int64_t ldy, float alpha, float beta, const spx_rowplan* plan,
-                    void* stream);
+                    void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------- reverse mode of SpMV / SpMM (Table 1) */
+
+/* Workspace bytes with which spx_sddmm repacks X into column-block slabs. */
+spx_status spx_sddmm_workspace_size(const spx_csr* A, int32_t k, int32_t col_block,
+                                    size_t* bytes);
 
 /* Gradient w.r.t. the sparse matrix of Y = A X (Table 1, SpMV/SpDMM row "A"):
  *   out[e] = scale * sum_c G[i,c] * X[j,c]   for every stored entry e = (i, j) of A,
  * i.e. (G X^T) masked to mask(A) -- an SDDMM.  A.values is not read.
- * G: device float32 m x k (ldg); X: device float32 n x k (ldx); out: device float32[nnz]. */
+ * G: device float32 m x k (ldg); X: device float32 n x k (ldx); out: device float32[nnz].
+ * col_block: dense columns per pass (0 = choose from the sizes); with several passes
+ * the partial dot products are added into out in column order.
+ * workspace: device scratch of spx_sddmm_workspace_size() bytes, or NULL (as spx_spmm). */
 spx_status spx_sddmm(const spx_csr* A, const float* G, int64_t ldg, const float* X,
-                     int64_t ldx, int32_t k, float scale, float* out, void* stream);
+                     int64_t ldx, int32_t k, float scale, float* out, int32_t col_block,
+                     void* workspace, size_t workspace_bytes, void* stream);
 
 /* The k = 1 case: out[e] = scale * u[i] * v[j] on mask(A) (Table 1, SpMV row "A";
  * with scale = -1 and u = lambda, v = x it is the SpSolve gradient w.r.t. A).
@@ -139,17 +160,27 @@ spx_status spx_csr_transpose(const spx_csr* A, int32_t* t_indptr, int32_t* t_ind
                              int32_t* perm, void* workspace, size_t workspace_bytes,
                              void* stream);
 
+/* Workspace bytes for spx_spmm_t: A^T's gathered values (4 * nnz) plus the column-block
+ * slabs of G (as spx_spmm).  AT is the transposed pattern (see below). */
+spx_status spx_spmm_t_workspace_size(const spx_csr* AT, int32_t k, const spx_rowplan* plan,
+                                     size_t* bytes);
+
 /* Gradient w.r.t. the dense operand of Y = A X (Table 1, SpMV/SpDMM row "x"/"B"):
  *   gX = alpha * A^T G + beta * gX,
- * computed as a row-wise product over the transposed pattern, gathering A's values
- * through perm (no atomics; deterministic).
+ * computed as a row-wise product over the transposed pattern (no atomics;
+ * deterministic).  A's values reach A^T's order through perm: with a workspace they
+ * are gathered once into it (one streaming pass) and G is repacked into slabs;
+ * with workspace == NULL every pass gathers the values through perm.
  * AT: the pattern of A^T from spx_csr_transpose (m = A.n rows, n = A.m columns) with
  *     AT.values = A.values (in A's order).  perm: device int32[nnz].
  * G: device float32 A.m x k (ldg).  gX: device float32 A.n x k (ldgx).
- * plan: optional row plan of the transposed pattern. */
+ * plan: optional row plan of the transposed pattern.
+ * workspace: device scratch of spx_spmm_t_workspace_size() bytes or NULL; a non-NULL
+ * workspace that is too small is an error. */
 spx_status spx_spmm_t(const spx_csr* AT, const int32_t* perm, const float* G, int64_t ldg,
                       int32_t k, float* gX, int64_t ldgx, float alpha, float beta,
-                      const spx_rowplan* plan, void* stream);
+                      const spx_rowplan* plan, void* workspace, size_t workspace_bytes,
+                      void* stream);
 
 #ifdef __cplusplus
 }

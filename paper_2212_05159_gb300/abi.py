@@ -43,7 +43,8 @@ class spx_csr(ctypes.Structure):
 
 class spx_rowplan(ctypes.Structure):
     _fields_ = [("long_rows", ctypes.c_void_p), ("n_long", ctypes.c_int32),
-                ("threshold", ctypes.c_int32)]
+                ("threshold", ctypes.c_int32), ("col_block", ctypes.c_int32),
+                ("rows_per_group", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -60,12 +61,15 @@ SIGNATURES = {
     "spx_csr_validate": [_CSRP, _P, _SZ, _P],
     "spx_rowplan_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_rowplan_build": [_CSRP, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
-    "spx_spmm": [_CSRP, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P],
-    "spx_sddmm": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, _P],
+    "spx_spmm_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
+    "spx_spmm": [_CSRP, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
+    "spx_sddmm_workspace_size": [_CSRP, _I32, _I32, ctypes.POINTER(_SZ)],
+    "spx_sddmm": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, _I32, _P, _SZ, _P],
     "spx_masked_outer": [_CSRP, _P, _P, _F, _P, _P],
     "spx_transpose_workspace_size": [_I32, _I32, _I64, ctypes.POINTER(_SZ)],
     "spx_csr_transpose": [_CSRP, _P, _P, _P, _P, _SZ, _P],
-    "spx_spmm_t": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P],
+    "spx_spmm_t_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
+    "spx_spmm_t": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
 }
 
 
@@ -149,23 +153,45 @@ def spx_rowplan_build(A: spx_csr, threshold: int, device):
     _check(lib().spx_rowplan_build(ctypes.byref(A), int(threshold), ptr(rows), ctypes.byref(n_long),
                                    ptr(ws), ws.numel(), _stream()), "spx_rowplan_build")
     rows = rows[: n_long.value].clone() if n_long.value > 0 else rows[:0]
-    plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold))
+    plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold), 0, 0)
     return rows, plan
 
 
-def spx_spmm(A: spx_csr, X, Y, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None):
+def _planp(plan):
+    return ctypes.byref(plan) if plan is not None else None
+
+
+def _wsargs(ws):
+    return (ptr(ws), ws.numel()) if ws is not None else (None, 0)
+
+
+def spx_spmm_workspace_size(A: spx_csr, k: int, plan: spx_rowplan | None = None) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_spmm_workspace_size(ctypes.byref(A), int(k), _planp(plan), ctypes.byref(sz)),
+           "spx_spmm_workspace_size")
+    return sz.value
+
+
+def spx_spmm(A: spx_csr, X, Y, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None, ws=None):
     px, ldx = _dense(X, "X")
     py, ldy = _dense(Y, "Y")
     _check(lib().spx_spmm(ctypes.byref(A), px, ldx, X.shape[1], py, ldy, float(alpha), float(beta),
-                          ctypes.byref(plan) if plan is not None else None, _stream()), "spx_spmm")
+                          _planp(plan), *_wsargs(ws), _stream()), "spx_spmm")
     return Y
 
 
-def spx_sddmm(A: spx_csr, G, X, out, scale=1.0):
+def spx_sddmm_workspace_size(A: spx_csr, k: int, col_block: int = 0) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_sddmm_workspace_size(ctypes.byref(A), int(k), int(col_block), ctypes.byref(sz)),
+           "spx_sddmm_workspace_size")
+    return sz.value
+
+
+def spx_sddmm(A: spx_csr, G, X, out, scale=1.0, col_block=0, ws=None):
     pg, ldg = _dense(G, "G")
     px, ldx = _dense(X, "X")
     _check(lib().spx_sddmm(ctypes.byref(A), pg, ldg, px, ldx, G.shape[1], float(scale), ptr(out),
-                           _stream()), "spx_sddmm")
+                           int(col_block), *_wsargs(ws), _stream()), "spx_sddmm")
     return out
 
 
@@ -189,10 +215,17 @@ def spx_csr_transpose(A: spx_csr, device):
     return t_ip, t_ix[: A.nnz], perm[: A.nnz]
 
 
-def spx_spmm_t(AT: spx_csr, perm, G, gX, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None):
+def spx_spmm_t_workspace_size(AT: spx_csr, k: int, plan: spx_rowplan | None = None) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_spmm_t_workspace_size(ctypes.byref(AT), int(k), _planp(plan), ctypes.byref(sz)),
+           "spx_spmm_t_workspace_size")
+    return sz.value
+
+
+def spx_spmm_t(AT: spx_csr, perm, G, gX, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None,
+               ws=None):
     pg, ldg = _dense(G, "G")
     px, ldx = _dense(gX, "gX")
     _check(lib().spx_spmm_t(ctypes.byref(AT), ptr(perm), pg, ldg, G.shape[1], px, ldx, float(alpha),
-                            float(beta), ctypes.byref(plan) if plan is not None else None, _stream()),
-           "spx_spmm_t")
+                            float(beta), _planp(plan), *_wsargs(ws), _stream()), "spx_spmm_t")
     return gX

@@ -3,49 +3,49 @@
 //   spx_spmm_t  gX = alpha * A^T G + beta * gX     (Table 1, gradient w.r.t. the dense
 //                                                   operand, on the transposed pattern)
 //
-// Mapping (HBM-bound gather; no tensor cores: each A entry is used once per output row):
-//   * a "row slot" of S lanes (S | 32) owns one row; inside it LPR lanes span the k
-//     columns with float4 loads (VEC = 4) and G = S / LPR lane groups walk the row's
-//     entries with stride G, so one warp issues G coalesced row-gathers of X at a time;
-//   * partial sums of the G groups are combined with xor-shuffles in a fixed order;
-//   * rows longer than the plan threshold are taken by whole thread blocks (8 warps,
-//     8*G entries in flight) that reduce through shared memory in warp order; those
-//     blocks are the lowest block ids of the same launch, so they start first and
-//     overlap the short rows.
-// Every output is reduced in a fixed order: results are deterministic.
-// CSR streams are read with evict-first loads so that L2 keeps the gathered X rows.
+// HBM-bound gathers; no tensor cores (each stored entry is used once per output row).
+//
+// Column blocks.  The dense operand is gathered one row slab at a time: a pass covers
+// `col_block` columns, so the slab that the random column indices touch (n x col_block
+// floats) stays resident in L2 while the CSR streams pass through with evict-first
+// loads.  One launch per block, blocks in column order.
+//
+// Short rows.  A lane group of LPR lanes spans the block's columns with float4 loads
+// and owns whole rows (rows_per_group consecutive rows per group): it loads the (column,
+// value) pairs of the row 8 at a time -- the next batch is fetched while the current
+// one is gathered -- and issues the 8 row gathers of X back to back, so each lane has
+// up to 8 independent loads in flight.  One group per row: no cross-lane reduction.
+//
+// Long rows (more entries than the plan threshold) are taken by whole thread blocks:
+// the block's groups take batches of 8 entries round-robin, then reduce by xor-shuffles
+// inside each warp and through shared memory across warps, in a fixed order.  Those
+// blocks have the lowest block ids of the launch, so they start first and overlap the
+// short rows.
+//
+// Every output element is a fixed-order sum: results are deterministic.
 #include <limits.h>
 
 #include "common.cuh"
 #include "scan.cuh"
+#include "slab.cuh"
 
 namespace spx {
 namespace {
 
 constexpr int SPMM_THREADS = 256;
 constexpr int SPMM_WARPS = SPMM_THREADS / 32;
+constexpr int BATCH = 8;                       // entries per gather batch
 
 template <int VEC>
-struct Vec;
-template <>
-struct Vec<4> {
-    using T = float4;
-};
-template <>
-struct Vec<1> {
-    using T = float;
-};
-
-template <int VEC>
-__device__ __forceinline__ void fma_row(float (&acc)[VEC], float v, const float* __restrict__ p) {
+__device__ __forceinline__ void fma_row(float (&acc)[VEC], float v, const float* __restrict__ p, uint64_t pol) {
     if constexpr (VEC == 4) {
-        float4 x = __ldg(reinterpret_cast<const float4*>(p));
+        float4 x = ld_hint4(p, pol);
         acc[0] = fmaf(v, x.x, acc[0]);
         acc[1] = fmaf(v, x.y, acc[1]);
         acc[2] = fmaf(v, x.z, acc[2]);
         acc[3] = fmaf(v, x.w, acc[3]);
     } else {
-        acc[0] = fmaf(v, __ldg(p), acc[0]);
+        acc[0] = fmaf(v, ld_hint(p, pol), acc[0]);
     }
 }
 
@@ -69,107 +69,144 @@ __device__ __forceinline__ void store_row(float* __restrict__ y, const float (&a
 }
 
 template <bool PERM>
-__device__ __forceinline__ float load_val(const float* __restrict__ vals, const int32_t* __restrict__ perm,
-                                          int e) {
+__device__ __forceinline__ float load_val(const float* __restrict__ vals, const int32_t* __restrict__ perm, int e,
+                                          uint64_t pol) {
     if constexpr (PERM)
-        return __ldg(vals + ld_stream(perm + e));
+        return __ldg(vals + ld_hint(perm + e, pol));
     else
-        return ld_stream(vals + e);
+        return ld_hint(vals + e, pol);
 }
 
-// blocks [0, long_blocks) process plan rows; the others process short rows.
-template <int VEC, bool PERM>
+// Entries [e, e + BATCH) of a row ending at b: lane c holds entries c*SLOTS .. c*SLOTS +
+// SLOTS - 1 of the batch (contiguous per lane); column -1 marks "no entry".
+template <int LPR, bool PERM>
+__device__ __forceinline__ void load_batch(int (&j)[(BATCH + LPR - 1) / LPR], float (&v)[(BATCH + LPR - 1) / LPR],
+                                           int e, int b, int c, const int32_t* __restrict__ indices,
+                                           const float* __restrict__ vals, const int32_t* __restrict__ perm,
+                                           uint64_t pol) {
+    constexpr int SLOTS = (BATCH + LPR - 1) / LPR;
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) {
+        const int q = c * SLOTS + s;
+        const int ee = e + q;
+        if (q < BATCH && ee < b) {
+            j[s] = ld_hint(indices + ee, pol);
+            v[s] = load_val<PERM>(vals, perm, ee, pol);
+        } else {
+            j[s] = -1;
+            v[s] = 0.f;
+        }
+    }
+}
+
+// Gathers one batch: acc += v_q * X[j_q, xcol .. xcol+VEC) for the 8 entries of the batch.
+template <int VEC, int LPR>
+__device__ __forceinline__ void gather_batch(float (&acc)[VEC], const int (&j)[(BATCH + LPR - 1) / LPR],
+                                             const float (&v)[(BATCH + LPR - 1) / LPR], unsigned gmask,
+                                             bool colok, const float* __restrict__ X, int64_t ldx, int xcol,
+                                             uint64_t pol) {
+    constexpr int SLOTS = (BATCH + LPR - 1) / LPR;
+#pragma unroll
+    for (int q = 0; q < BATCH; ++q) {
+        const int jq = __shfl_sync(gmask, j[q % SLOTS], q / SLOTS, LPR);
+        const float vq = __shfl_sync(gmask, v[q % SLOTS], q / SLOTS, LPR);
+        if (jq >= 0 && colok) fma_row<VEC>(acc, vq, X + (int64_t)jq * ldx + xcol, pol);
+    }
+}
+
+template <int VEC, int LPR, bool PERM>
 __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
     int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
     const float* __restrict__ vals, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t ldx,
-    int32_t k, float* __restrict__ Y, int64_t ldy, float alpha, float beta, int lpr_log2, int s_log2,
-    int32_t threshold, const int32_t* __restrict__ long_rows, int32_t n_long, int32_t long_blocks) {
+    int32_t x_shift, int32_t col_begin, int32_t col_end, float* __restrict__ Y, int64_t ldy, float alpha, float beta,
+    int32_t rows_per_group, int32_t threshold, const int32_t* __restrict__ long_rows, int32_t n_long,
+    int32_t long_blocks) {
+    constexpr int G = 32 / LPR;                      // lane groups per warp
+    constexpr int SLOTS = (BATCH + LPR - 1) / LPR;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int LPR = 1 << lpr_log2;
-    const int c = lane & (LPR - 1);           // column lane inside the slot
-    const int colstep = LPR * VEC;
+    const int g = lane / LPR;
+    const int c = lane % LPR;
+    const unsigned gmask = LPR == 32 ? FULL : (((1u << LPR) - 1u) << (g * LPR));
+    const int col = col_begin + c * VEC;
+    const int xcol = col - x_shift;
+    const bool colok = col < col_end;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
 
     if ((int)blockIdx.x < long_blocks) {
-        // ---------------- long rows: the whole block on one row, groups of LPR lanes
-        __shared__ float red[SPMM_WARPS][128];
-        const int Gw = 32 >> lpr_log2;         // groups per warp
-        const int g = lane >> lpr_log2;
-        const int gid = warp * Gw + g;
-        const int Gb = SPMM_WARPS * Gw;        // groups per block
+        // ---------------- long rows: all groups of the block on one row
+        __shared__ float red[SPMM_WARPS][32 * VEC];
+        const int gid = warp * G + g;
+        constexpr int GB = SPMM_WARPS * G;
         for (int q = blockIdx.x; q < n_long; q += long_blocks) {
             const int row = long_rows[q];
             const int a = indptr[row], b = indptr[row + 1];
-            for (int col0 = 0; col0 < k; col0 += colstep) {
-                const int col = col0 + c * VEC;
-                const bool colok = col < k;
-                float acc[VEC];
+            float acc[VEC];
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-                if (colok) {
-#pragma unroll 4
-                    for (int e = a + gid; e < b; e += Gb) {
-                        const int j = ld_stream(indices + e);
-                        const float av = load_val<PERM>(vals, perm, e);
-                        fma_row<VEC>(acc, av, X + (int64_t)j * ldx + col);
-                    }
-                }
-                for (int off = LPR; off < 32; off <<= 1)
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(FULL, acc[v], off);
-                if (g == 0)
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) red[warp][c * VEC + v] = acc[v];
-                __syncthreads();
-                if (warp == 0 && g == 0 && colok) {
-                    float tot[VEC];
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) tot[v] = red[0][c * VEC + v];
-                    for (int w = 1; w < SPMM_WARPS; ++w)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) tot[v] += red[w][c * VEC + v];
-                    store_row<VEC>(Y + (int64_t)row * ldy + col, tot, alpha, beta);
-                }
-                __syncthreads();
+            for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+            for (int e = a + gid * BATCH; e < b; e += GB * BATCH) {
+                int j[SLOTS];
+                float vv[SLOTS];
+                load_batch<LPR, PERM>(j, vv, e, b, c, indices, vals, perm, pol_stream);
+                gather_batch<VEC, LPR>(acc, j, vv, gmask, colok, X, ldx, xcol, pol_keep);
             }
+#pragma unroll
+            for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(FULL, acc[v], off);
+            if (g == 0)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) red[warp][c * VEC + v] = acc[v];
+            __syncthreads();
+            if (warp == 0 && g == 0 && colok) {
+                float tot[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) tot[v] = red[0][c * VEC + v];
+                for (int w = 1; w < SPMM_WARPS; ++w)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) tot[v] += red[w][c * VEC + v];
+                store_row<VEC>(Y + (int64_t)row * ldy + col, tot, alpha, beta);
+            }
+            __syncthreads();
         }
         return;
     }
 
-    // ---------------- short rows: S lanes per row
-    const int S = 1 << s_log2;
-    const int sl = lane & (S - 1);
-    const int g = sl >> lpr_log2;
-    const int G = S >> lpr_log2;
-    const int64_t gw = ((int64_t)(blockIdx.x - long_blocks) * SPMM_THREADS + threadIdx.x) >> 5;
-    const int64_t row = (gw << (5 - s_log2)) + (lane >> s_log2);
-    int a = 0, b = 0;
-    bool active = row < m;
-    if (active) {
-        a = indptr[row];
-        b = indptr[row + 1];
-        if (b - a > threshold) active = false;     // taken by the long-row blocks
-    }
-    if (!active) b = a;
-    for (int col0 = 0; col0 < k; col0 += colstep) {
-        const int col = col0 + c * VEC;
-        const bool colok = col < k;
+    // ---------------- short rows: one lane group per row
+    const int64_t wglobal = ((int64_t)(blockIdx.x - long_blocks) * SPMM_THREADS + threadIdx.x) >> 5;
+    const int64_t row0 = (wglobal * G + g) * rows_per_group;
+    for (int p = 0; p < rows_per_group; ++p) {
+        const int64_t row = row0 + p;
+        if (row >= m) break;
+        const int a = indptr[row], b = indptr[row + 1];
+        if (b - a > threshold) continue;            // a long-row block takes it
         float acc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
-        if (colok) {
-#pragma unroll 4
-            for (int e = a + g; e < b; e += G) {
-                const int j = ld_stream(indices + e);
-                const float av = load_val<PERM>(vals, perm, e);
-                fma_row<VEC>(acc, av, X + (int64_t)j * ldx + col);
-            }
-        }
-        for (int off = LPR; off < S; off <<= 1)
+        int jn[SLOTS];
+        float vn[SLOTS];
+        load_batch<LPR, PERM>(jn, vn, a, b, c, indices, vals, perm, pol_stream);
+        for (int e = a; e < b; e += BATCH) {
+            int jc[SLOTS];
+            float vc[SLOTS];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(FULL, acc[v], off);
-        if (active && g == 0 && colok) store_row<VEC>(Y + row * ldy + col, acc, alpha, beta);
+            for (int s = 0; s < SLOTS; ++s) {
+                jc[s] = jn[s];
+                vc[s] = vn[s];
+            }
+            if (e + BATCH < b) load_batch<LPR, PERM>(jn, vn, e + BATCH, b, c, indices, vals, perm, pol_stream);
+            gather_batch<VEC, LPR>(acc, jc, vc, gmask, colok, X, ldx, xcol, pol_keep);
+        }
+        if (colok) store_row<VEC>(Y + row * ldy + col, acc, alpha, beta);
     }
+}
+
+__global__ void gather_values_kernel(int64_t nnz, const int32_t* __restrict__ perm, const float* __restrict__ vals,
+                                     float* __restrict__ out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride)
+        __stcs(out + e, __ldg(vals + ld_stream(perm + e)));
 }
 
 int ilog2_ceil(int64_t x) {
@@ -180,22 +217,62 @@ int ilog2_ceil(int64_t x) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+template <int VEC, bool PERM>
+spx_status launch_lpr(int lpr, unsigned grid, cudaStream_t st, const spx_csr* A, const int32_t* perm,
+                      const float* vals, const float* X, int64_t ldx, int32_t xs, int32_t c0, int32_t c1, float* Y,
+                      int64_t ldy, float alpha, float beta, int32_t rpg, int32_t thr, const int32_t* lr,
+                      int32_t n_long, int32_t long_blocks) {
+#define SPX_SPMM_CASE(L)                                                                                        \
+    case L:                                                                                                     \
+        spmm_kernel<VEC, L, PERM><<<grid, SPMM_THREADS, 0, st>>>(A->m, A->indptr, A->indices, vals, perm, X, ldx, \
+                                                                 xs, c0, c1, Y, ldy, alpha, beta, rpg, thr, lr,  \
+                                                                 n_long, long_blocks);                           \
+        break;
+    switch (lpr) {
+        SPX_SPMM_CASE(1)
+        SPX_SPMM_CASE(2)
+        SPX_SPMM_CASE(4)
+        SPX_SPMM_CASE(8)
+        SPX_SPMM_CASE(16)
+        SPX_SPMM_CASE(32)
+        default: return set_error(SPX_INVALID_ARG, "spmm: bad lane count %d", lpr);
+    }
+#undef SPX_SPMM_CASE
+    return SPX_OK;
+}
+
+struct SpmmShape {
+    bool vec4;
+    int32_t cb;        // columns per pass
+    int32_t lpr;       // lanes per row group
+    int32_t rpg;       // rows per group
+    size_t slab;       // bytes of the repacked dense operand (0 = gather the strided operand)
+};
+
+SpmmShape spmm_shape(const spx_csr* A, int32_t k, const spx_rowplan* plan, bool vec4) {
+    SpmmShape sh{};
+    sh.vec4 = vec4;
+    const int VEC = vec4 ? 4 : 1;
+    int32_t cb = plan && plan->col_block > 0 ? plan->col_block : slab_col_block(A->n, k);
+    if (cb > k) cb = k;
+    if (vec4 && cb % 4 != 0) cb = (cb + 3) / 4 * 4;
+    if (cb > 32 * VEC) cb = 32 * VEC;
+    sh.cb = cb;
+    int lpr = 1 << ilog2_ceil((cb + VEC - 1) / VEC);
+    sh.lpr = lpr > 32 ? 32 : lpr;
+    sh.rpg = plan && plan->rows_per_group > 0 ? plan->rows_per_group : 2;
+    sh.slab = vec4 ? slab_bytes(A->n, k, cb) : 0;
+    return sh;
+}
+
 template <bool PERM>
-spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* X, int64_t ldx, int32_t k,
-                       float* Y, int64_t ldy, float alpha, float beta, const spx_rowplan* plan,
-                       cudaStream_t st, const char* who) {
+spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals, const float* X, int64_t ldx,
+                       int32_t k, float* Y, int64_t ldy, float alpha, float beta, const spx_rowplan* plan,
+                       float* slab_ws, size_t slab_ws_bytes, cudaStream_t st, const char* who) {
     if (A->m == 0 || k == 0) return SPX_OK;
     const bool vec4 = (k % 4 == 0) && (ldx % 4 == 0) && (ldy % 4 == 0) && aligned16(X) && aligned16(Y);
-    const int VEC = vec4 ? 4 : 1;
-    const int64_t lanes_needed = (k + VEC - 1) / VEC;
-    int lpr_log2 = ilog2_ceil(lanes_needed);
-    if (lpr_log2 > 5) lpr_log2 = 5;
-    // groups per row ~ half the mean row length (at least one), slot width <= 32 lanes
-    const double mean = A->m > 0 ? (double)A->nnz / (double)A->m : 0.0;
-    int glog = ilog2_ceil((int64_t)(mean / 2.0 + 0.999));
-    int s_log2 = lpr_log2 + glog;
-    if (s_log2 > 5) s_log2 = 5;
-    if (s_log2 < lpr_log2) s_log2 = lpr_log2;
+    const SpmmShape sh = spmm_shape(A, k, plan, vec4);
+    const bool use_slab = sh.slab > 0 && slab_ws != nullptr && slab_ws_bytes >= sh.slab;
 
     int32_t threshold = INT_MAX;
     const int32_t* long_rows = nullptr;
@@ -207,19 +284,24 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* X, in
         n_long = plan->n_long;
         long_blocks = n_long < 4 * num_sms() ? n_long : 4 * num_sms();
     }
-    const int64_t rows_per_block = (int64_t)SPMM_WARPS << (5 - s_log2);
+    const int G = 32 / sh.lpr;
+    const int64_t rows_per_block = (int64_t)SPMM_WARPS * G * sh.rpg;
     const int64_t short_blocks = ((int64_t)A->m + rows_per_block - 1) / rows_per_block;
     const int64_t grid = short_blocks + long_blocks;
     if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
-    if (vec4)
-        spmm_kernel<4, PERM><<<(unsigned)grid, SPMM_THREADS, 0, st>>>(
-            A->m, A->indptr, A->indices, A->values, perm, X, ldx, k, Y, ldy, alpha, beta, lpr_log2, s_log2,
-            threshold, long_rows, n_long, long_blocks);
-    else
-        spmm_kernel<1, PERM><<<(unsigned)grid, SPMM_THREADS, 0, st>>>(
-            A->m, A->indptr, A->indices, A->values, perm, X, ldx, k, Y, ldy, alpha, beta, lpr_log2, s_log2,
-            threshold, long_rows, n_long, long_blocks);
-    SPX_CHECK_LAUNCH(who);
+    if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, sh.cb, slab_ws, st));
+    for (int32_t c0 = 0; c0 < k; c0 += sh.cb) {
+        const int32_t c1 = c0 + sh.cb < k ? c0 + sh.cb : k;
+        const float* Xp = use_slab ? slab_ws + (int64_t)(c0 / sh.cb) * A->n * sh.cb : X;
+        const int64_t ldp = use_slab ? sh.cb : ldx;
+        const int32_t xs = use_slab ? c0 : 0;
+        spx_status s = vec4 ? launch_lpr<4, PERM>(sh.lpr, (unsigned)grid, st, A, perm, vals, Xp, ldp, xs, c0, c1, Y,
+                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks)
+                            : launch_lpr<1, PERM>(sh.lpr, (unsigned)grid, st, A, perm, vals, Xp, ldp, xs, c0, c1, Y,
+                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks);
+        if (s != SPX_OK) return s;
+        SPX_CHECK_LAUNCH(who);
+    }
     return SPX_OK;
 }
 
@@ -240,6 +322,8 @@ size_t rowplan_ws(int32_t m) {
     size_t b = (((size_t)m + 1) * 4 + 255) & ~size_t(255);
     return a + b + scan_workspace_bytes<int32_t>(m);
 }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 }  // namespace spx
@@ -286,20 +370,67 @@ static spx_status check_dense(const void* p, int64_t rows, int64_t ld, int32_t k
     return SPX_OK;
 }
 
+static bool vec4_ok(int32_t k, int64_t ldx, int64_t ldy, const void* X, const void* Y) {
+    return (k % 4 == 0) && (ldx % 4 == 0) && (ldy % 4 == 0) && aligned16(X) && aligned16(Y);
+}
+
+extern "C" spx_status spx_spmm_workspace_size(const spx_csr* A, int32_t k, const spx_rowplan* plan, size_t* bytes) {
+    SPX_TRY(check_csr(A, false, "spx_spmm_workspace_size"));
+    if (!bytes || k < 0) return set_error(SPX_INVALID_ARG, "spx_spmm_workspace_size: bad arguments");
+    *bytes = k > 0 && k % 4 == 0 ? align256(spmm_shape(A, k, plan, true).slab) : 0;
+    return SPX_OK;
+}
+
 extern "C" spx_status spx_spmm(const spx_csr* A, const float* X, int64_t ldx, int32_t k, float* Y,
-                               int64_t ldy, float alpha, float beta, const spx_rowplan* plan, void* stream) {
+                               int64_t ldy, float alpha, float beta, const spx_rowplan* plan, void* ws,
+                               size_t ws_bytes, void* stream) {
     SPX_TRY(check_csr(A, true, "spx_spmm"));
     SPX_TRY(check_dense(X, A->n, ldx, k, "spx_spmm", "X"));
     SPX_TRY(check_dense(Y, A->m, ldy, k, "spx_spmm", "Y"));
-    return launch_spmm<false>(A, nullptr, X, ldx, k, Y, ldy, alpha, beta, plan, as_stream(stream), "spx_spmm");
+    if (ws && k > 0) {
+        const size_t need = spmm_shape(A, k, plan, vec4_ok(k, ldx, ldy, X, Y)).slab;
+        if (ws_bytes < need)
+            return set_error(SPX_OOM_WORKSPACE, "spx_spmm: workspace %zu < %zu", ws_bytes, need);
+    }
+    return launch_spmm<false>(A, nullptr, A->values, X, ldx, k, Y, ldy, alpha, beta, plan, static_cast<float*>(ws),
+                              ws_bytes, as_stream(stream), "spx_spmm");
+}
+
+// A^T's gathered values first, then the repacked slabs of G.
+static size_t spmm_t_need(const spx_csr* AT, int32_t k, const spx_rowplan* plan, bool vec4) {
+    return align256((size_t)AT->nnz * 4) + spmm_shape(AT, k, plan, vec4).slab;
+}
+
+extern "C" spx_status spx_spmm_t_workspace_size(const spx_csr* AT, int32_t k, const spx_rowplan* plan,
+                                                size_t* bytes) {
+    SPX_TRY(check_csr(AT, false, "spx_spmm_t_workspace_size"));
+    if (!bytes || k < 0) return set_error(SPX_INVALID_ARG, "spx_spmm_t_workspace_size: bad arguments");
+    *bytes = align256(spmm_t_need(AT, k, plan, k % 4 == 0));
+    return SPX_OK;
 }
 
 extern "C" spx_status spx_spmm_t(const spx_csr* AT, const int32_t* perm, const float* G, int64_t ldg,
                                  int32_t k, float* gX, int64_t ldgx, float alpha, float beta,
-                                 const spx_rowplan* plan, void* stream) {
+                                 const spx_rowplan* plan, void* ws, size_t ws_bytes, void* stream) {
     SPX_TRY(check_csr(AT, true, "spx_spmm_t"));
     if (AT->nnz > 0 && !perm) return set_error(SPX_INVALID_ARG, "spx_spmm_t: NULL perm");
     SPX_TRY(check_dense(G, AT->n, ldg, k, "spx_spmm_t", "G"));
     SPX_TRY(check_dense(gX, AT->m, ldgx, k, "spx_spmm_t", "gX"));
-    return launch_spmm<true>(AT, perm, G, ldg, k, gX, ldgx, alpha, beta, plan, as_stream(stream), "spx_spmm_t");
+    cudaStream_t st = as_stream(stream);
+    if (!ws) return launch_spmm<true>(AT, perm, AT->values, G, ldg, k, gX, ldgx, alpha, beta, plan, nullptr, 0, st,
+                                      "spx_spmm_t");
+    const size_t need = spmm_t_need(AT, k, plan, vec4_ok(k, ldg, ldgx, G, gX));
+    if (ws_bytes < need) return set_error(SPX_OOM_WORKSPACE, "spx_spmm_t: workspace %zu < %zu", ws_bytes, need);
+    if (AT->nnz == 0 || AT->m == 0 || k == 0)
+        return launch_spmm<false>(AT, nullptr, AT->values, G, ldg, k, gX, ldgx, alpha, beta, plan, nullptr, 0, st,
+                                  "spx_spmm_t");
+    float* tv = static_cast<float*>(ws);
+    const size_t voff = align256((size_t)AT->nnz * 4);
+    int64_t blocks = (AT->nnz + 255) / 256;
+    int64_t cap = (int64_t)num_sms() * 16;
+    gather_values_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(AT->nnz, perm, AT->values, tv);
+    SPX_CHECK_LAUNCH("spx_spmm_t gather");
+    return launch_spmm<false>(AT, nullptr, tv, G, ldg, k, gX, ldgx, alpha, beta, plan,
+                              reinterpret_cast<float*>(static_cast<char*>(ws) + voff), ws_bytes - voff, st,
+                              "spx_spmm_t");
 }

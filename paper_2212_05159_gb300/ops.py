@@ -11,6 +11,10 @@ from . import abi
 from .csr import CSR
 
 
+def _workspace(nbytes: int, device):
+    return abi.workspace(nbytes, device) if nbytes > 0 else None
+
+
 def _as2d(t: torch.Tensor):
     return (t.unsqueeze(1), True) if t.dim() == 1 else (t, False)
 
@@ -21,7 +25,10 @@ def spmm(A: CSR, X: torch.Tensor, values: torch.Tensor | None = None, out=None,
     X2, vec = _as2d(X)
     Y = out if out is not None else torch.empty(A.m, X2.shape[1], dtype=torch.float32, device=X.device)
     Y2, _ = _as2d(Y)
-    abi.spx_spmm(A.struct(values), X2, Y2, alpha, beta, A.plan() if use_plan else None)
+    st = A.struct(values)
+    plan = A.plan() if use_plan else None
+    ws = _workspace(abi.spx_spmm_workspace_size(st, X2.shape[1], plan), X.device)
+    abi.spx_spmm(st, X2, Y2, alpha, beta, plan, ws)
     return Y2.squeeze(1) if vec else Y2
 
 
@@ -33,7 +40,9 @@ def sddmm(A: CSR, G: torch.Tensor, X: torch.Tensor, scale: float = 1.0, out=None
     if G2.shape[1] == 1 and G2.is_contiguous() and X2.is_contiguous():
         abi.spx_masked_outer(A.struct(), G2, X2, o, scale)
     else:
-        abi.spx_sddmm(A.struct(), G2, X2, o, scale)
+        st = A.struct()
+        ws = _workspace(abi.spx_sddmm_workspace_size(st, G2.shape[1]), G.device)
+        abi.spx_sddmm(st, G2, X2, o, scale, 0, ws)
     return o
 
 
@@ -51,5 +60,8 @@ def spmm_t(A: CSR, G: torch.Tensor, values: torch.Tensor | None = None, out=None
     gX = out if out is not None else torch.empty(A.n, G2.shape[1], dtype=torch.float32, device=G.device)
     gX2, _ = _as2d(gX)
     _, _, perm = A.transpose_pattern()
-    abi.spx_spmm_t(A.t_struct(values), perm, G2, gX2, alpha, beta, A.t_plan() if use_plan else None)
+    st = A.t_struct(values)
+    plan = A.t_plan() if use_plan else None
+    ws = _workspace(abi.spx_spmm_t_workspace_size(st, G2.shape[1], plan), G.device)
+    abi.spx_spmm_t(st, perm, G2, gX2, alpha, beta, plan, ws)
     return gX2.squeeze(1) if vec else gX2

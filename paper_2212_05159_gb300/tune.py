@@ -1,0 +1,135 @@
+"""Autotuner for the launch parameters of the row-wise products and of SDDMM.
+
+For a given pattern and dense width k it times the candidate column blocks (columns
+gathered per pass) and rows-per-group settings with CUDA events on the current
+stream and keeps the fastest.  Results are cached per (pattern statistics, k, kind) in
+memory and in ``_build/tune_cache.json``.  Timing only: the kernels computed with any
+candidate give results within the same tolerance (the column split changes only which
+pass adds which columns, never the order of a sum).
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+from . import abi
+from .csr import CSR
+
+_CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune_cache.json")
+_lock = threading.Lock()
+_cache: dict | None = None
+
+
+def _load():
+    global _cache
+    if _cache is None:
+        try:
+            with open(_CACHE_PATH) as fh:
+                _cache = json.load(fh)
+        except (OSError, ValueError):
+            _cache = {}
+    return _cache
+
+
+def _save():
+    try:
+        os.makedirs(os.path.dirname(_CACHE_PATH), exist_ok=True)
+        tmp = _CACHE_PATH + f".tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(_cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, _CACHE_PATH)
+    except OSError:
+        pass
+
+
+def _key(A: CSR, k: int, kind: str) -> str:
+    return f"{kind}:m={A.m}:n={A.n}:nnz={A.nnz}:k={k}"
+
+
+def _time(fn, reps=3):
+    fn()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _col_blocks(k: int):
+    c = sorted({k} | {b for b in (128, 64, 32, 16, 8, 4) if b < k and (k % 4 != 0 or b % 4 == 0)},
+               reverse=True)
+    return c
+
+
+def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
+    """Best (col_block, rows_per_group) for spx_spmm (or spx_spmm_t when transposed)."""
+    kind = "spmm_t" if transposed else "spmm"
+    key = _key(A, k, kind)
+    with _lock:
+        c = _load()
+        if key in c and not force:
+            return tuple(c[key]["best"])
+    dev = A.device
+    rows_in, rows_out = (A.m, A.n) if transposed else (A.n, A.m)
+    X = torch.randn(rows_in, k, device=dev)
+    Y = torch.empty(rows_out, k, device=dev)
+    base = A.t_plan() if transposed else A.plan()
+    best, best_ms, table = None, float("inf"), {}
+    for cb in _col_blocks(k):
+        for rpg in (1, 2, 4):
+            plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg)
+            if transposed:
+                _, _, perm = A.transpose_pattern()
+                s = A.t_struct()
+                ws = abi.workspace(abi.spx_spmm_t_workspace_size(s, k, plan), dev)
+                fn = lambda: abi.spx_spmm_t(s, perm, X, Y, 1.0, 0.0, plan, ws)  # noqa: E731
+            else:
+                s = A.struct()
+                ws = abi.workspace(abi.spx_spmm_workspace_size(s, k, plan), dev)
+                fn = lambda: abi.spx_spmm(s, X, Y, 1.0, 0.0, plan, ws)  # noqa: E731
+            ms = _time(fn)
+            del ws
+            table[f"{cb},{rpg}"] = ms
+            if ms < best_ms:
+                best, best_ms = (cb, rpg), ms
+    with _lock:
+        _load()[key] = {"best": list(best), "ms": best_ms, "table": table}
+        _save()
+    return best
+
+
+def tune_sddmm(A: CSR, k: int, force: bool = False) -> int:
+    """Best column block for spx_sddmm."""
+    key = _key(A, k, "sddmm")
+    with _lock:
+        c = _load()
+        if key in c and not force:
+            return int(c[key]["best"])
+    dev = A.device
+    G = torch.randn(A.m, k, device=dev)
+    X = torch.randn(A.n, k, device=dev)
+    out = torch.empty(A.nnz, device=dev)
+    s = A.struct()
+    best, best_ms, table = None, float("inf"), {}
+    for cb in _col_blocks(k):
+        ws = abi.workspace(abi.spx_sddmm_workspace_size(s, k, cb), dev)
+        ms = _time(lambda: abi.spx_sddmm(s, G, X, out, 1.0, cb, ws))
+        table[str(cb)] = ms
+        if ms < best_ms:
+            best, best_ms = cb, ms
+    with _lock:
+        _load()[key] = {"best": best, "ms": best_ms, "table": table}
+        _save()
+    return best
+
+
+def tuned_plan(A: CSR, k: int, transposed: bool = False):
+    base = A.t_plan() if transposed else A.plan()
+    cb, rpg = tune_rows(A, k, transposed)
+    return abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg)

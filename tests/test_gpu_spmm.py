@@ -181,3 +181,36 @@ def test_full_size_powerlaw_sampled(k):
     np.testing.assert_array_equal(d_ip, t_ip)
     np.testing.assert_array_equal(d_ix, t_ix)
     np.testing.assert_array_equal(d_perm, perm)
+
+
+@pytest.mark.parametrize("cb,rpg", [(4, 1), (8, 3), (16, 2), (32, 4)])
+def test_tuning_variants_match_oracle(mat, cb, rpg):
+    """Every column-block / rows-per-group setting the autotuner may pick is correct."""
+    from paper_2212_05159_gb300 import abi
+    name, A, dA = mat
+    k = 32
+    X = synth.normal((A.n, k), seed=40)
+    G = synth.normal((A.m, k), seed=41)
+    base = dA.plan()
+    plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg)
+    Y = torch.empty(A.m, k, device="cuda")
+    ws = abi.workspace(abi.spx_spmm_workspace_size(dA.struct(), k, plan), "cuda")
+    abi.spx_spmm(dA.struct(), dev(X), Y, 1.0, 0.0, plan, ws)
+    assert_close_normalised(host(Y), oracle.spmm(A, X), oracle.spmm(abs_csr(A), np.abs(X)),
+                            what=f"spmm {name} cb={cb} rpg={rpg}")
+    tb = dA.t_plan()
+    tplan = abi.spx_rowplan(tb.long_rows, tb.n_long, tb.threshold, cb, rpg)
+    gX = torch.empty(A.n, k, device="cuda")
+    _, _, perm = dA.transpose_pattern()
+    abi.spx_spmm_t(dA.t_struct(), perm, dev(G), gX, 1.0, 0.0, tplan, None)   # gather through perm
+    assert_close_normalised(host(gX), oracle.spmm_t(A, G), oracle.spmm_t(abs_csr(A), np.abs(G)),
+                            what=f"spmm_t {name} cb={cb} no workspace")
+    abi.spx_spmm_t(dA.t_struct(), perm, dev(G), gX, 1.0, 0.0, tplan,
+                   abi.workspace(abi.spx_spmm_t_workspace_size(dA.t_struct(), k, tplan), "cuda"))
+    assert_close_normalised(host(gX), oracle.spmm_t(A, G), oracle.spmm_t(abs_csr(A), np.abs(G)),
+                            what=f"spmm_t {name} cb={cb}")
+    out = torch.empty(A.nnz, device="cuda")
+    abi.spx_sddmm(dA.struct(), dev(G), dev(X), out, 1.0, cb,
+                  abi.workspace(abi.spx_sddmm_workspace_size(dA.struct(), k, cb), "cuda"))
+    assert_close_normalised(host(out), oracle.sddmm(A, G, X), oracle.sddmm(A, np.abs(G), np.abs(X)),
+                            what=f"sddmm {name} cb={cb}")
