@@ -182,6 +182,96 @@ spx_status spx_spmm_t(const spx_csr* AT, const int32_t* perm, const float* G, in
                       const spx_rowplan* plan, void* workspace, size_t workspace_bytes,
                       void* stream);
 
+/* ------------------------------------- SpSpMM / SpGEMM (Section 3.1.2, Table 1) */
+
+/* Workspace bytes of the SpGEMM calls for an m-row A (per-row counts, offsets and the
+ * list of rows too large for one warp).  The same workspace must be passed to
+ * analyse, symbolic, fill and numeric of one product, in that order. */
+spx_status spx_spgemm_workspace_size(int32_t m, size_t* bytes);
+
+/* C = A B, step 1 (expand): per-row product counts P_i = sum_{k in A_i} |B_k| and their
+ * prefix sums.  Writes the total number of products to *products_host; the symbolic
+ * step needs 4 * products bytes of scratch.  A, B patterns only.  Synchronizes. */
+spx_status spx_spgemm_analyse(const spx_csr* A, const spx_csr* B, int64_t* products_host,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
+/* Step 2 (sort / compress): the pattern of C is the structural product -- every (i, j)
+ * reached by some A_ik B_kj, with no dropping of numerical zeros.  Writes C_indptr
+ * (device int32[m+1]) and nnz(C) to *nnz_c_host, and keeps each row's sorted unique
+ * columns in `scratch` (device, >= 4 * products bytes) for spx_spgemm_fill.
+ * Synchronizes. */
+spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, int32_t* c_indptr,
+                               int64_t* nnz_c_host, void* workspace, size_t workspace_bytes,
+                               void* scratch, size_t scratch_bytes, void* stream);
+
+/* Step 3: C_indices (device int32[nnz(C)], sorted within rows) from the scratch. */
+spx_status spx_spgemm_fill(const spx_csr* A, const int32_t* c_indptr, int32_t* c_indices,
+                           const void* workspace, size_t workspace_bytes, const void* scratch,
+                           void* stream);
+
+/* Step 4: C values on C's pattern, C_ij = sum_{k in A_i, in A's order} A_ik B_kj
+ * (deterministic).  C: the pattern from steps 2-3 (C.values ignored); c_values: device
+ * float32[nnz(C)].  Needs the workspace of step 1 (row classes).  May be repeated for
+ * new values of A and B with the same patterns. */
+spx_status spx_spgemm_numeric(const spx_csr* A, const spx_csr* B, const spx_csr* C,
+                              float* c_values, const void* workspace, size_t workspace_bytes,
+                              void* stream);
+
+/* Reverse mode of C = A B with V = dL/dC given on C's pattern (Table 1, SpSpMM):
+ *   ga[(i,k)] = sum_{j in B_k} V_ij B_kj          ((V B^T) masked to A; needs B.values)
+ *   gb[(k,j)] = sum_{i : A_ik stored} A_ik V_ij   ((A^T V) masked to B; needs A.values and
+ *                                                   A's transpose from spx_csr_transpose)
+ * Either output may be NULL.  gc: device float32[nnz(C)]; ga: float32[nnz(A)];
+ * gb: float32[nnz(B)].  Deterministic. */
+spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, const spx_csr* C,
+                               const float* gc, float* ga, float* gb,
+                               const int32_t* at_indptr, const int32_t* at_indices,
+                               const int32_t* a_perm, void* stream);
+
+/* dst[e] = src[perm[e]] for e < nnz -- e.g. A^T's values from A's through the
+ * permutation of spx_csr_transpose.  Device pointers. */
+spx_status spx_gather_values(int64_t nnz, const int32_t* perm, const float* src, float* dst,
+                             void* stream);
+
+/* ------------------------------ differentiable sparse solve (Section 4.3, Table 1) */
+
+/* Workspace bytes of spx_cg_batched for an n-row batch (six float vectors). */
+spx_status spx_cg_workspace_size(int32_t n, size_t* bytes);
+
+/* Batched PCG: solves A_s x_s = b_s for every diagonal block s of the block-diagonal
+ * SPD matrix A (row offsets sys_ptr, device int32[nsys+1]; A's column indices are global
+ * and stay inside their block), from x0 = 0, until the TRUE relative residual
+ * ||b_s - A_s x_s|| / ||b_s||, computed in FP64, is <= tol, or maxit iterations.
+ * The iteration runs in FP32 with reliable updates into the FP64 solution whenever the
+ * recurrence residual drops by the factor `delta` (0 < delta < 1, e.g. 0.1); inner
+ * products accumulate in double-float and are combined in FP64.
+ * order: optional device int32[nsys], the order in which systems are taken (largest
+ *        first balances the load); NULL = natural order.
+ * b: device float32[n]; x: device float64[n] (output).
+ * pc_kind: 0 none, 1 Jacobi (pc_diag_inv = device float32[n] holding 1 / a_ii),
+ *          2 M = L L^T (Section 4.3): L lower-triangular CSR with values on the
+ *          diagonal blocks and LT its transpose with values (spx_csr_transpose +
+ *          spx_gather_values).
+ * iters, status (spx_status per system: OK, MAXITER, BREAKDOWN, NONFINITE): device
+ * int32[nsys]; relres: device float64[nsys], the true relative residual of the
+ * returned x.  One launch of thread-block clusters (8 blocks per system); capturable
+ * in a CUDA graph.  The call's own status reports argument / launch errors only. */
+spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
+                          const int32_t* order, const float* b, double* x, int32_t pc_kind,
+                          const float* pc_diag_inv, const spx_csr* L, const spx_csr* LT,
+                          double tol, int32_t maxit, double delta, int32_t* iters,
+                          int32_t* status, double* relres, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* dinv[i] = 1 / a_ii (0 where the diagonal is absent or zero); device float32[m]. */
+spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream);
+
+/* out[e] = (float)(scale * u[i] * v[j]) on mask(A) with FP64 u, v: the SpSolve
+ * gradient w.r.t. A, -(A^{-T} g) x^T masked to A (Table 1), with scale = -1,
+ * u = lambda = A^{-T} g and v = x. */
+spx_status spx_masked_outer_f64(const spx_csr* A, const double* u, const double* v,
+                                double scale, float* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

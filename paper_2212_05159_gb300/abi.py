@@ -70,6 +70,18 @@ SIGNATURES = {
     "spx_csr_transpose": [_CSRP, _P, _P, _P, _P, _SZ, _P],
     "spx_spmm_t_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
     "spx_spmm_t": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
+    "spx_spgemm_workspace_size": [_I32, ctypes.POINTER(_SZ)],
+    "spx_spgemm_analyse": [_CSRP, _CSRP, ctypes.POINTER(_I64), _P, _SZ, _P],
+    "spx_spgemm_symbolic": [_CSRP, _CSRP, _P, ctypes.POINTER(_I64), _P, _SZ, _P, _SZ, _P],
+    "spx_spgemm_fill": [_CSRP, _P, _P, _P, _SZ, _P, _P],
+    "spx_spgemm_numeric": [_CSRP, _CSRP, _CSRP, _P, _P, _SZ, _P],
+    "spx_spgemm_backward": [_CSRP, _CSRP, _CSRP, _P, _P, _P, _P, _P, _P, _P],
+    "spx_gather_values": [_I64, _P, _P, _P, _P],
+    "spx_cg_workspace_size": [_I32, ctypes.POINTER(_SZ)],
+    "spx_cg_batched": [_CSRP, _P, _I32, _P, _P, _P, _I32, _P, _CSRP, _CSRP, _D, _I32, _D, _P, _P, _P, _P,
+                       _SZ, _P],
+    "spx_diag_inverse": [_CSRP, _P, _P],
+    "spx_masked_outer_f64": [_CSRP, _P, _P, _D, _P, _P],
 }
 
 
@@ -229,3 +241,75 @@ def spx_spmm_t(AT: spx_csr, perm, G, gX, alpha=1.0, beta=0.0, plan: spx_rowplan 
     _check(lib().spx_spmm_t(ctypes.byref(AT), ptr(perm), pg, ldg, G.shape[1], px, ldx, float(alpha),
                             float(beta), _planp(plan), *_wsargs(ws), _stream()), "spx_spmm_t")
     return gX
+
+
+# ------------------------------------------------------------------ SpGEMM
+def spx_spgemm_workspace_size(m: int) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_spgemm_workspace_size(int(m), ctypes.byref(sz)), "spx_spgemm_workspace_size")
+    return sz.value
+
+
+def spx_spgemm_analyse(A: spx_csr, B: spx_csr, ws) -> int:
+    prods = _I64(0)
+    _check(lib().spx_spgemm_analyse(ctypes.byref(A), ctypes.byref(B), ctypes.byref(prods), ptr(ws),
+                                    ws.numel(), _stream()), "spx_spgemm_analyse")
+    return prods.value
+
+
+def spx_spgemm_symbolic(A: spx_csr, B: spx_csr, c_indptr, ws, scratch) -> int:
+    nnz = _I64(0)
+    _check(lib().spx_spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), ptr(c_indptr), ctypes.byref(nnz),
+                                     ptr(ws), ws.numel(), ptr(scratch), scratch.numel(), _stream()),
+           "spx_spgemm_symbolic")
+    return nnz.value
+
+
+def spx_spgemm_fill(A: spx_csr, c_indptr, c_indices, ws, scratch):
+    _check(lib().spx_spgemm_fill(ctypes.byref(A), ptr(c_indptr), ptr(c_indices), ptr(ws), ws.numel(),
+                                 ptr(scratch), _stream()), "spx_spgemm_fill")
+
+
+def spx_spgemm_numeric(A: spx_csr, B: spx_csr, C: spx_csr, c_values, ws):
+    _check(lib().spx_spgemm_numeric(ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), ptr(c_values),
+                                    ptr(ws), ws.numel(), _stream()), "spx_spgemm_numeric")
+
+
+def spx_spgemm_backward(A: spx_csr, B: spx_csr, C: spx_csr, gc, ga, gb, at_indptr=None, at_indices=None,
+                        a_perm=None):
+    _check(lib().spx_spgemm_backward(ctypes.byref(A), ctypes.byref(B), ctypes.byref(C), ptr(gc), ptr(ga),
+                                     ptr(gb), ptr(at_indptr), ptr(at_indices), ptr(a_perm), _stream()),
+           "spx_spgemm_backward")
+
+
+# ------------------------------------------------------------------ solve
+def spx_gather_values(perm, src, dst):
+    _check(lib().spx_gather_values(int(perm.numel()), ptr(perm), ptr(src), ptr(dst), _stream()),
+           "spx_gather_values")
+    return dst
+
+
+def spx_cg_workspace_size(n: int) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_cg_workspace_size(int(n), ctypes.byref(sz)), "spx_cg_workspace_size")
+    return sz.value
+
+
+def spx_cg_batched(A: spx_csr, sys_ptr, nsys: int, order, b, x, pc_kind: int, dinv, L: spx_csr | None,
+                   LT: spx_csr | None, tol: float, maxit: int, delta: float, iters, status, relres, ws):
+    _check(lib().spx_cg_batched(ctypes.byref(A), ptr(sys_ptr), int(nsys), ptr(order), ptr(b), ptr(x),
+                                int(pc_kind), ptr(dinv), ctypes.byref(L) if L is not None else None,
+                                ctypes.byref(LT) if LT is not None else None, float(tol), int(maxit),
+                                float(delta), ptr(iters), ptr(status), ptr(relres), ptr(ws), ws.numel(),
+                                _stream()), "spx_cg_batched")
+
+
+def spx_diag_inverse(A: spx_csr, dinv):
+    _check(lib().spx_diag_inverse(ctypes.byref(A), ptr(dinv), _stream()), "spx_diag_inverse")
+    return dinv
+
+
+def spx_masked_outer_f64(A: spx_csr, u, v, out, scale=1.0):
+    _check(lib().spx_masked_outer_f64(ctypes.byref(A), ptr(u), ptr(v), float(scale), ptr(out), _stream()),
+           "spx_masked_outer_f64")
+    return out

@@ -33,3 +33,20 @@ class SpMM(torch.autograd.Function):
 
 def spmm(A: CSR, X: torch.Tensor, values: torch.Tensor | None = None) -> torch.Tensor:
     return SpMM.apply(A.values if values is None else values, X, A)
+
+
+class SpGEMM(torch.autograd.Function):
+    """values of C = A B on the plan's pattern.  VJPs (Table 1, SpSpMM):
+    dL/dA = (V B^T) masked to A,  dL/dB = (A^T V) masked to B."""
+
+    @staticmethod
+    def forward(ctx, a_values, b_values, plan):
+        ctx.plan = plan
+        ctx.save_for_backward(a_values, b_values)
+        return plan.numeric(a_values, b_values)
+
+    @staticmethod
+    def backward(ctx, gc):
+        a_values, b_values = ctx.saved_tensors
+        ga, gb = ctx.plan.backward(gc, a_values, b_values, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return ga, gb, None

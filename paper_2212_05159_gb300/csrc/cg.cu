@@ -1,0 +1,435 @@
+// Batched preconditioned conjugate gradient on a block-diagonal CSR matrix (one SPD
+// system per block), the differentiable sparse solve of Section 4.3 / Table 1 (SpSolve)
+// with the direct solve replaced by PCG, and its adjoint.
+//
+// One persistent launch.  Each thread-block cluster (CL blocks on CL SMs) takes one
+// system at a time from a queue (largest first when an order is given) and runs PCG on
+// it to completion; its blocks split the system's rows.  Dot products are reduced inside
+// each block and then across the cluster through distributed shared memory (one cluster
+// barrier per reduction, partials double-buffered, summed in rank order: deterministic).
+// With few clusters active at once, the vectors of the systems in flight stay in L2.
+//
+// Precision (GB300 has ~1/60 of its FP32 rate in FP64): the iteration runs in FP32 with
+// "reliable updates" -- the solution accumulates in an FP32 partial that is folded into
+// the FP64 x whenever the recurrence residual has dropped by `delta` (and at the end);
+// at every fold the residual is recomputed in FP64 as b - A x and that true residual
+// decides convergence (||b - A x|| <= tol ||b||).  Inner products accumulate per thread
+// in double-float (an FP32 pair with exact products, ~44 significant bits) and are
+// combined in FP64.  Preconditioners: none, Jacobi (z = D^-1 r), and the factored
+// approximate inverse M = L L^T of Section 4.3 (z = L (L^T r), two sparse products).
+//
+// Status per system: SPX_OK, SPX_MAXITER, SPX_BREAKDOWN (p^T A p <= 0 or r^T z <= 0),
+// SPX_NONFINITE.  No spin waits: only cluster / block barriers.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace spx {
+namespace {
+
+constexpr int CG_THREADS = 512;
+constexpr int CG_WARPS = CG_THREADS / 32;
+
+struct CgArgs {
+    int32_t nsys;
+    const int32_t* sys_ptr;
+    const int32_t* order;
+    const int32_t* a_ptr;
+    const int32_t* a_idx;
+    const float* a_val;
+    const float* b;
+    double* x;
+    int32_t pc;
+    const float* dinv;
+    const int32_t* l_ptr;
+    const int32_t* l_idx;
+    const float* l_val;
+    const int32_t* lt_ptr;
+    const int32_t* lt_idx;
+    const float* lt_val;
+    float* r;
+    float* p;
+    float* q;
+    float* z;
+    float* w;
+    float* xp;
+    double tol;
+    double delta;
+    int32_t maxit;
+    int32_t* iters;
+    int32_t* status;
+    double* relres;
+    int32_t* queue;
+};
+
+// ---------------------------------------------------------------- double-float sums
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add_prod(DF& s, float a, float b) {
+    const float ph = a * b;
+    const float pl = fmaf(a, b, -ph);          // exact: a*b = ph + pl
+    const float t = s.hi + ph;
+    const float bp = t - s.hi;
+    const float err = (s.hi - (t - bp)) + (ph - bp);
+    s.hi = t;
+    s.lo += err + pl;
+}
+
+__device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
+
+// Sums NV values over the cluster: block tree in FP64, then the CL block partials read
+// through DSMEM in rank order.  slot alternates so one barrier per reduction suffices.
+template <int NV>
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[NV], double (*red)[4],
+                                           double (*part)[4], int& slot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < CG_WARPS; ++w) s += red[w][k];
+            part[slot][k] = s;
+        }
+    }
+    cl.sync();
+    const unsigned ncl = cl.num_blocks();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+    for (unsigned rk = 0; rk < ncl; ++rk) {
+        const double* rp = cl.map_shared_rank(&part[slot][0], rk);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += rp[k];
+    }
+    slot ^= 1;
+}
+
+__device__ __forceinline__ float spmv_row(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                          const float* __restrict__ val, const float* __restrict__ x, int i) {
+    float s = 0.f;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) s = fmaf(val[e], x[idx[e]], s);
+    return s;
+}
+
+// z = M r on rows [lo, hi) of the system (the caller barriers around LLT's two halves)
+__device__ __forceinline__ void apply_pc_local(const CgArgs& a, int lo, int hi) {
+    if (a.pc == 1) {
+        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) a.z[i] = a.dinv[i] * a.r[i];
+    } else if (a.pc == 0) {
+        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) a.z[i] = a.r[i];
+    }
+}
+
+__device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi) {
+    if (a.pc == 2) {
+        cl.sync();                                               // r complete
+        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
+            a.w[i] = spmv_row(a.lt_ptr, a.lt_idx, a.lt_val, a.r, i);   // w = L^T r
+        cl.sync();                                               // w complete
+        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
+            a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.w, i);      // z = L w
+    } else {
+        apply_pc_local(a, lo, hi);
+    }
+}
+
+// r = b - A x in FP64 on [lo, hi); returns the thread's partial of ||r||^2 in FP64.
+__device__ __forceinline__ double true_residual(const CgArgs& a, int lo, int hi) {
+    double s = 0.0;
+    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+        double t = (double)a.b[i];
+        for (int e = a.a_ptr[i]; e < a.a_ptr[i + 1]; ++e) t -= (double)a.a_val[e] * a.x[a.a_idx[e]];
+        a.r[i] = (float)t;
+        s += t * t;
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    const unsigned ncl = cl.num_blocks();
+    __shared__ double red[CG_WARPS][4];
+    __shared__ double part[2][4];
+    __shared__ int sys_sh;
+    int slot = 0;
+
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) sys_sh = atomicAdd(a.queue, 1);
+        cl.sync();
+        const int s = *cl.map_shared_rank(&sys_sh, 0);
+        cl.sync();
+        if (s >= a.nsys) break;
+        const int sid = a.order ? a.order[s] : s;
+        const int R0 = a.sys_ptr[sid], R1 = a.sys_ptr[sid + 1];
+        const int chunk = (R1 - R0 + (int)ncl - 1) / (int)ncl;
+        const int lo = min(R1, R0 + (int)rank * chunk), hi = min(R1, lo + chunk);
+
+        // ---- x = 0, r = b, z = M r, p = z
+        double v2[2] = {0.0, 0.0};
+        {
+            DF bb{0.f, 0.f};
+            for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                const float bi = a.b[i];
+                a.x[i] = 0.0;
+                a.xp[i] = 0.f;
+                a.r[i] = bi;
+                df_add_prod(bb, bi, bi);
+            }
+            v2[0] = df_value(bb);
+        }
+        apply_pc(a, cl, lo, hi);
+        {
+            DF rz{0.f, 0.f};
+            for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                const float zi = a.z[i];
+                a.p[i] = zi;
+                df_add_prod(rz, a.r[i], zi);
+            }
+            v2[1] = df_value(rz);
+        }
+        cluster_sum<2>(cl, v2, red, part, slot);
+        const double bnorm = sqrt(v2[0]);
+        double rz = v2[1];
+        double ref = bnorm;                 // residual norm at the last fold
+        double last_true = 1.0;
+        int status = SPX_MAXITER, it = 0;
+        bool dirty = false;                 // xp holds an unfolded part
+        if (bnorm == 0.0) {
+            status = SPX_OK;
+            last_true = 0.0;
+        } else if (!isfinite(rz) || !isfinite(bnorm)) {
+            status = SPX_NONFINITE;
+        } else if (!(rz > 0.0)) {
+            status = SPX_BREAKDOWN;
+        } else {
+            while (it < a.maxit) {
+                cl.sync();                                      // p complete
+                double v1[1];
+                {
+                    DF pq{0.f, 0.f};
+                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                        const float qi = spmv_row(a.a_ptr, a.a_idx, a.a_val, a.p, i);
+                        a.q[i] = qi;
+                        df_add_prod(pq, a.p[i], qi);
+                    }
+                    v1[0] = df_value(pq);
+                }
+                cluster_sum<1>(cl, v1, red, part, slot);
+                const double pq = v1[0];
+                if (!isfinite(pq)) { status = SPX_NONFINITE; break; }
+                if (!(pq > 0.0)) { status = SPX_BREAKDOWN; break; }
+                const float alpha = (float)(rz / pq);
+                for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                    a.xp[i] = fmaf(alpha, a.p[i], a.xp[i]);
+                    a.r[i] = fmaf(-alpha, a.q[i], a.r[i]);
+                }
+                dirty = true;
+                ++it;
+                apply_pc(a, cl, lo, hi);
+                {
+                    DF rzs{0.f, 0.f}, rrs{0.f, 0.f};
+                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                        const float ri = a.r[i];
+                        df_add_prod(rzs, ri, a.z[i]);
+                        df_add_prod(rrs, ri, ri);
+                    }
+                    v2[0] = df_value(rzs);
+                    v2[1] = df_value(rrs);
+                }
+                cluster_sum<2>(cl, v2, red, part, slot);
+                double rz_new = v2[0];
+                const double rnorm = sqrt(v2[1]);
+                if (!isfinite(rz_new) || !isfinite(rnorm)) { status = SPX_NONFINITE; break; }
+                if (rnorm <= a.delta * ref || rnorm <= a.tol * bnorm) {
+                    // ---- reliable update: fold xp into x (FP64), true residual in FP64
+                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                        a.x[i] += (double)a.xp[i];
+                        a.xp[i] = 0.f;
+                    }
+                    dirty = false;
+                    cl.sync();                                  // x complete
+                    double v64[1] = {true_residual(a, lo, hi)};
+                    cluster_sum<1>(cl, v64, red, part, slot);
+                    const double tn = sqrt(v64[0]);
+                    last_true = tn / bnorm;
+                    ref = tn;
+                    if (!isfinite(tn)) { status = SPX_NONFINITE; break; }
+                    if (tn <= a.tol * bnorm) { status = SPX_OK; break; }
+                    apply_pc(a, cl, lo, hi);
+                    DF rzs{0.f, 0.f};
+                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) df_add_prod(rzs, a.r[i], a.z[i]);
+                    double vz[1] = {df_value(rzs)};
+                    cluster_sum<1>(cl, vz, red, part, slot);
+                    rz_new = vz[0];
+                }
+                if (!(rz_new > 0.0)) { status = SPX_BREAKDOWN; break; }
+                const float beta = (float)(rz_new / rz);
+                rz = rz_new;
+                for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) a.p[i] = fmaf(beta, a.p[i], a.z[i]);
+            }
+        }
+        if (dirty) {
+            // fold the remainder and report the true residual of the returned x
+            for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                a.x[i] += (double)a.xp[i];
+                a.xp[i] = 0.f;
+            }
+            cl.sync();
+            double v64[1] = {true_residual(a, lo, hi)};
+            cluster_sum<1>(cl, v64, red, part, slot);
+            last_true = bnorm > 0.0 ? sqrt(v64[0]) / bnorm : 0.0;
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            a.iters[sid] = it;
+            a.status[sid] = status;
+            a.relres[sid] = last_true;
+        }
+        cl.sync();                                              // finish before the next system
+    }
+}
+
+__global__ void diag_inverse_kernel(int32_t m, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                    const float* __restrict__ val, float* __restrict__ dinv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    float d = 0.f;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e)
+        if (idx[e] == i) d = val[e];
+    dinv[i] = d != 0.f ? 1.f / d : 0.f;
+}
+
+__global__ void masked_outer_f64_kernel(int32_t m, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                        const double* __restrict__ u, const double* __restrict__ v, double scale,
+                                        float* __restrict__ out) {
+    // one warp per row
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= m) return;
+    const double ui = scale * u[row];
+    for (int e = ptr[row] + lane; e < ptr[row + 1]; e += 32) out[e] = (float)(ui * v[idx[e]]);
+}
+
+int cg_cluster_size() { return 8; }
+
+}  // namespace
+}  // namespace spx
+
+using namespace spx;
+
+extern "C" spx_status spx_cg_workspace_size(int32_t n, size_t* bytes) {
+    if (!bytes || n < 0) return set_error(SPX_INVALID_ARG, "spx_cg_workspace_size: bad arguments");
+    const size_t v = ((size_t)n * 4 + 255) & ~size_t(255);
+    *bytes = 6 * v + 256;
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys, const int32_t* order,
+                                     const float* b, double* x, int32_t pc_kind, const float* pc_diag_inv,
+                                     const spx_csr* L, const spx_csr* LT, double tol, int32_t maxit, double delta,
+                                     int32_t* iters, int32_t* status, double* relres, void* ws, size_t ws_bytes,
+                                     void* stream) {
+    SPX_TRY(check_csr(A, true, "spx_cg_batched"));
+    if (A->m != A->n) return set_error(SPX_INVALID_ARG, "spx_cg_batched: A must be square");
+    if (nsys < 0 || (nsys > 0 && (!sys_ptr || !b || !x || !iters || !status || !relres)))
+        return set_error(SPX_INVALID_ARG, "spx_cg_batched: NULL argument");
+    if (pc_kind < 0 || pc_kind > 2) return set_error(SPX_INVALID_ARG, "spx_cg_batched: unknown preconditioner");
+    if (pc_kind == 1 && !pc_diag_inv) return set_error(SPX_INVALID_ARG, "spx_cg_batched: Jacobi needs D^-1");
+    if (pc_kind == 2) {
+        SPX_TRY(check_csr(L, true, "spx_cg_batched (L)"));
+        SPX_TRY(check_csr(LT, true, "spx_cg_batched (L^T)"));
+        if (L->m != A->m || LT->m != A->m) return set_error(SPX_INVALID_ARG, "spx_cg_batched: L shape");
+    }
+    if (!(tol > 0.0) || maxit < 0 || !(delta > 0.0 && delta < 1.0))
+        return set_error(SPX_INVALID_ARG, "spx_cg_batched: tol > 0, maxit >= 0, 0 < delta < 1 required");
+    size_t need = 0;
+    spx_cg_workspace_size(A->m, &need);
+    if (!ws || ws_bytes < need) return set_error(SPX_OOM_WORKSPACE, "spx_cg_batched: workspace %zu < %zu", ws_bytes, need);
+    if (nsys == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    const size_t v = ((size_t)A->m * 4 + 255) & ~size_t(255);
+    char* w = static_cast<char*>(ws);
+    CgArgs a{};
+    a.nsys = nsys;
+    a.sys_ptr = sys_ptr;
+    a.order = order;
+    a.a_ptr = A->indptr;
+    a.a_idx = A->indices;
+    a.a_val = A->values;
+    a.b = b;
+    a.x = x;
+    a.pc = pc_kind;
+    a.dinv = pc_diag_inv;
+    if (pc_kind == 2) {
+        a.l_ptr = L->indptr; a.l_idx = L->indices; a.l_val = L->values;
+        a.lt_ptr = LT->indptr; a.lt_idx = LT->indices; a.lt_val = LT->values;
+    }
+    a.r = (float*)(w + 0 * v);
+    a.p = (float*)(w + 1 * v);
+    a.q = (float*)(w + 2 * v);
+    a.z = (float*)(w + 3 * v);
+    a.w = (float*)(w + 4 * v);
+    a.xp = (float*)(w + 5 * v);
+    a.queue = (int32_t*)(w + 6 * v);
+    a.tol = tol;
+    a.delta = delta;
+    a.maxit = maxit;
+    a.iters = iters;
+    a.status = status;
+    a.relres = relres;
+    SPX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "spx_cg_batched memset");
+
+    const int cl = cg_cluster_size();
+    int clusters = 2 * num_sms() / cl;
+    if (clusters < 1) clusters = 1;
+    if (clusters > nsys) clusters = nsys;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(clusters * cl));
+    cfg.blockDim = dim3(CG_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel, a), "spx_cg_batched launch");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream) {
+    SPX_TRY(check_csr(A, true, "spx_diag_inverse"));
+    if (A->m > 0 && !dinv) return set_error(SPX_INVALID_ARG, "spx_diag_inverse: NULL output");
+    if (A->m == 0) return SPX_OK;
+    diag_inverse_kernel<<<(unsigned)((A->m + 255) / 256), 256, 0, as_stream(stream)>>>(A->m, A->indptr, A->indices,
+                                                                                       A->values, dinv);
+    SPX_CHECK_LAUNCH("spx_diag_inverse");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_masked_outer_f64(const spx_csr* A, const double* u, const double* v, double scale, float* out,
+                                           void* stream) {
+    SPX_TRY(check_csr(A, false, "spx_masked_outer_f64"));
+    if (A->nnz > 0 && (!u || !v || !out)) return set_error(SPX_INVALID_ARG, "spx_masked_outer_f64: NULL operand");
+    if (A->m == 0) return SPX_OK;
+    const int64_t threads = (int64_t)A->m * 32;
+    masked_outer_f64_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, as_stream(stream)>>>(
+        A->m, A->indptr, A->indices, u, v, scale, out);
+    SPX_CHECK_LAUNCH("spx_masked_outer_f64");
+    return SPX_OK;
+}

@@ -1,0 +1,498 @@
+// Sparse x sparse product C = A B, all CSR (Section 3.1.2), and its reverse mode
+// (Table 1, SpSpMM rows): gA = (V B^T) masked to A, gB = (A^T V) masked to B, with V
+// given on C's pattern.
+//
+// Forward, expand / sort / compress per row (the ESC scheme the paper follows):
+//   analyse   products P_i = sum_{k in A_i} |B_k|, their prefix sums, and the list of
+//             "big" rows (P_i > WARP_CAP);
+//   symbolic  per row: expand the P_i product columns, sort, keep the unique ones; the
+//             sorted unique columns go to a products-sized scratch at offset Pptr[i] and
+//             their count to row_nnz[i]; C_indptr = scan(row_nnz).  One warp per row
+//             (shared-memory bitonic sort); a big row takes a whole block and a shared
+//             bitmap of the column space (chunked), which yields the columns already
+//             sorted.  mask(C) is structural: no numerical-zero dropping.
+//   fill      copies the unique columns into C_indices.
+//   numeric   per row, C_ij = sum over k in A_i (in A's order) of A_ik B_kj: the row's
+//             accumulator is walked k by k; within one k the columns of B_k are distinct,
+//             so lanes never collide and the order of every sum is fixed (deterministic).
+// Reverse:
+//   gA[(i,k)] = sum_{j in B_k} V[i,j] B[k,j]: one warp per row i, C_i's columns and V's
+//             values staged in shared memory, one lane per stored (i,k), binary search
+//             of each j in C_i.
+//   gB[(k,j)] = sum_{i in A^T_k} A[i,k] V[i,j]: the "SpGEMM on the columns of A" of
+//             Section 3.1.2 -- one warp per row k of B over the transposed pattern of A,
+//             lanes over B_k's entries, binary search of j in C_i, i in increasing order.
+// All integer work is exact; every floating-point sum has a fixed order.
+#include <limits.h>
+
+#include "common.cuh"
+#include "scan.cuh"
+
+namespace spx {
+namespace {
+
+constexpr int WARP_CAP = 512;          // products per row handled by one warp
+constexpr int SYM_WARPS = 8;           // warps per block, symbolic / fill
+constexpr int NUM_WARPS = 4;           // warps per block, numeric
+constexpr int BIG_THREADS = 512;
+constexpr int BITMAP_WORDS = 8192;     // 32 KB shared bitmap: 262144 columns per chunk
+
+inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct GemmLayout {
+    size_t prod, pptr, row_nnz, flags, big_pos, big_rows, scan64, scan32, total;
+};
+
+GemmLayout gemm_layout(int32_t m) {
+    GemmLayout L{};
+    size_t o = 0;
+    L.prod = o;     o = al(o + 4 * (size_t)m);
+    L.pptr = o;     o = al(o + 8 * ((size_t)m + 1));
+    L.row_nnz = o;  o = al(o + 4 * (size_t)m);
+    L.flags = o;    o = al(o + 4 * (size_t)m);
+    L.big_pos = o;  o = al(o + 4 * ((size_t)m + 1));
+    L.big_rows = o; o = al(o + 4 * ((size_t)m + 1));
+    L.scan64 = o;   o = al(o + scan_workspace_bytes<int64_t>(m));
+    L.scan32 = o;   o = al(o + scan_workspace_bytes<int32_t>(m));
+    L.total = o;
+    return L;
+}
+
+// ------------------------------------------------------------------ analyse
+__global__ void products_kernel(int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx,
+                                const int32_t* __restrict__ b_ptr, int32_t* __restrict__ prod,
+                                int32_t* __restrict__ big) {
+    // 8 lanes per row
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t row = t >> 3;
+    const int sub = threadIdx.x & 7;
+    int64_t s = 0;
+    if (row < m) {
+        for (int e = a_ptr[row] + sub; e < a_ptr[row + 1]; e += 8) {
+            const int k = a_idx[e];
+            s += b_ptr[k + 1] - b_ptr[k];
+        }
+    }
+#pragma unroll
+    for (int o = 4; o >= 1; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (row < m && sub == 0) {
+        const int32_t p = s > INT_MAX ? INT_MAX : (int32_t)s;
+        prod[row] = p;
+        big[row] = p > WARP_CAP ? 1 : 0;
+    }
+}
+
+__global__ void compact_kernel(int32_t m, const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
+                               int32_t* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m && flags[i]) out[pos[i]] = (int32_t)i;
+}
+
+// ------------------------------------------------------------------ symbolic (warp rows)
+__device__ __forceinline__ void warp_bitonic_sort(int* keys, int Q, int lane) {
+    for (int size = 2; size <= Q; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < (Q >> 1); t += 32) {
+                const int i = 2 * stride * (t / stride) + (t % stride);
+                const int j = i + stride;
+                const bool up = (i & size) == 0;
+                const int a = keys[i], b = keys[j];
+                if ((a > b) == up) {
+                    keys[i] = b;
+                    keys[j] = a;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Sorted unique product columns of row i -> tmp + pptr[i]; count -> row_nnz[i].
+__global__ void __launch_bounds__(SYM_WARPS * 32) symbolic_warp_kernel(
+    int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const int32_t* __restrict__ prod, const int64_t* __restrict__ pptr,
+    int32_t* __restrict__ tmp, int32_t* __restrict__ row_nnz) {
+    __shared__ int keys_all[SYM_WARPS][WARP_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * SYM_WARPS + warp;
+    if (row >= m) return;
+    const int P = prod[row];
+    if (P > WARP_CAP) return;                       // a big-row block takes it
+    int* keys = keys_all[warp];
+    // expand
+    int pos = 0;
+    for (int e = a_ptr[row]; e < a_ptr[row + 1]; ++e) {
+        const int k = a_idx[e];
+        const int b0 = b_ptr[k], len = b_ptr[k + 1] - b0;
+        for (int t = lane; t < len; t += 32) keys[pos + t] = b_idx[b0 + t];
+        pos += len;
+    }
+    int Q = 1;
+    while (Q < P) Q <<= 1;
+    for (int t = P + lane; t < Q; t += 32) keys[t] = INT_MAX;
+    __syncwarp();
+    warp_bitonic_sort(keys, Q, lane);
+    // compress: keep the first of each run, in order
+    int32_t* out = tmp + pptr[row];
+    int base = 0;
+    for (int t0 = 0; t0 < P; t0 += 32) {
+        const int t = t0 + lane;
+        const bool keep = t < P && (t == 0 || keys[t] != keys[t - 1]);
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) out[base + __popc(bal & lanemask_lt())] = keys[t];
+        base += __popc(bal);
+    }
+    if (lane == 0) row_nnz[row] = base;
+}
+
+// ------------------------------------------------------------------ symbolic (big rows)
+// One block per big row; the column space is visited in chunks of BITMAP_WORDS*32.
+__global__ void __launch_bounds__(BIG_THREADS) symbolic_big_kernel(
+    const int32_t* __restrict__ big_rows, const int32_t* __restrict__ n_big_dev, int32_t p,
+    const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const int64_t* __restrict__ pptr, int32_t* __restrict__ tmp,
+    int32_t* __restrict__ row_nnz) {
+    __shared__ unsigned bits[BITMAP_WORDS];
+    __shared__ int warp_sums[BIG_THREADS / 32 + 1];
+    const int n_big = *n_big_dev;
+    constexpr int WPT = BITMAP_WORDS / BIG_THREADS;           // words per thread
+    for (int q = blockIdx.x; q < n_big; q += gridDim.x) {
+        const int row = big_rows[q];
+        const int ea = a_ptr[row], eb = a_ptr[row + 1];
+        int32_t* out = tmp + pptr[row];
+        int written = 0;
+        for (int64_t c0 = 0; c0 < p; c0 += (int64_t)BITMAP_WORDS * 32) {
+            for (int w = threadIdx.x; w < BITMAP_WORDS; w += BIG_THREADS) bits[w] = 0u;
+            __syncthreads();
+            for (int e = ea + threadIdx.x; e < eb; e += BIG_THREADS) {
+                const int k = a_idx[e];
+                for (int f = b_ptr[k]; f < b_ptr[k + 1]; ++f) {
+                    const int64_t j = (int64_t)b_idx[f] - c0;
+                    if (j >= 0 && j < (int64_t)BITMAP_WORDS * 32) atomicOr(&bits[j >> 5], 1u << (j & 31));
+                }
+            }
+            __syncthreads();
+            // thread t owns words [t*WPT, (t+1)*WPT): exclusive scan of their popcounts
+            int cnt = 0;
+#pragma unroll
+            for (int u = 0; u < WPT; ++u) cnt += __popc(bits[threadIdx.x * WPT + u]);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) warp_sums[warp] = inc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int run = 0;
+                for (int w = 0; w < BIG_THREADS / 32; ++w) {
+                    int v = warp_sums[w];
+                    warp_sums[w] = run;
+                    run += v;
+                }
+                warp_sums[BIG_THREADS / 32] = run;
+            }
+            __syncthreads();
+            int wpos = written + warp_sums[warp] + inc - cnt;
+#pragma unroll
+            for (int u = 0; u < WPT; ++u) {
+                unsigned word = bits[threadIdx.x * WPT + u];
+                while (word) {
+                    const int bpos = __ffs(word) - 1;
+                    word &= word - 1;
+                    out[wpos++] = (int32_t)(c0 + (int64_t)(threadIdx.x * WPT + u) * 32 + bpos);
+                }
+            }
+            written += warp_sums[BIG_THREADS / 32];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) row_nnz[row] = written;
+    }
+}
+
+__global__ void fill_kernel(int32_t m, const int64_t* __restrict__ pptr, const int32_t* __restrict__ tmp,
+                            const int32_t* __restrict__ c_ptr, int32_t* __restrict__ c_idx) {
+    // one warp per row
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= m) return;
+    const int32_t* src = tmp + pptr[row];
+    const int a = c_ptr[row], n = c_ptr[row + 1] - a;
+    for (int t = lane; t < n; t += 32) c_idx[a + t] = src[t];
+}
+
+// ------------------------------------------------------------------ numeric
+__device__ __forceinline__ int lower_bound_i32(const int* __restrict__ a, int n, int key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(NUM_WARPS * 32) numeric_warp_kernel(
+    int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const float* __restrict__ a_val,
+    const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_idx, const float* __restrict__ b_val,
+    const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx, const int32_t* __restrict__ prod,
+    float* __restrict__ c_val) {
+    __shared__ int cols_all[NUM_WARPS][WARP_CAP];
+    __shared__ float acc_all[NUM_WARPS][WARP_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * NUM_WARPS + warp;
+    if (row >= m || prod[row] > WARP_CAP) return;
+    int* cols = cols_all[warp];
+    float* acc = acc_all[warp];
+    const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
+    for (int t = lane; t < nc; t += 32) {
+        cols[t] = c_idx[c0 + t];
+        acc[t] = 0.f;
+    }
+    __syncwarp();
+    for (int e = a_ptr[row]; e < a_ptr[row + 1]; ++e) {
+        const int k = a_idx[e];
+        const float av = a_val[e];
+        for (int f = b_ptr[k] + lane; f < b_ptr[k + 1]; f += 32) {
+            const int pos = lower_bound_i32(cols, nc, b_idx[f]);
+            acc[pos] = fmaf(av, b_val[f], acc[pos]);
+        }
+        __syncwarp();
+    }
+    for (int t = lane; t < nc; t += 32) c_val[c0 + t] = acc[t];
+}
+
+__global__ void __launch_bounds__(BIG_THREADS) numeric_big_kernel(
+    const int32_t* __restrict__ big_rows, const int32_t* __restrict__ n_big_dev, const int32_t* __restrict__ a_ptr,
+    const int32_t* __restrict__ a_idx, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const float* __restrict__ b_val, const int32_t* __restrict__ c_ptr,
+    const int32_t* __restrict__ c_idx, float* __restrict__ c_val) {
+    const int n_big = *n_big_dev;
+    for (int q = blockIdx.x; q < n_big; q += gridDim.x) {
+        const int row = big_rows[q];
+        const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
+        for (int t = threadIdx.x; t < nc; t += BIG_THREADS) c_val[c0 + t] = 0.f;
+        __syncthreads();
+        for (int e = a_ptr[row]; e < a_ptr[row + 1]; ++e) {
+            const int k = a_idx[e];
+            const float av = a_val[e];
+            for (int f = b_ptr[k] + threadIdx.x; f < b_ptr[k + 1]; f += BIG_THREADS) {
+                const int pos = c0 + lower_bound_i32(c_idx + c0, nc, b_idx[f]);
+                c_val[pos] = fmaf(av, b_val[f], c_val[pos]);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ backward
+// gA[(i,k)] = sum_{f in B_k} V[i, B_idx[f]] * B_val[f]   (V on C's pattern)
+__global__ void __launch_bounds__(NUM_WARPS * 32) grad_a_kernel(
+    int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const float* __restrict__ b_val, const int32_t* __restrict__ c_ptr,
+    const int32_t* __restrict__ c_idx, const float* __restrict__ gc, float* __restrict__ ga) {
+    __shared__ int cols_all[NUM_WARPS][WARP_CAP];
+    __shared__ float v_all[NUM_WARPS][WARP_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * NUM_WARPS + warp;
+    if (row >= m) return;
+    const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
+    const bool staged = nc <= WARP_CAP;
+    const int* cols = staged ? cols_all[warp] : c_idx + c0;
+    const float* v = staged ? v_all[warp] : gc + c0;
+    if (staged) {
+        for (int t = lane; t < nc; t += 32) {
+            cols_all[warp][t] = c_idx[c0 + t];
+            v_all[warp][t] = gc[c0 + t];
+        }
+    }
+    __syncwarp();
+    for (int e = a_ptr[row] + lane; e < a_ptr[row + 1]; e += 32) {
+        const int k = a_idx[e];
+        float s = 0.f;
+        for (int f = b_ptr[k]; f < b_ptr[k + 1]; ++f) {
+            const int j = b_idx[f];
+            const int pos = lower_bound_i32(cols, nc, j);
+            if (pos < nc && cols[pos] == j) s = fmaf(v[pos], b_val[f], s);
+        }
+        ga[e] = s;
+    }
+}
+
+// gB[(k,j)] = sum_{i in A^T_k, increasing} A[i,k] * V[i,j]
+__global__ void __launch_bounds__(256) grad_b_kernel(
+    int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
+    const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx,
+    const float* __restrict__ gc, float* __restrict__ gb) {
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= kb) return;
+    const int ia = at_ptr[k], ib = at_ptr[k + 1];
+    for (int f = b_ptr[k] + lane; f < b_ptr[k + 1]; f += 32) {
+        const int j = b_idx[f];
+        float s = 0.f;
+        for (int t = ia; t < ib; ++t) {
+            const int i = at_idx[t];
+            const float aik = a_val[a_perm[t]];
+            const int c0 = c_ptr[i], nc = c_ptr[i + 1] - c0;
+            const int pos = lower_bound_i32(c_idx + c0, nc, j);
+            if (pos < nc && c_idx[c0 + pos] == j) s = fmaf(aik, gc[c0 + pos], s);
+        }
+        gb[f] = s;
+    }
+}
+
+int big_grid() { return num_sms() * 2; }
+
+spx_status check_pair(const spx_csr* A, const spx_csr* B, bool vals, const char* who) {
+    SPX_TRY(check_csr(A, vals, who));
+    SPX_TRY(check_csr(B, vals, who));
+    if (A->n != B->m) return set_error(SPX_INVALID_ARG, "%s: inner dimensions differ (%d vs %d)", who, A->n, B->m);
+    return SPX_OK;
+}
+
+}  // namespace
+}  // namespace spx
+
+using namespace spx;
+
+extern "C" spx_status spx_spgemm_workspace_size(int32_t m, size_t* bytes) {
+    if (!bytes || m < 0) return set_error(SPX_INVALID_ARG, "spx_spgemm_workspace_size: bad arguments");
+    *bytes = gemm_layout(m).total;
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_spgemm_analyse(const spx_csr* A, const spx_csr* B, int64_t* products_host, void* ws,
+                                         size_t ws_bytes, void* stream) {
+    SPX_TRY(check_pair(A, B, false, "spx_spgemm_analyse"));
+    if (!products_host) return set_error(SPX_INVALID_ARG, "spx_spgemm_analyse: NULL output");
+    const GemmLayout L = gemm_layout(A->m);
+    if (!ws || ws_bytes < L.total)
+        return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_analyse: workspace %zu < %zu", ws_bytes, L.total);
+    cudaStream_t st = as_stream(stream);
+    char* w = static_cast<char*>(ws);
+    int32_t* prod = (int32_t*)(w + L.prod);
+    int64_t* pptr = (int64_t*)(w + L.pptr);
+    int32_t* flags = (int32_t*)(w + L.flags);
+    int32_t* bpos = (int32_t*)(w + L.big_pos);
+    int32_t* brows = (int32_t*)(w + L.big_rows);
+    if (A->m > 0) {
+        int64_t threads = (int64_t)A->m * 8;
+        products_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A->m, A->indptr, A->indices, B->indptr,
+                                                                           prod, flags);
+        SPX_CHECK_LAUNCH("spgemm products");
+    }
+    SPX_TRY((scan_counts<int32_t, int64_t>(prod, pptr, A->m, (int64_t*)(w + L.scan64), st)));
+    SPX_TRY((scan_counts<int32_t, int32_t>(flags, bpos, A->m, (int32_t*)(w + L.scan32), st)));
+    if (A->m > 0) {
+        compact_kernel<<<(unsigned)((A->m + 255) / 256), 256, 0, st>>>(A->m, flags, bpos, brows);
+        SPX_CHECK_LAUNCH("spgemm compact");
+    }
+    SPX_CUDA(cudaMemcpyAsync(products_host, pptr + A->m, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+             "spx_spgemm_analyse copy");
+    SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_analyse sync");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, int32_t* c_indptr, int64_t* nnz_c_host,
+                                          void* ws, size_t ws_bytes, void* tmp, size_t tmp_bytes, void* stream) {
+    SPX_TRY(check_pair(A, B, false, "spx_spgemm_symbolic"));
+    if (!c_indptr || !nnz_c_host) return set_error(SPX_INVALID_ARG, "spx_spgemm_symbolic: NULL output");
+    const GemmLayout L = gemm_layout(A->m);
+    if (!ws || ws_bytes < L.total)
+        return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_symbolic: workspace %zu < %zu", ws_bytes, L.total);
+    cudaStream_t st = as_stream(stream);
+    char* w = static_cast<char*>(ws);
+    const int64_t* pptr = (const int64_t*)(w + L.pptr);
+    int64_t products = 0;
+    SPX_CUDA(cudaMemcpyAsync(&products, pptr + A->m, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+             "spx_spgemm_symbolic copy");
+    SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_symbolic sync");
+    if (tmp_bytes < (size_t)products * 4 || (products > 0 && !tmp))
+        return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_symbolic: scratch %zu < %lld", tmp_bytes,
+                         (long long)products * 4);
+    int32_t* row_nnz = (int32_t*)(w + L.row_nnz);
+    if (A->m > 0) {
+        symbolic_warp_kernel<<<(unsigned)((A->m + SYM_WARPS - 1) / SYM_WARPS), SYM_WARPS * 32, 0, st>>>(
+            A->m, A->indptr, A->indices, B->indptr, B->indices, (const int32_t*)(w + L.prod), pptr, (int32_t*)tmp,
+            row_nnz);
+        SPX_CHECK_LAUNCH("spgemm symbolic");
+        symbolic_big_kernel<<<big_grid(), BIG_THREADS, 0, st>>>(
+            (const int32_t*)(w + L.big_rows), (const int32_t*)(w + L.big_pos) + A->m, B->n, A->indptr, A->indices,
+            B->indptr, B->indices, pptr, (int32_t*)tmp, row_nnz);
+        SPX_CHECK_LAUNCH("spgemm symbolic big");
+    }
+    SPX_TRY((scan_counts<int32_t, int32_t>(row_nnz, c_indptr, A->m, (int32_t*)(w + L.scan32), st)));
+    int32_t nnz = 0;
+    SPX_CUDA(cudaMemcpyAsync(&nnz, c_indptr + A->m, sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+             "spx_spgemm_symbolic copy");
+    SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_symbolic sync");
+    *nnz_c_host = nnz;
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_spgemm_fill(const spx_csr* A, const int32_t* c_indptr, int32_t* c_indices, const void* ws,
+                                      size_t ws_bytes, const void* tmp, void* stream) {
+    SPX_TRY(check_csr(A, false, "spx_spgemm_fill"));
+    const GemmLayout L = gemm_layout(A->m);
+    if (!ws || ws_bytes < L.total) return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_fill: workspace too small");
+    if (!c_indptr || !c_indices) return set_error(SPX_INVALID_ARG, "spx_spgemm_fill: NULL output");
+    if (A->m == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    const char* w = static_cast<const char*>(ws);
+    int64_t threads = (int64_t)A->m * 32;
+    fill_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A->m, (const int64_t*)(w + L.pptr),
+                                                                     (const int32_t*)tmp, c_indptr, c_indices);
+    SPX_CHECK_LAUNCH("spgemm fill");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_spgemm_numeric(const spx_csr* A, const spx_csr* B, const spx_csr* C, float* c_values,
+                                         const void* ws, size_t ws_bytes, void* stream) {
+    SPX_TRY(check_pair(A, B, true, "spx_spgemm_numeric"));
+    SPX_TRY(check_csr(C, false, "spx_spgemm_numeric"));
+    if (C->m != A->m || C->n != B->n) return set_error(SPX_INVALID_ARG, "spx_spgemm_numeric: C shape");
+    const GemmLayout L = gemm_layout(A->m);
+    if (!ws || ws_bytes < L.total) return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_numeric: workspace too small");
+    if (C->nnz > 0 && !c_values) return set_error(SPX_INVALID_ARG, "spx_spgemm_numeric: NULL output");
+    if (A->m == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    const char* w = static_cast<const char*>(ws);
+    numeric_warp_kernel<<<(unsigned)((A->m + NUM_WARPS - 1) / NUM_WARPS), NUM_WARPS * 32, 0, st>>>(
+        A->m, A->indptr, A->indices, A->values, B->indptr, B->indices, B->values, C->indptr, C->indices,
+        (const int32_t*)(w + L.prod), c_values);
+    SPX_CHECK_LAUNCH("spgemm numeric");
+    numeric_big_kernel<<<big_grid(), BIG_THREADS, 0, st>>>(
+        (const int32_t*)(w + L.big_rows), (const int32_t*)(w + L.big_pos) + A->m, A->indptr, A->indices, A->values,
+        B->indptr, B->indices, B->values, C->indptr, C->indices, c_values);
+    SPX_CHECK_LAUNCH("spgemm numeric big");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, const spx_csr* C, const float* gc,
+                                          float* ga, float* gb, const int32_t* at_indptr, const int32_t* at_indices,
+                                          const int32_t* a_perm, void* stream) {
+    SPX_TRY(check_pair(A, B, false, "spx_spgemm_backward"));
+    SPX_TRY(check_csr(C, false, "spx_spgemm_backward"));
+    if (C->m != A->m || C->n != B->n) return set_error(SPX_INVALID_ARG, "spx_spgemm_backward: C shape");
+    if (C->nnz > 0 && !gc) return set_error(SPX_INVALID_ARG, "spx_spgemm_backward: NULL V");
+    cudaStream_t st = as_stream(stream);
+    if (ga && A->m > 0) {
+        if (B->nnz > 0 && !B->values) return set_error(SPX_INVALID_ARG, "spx_spgemm_backward: B values needed");
+        grad_a_kernel<<<(unsigned)((A->m + NUM_WARPS - 1) / NUM_WARPS), NUM_WARPS * 32, 0, st>>>(
+            A->m, A->indptr, A->indices, B->indptr, B->indices, B->values, C->indptr, C->indices, gc, ga);
+        SPX_CHECK_LAUNCH("spgemm grad_a");
+    }
+    if (gb && B->m > 0) {
+        if (!at_indptr || (A->nnz > 0 && (!at_indices || !a_perm || !A->values)))
+            return set_error(SPX_INVALID_ARG, "spx_spgemm_backward: grad B needs A's transpose and values");
+        int64_t threads = (int64_t)B->m * 32;
+        grad_b_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+            B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices, C->indptr, C->indices, gc, gb);
+        SPX_CHECK_LAUNCH("spgemm grad_b");
+    }
+    return SPX_OK;
+}

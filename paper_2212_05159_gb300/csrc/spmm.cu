@@ -434,3 +434,15 @@ extern "C" spx_status spx_spmm_t(const spx_csr* AT, const int32_t* perm, const f
                               reinterpret_cast<float*>(static_cast<char*>(ws) + voff), ws_bytes - voff, st,
                               "spx_spmm_t");
 }
+
+extern "C" spx_status spx_gather_values(int64_t nnz, const int32_t* perm, const float* src, float* dst,
+                                        void* stream) {
+    if (nnz < 0 || (nnz > 0 && (!perm || !src || !dst)))
+        return set_error(SPX_INVALID_ARG, "spx_gather_values: bad arguments");
+    if (nnz == 0) return SPX_OK;
+    int64_t blocks = (nnz + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    gather_values_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, as_stream(stream)>>>(nnz, perm, src, dst);
+    SPX_CHECK_LAUNCH("spx_gather_values");
+    return SPX_OK;
+}

@@ -65,3 +65,45 @@ def spmm_t(A: CSR, G: torch.Tensor, values: torch.Tensor | None = None, out=None
     ws = _workspace(abi.spx_spmm_t_workspace_size(st, G2.shape[1], plan), G.device)
     abi.spx_spmm_t(st, perm, G2, gX2, alpha, beta, plan, ws)
     return gX2.squeeze(1) if vec else gX2
+
+
+class SpGEMMPlan:
+    """Pattern of C = A B and the per-row classes, built once per (pattern A, pattern B)."""
+
+    def __init__(self, A: CSR, B: CSR):
+        if A.n != B.m:
+            raise ValueError("inner dimensions differ")
+        self.A, self.B = A, B
+        dev = A.device
+        sA, sB = A.struct(), B.struct()
+        self.ws = abi.workspace(abi.spx_spgemm_workspace_size(A.m), dev)
+        self.products = abi.spx_spgemm_analyse(sA, sB, self.ws)
+        scratch = abi.workspace(4 * self.products, dev)
+        c_ip = torch.empty(A.m + 1, dtype=torch.int32, device=dev)
+        nnz = abi.spx_spgemm_symbolic(sA, sB, c_ip, self.ws, scratch)
+        c_ix = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        abi.spx_spgemm_fill(sA, c_ip, c_ix, self.ws, scratch)
+        del scratch
+        self.C = CSR(c_ip, c_ix[:nnz], None, (A.m, B.n))
+
+    def numeric(self, a_values=None, b_values=None, out=None) -> torch.Tensor:
+        o = out if out is not None else torch.empty(self.C.nnz, dtype=torch.float32, device=self.A.device)
+        abi.spx_spgemm_numeric(self.A.struct(a_values), self.B.struct(b_values), self.C.struct(), o, self.ws)
+        return o
+
+    def backward(self, gc: torch.Tensor, a_values=None, b_values=None, need_a=True, need_b=True):
+        dev = self.A.device
+        ga = torch.empty(self.A.nnz, dtype=torch.float32, device=dev) if need_a else None
+        gb = torch.empty(self.B.nnz, dtype=torch.float32, device=dev) if need_b else None
+        t_ip = t_ix = perm = None
+        if need_b:
+            t_ip, t_ix, perm = self.A.transpose_pattern()
+        abi.spx_spgemm_backward(self.A.struct(a_values), self.B.struct(b_values), self.C.struct(),
+                                gc.contiguous(), ga, gb, t_ip, t_ix, perm)
+        return ga, gb
+
+
+def spgemm(A: CSR, B: CSR) -> CSR:
+    """C = A B with the structural pattern (Section 3.1.2)."""
+    plan = SpGEMMPlan(A, B)
+    return plan.C.with_values(plan.numeric())

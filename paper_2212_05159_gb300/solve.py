@@ -1,0 +1,113 @@
+"""Differentiable batched sparse solve: PCG forward, PCG adjoint backward.
+
+Table 1 (SpSolve): for x = A^{-1} b the VJPs are grad_b = A^{-T} v and
+grad_A = -(A^{-T} v) x^T masked to mask(A).  The paper computes A^{-T} v with the LU
+factors of its direct solve (Section 3.1.6); here A is SPD and block-diagonal (a batch of
+independent systems), A^{-T} = A^{-1}, and both solves are the same batched PCG kernel.
+The adjoint needs only x and v: no iterate of the forward solve is stored.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import abi
+from .csr import CSR
+
+PC = {"none": 0, "jacobi": 1, "llt": 2}
+
+
+class SystemBatch:
+    """A block-diagonal batch of SPD systems on the device with its solver scratch."""
+
+    def __init__(self, A: CSR, sys_ptr):
+        self.A = A
+        ptr = np.asarray(sys_ptr, dtype=np.int32)
+        self.nsys = len(ptr) - 1
+        self.sys_ptr_host = ptr
+        self.sys_ptr = torch.from_numpy(ptr).to(A.device)
+        sizes = np.diff(ptr.astype(np.int64))
+        # largest systems first: the longest solves start first (load balance)
+        self.order = torch.from_numpy(np.argsort(-sizes, kind="stable").astype(np.int32)).to(A.device)
+        self.ws = abi.workspace(abi.spx_cg_workspace_size(A.m), A.device)
+        self._dinv = None
+        self.iters = torch.zeros(self.nsys, dtype=torch.int32, device=A.device)
+        self.status = torch.zeros(self.nsys, dtype=torch.int32, device=A.device)
+        self.relres = torch.zeros(self.nsys, dtype=torch.float64, device=A.device)
+
+    def dinv(self, values=None):
+        if values is not None:
+            d = torch.empty(self.A.m, dtype=torch.float32, device=self.A.device)
+            return abi.spx_diag_inverse(self.A.struct(values), d)
+        if self._dinv is None:
+            self._dinv = torch.empty(self.A.m, dtype=torch.float32, device=self.A.device)
+            abi.spx_diag_inverse(self.A.struct(), self._dinv)
+        return self._dinv
+
+
+class Factor:
+    """M = L L^T with L lower-triangular on a fixed pattern (Section 4.3)."""
+
+    def __init__(self, L: CSR):
+        self.L = L
+        t_ip, t_ix, perm = L.transpose_pattern()
+        self.perm = perm
+        self.lt_vals = torch.empty(L.nnz, dtype=torch.float32, device=L.device)
+        self._t_ip, self._t_ix = t_ip, t_ix
+        self.refresh()
+
+    def refresh(self, values: torch.Tensor | None = None):
+        if values is not None:
+            self.L = self.L.with_values(values)
+        abi.spx_gather_values(self.perm, self.L.values, self.lt_vals)
+        return self
+
+    def structs(self):
+        lt = abi.csr_struct(self.L.n, self.L.m, self._t_ip, self._t_ix, self.lt_vals)
+        return self.L.struct(), lt
+
+
+def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor | None = None,
+       tol: float = 1e-8, maxit: int | None = None, delta: float = 0.1, values: torch.Tensor | None = None,
+       x: torch.Tensor | None = None):
+    """Solve every system of the batch; returns (x float64, iters, status, relres) tensors."""
+    A = batch.A
+    if maxit is None:
+        maxit = int(10 * np.diff(batch.sys_ptr_host).max(initial=1))
+    x = x if x is not None else torch.empty(A.m, dtype=torch.float64, device=A.device)
+    kind = PC[pc]
+    dinv = batch.dinv(values) if kind == 1 else None
+    L = LT = None
+    if kind == 2:
+        if factor is None:
+            raise ValueError("pc='llt' needs a Factor")
+        L, LT = factor.structs()
+    abi.spx_cg_batched(A.struct(values), batch.sys_ptr, batch.nsys, batch.order, b.contiguous(), x, kind,
+                       dinv, L, LT, tol, maxit, delta, batch.iters, batch.status, batch.relres, batch.ws)
+    return x, batch.iters, batch.status, batch.relres
+
+
+class Solve(torch.autograd.Function):
+    """x = A^{-1} b for a batch of SPD systems (float32 values and b, float64 x).
+    Backward (Table 1, SpSolve): lam = A^{-T} v by the same PCG, grad_b = lam,
+    grad_A = -(lam x^T) masked to mask(A)."""
+
+    @staticmethod
+    def forward(ctx, values, b, batch, pc="jacobi", tol=1e-8, maxit=None):
+        x, _, status, _ = cg(batch, b, pc=pc, tol=tol, maxit=maxit, values=values)
+        ctx.batch, ctx.pc, ctx.tol, ctx.maxit = batch, pc, tol, maxit
+        ctx.save_for_backward(values, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, v):
+        values, x = ctx.saved_tensors
+        batch = ctx.batch
+        lam, _, _, _ = cg(batch, v.to(torch.float32).contiguous(), pc=ctx.pc, tol=ctx.tol, maxit=ctx.maxit,
+                          values=values)
+        g_vals = None
+        if ctx.needs_input_grad[0]:
+            g_vals = torch.empty(batch.A.nnz, dtype=torch.float32, device=values.device)
+            abi.spx_masked_outer_f64(batch.A.struct(values), lam, x, g_vals, -1.0)
+        g_b = lam.to(torch.float32) if ctx.needs_input_grad[1] else None
+        return g_vals, g_b, None, None, None, None

@@ -1,0 +1,150 @@
+"""GPU parity of the batched PCG solve and its adjoint against the FP64 oracle
+(Section 4.3 PCG, Table 1 SpSolve VJPs), through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import assert_close_normalised
+
+pytestmark = pytest.mark.gpu
+spx = pytest.importorskip("paper_2212_05159_gb300")
+from paper_2212_05159_gb300 import solve  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def _block(A, ptr, s):
+    a, c = int(ptr[s]), int(ptr[s + 1])
+    e0, e1 = int(A.indptr[a]), int(A.indptr[c])
+    return synth.CSR(c - a, c - a, A.indptr[a:c + 1] - e0, A.indices[e0:e1] - a, A.values[e0:e1]), a, c
+
+
+def _true_relres(A, x, b):
+    r = np.asarray(b, np.float64) - oracle.spmm(A, x)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    A, ptr, sides, _ = synth.diffusion_batch(12, seed=3, side_lo=4, side_hi=40, sigma=1.0)
+    return A, ptr, solve.SystemBatch(spx.CSR.from_host(A), ptr)
+
+
+@pytest.mark.parametrize("pc", ["none", "jacobi"])
+def test_cg_matches_oracle(small_batch, pc):
+    A, ptr, batch = small_batch
+    b = synth.normal(A.m, seed=7)
+    x, iters, status, relres = solve.cg(batch, dev(b), pc=pc, tol=1e-8)
+    x = host(x)
+    assert np.all(host(status) == 0)
+    for s in range(batch.nsys):
+        As, a, c = _block(A, ptr, s)
+        rr = _true_relres(As, x[a:c], b[a:c])
+        assert rr <= 1e-8, (s, rr)
+        assert abs(rr - host(relres)[s]) <= 1e-9 + 1e-3 * rr
+        xo, st, it = oracle.pcg(As, b[a:c], tol=1e-12, pc=pc)
+        # x agrees with the FP64 solution to the conditioning of the system
+        assert np.linalg.norm(x[a:c] - xo) <= 1e-5 * np.linalg.norm(xo)
+        # the FP32 iteration with reliable updates needs about as many steps as FP64 PCG
+        _, _, it8 = oracle.pcg(As, b[a:c], tol=1e-8, pc=pc)
+        assert host(iters)[s] <= 1.5 * it8 + 5
+
+
+def test_llt_factor_matches_oracle(small_batch):
+    A, ptr, batch = small_batch
+    l_ip, l_ix, _ = oracle.tril_pattern(A)
+    d = oracle.diagonal(A)
+    rows = np.repeat(np.arange(A.m), np.diff(l_ip))
+    rng = np.random.default_rng(1)
+    lv = rng.uniform(-0.1, 0.1, l_ix.size) / np.sqrt(d[rows])
+    on = rows == l_ix
+    lv[on] = 1.0 / np.sqrt(d[rows[on]])
+    Lh = synth.CSR(A.m, A.m, l_ip, l_ix, lv.astype(np.float32))
+    fac = solve.Factor(spx.CSR.from_host(Lh))
+    b = synth.normal(A.m, seed=5)
+    x, iters, status, relres = solve.cg(batch, dev(b), pc="llt", factor=fac, tol=1e-8)
+    x = host(x)
+    assert np.all(host(status) == 0)
+    for s in range(batch.nsys):
+        As, a, c = _block(A, ptr, s)
+        assert _true_relres(As, x[a:c], b[a:c]) <= 1e-8
+        Ls, _, _ = _block(Lh, ptr, s)
+        _, _, it8 = oracle.pcg(As, b[a:c], tol=1e-8, pc="llt", L=(Ls.indptr, Ls.indices, Ls.values))
+        assert host(iters)[s] <= 1.5 * it8 + 5
+
+
+def test_status_codes():
+    A = synth.poisson2d(12)
+    ptr = np.array([0, A.m], np.int32)
+    batch = solve.SystemBatch(spx.CSR.from_host(A), ptr)
+    b = synth.normal(A.m, seed=1)
+    _, it, st, _ = solve.cg(batch, dev(b), pc="jacobi", tol=1e-12, maxit=3)
+    assert host(st)[0] == 5 and host(it)[0] == 3                       # SPX_MAXITER
+    bad = b.copy()
+    bad[3] = np.nan
+    _, _, st, _ = solve.cg(batch, dev(bad), pc="jacobi")
+    assert host(st)[0] == 7                                           # SPX_NONFINITE
+    n = A.m
+    Lz = synth.CSR(n, n, np.arange(n + 1), np.arange(n), np.where(np.arange(n) % 2 == 0, 0.0, 1.0))
+    fac = solve.Factor(spx.CSR.from_host(Lz))
+    e = np.zeros(n, np.float32)
+    e[0] = 1.0
+    _, _, st, _ = solve.cg(batch, dev(e), pc="llt", factor=fac)
+    assert host(st)[0] == 6                                           # SPX_BREAKDOWN
+    x, it, st, rr = solve.cg(batch, dev(np.zeros(n, np.float32)), pc="jacobi")
+    assert host(st)[0] == 0 and host(it)[0] == 0 and np.all(host(x) == 0)
+
+
+def test_eigenvector_one_iteration():
+    N = 15
+    A = synth.poisson2d(N)
+    ix, iy = np.meshgrid(np.arange(1, N + 1), np.arange(1, N + 1), indexing="ij")
+    v = (np.sin(ix * 2 * np.pi / (N + 1)) * np.sin(iy * 3 * np.pi / (N + 1))).ravel().astype(np.float32)
+    batch = solve.SystemBatch(spx.CSR.from_host(A), np.array([0, A.m], np.int32))
+    x, it, st, rr = solve.cg(batch, dev(v), pc="none", tol=1e-6)
+    assert host(st)[0] == 0 and host(it)[0] <= 2
+
+
+def test_adjoint_matches_oracle(small_batch):
+    A, ptr, batch = small_batch
+    b = synth.normal(A.m, seed=2)
+    g = synth.normal(A.m, seed=3)
+    vals = dev(A.values).requires_grad_(True)
+    bt = dev(b).requires_grad_(True)
+    x = solve.Solve.apply(vals, bt, batch, "jacobi", 1e-10)
+    x.backward(dev(g.astype(np.float64)))
+    gA = host(vals.grad)
+    gb = host(bt.grad)
+    xh = host(x)
+    for s in range(batch.nsys):
+        As, a, c = _block(A, ptr, s)
+        e0, e1 = int(A.indptr[a]), int(A.indptr[c])
+        lam, ga = oracle.solve_adjoint(As, xh[a:c], g[a:c])
+        np.testing.assert_allclose(gb[a:c], lam, rtol=0, atol=1e-6 * np.abs(lam).max())
+        norm = oracle.sddmm(As, np.abs(lam).reshape(-1, 1), np.abs(xh[a:c]).reshape(-1, 1))
+        # lam carries the solve's own error (tol 1e-10 times the conditioning)
+        assert_close_normalised(gA[e0:e1], ga, norm, rel=1e-5, what=f"grad A system {s}")
+
+
+def test_full_size_batch_256():
+    """The 256-system workload (sides 32..256) with Jacobi, checked on sampled systems."""
+    A, ptr, sides, _ = synth.diffusion_batch(256, seed=0, side_lo=32, side_hi=256, sigma=1.0)
+    batch = solve.SystemBatch(spx.CSR.from_host(A), ptr)
+    b = synth.normal(A.m, seed=1)
+    x, iters, status, relres = solve.cg(batch, dev(b), pc="jacobi", tol=1e-8)
+    torch.cuda.synchronize()
+    assert np.all(host(status) == 0)
+    assert np.all(host(relres) <= 1e-8)
+    xh = host(x)
+    order = np.argsort(np.diff(ptr))
+    for s in list(order[:2]) + list(order[-2:]):
+        As, a, c = _block(A, ptr, s)
+        assert _true_relres(As, xh[a:c], b[a:c]) <= 1e-8
