@@ -251,7 +251,9 @@ spx_status spx_cg_workspace_size(int32_t n, size_t* bytes);
  * pc_kind: 0 none, 1 Jacobi (pc_diag_inv = device float32[n] holding 1 / a_ii),
  *          2 M = L L^T (Section 4.3): L lower-triangular CSR with values on the
  *          diagonal blocks and LT its transpose with values (spx_csr_transpose +
- *          spx_gather_values).
+ *          spx_gather_values), applied as two sparse products,
+ *          3 an explicit SPD sparse M passed as L (LT unused), applied as one
+ *          sparse product -- e.g. L L^T formed once with the SpGEMM calls.
  * iters, status (spx_status per system: OK, MAXITER, BREAKDOWN, NONFINITE): device
  * int32[nsys]; relres: device float64[nsys], the true relative residual of the
  * returned x.  One launch of thread-block clusters (8 blocks per system); capturable
@@ -271,6 +273,102 @@ spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream);
  * u = lambda = A^{-T} g and v = x. */
 spx_status spx_masked_outer_f64(const spx_csr* A, const double* u, const double* v,
                                 double scale, float* out, void* stream);
+
+/* ----------------------- learned preconditioner (Section 4.3) and its network */
+
+/* Workspace bytes of spx_pcg_train for an n-row batch and n_it iterations
+ * (5 (n_it + 1) + 6 float vectors: the stored iterates and the adjoint vectors). */
+spx_status spx_pcg_train_workspace_size(int32_t n, int32_t n_it, size_t* bytes);
+
+/* Loss of n_it unrolled PCG iterations with M = L L^T from x0 = 0 (Section 4.3):
+ *   loss_s = sum_{i=1..n_it} weights[i-1] ||r_i|| / ||b_s||   for every system s,
+ * and grad_L = d(mean_s loss_s) / d L.values on L's pattern (reverse mode through the
+ * iterations; A itself is not differentiated and is assumed symmetric).
+ * A, sys_ptr: the block-diagonal batch as in spx_cg_batched; L: lower-triangular CSR
+ * with values on the diagonal blocks; LT: its transpose with values.  weights: device
+ * float32[n_it] (e.g. gamma^(n_it-i) normalised); b: device float32[n].
+ * loss: device float32[nsys]; grad_L: device float32[nnz(L)] (overwritten).
+ * 1 <= n_it <= 64.  One thread block per system; deterministic. */
+spx_status spx_pcg_train(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
+                         const spx_csr* L, const spx_csr* LT, const float* b, int32_t n_it,
+                         const float* weights, float* loss, float* grad_L, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/* Scale-free inputs of the network: d[i] = a_ii^(-1/2), e_vals[k] = d_i a_ij d_j on A's
+ * pattern, feats[i, 0..3] = [1, sum_{j != i} e_ij, min_{j != i} e_ij, max_{j != i} e_ij]
+ * (the last three 0 for a row without off-diagonal entries).  Device float32. */
+spx_status spx_mpnn_features(const spx_csr* A, float* d, float* e_vals, float* feats,
+                             void* stream);
+
+/* Dense layer Y = [X1 X2] W + b on n rows (X1: n x K1, X2: n x K2 or NULL with K2 = 0,
+ * W: (K1+K2) x N row-major BF16, b: float32[N] or NULL; K1 + K2 <= 128, N <= 128).
+ * mode 0: Y = pre-activation; 1: Y = relu(pre); 2: U = pre and Y = Hin + relu(pre)
+ * (residual layer; Hin, Y, U: n x N).  FP32 accumulation.  Device pointers. */
+spx_status spx_dense_forward(int64_t n, const float* X1, int32_t K1, const float* X2, int32_t K2,
+                             const void* W_bf16, const float* bias, int32_t N, int32_t mode,
+                             const float* Hin, float* Y, float* U, void* stream);
+
+/* Data gradient [dX1 dX2] = G W^T (or += with accumulate != 0); dX2 may be NULL. */
+spx_status spx_dense_backward_data(int64_t n, const float* G, int32_t N, const void* W_bf16,
+                                   int32_t K1, int32_t K2, float* dX1, float* dX2,
+                                   int32_t accumulate, void* stream);
+
+/* Workspace bytes of spx_dense_backward_weight ((K + 1) * N <= 8448). */
+spx_status spx_dense_backward_weight_workspace_size(int64_t n, int32_t K, int32_t N,
+                                                    size_t* bytes);
+
+/* Weight gradient dW = [X1 X2]^T G (K x N, float32) and db = column sums of G (or NULL);
+ * per-block partial sums added in a fixed order (deterministic). */
+spx_status spx_dense_backward_weight(int64_t n, const float* X1, int32_t K1, const float* X2,
+                                     int32_t K2, const float* G, int32_t N, float* dW,
+                                     float* db, void* workspace, size_t workspace_bytes,
+                                     void* stream);
+
+/* gu[t] = gh[t] if u[t] > 0 else 0 (the derivative of relu at the pre-activation u). */
+spx_status spx_relu_backward(int64_t count, const float* gh, const float* u, float* gu,
+                             void* stream);
+
+/* Workspace bytes of spx_tril_pattern. */
+spx_status spx_tril_workspace_size(int32_t n, size_t* bytes);
+
+/* The pattern of tril(A) (entries with j <= i): l_indptr (device int32[m+1]) and its
+ * nnz to *nnz_host (synchronizes); when l_indices and l_src are non-NULL (device
+ * int32[nnz]) also the columns and, for each entry, its position in A. */
+spx_status spx_tril_pattern(const spx_csr* A, int32_t* l_indptr, int32_t* l_indices,
+                            int32_t* l_src, int64_t* nnz_host, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/* Edge head on tril(A) (hidden width 64): for each stored (i, j) of Lpat,
+ *   o = relu(P_i + Q_j + e_ij u + c) . v + (bd if i == j else bo),
+ *   L = d_i * (softplus(o) if i == j else o).
+ * e_low: e values on Lpat; P, Q: n x 64; u, c, v: float32[64]; bd, bo: float32[1]. */
+spx_status spx_edge_forward(const spx_csr* Lpat, const float* e_low, const float* d,
+                            const float* P, const float* Q, const float* u, const float* c,
+                            const float* v, const float* bd, const float* bo, float* L_values,
+                            void* stream);
+
+/* Workspace bytes of spx_edge_backward. */
+spx_status spx_edge_backward_workspace_size(int32_t n, size_t* bytes);
+
+/* Reverse of spx_edge_forward for the upstream gradient gL (on Lpat): gP, gQ (n x 64,
+ * overwritten) and gparams = [gv (64), gc (64), gu (64), gbd, gbo] (float32[194]).
+ * lt_*: the transpose of Lpat (spx_csr_transpose).  Deterministic. */
+spx_status spx_edge_backward(const spx_csr* Lpat, const int32_t* lt_indptr,
+                             const int32_t* lt_indices, const int32_t* lt_perm,
+                             const float* e_low, const float* d, const float* P, const float* Q,
+                             const float* u, const float* c, const float* v, const float* bd,
+                             const float* bo, const float* gL, float* gP, float* gQ,
+                             float* gparams, void* workspace, size_t workspace_bytes,
+                             void* stream);
+
+/* One Adam step on `count` float32 parameters (step >= 1 is the step number); when
+ * params_bf16 is non-NULL the updated values are also written there as BF16. */
+spx_status spx_adam_step(int64_t count, float* params, const float* grads, float* m, float* v,
+                         int32_t step, float lr, float beta1, float beta2, float eps,
+                         void* params_bf16, void* stream);
+
+/* dst[t] = (bf16) src[t]. */
+spx_status spx_to_bf16(int64_t count, const float* src, void* dst, void* stream);
 
 #ifdef __cplusplus
 }

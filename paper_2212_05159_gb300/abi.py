@@ -82,6 +82,22 @@ SIGNATURES = {
                        _SZ, _P],
     "spx_diag_inverse": [_CSRP, _P, _P],
     "spx_masked_outer_f64": [_CSRP, _P, _P, _D, _P, _P],
+    "spx_pcg_train_workspace_size": [_I32, _I32, ctypes.POINTER(_SZ)],
+    "spx_pcg_train": [_CSRP, _P, _I32, _CSRP, _CSRP, _P, _I32, _P, _P, _P, _P, _SZ, _P],
+    "spx_mpnn_features": [_CSRP, _P, _P, _P, _P],
+    "spx_dense_forward": [_I64, _P, _I32, _P, _I32, _P, _P, _I32, _I32, _P, _P, _P, _P],
+    "spx_dense_backward_data": [_I64, _P, _I32, _P, _I32, _I32, _P, _P, _I32, _P],
+    "spx_dense_backward_weight_workspace_size": [_I64, _I32, _I32, ctypes.POINTER(_SZ)],
+    "spx_dense_backward_weight": [_I64, _P, _I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P],
+    "spx_relu_backward": [_I64, _P, _P, _P, _P],
+    "spx_tril_workspace_size": [_I32, ctypes.POINTER(_SZ)],
+    "spx_tril_pattern": [_CSRP, _P, _P, _P, ctypes.POINTER(_I64), _P, _SZ, _P],
+    "spx_edge_forward": [_CSRP, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "spx_edge_backward_workspace_size": [_I32, ctypes.POINTER(_SZ)],
+    "spx_edge_backward": [_CSRP, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                          _SZ, _P],
+    "spx_adam_step": [_I64, _P, _P, _P, _P, _I32, _F, _F, _F, _F, _P, _P],
+    "spx_to_bf16": [_I64, _P, _P, _P],
 }
 
 
@@ -313,3 +329,76 @@ def spx_masked_outer_f64(A: spx_csr, u, v, out, scale=1.0):
     _check(lib().spx_masked_outer_f64(ctypes.byref(A), ptr(u), ptr(v), float(scale), ptr(out), _stream()),
            "spx_masked_outer_f64")
     return out
+
+
+# ------------------------------------------------------------------ learned preconditioner
+def _size(fn, *args):
+    sz = _SZ(0)
+    _check(getattr(lib(), fn)(*args, ctypes.byref(sz)), fn)
+    return sz.value
+
+
+def spx_pcg_train(A: spx_csr, sys_ptr, nsys, L: spx_csr, LT: spx_csr, b, n_it, weights, loss, grad_L, ws):
+    _check(lib().spx_pcg_train(ctypes.byref(A), ptr(sys_ptr), int(nsys), ctypes.byref(L), ctypes.byref(LT),
+                               ptr(b), int(n_it), ptr(weights), ptr(loss), ptr(grad_L), ptr(ws), ws.numel(),
+                               _stream()), "spx_pcg_train")
+
+
+def spx_mpnn_features(A: spx_csr, d, e_vals, feats):
+    _check(lib().spx_mpnn_features(ctypes.byref(A), ptr(d), ptr(e_vals), ptr(feats), _stream()),
+           "spx_mpnn_features")
+
+
+def spx_dense_forward(n, X1, K1, X2, K2, W16, bias, N, mode, Hin, Y, U=None):
+    _check(lib().spx_dense_forward(int(n), ptr(X1), int(K1), ptr(X2), int(K2), ptr(W16), ptr(bias), int(N),
+                                   int(mode), ptr(Hin), ptr(Y), ptr(U), _stream()), "spx_dense_forward")
+
+
+def spx_dense_backward_data(n, G, N, W16, K1, K2, dX1, dX2, accumulate):
+    _check(lib().spx_dense_backward_data(int(n), ptr(G), int(N), ptr(W16), int(K1), int(K2), ptr(dX1), ptr(dX2),
+                                         int(accumulate), _stream()), "spx_dense_backward_data")
+
+
+def spx_dense_backward_weight(n, X1, K1, X2, K2, G, N, dW, db, ws):
+    _check(lib().spx_dense_backward_weight(int(n), ptr(X1), int(K1), ptr(X2), int(K2), ptr(G), int(N), ptr(dW),
+                                           ptr(db), ptr(ws), ws.numel(), _stream()), "spx_dense_backward_weight")
+
+
+def spx_relu_backward(gh, u, gu):
+    _check(lib().spx_relu_backward(int(gh.numel()), ptr(gh), ptr(u), ptr(gu), _stream()), "spx_relu_backward")
+
+
+def spx_tril_pattern(A: spx_csr, device):
+    """Returns (l_indptr, l_indices, l_src) int32 tensors of tril(A)."""
+    ws = workspace(_size("spx_tril_workspace_size", int(A.m)), device)
+    ip = torch.empty(A.m + 1, dtype=torch.int32, device=device)
+    nnz = _I64(0)
+    _check(lib().spx_tril_pattern(ctypes.byref(A), ptr(ip), None, None, ctypes.byref(nnz), ptr(ws), ws.numel(),
+                                  _stream()), "spx_tril_pattern")
+    ix = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=device)
+    src = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=device)
+    _check(lib().spx_tril_pattern(ctypes.byref(A), ptr(ip), ptr(ix), ptr(src), ctypes.byref(nnz), ptr(ws),
+                                  ws.numel(), _stream()), "spx_tril_pattern")
+    return ip, ix[: nnz.value], src[: nnz.value]
+
+
+def spx_edge_forward(Lpat: spx_csr, e_low, d, P, Q, u, c, v, bd, bo, L_values):
+    _check(lib().spx_edge_forward(ctypes.byref(Lpat), ptr(e_low), ptr(d), ptr(P), ptr(Q), ptr(u), ptr(c), ptr(v),
+                                  ptr(bd), ptr(bo), ptr(L_values), _stream()), "spx_edge_forward")
+
+
+def spx_edge_backward(Lpat: spx_csr, lt_ip, lt_ix, lt_perm, e_low, d, P, Q, u, c, v, bd, bo, gL, gP, gQ,
+                      gparams, ws):
+    _check(lib().spx_edge_backward(ctypes.byref(Lpat), ptr(lt_ip), ptr(lt_ix), ptr(lt_perm), ptr(e_low), ptr(d),
+                                   ptr(P), ptr(Q), ptr(u), ptr(c), ptr(v), ptr(bd), ptr(bo), ptr(gL), ptr(gP),
+                                   ptr(gQ), ptr(gparams), ptr(ws), ws.numel(), _stream()), "spx_edge_backward")
+
+
+def spx_adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, params_bf16=None):
+    _check(lib().spx_adam_step(int(params.numel()), ptr(params), ptr(grads), ptr(m), ptr(v), int(step),
+                               float(lr), float(beta1), float(beta2), float(eps), ptr(params_bf16), _stream()),
+           "spx_adam_step")
+
+
+def spx_to_bf16(src, dst):
+    _check(lib().spx_to_bf16(int(src.numel()), ptr(src), ptr(dst), _stream()), "spx_to_bf16")

@@ -15,8 +15,9 @@
 // at every fold the residual is recomputed in FP64 as b - A x and that true residual
 // decides convergence (||b - A x|| <= tol ||b||).  Inner products accumulate per thread
 // in double-float (an FP32 pair with exact products, ~44 significant bits) and are
-// combined in FP64.  Preconditioners: none, Jacobi (z = D^-1 r), and the factored
-// approximate inverse M = L L^T of Section 4.3 (z = L (L^T r), two sparse products).
+// combined in FP64.  Preconditioners: none, Jacobi (z = D^-1 r), the factored
+// approximate inverse M = L L^T of Section 4.3 (z = L (L^T r), two sparse products), and
+// an explicit sparse M (z = M r, one product; e.g. L L^T formed once by SpGEMM).
 //
 // Status per system: SPX_OK, SPX_MAXITER, SPX_BREAKDOWN (p^T A p <= 0 or r^T z <= 0),
 // SPX_NONFINITE.  No spin waits: only cluster / block barriers.
@@ -134,7 +135,11 @@ __device__ __forceinline__ void apply_pc_local(const CgArgs& a, int lo, int hi) 
 }
 
 __device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi) {
-    if (a.pc == 2) {
+    if (a.pc == 3) {
+        cl.sync();                                               // r complete
+        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
+            a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.r, i);      // z = M r
+    } else if (a.pc == 2) {
         cl.sync();                                               // r complete
         for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
             a.w[i] = spmv_row(a.lt_ptr, a.lt_idx, a.lt_val, a.r, i);   // w = L^T r
@@ -346,8 +351,12 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     if (A->m != A->n) return set_error(SPX_INVALID_ARG, "spx_cg_batched: A must be square");
     if (nsys < 0 || (nsys > 0 && (!sys_ptr || !b || !x || !iters || !status || !relres)))
         return set_error(SPX_INVALID_ARG, "spx_cg_batched: NULL argument");
-    if (pc_kind < 0 || pc_kind > 2) return set_error(SPX_INVALID_ARG, "spx_cg_batched: unknown preconditioner");
+    if (pc_kind < 0 || pc_kind > 3) return set_error(SPX_INVALID_ARG, "spx_cg_batched: unknown preconditioner");
     if (pc_kind == 1 && !pc_diag_inv) return set_error(SPX_INVALID_ARG, "spx_cg_batched: Jacobi needs D^-1");
+    if (pc_kind == 3) {
+        SPX_TRY(check_csr(L, true, "spx_cg_batched (M)"));
+        if (L->m != A->m) return set_error(SPX_INVALID_ARG, "spx_cg_batched: M shape");
+    }
     if (pc_kind == 2) {
         SPX_TRY(check_csr(L, true, "spx_cg_batched (L)"));
         SPX_TRY(check_csr(LT, true, "spx_cg_batched (L^T)"));
@@ -373,6 +382,9 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     a.x = x;
     a.pc = pc_kind;
     a.dinv = pc_diag_inv;
+    if (pc_kind == 3) {
+        a.l_ptr = L->indptr; a.l_idx = L->indices; a.l_val = L->values;
+    }
     if (pc_kind == 2) {
         a.l_ptr = L->indptr; a.l_idx = L->indices; a.l_val = L->values;
         a.lt_ptr = LT->indptr; a.lt_idx = LT->indices; a.lt_val = LT->values;

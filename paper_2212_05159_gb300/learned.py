@@ -1,0 +1,251 @@
+"""Learned preconditioner: a message-passing network emits L on tril(A); M = L L^T.
+
+Section 4.3 learns a lower-triangular L with M = L L^T by minimising the weighted
+residual history of N_it PCG iterations.  Here L's values come from a small
+message-passing network applied to each system, so one set of weights serves every
+system of a family; it is trained by back-propagating that loss through the library's
+own kernels (spx_pcg_train for the unrolled PCG, then the network's reverse pass).
+
+Network (hidden width 64, 3 message-passing layers, BF16 weights, FP32 accumulation):
+  d_i = a_ii^-1/2, e_ij = d_i a_ij d_j,  f_i = [1, sum_{j!=i} e_ij, min, max]
+  h = relu(f W0 + b0);  3 x { g = E h;  h = h + relu([h g] Wl + bl) }
+  P = h Ua,  Q = h Ub;  for (i, j) in tril(A):
+  o = relu(P_i + Q_j + e_ij u + c) . v + (bd | bo),  L_ij = d_i (softplus(o) | o)
+At initialisation v = 0, bo = 0, softplus(bd) = 1, so L = D^-1/2 and M = D^-1 (Jacobi).
+Every arithmetic step runs in a CUDA kernel of the library; this module allocates
+buffers and sequences the calls.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import abi
+from .csr import CSR
+from .ops import SpGEMMPlan
+
+H = 64
+F_IN = 4
+LAYERS = 3
+BD_INIT = math.log(math.e - 1.0)
+
+# name, shape, stored as BF16 for the dense kernels
+PARAMS = [("W0", (F_IN, H), True), ("b0", (H,), False)]
+for _l in range(1, LAYERS + 1):
+    PARAMS += [(f"W{_l}", (2 * H, H), True), (f"b{_l}", (H,), False)]
+PARAMS += [("Ua", (H, H), True), ("Ub", (H, H), True), ("u", (H,), False), ("c", (H,), False),
+           ("v", (H,), False), ("bd", (1,), False), ("bo", (1,), False)]
+
+
+def loss_weights(n_it: int, gamma: float) -> np.ndarray:
+    w = gamma ** (n_it - np.arange(1, n_it + 1, dtype=np.float64))
+    return (w / w.sum()).astype(np.float32)
+
+
+def default_init(seed: int) -> dict:
+    """Glorot-uniform matrices, zero biases, random u, v = 0, softplus(bd) = 1."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for name, shp, _ in PARAMS:
+        if len(shp) == 2:
+            lim = math.sqrt(6.0 / (shp[0] + shp[1]))
+            p[name] = rng.uniform(-lim, lim, shp).astype(np.float32)
+        else:
+            p[name] = np.zeros(shp, np.float32)
+    p["u"] = rng.uniform(-1, 1, (H,)).astype(np.float32)
+    p["bd"] = np.array([BD_INIT], np.float32)
+    return p
+
+
+class Graph:
+    """Per-batch inputs of the network: features, e on A and on tril(A), tril patterns."""
+
+    def __init__(self, A: CSR):
+        dev = A.device
+        self.A = A
+        n = A.m
+        self.n = n
+        self.d = torch.empty(n, dtype=torch.float32, device=dev)
+        self.e = torch.empty(max(A.nnz, 1), dtype=torch.float32, device=dev)[: A.nnz]
+        self.f = torch.empty(n, F_IN, dtype=torch.float32, device=dev)
+        abi.spx_mpnn_features(A.struct(), self.d, self.e, self.f)
+        self.E = A.with_values(self.e)
+        l_ip, l_ix, l_src = abi.spx_tril_pattern(A.struct(), dev)
+        self.Lpat = CSR(l_ip, l_ix, None, (n, n))
+        self.e_low = torch.empty(l_ix.numel(), dtype=torch.float32, device=dev)
+        abi.spx_gather_values(l_src, self.e, self.e_low)
+        self.lt_ip, self.lt_ix, self.lt_perm = self.Lpat.transpose_pattern()
+
+    def LT_struct(self, L_values: torch.Tensor, out: torch.Tensor):
+        """A^T-pattern view of L with its values gathered into `out`."""
+        abi.spx_gather_values(self.lt_perm, L_values, out)
+        return abi.csr_struct(self.n, self.n, self.lt_ip, self.lt_ix, out)
+
+
+class MPNN:
+    """Weights (FP32 master + BF16 copy), Adam state, forward and reverse passes."""
+
+    def __init__(self, device="cuda", seed: int = 0, params: dict | None = None):
+        self.device = device
+        self.offsets = {}
+        o = 0
+        for name, shp, _ in PARAMS:
+            size = int(np.prod(shp))
+            self.offsets[name] = (o, shp)
+            o += size
+        self.count = o
+        self.flat = torch.zeros(o, dtype=torch.float32, device=device)
+        self.flat16 = torch.zeros(o, dtype=torch.bfloat16, device=device)
+        self.grad = torch.zeros(o, dtype=torch.float32, device=device)
+        self.m = torch.zeros(o, dtype=torch.float32, device=device)
+        self.v = torch.zeros(o, dtype=torch.float32, device=device)
+        self.step_count = 0
+        self.set_params(params if params is not None else default_init(seed))
+
+    def view(self, buf, name):
+        o, shp = self.offsets[name]
+        return buf[o:o + int(np.prod(shp))].view(*shp)
+
+    def set_params(self, params: dict):
+        host = np.zeros(self.count, np.float32)
+        for name, shp, _ in PARAMS:
+            o, _ = self.offsets[name]
+            host[o:o + int(np.prod(shp))] = np.asarray(params[name], np.float32).reshape(-1)
+        self.flat.copy_(torch.from_numpy(host))
+        abi.spx_to_bf16(self.flat, self.flat16)
+
+    def get_params(self) -> dict:
+        host = self.flat.cpu().numpy()
+        out = {}
+        for name, shp, _ in PARAMS:
+            o, _ = self.offsets[name]
+            out[name] = host[o:o + int(np.prod(shp))].reshape(shp).copy()
+        return out
+
+    def p(self, name):
+        return self.view(self.flat, name)
+
+    def p16(self, name):
+        return self.view(self.flat16, name)
+
+    def g(self, name):
+        return self.view(self.grad, name)
+
+    # ------------------------------------------------------------------ forward
+    def forward(self, G: Graph):
+        """L values on G.Lpat; returns (L, saved activations)."""
+        n, dev = G.n, self.device
+        emp = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
+        h0 = emp(n, H)
+        abi.spx_dense_forward(n, G.f, F_IN, None, 0, self.p16("W0"), self.p("b0"), H, 1, None, h0)
+        hs, gs, us = [h0], [], []
+        Es = G.E.struct()
+        plan = G.E.plan()
+        for layer in range(1, LAYERS + 1):
+            h = hs[-1]
+            g = emp(n, H)
+            abi.spx_spmm(Es, h, g, 1.0, 0.0, plan)
+            u = emp(n, H)
+            hn = emp(n, H)
+            abi.spx_dense_forward(n, h, H, g, H, self.p16(f"W{layer}"), self.p(f"b{layer}"), H, 2, h, hn, u)
+            hs.append(hn)
+            gs.append(g)
+            us.append(u)
+        hL = hs[-1]
+        P, Q = emp(n, H), emp(n, H)
+        abi.spx_dense_forward(n, hL, H, None, 0, self.p16("Ua"), None, H, 0, None, P)
+        abi.spx_dense_forward(n, hL, H, None, 0, self.p16("Ub"), None, H, 0, None, Q)
+        L = emp(G.Lpat.nnz)
+        abi.spx_edge_forward(G.Lpat.struct(), G.e_low, G.d, P, Q, self.p("u"), self.p("c"), self.p("v"),
+                             self.p("bd"), self.p("bo"), L)
+        return L, {"hs": hs, "gs": gs, "us": us, "P": P, "Q": Q}
+
+    # ------------------------------------------------------------------ reverse
+    def backward(self, G: Graph, saved, gL: torch.Tensor):
+        """Accumulates d loss / d params into self.grad (overwritten) from gL on G.Lpat."""
+        n, dev = G.n, self.device
+        emp = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
+        hs, gs, us, P, Q = saved["hs"], saved["gs"], saved["us"], saved["P"], saved["Q"]
+        gP, gQ = emp(n, H), emp(n, H)
+        gpar = emp(3 * H + 2)
+        ews = abi.workspace(abi._size("spx_edge_backward_workspace_size", int(n)), dev)
+        abi.spx_edge_backward(G.Lpat.struct(), G.lt_ip, G.lt_ix, G.lt_perm, G.e_low, G.d, P, Q, self.p("u"),
+                              self.p("c"), self.p("v"), self.p("bd"), self.p("bo"), gL, gP, gQ, gpar, ews)
+        self.g("v").copy_(gpar[0:H])
+        self.g("c").copy_(gpar[H:2 * H])
+        self.g("u").copy_(gpar[2 * H:3 * H])
+        self.g("bd").copy_(gpar[3 * H:3 * H + 1])
+        self.g("bo").copy_(gpar[3 * H + 1:3 * H + 2])
+
+        def wgrad(X1, K1, X2, K2, Gm, N, dW, db):
+            ws = abi.workspace(abi._size("spx_dense_backward_weight_workspace_size", int(n), int(K1 + K2),
+                                         int(N)), dev)
+            abi.spx_dense_backward_weight(n, X1, K1, X2, K2, Gm, N, dW, db, ws)
+
+        hL = hs[-1]
+        wgrad(hL, H, None, 0, gP, H, self.g("Ua"), None)
+        wgrad(hL, H, None, 0, gQ, H, self.g("Ub"), None)
+        gh = emp(n, H)
+        abi.spx_dense_backward_data(n, gP, H, self.p16("Ua"), H, 0, gh, None, 0)
+        abi.spx_dense_backward_data(n, gQ, H, self.p16("Ub"), H, 0, gh, None, 1)
+        Es = G.E.struct()
+        plan = G.E.plan()
+        for layer in range(LAYERS, 0, -1):
+            h_in, g, u = hs[layer - 1], gs[layer - 1], us[layer - 1]
+            gu = emp(n, H)
+            abi.spx_relu_backward(gh, u, gu)
+            wgrad(h_in, H, g, H, gu, H, self.g(f"W{layer}"), self.g(f"b{layer}"))
+            gg = torch.zeros(n, H, dtype=torch.float32, device=dev)
+            # h_out = h_in + relu(u): gh_in = gh_out + (gu W^T)[:, :H]; gg = (gu W^T)[:, H:]
+            abi.spx_dense_backward_data(n, gu, H, self.p16(f"W{layer}"), H, H, gh, gg, 1)
+            # g = E h_in  ->  gh_in += E^T gg  (E is symmetric for symmetric A)
+            abi.spx_spmm(Es, gg, gh, 1.0, 1.0, plan)
+        gu0 = emp(n, H)
+        abi.spx_relu_backward(gh, hs[0], gu0)
+        wgrad(G.f, F_IN, None, 0, gu0, H, self.g("W0"), self.g("b0"))
+        return self.grad
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step_count += 1
+        abi.spx_adam_step(self.flat, self.grad, self.m, self.v, self.step_count, lr, beta1, beta2, eps,
+                          self.flat16)
+
+
+class Trainer:
+    """Unrolled-PCG training of the network on block-diagonal batches of systems."""
+
+    def __init__(self, net: MPNN, n_it: int = 4, gamma: float = 0.6, lr: float = 1e-3):
+        self.net, self.n_it, self.gamma, self.lr = net, n_it, gamma, lr
+        self.wts = torch.from_numpy(loss_weights(n_it, gamma)).to(net.device)
+
+    def loss_and_grad(self, A: CSR, sys_ptr: torch.Tensor, nsys: int, b: torch.Tensor, G: Graph | None = None):
+        """Mean loss over the systems and the L gradient (the network is not updated)."""
+        G = G or Graph(A)
+        L, saved = self.net.forward(G)
+        lt_vals = torch.empty_like(L)
+        LT = G.LT_struct(L, lt_vals)
+        Ls = abi.csr_struct(G.n, G.n, G.Lpat.indptr, G.Lpat.indices, L)
+        ws = abi.workspace(abi._size("spx_pcg_train_workspace_size", int(G.n), int(self.n_it)), A.device)
+        loss = torch.empty(nsys, dtype=torch.float32, device=A.device)
+        gL = torch.empty_like(L)
+        abi.spx_pcg_train(A.struct(), sys_ptr, nsys, Ls, LT, b, self.n_it, self.wts, loss, gL, ws)
+        return loss, gL, L, G, saved
+
+    def step(self, A: CSR, sys_ptr: torch.Tensor, nsys: int, b: torch.Tensor):
+        loss, gL, L, G, saved = self.loss_and_grad(A, sys_ptr, nsys, b)
+        self.net.backward(G, saved, gL)
+        self.net.adam(self.lr)
+        return loss
+
+
+def explicit_M(G: Graph, L_values: torch.Tensor):
+    """M = L L^T formed once with the library's SpGEMM (one sparse product per PCG step)."""
+    dev = L_values.device
+    Lc = G.Lpat.with_values(L_values)
+    lt_vals = torch.empty_like(L_values)
+    abi.spx_gather_values(G.lt_perm, L_values, lt_vals)
+    LTc = CSR(G.lt_ip, G.lt_ix, lt_vals, (G.n, G.n))
+    plan = SpGEMMPlan(Lc, LTc)
+    return plan.C.with_values(plan.numeric()), plan

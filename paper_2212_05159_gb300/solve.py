@@ -14,7 +14,7 @@ import torch
 from . import abi
 from .csr import CSR
 
-PC = {"none": 0, "jacobi": 1, "llt": 2}
+PC = {"none": 0, "jacobi": 1, "llt": 2, "M": 3}
 
 
 class SystemBatch:
@@ -69,8 +69,11 @@ class Factor:
 
 def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor | None = None,
        tol: float = 1e-8, maxit: int | None = None, delta: float = 0.1, values: torch.Tensor | None = None,
-       x: torch.Tensor | None = None):
-    """Solve every system of the batch; returns (x float64, iters, status, relres) tensors."""
+       x: torch.Tensor | None = None, M: CSR | None = None):
+    """Solve every system of the batch; returns (x float64, iters, status, relres) tensors.
+
+    pc: "none", "jacobi", "llt" (factor: M = L L^T as two products) or "M" (an explicit
+    sparse SPD M, one product per iteration)."""
     A = batch.A
     if maxit is None:
         maxit = int(10 * np.diff(batch.sys_ptr_host).max(initial=1))
@@ -82,6 +85,10 @@ def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor |
         if factor is None:
             raise ValueError("pc='llt' needs a Factor")
         L, LT = factor.structs()
+    if kind == 3:
+        if M is None:
+            raise ValueError("pc='M' needs M")
+        L = M.struct()
     abi.spx_cg_batched(A.struct(values), batch.sys_ptr, batch.nsys, batch.order, b.contiguous(), x, kind,
                        dinv, L, LT, tol, maxit, delta, batch.iters, batch.status, batch.relres, batch.ws)
     return x, batch.iters, batch.status, batch.relres

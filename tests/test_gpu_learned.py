@@ -1,0 +1,149 @@
+"""GPU parity of the learned-preconditioner path against the FP64 oracle:
+the unrolled PCG loss and its L gradient (Section 4.3), the network's forward and
+reverse passes, and a training run that must beat the untrained (Jacobi) start."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import mpnn as ompnn
+from oracle import pcg_unrolled
+
+pytestmark = pytest.mark.gpu
+spx = pytest.importorskip("paper_2212_05159_gb300")
+from paper_2212_05159_gb300 import learned, solve  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def _batch(sides, seed, sigma=1.0):
+    mats = [synth.diffusion2d(s, sigma, seed + i) for i, s in enumerate(sides)]
+    return synth.block_diag(mats)
+
+
+def _factor(A, seed, spread=0.2):
+    l_ip, l_ix, _ = oracle.tril_pattern(A)
+    rows = np.repeat(np.arange(A.m), np.diff(l_ip))
+    d = oracle.diagonal(A)
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-spread, spread, l_ix.size) / np.sqrt(d[rows])
+    on = rows == l_ix
+    v[on] = (1.0 + rng.uniform(-0.1, 0.1, int(on.sum()))) / np.sqrt(d[rows[on]])
+    return synth.CSR(A.m, A.m, l_ip, l_ix, v.astype(np.float32))
+
+
+@pytest.mark.parametrize("n_it,gamma", [(4, 0.6), (10, 0.8)])
+def test_pcg_train_matches_oracle(n_it, gamma):
+    A, ptr = _batch([5, 9, 12, 3, 16], seed=2)
+    L = _factor(A, seed=3)
+    b = synth.normal(A.m, seed=4)
+    loss_o, g_o, _ = pcg_unrolled.forward_backward(A, L, b.astype(np.float64), ptr, n_it=n_it, gamma=gamma)
+    dA, dL = spx.CSR.from_host(A), spx.CSR.from_host(L)
+    t_ip, t_ix, perm = dL.transpose_pattern()
+    ltv = torch.empty(L.nnz, device="cuda")
+    spx.abi.spx_gather_values(perm, dL.values, ltv)
+    LT = spx.abi.csr_struct(A.m, A.m, t_ip, t_ix, ltv)
+    wts = dev(learned.loss_weights(n_it, gamma))
+    ws = spx.abi.workspace(spx.abi._size("spx_pcg_train_workspace_size", A.m, n_it), "cuda")
+    loss = torch.empty(len(ptr) - 1, device="cuda")
+    gL = torch.empty(L.nnz, device="cuda")
+    spx.abi.spx_pcg_train(dA.struct(), dev(ptr), len(ptr) - 1, dL.struct(), LT, dev(b), n_it, wts, loss, gL, ws)
+    assert abs(float(host(loss).mean()) - loss_o) <= 1e-5 * abs(loss_o)
+    g = host(gL)
+    # per system: FP32 vectors through n_it iterations forward and back
+    for s in range(len(ptr) - 1):
+        e0, e1 = int(L.indptr[ptr[s]]), int(L.indptr[ptr[s + 1]])
+        scale = np.abs(g_o[e0:e1]).max()
+        assert np.abs(g[e0:e1] - g_o[e0:e1]).max() <= 2e-4 * scale, s
+
+
+def _bf16_round(p):
+    """The network's dense weights are BF16: give the oracle the same rounded weights."""
+    out = {}
+    for name, shp, is16 in learned.PARAMS:
+        v = np.asarray(p[name], np.float32)
+        if is16:
+            v = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy()
+        out[name] = v
+    return out
+
+
+def _rand_params(seed):
+    p = ompnn.init_params(seed)
+    rng = np.random.default_rng(seed + 1)
+    p["v"] = rng.normal(0, 0.3, p["v"].shape).astype(np.float32)
+    p["c"] = rng.normal(0, 0.1, p["c"].shape).astype(np.float32)
+    p["bo"] = np.array([0.05], np.float32)
+    for k in ("b0", "b1", "b2", "b3"):
+        p[k] = rng.normal(0, 0.1, p[k].shape).astype(np.float32)
+    return _bf16_round(p)
+
+
+def test_mpnn_forward_backward_match_oracle():
+    A, ptr = _batch([6, 11, 8], seed=5, sigma=1.5)
+    p = _rand_params(7)
+    net = learned.MPNN(params=p)
+    dA = spx.CSR.from_host(A)
+    G = learned.Graph(dA)
+    L, saved = net.forward(G)
+    tp = ompnn.params_to_torch(p)
+    Lo, (ri, ci) = ompnn.forward(A, tp)
+    l_ip = host(G.Lpat.indptr)
+    rows = np.repeat(np.arange(A.m), np.diff(l_ip))
+    np.testing.assert_array_equal(rows, ri)
+    np.testing.assert_array_equal(host(G.Lpat.indices), ci)
+    Lg, Lr = host(L), Lo.detach().numpy()
+    assert np.abs(Lg - Lr).max() <= 1e-4 * np.abs(Lr).max()
+    gL = synth.normal(Lg.size, seed=8)
+    net.backward(G, saved, dev(gL))
+    (Lo * torch.from_numpy(gL.astype(np.float64))).sum().backward()
+    for name, _, _ in learned.PARAMS:
+        got = host(net.g(name)).reshape(-1)
+        ref = tp[name].grad.numpy().reshape(-1)
+        assert np.abs(got - ref).max() <= 2e-4 * max(np.abs(ref).max(), 1e-6), name
+
+
+def test_initial_network_is_jacobi():
+    A, ptr = _batch([7, 9], seed=1)
+    net = learned.MPNN(seed=0)
+    G = learned.Graph(spx.CSR.from_host(A))
+    L, _ = net.forward(G)
+    Lh = host(L)
+    rows = np.repeat(np.arange(A.m), np.diff(host(G.Lpat.indptr)))
+    on = rows == host(G.Lpat.indices)
+    d = oracle.diagonal(A)
+    np.testing.assert_allclose(Lh[on], 1 / np.sqrt(d), rtol=2e-6)
+    assert np.all(Lh[~on] == 0)
+
+
+def test_training_beats_the_untrained_start():
+    """A short training run on small diffusion systems must cut held-out PCG iterations
+    below the untrained network's (M = D^-1, i.e. Jacobi)."""
+    torch.manual_seed(0)
+    net = learned.MPNN(seed=0)
+    tr = learned.Trainer(net, n_it=8, gamma=0.8, lr=3e-3)
+    for step in range(150):
+        A, ptr, _, _ = synth.diffusion_batch(16, seed=100 + step, side_lo=12, side_hi=32, sigma=(0.5, 2.0))
+        b = synth.normal(A.m, seed=1000 + step)
+        tr.step(spx.CSR.from_host(A), dev(ptr), len(ptr) - 1, dev(b))
+    A, ptr, _, _ = synth.diffusion_batch(8, seed=9999, side_lo=40, side_hi=48, sigma=1.0)
+    dA = spx.CSR.from_host(A)
+    batch = solve.SystemBatch(dA, ptr)
+    b = dev(synth.normal(A.m, seed=5))
+    _, it_j, st_j, _ = solve.cg(batch, b, pc="jacobi", tol=1e-8)
+    it_j = host(it_j).copy()
+    G = learned.Graph(dA)
+    L, _ = net.forward(G)
+    M, _ = learned.explicit_M(G, L)
+    _, it_l, st_l, rr = solve.cg(batch, b, pc="M", M=M, tol=1e-8)
+    it_l = host(it_l)
+    assert np.all(host(st_l) == 0) and np.all(host(rr) <= 1e-8)
+    print("iterations jacobi", it_j.tolist(), "learned", it_l.tolist())
+    assert it_l.sum() < 0.85 * it_j.sum()
