@@ -253,7 +253,11 @@ spx_status spx_cg_workspace_size(int32_t n, size_t* bytes);
  *          diagonal blocks and LT its transpose with values (spx_csr_transpose +
  *          spx_gather_values), applied as two sparse products,
  *          3 an explicit SPD sparse M passed as L (LT unused), applied as one
- *          sparse product -- e.g. L L^T formed once with the SpGEMM calls.
+ *          sparse product -- e.g. L L^T formed once with the SpGEMM calls,
+ *          4 IC(0): L the factor from spx_ic0_factor, LT its transpose with values,
+ *          ic0_levels = {sys_lev_off, lev_ptr, lev_rows} from spx_ic0_analyse (a host
+ *          array of three device pointers); the two triangular solves run level by level
+ *          on the first block of each cluster.  Ignored (may be NULL) for kinds 0-3.
  * iters, status (spx_status per system: OK, MAXITER, BREAKDOWN, NONFINITE): device
  * int32[nsys]; relres: device float64[nsys], the true relative residual of the
  * returned x.  One launch of thread-block clusters (8 blocks per system); capturable
@@ -261,9 +265,9 @@ spx_status spx_cg_workspace_size(int32_t n, size_t* bytes);
 spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
                           const int32_t* order, const float* b, double* x, int32_t pc_kind,
                           const float* pc_diag_inv, const spx_csr* L, const spx_csr* LT,
-                          double tol, int32_t maxit, double delta, int32_t* iters,
-                          int32_t* status, double* relres, void* workspace,
-                          size_t workspace_bytes, void* stream);
+                          const int32_t* const* ic0_levels, double tol, int32_t maxit,
+                          double delta, int32_t* iters, int32_t* status, double* relres,
+                          void* workspace, size_t workspace_bytes, void* stream);
 
 /* dinv[i] = 1 / a_ii (0 where the diagonal is absent or zero); device float32[m]. */
 spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream);
@@ -369,6 +373,30 @@ spx_status spx_adam_step(int64_t count, float* params, const float* grads, float
 
 /* dst[t] = (bf16) src[t]. */
 spx_status spx_to_bf16(int64_t count, const float* src, void* dst, void* stream);
+
+/* ---------------------------------------- IC(0) baseline (Section 3.1.5 solves) */
+
+/* Workspace bytes of spx_ic0_analyse. */
+spx_status spx_ic0_workspace_size(int32_t n, int32_t nsys, size_t* bytes);
+
+/* Level schedule of the lower-triangular pattern Lpat (e.g. tril(A) from
+ * spx_tril_pattern) per system of a block-diagonal batch: level(i) = 0 without
+ * off-diagonal entries, else 1 + the largest level among its columns j < i.
+ * Outputs (device int32): sys_lev_off[nsys+1] (offsets into lev_ptr), lev_ptr[n + nsys]
+ * (per system: start of each level in lev_rows, then the end), lev_rows[n] (rows
+ * grouped by level, increasing within a level).  One thread per system. */
+spx_status spx_ic0_analyse(const spx_csr* Lpat, const int32_t* sys_ptr, int32_t nsys,
+                           int32_t* sys_lev_off, int32_t* lev_ptr, int32_t* lev_rows,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* Zero-fill incomplete Cholesky on tril(A)'s pattern (Saad Sec. 10.3): L L^T agrees with
+ * A on the pattern.  l_src[e]: the position in A of tril entry e (spx_tril_pattern);
+ * a_values: A's values; l_values: output float32[nnz(Lpat)]; status: per system SPX_OK or
+ * SPX_BREAKDOWN (a non-positive pivot).  One thread block per system, level by level. */
+spx_status spx_ic0_factor(const spx_csr* Lpat, const int32_t* l_src, const float* a_values,
+                          int32_t nsys, const int32_t* sys_lev_off, const int32_t* lev_ptr,
+                          const int32_t* lev_rows, float* l_values, int32_t* status,
+                          void* stream);
 
 #ifdef __cplusplus
 }

@@ -78,8 +78,11 @@ SIGNATURES = {
     "spx_spgemm_backward": [_CSRP, _CSRP, _CSRP, _P, _P, _P, _P, _P, _P, _P],
     "spx_gather_values": [_I64, _P, _P, _P, _P],
     "spx_cg_workspace_size": [_I32, ctypes.POINTER(_SZ)],
-    "spx_cg_batched": [_CSRP, _P, _I32, _P, _P, _P, _I32, _P, _CSRP, _CSRP, _D, _I32, _D, _P, _P, _P, _P,
-                       _SZ, _P],
+    "spx_cg_batched": [_CSRP, _P, _I32, _P, _P, _P, _I32, _P, _CSRP, _CSRP, ctypes.POINTER(_P), _D, _I32, _D,
+                       _P, _P, _P, _P, _SZ, _P],
+    "spx_ic0_workspace_size": [_I32, _I32, ctypes.POINTER(_SZ)],
+    "spx_ic0_analyse": [_CSRP, _P, _I32, _P, _P, _P, _P, _SZ, _P],
+    "spx_ic0_factor": [_CSRP, _P, _P, _I32, _P, _P, _P, _P, _P, _P],
     "spx_diag_inverse": [_CSRP, _P, _P],
     "spx_masked_outer_f64": [_CSRP, _P, _P, _D, _P, _P],
     "spx_pcg_train_workspace_size": [_I32, _I32, ctypes.POINTER(_SZ)],
@@ -312,12 +315,35 @@ def spx_cg_workspace_size(n: int) -> int:
 
 
 def spx_cg_batched(A: spx_csr, sys_ptr, nsys: int, order, b, x, pc_kind: int, dinv, L: spx_csr | None,
-                   LT: spx_csr | None, tol: float, maxit: int, delta: float, iters, status, relres, ws):
+                   LT: spx_csr | None, tol: float, maxit: int, delta: float, iters, status, relres, ws,
+                   ic0_levels=None):
+    lev = None
+    if ic0_levels is not None:
+        lev = (ctypes.c_void_p * 3)(*[t.data_ptr() for t in ic0_levels])
     _check(lib().spx_cg_batched(ctypes.byref(A), ptr(sys_ptr), int(nsys), ptr(order), ptr(b), ptr(x),
                                 int(pc_kind), ptr(dinv), ctypes.byref(L) if L is not None else None,
-                                ctypes.byref(LT) if LT is not None else None, float(tol), int(maxit),
+                                ctypes.byref(LT) if LT is not None else None, lev, float(tol), int(maxit),
                                 float(delta), ptr(iters), ptr(status), ptr(relres), ptr(ws), ws.numel(),
                                 _stream()), "spx_cg_batched")
+
+
+def spx_ic0_analyse(Lpat: spx_csr, sys_ptr, nsys: int, device):
+    """Returns (sys_lev_off, lev_ptr, lev_rows) int32 tensors."""
+    sz = _SZ(0)
+    _check(lib().spx_ic0_workspace_size(int(Lpat.m), int(nsys), ctypes.byref(sz)), "spx_ic0_workspace_size")
+    ws = workspace(sz.value, device)
+    off = torch.empty(nsys + 1, dtype=torch.int32, device=device)
+    lp = torch.empty(Lpat.m + nsys + 1, dtype=torch.int32, device=device)
+    rows = torch.empty(max(Lpat.m, 1), dtype=torch.int32, device=device)
+    _check(lib().spx_ic0_analyse(ctypes.byref(Lpat), ptr(sys_ptr), int(nsys), ptr(off), ptr(lp), ptr(rows), ptr(ws),
+                                 ws.numel(), _stream()), "spx_ic0_analyse")
+    return off, lp, rows
+
+
+def spx_ic0_factor(Lpat: spx_csr, l_src, a_values, nsys: int, levels, l_values, status):
+    off, lp, rows = levels
+    _check(lib().spx_ic0_factor(ctypes.byref(Lpat), ptr(l_src), ptr(a_values), int(nsys), ptr(off), ptr(lp),
+                                ptr(rows), ptr(l_values), ptr(status), _stream()), "spx_ic0_factor")
 
 
 def spx_diag_inverse(A: spx_csr, dinv):

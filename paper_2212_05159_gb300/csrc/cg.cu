@@ -17,7 +17,8 @@
 // in double-float (an FP32 pair with exact products, ~44 significant bits) and are
 // combined in FP64.  Preconditioners: none, Jacobi (z = D^-1 r), the factored
 // approximate inverse M = L L^T of Section 4.3 (z = L (L^T r), two sparse products), and
-// an explicit sparse M (z = M r, one product; e.g. L L^T formed once by SpGEMM).
+// an explicit sparse M (z = M r, one product; e.g. L L^T formed once by SpGEMM), and
+// IC(0) (z = (L L^T)^-1 r by two level-scheduled triangular solves).
 //
 // Status per system: SPX_OK, SPX_MAXITER, SPX_BREAKDOWN (p^T A p <= 0 or r^T z <= 0),
 // SPX_NONFINITE.  No spin waits: only cluster / block barriers.
@@ -64,6 +65,9 @@ struct CgArgs {
     int32_t* status;
     double* relres;
     int32_t* queue;
+    const int32_t* lev_off;   // IC(0): per-system offsets into lev_ptr
+    const int32_t* lev_ptr;   // IC(0): level l of a system = lev_rows[lev_ptr[l] .. lev_ptr[l+1])
+    const int32_t* lev_rows;
 };
 
 // ---------------------------------------------------------------- double-float sums
@@ -134,8 +138,41 @@ __device__ __forceinline__ void apply_pc_local(const CgArgs& a, int lo, int hi) 
     }
 }
 
-__device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi) {
-    if (a.pc == 3) {
+// IC(0): z = L^-T L^-1 r with level-scheduled triangular solves, run by the cluster's
+// first block (block barriers between levels) while the others wait at the cluster
+// barrier.  L: lower CSR (diagonal last in each row); LT: its transpose (diagonal first).
+__device__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) {
+    if (rank != 0) return;
+    const int32_t* lp = a.lev_ptr + a.lev_off[sid];
+    const int nl = a.lev_off[sid + 1] - a.lev_off[sid] - 1;
+    for (int l = 0; l < nl; ++l) {
+        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += CG_THREADS) {
+            const int i = a.lev_rows[q];
+            const int e1 = a.l_ptr[i + 1] - 1;
+            float s = a.r[i];
+            for (int e = a.l_ptr[i]; e < e1; ++e) s = fmaf(-a.l_val[e], a.w[a.l_idx[e]], s);
+            a.w[i] = s / a.l_val[e1];
+        }
+        __syncthreads();
+    }
+    for (int l = nl - 1; l >= 0; --l) {
+        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += CG_THREADS) {
+            const int i = a.lev_rows[q];
+            const int e0 = a.lt_ptr[i];
+            float s = a.w[i];
+            for (int e = e0 + 1; e < a.lt_ptr[i + 1]; ++e) s = fmaf(-a.lt_val[e], a.z[a.lt_idx[e]], s);
+            a.z[i] = s / a.lt_val[e0];
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi, unsigned rank, int sid) {
+    if (a.pc == 4) {
+        cl.sync();                                               // r complete
+        ic0_apply(a, rank, sid);
+        cl.sync();                                               // z complete
+    } else if (a.pc == 3) {
         cl.sync();                                               // r complete
         for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.r, i);      // z = M r
@@ -196,7 +233,7 @@ __global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
             }
             v2[0] = df_value(bb);
         }
-        apply_pc(a, cl, lo, hi);
+        apply_pc(a, cl, lo, hi, rank, sid);
         {
             DF rz{0.f, 0.f};
             for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
@@ -244,7 +281,7 @@ __global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
                 }
                 dirty = true;
                 ++it;
-                apply_pc(a, cl, lo, hi);
+                apply_pc(a, cl, lo, hi, rank, sid);
                 {
                     DF rzs{0.f, 0.f}, rrs{0.f, 0.f};
                     for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
@@ -274,7 +311,7 @@ __global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
                     ref = tn;
                     if (!isfinite(tn)) { status = SPX_NONFINITE; break; }
                     if (tn <= a.tol * bnorm) { status = SPX_OK; break; }
-                    apply_pc(a, cl, lo, hi);
+                    apply_pc(a, cl, lo, hi, rank, sid);
                     DF rzs{0.f, 0.f};
                     for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) df_add_prod(rzs, a.r[i], a.z[i]);
                     double vz[1] = {df_value(rzs)};
@@ -344,20 +381,22 @@ extern "C" spx_status spx_cg_workspace_size(int32_t n, size_t* bytes) {
 
 extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys, const int32_t* order,
                                      const float* b, double* x, int32_t pc_kind, const float* pc_diag_inv,
-                                     const spx_csr* L, const spx_csr* LT, double tol, int32_t maxit, double delta,
-                                     int32_t* iters, int32_t* status, double* relres, void* ws, size_t ws_bytes,
-                                     void* stream) {
+                                     const spx_csr* L, const spx_csr* LT, const int32_t* const* ic0_levels,
+                                     double tol, int32_t maxit, double delta, int32_t* iters, int32_t* status,
+                                     double* relres, void* ws, size_t ws_bytes, void* stream) {
     SPX_TRY(check_csr(A, true, "spx_cg_batched"));
     if (A->m != A->n) return set_error(SPX_INVALID_ARG, "spx_cg_batched: A must be square");
     if (nsys < 0 || (nsys > 0 && (!sys_ptr || !b || !x || !iters || !status || !relres)))
         return set_error(SPX_INVALID_ARG, "spx_cg_batched: NULL argument");
-    if (pc_kind < 0 || pc_kind > 3) return set_error(SPX_INVALID_ARG, "spx_cg_batched: unknown preconditioner");
+    if (pc_kind < 0 || pc_kind > 4) return set_error(SPX_INVALID_ARG, "spx_cg_batched: unknown preconditioner");
+    if (pc_kind == 4 && (!ic0_levels || !ic0_levels[0] || !ic0_levels[1] || !ic0_levels[2]))
+        return set_error(SPX_INVALID_ARG, "spx_cg_batched: IC(0) needs its level schedule");
     if (pc_kind == 1 && !pc_diag_inv) return set_error(SPX_INVALID_ARG, "spx_cg_batched: Jacobi needs D^-1");
     if (pc_kind == 3) {
         SPX_TRY(check_csr(L, true, "spx_cg_batched (M)"));
         if (L->m != A->m) return set_error(SPX_INVALID_ARG, "spx_cg_batched: M shape");
     }
-    if (pc_kind == 2) {
+    if (pc_kind == 2 || pc_kind == 4) {
         SPX_TRY(check_csr(L, true, "spx_cg_batched (L)"));
         SPX_TRY(check_csr(LT, true, "spx_cg_batched (L^T)"));
         if (L->m != A->m || LT->m != A->m) return set_error(SPX_INVALID_ARG, "spx_cg_batched: L shape");
@@ -385,7 +424,7 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     if (pc_kind == 3) {
         a.l_ptr = L->indptr; a.l_idx = L->indices; a.l_val = L->values;
     }
-    if (pc_kind == 2) {
+    if (pc_kind == 2 || pc_kind == 4) {
         a.l_ptr = L->indptr; a.l_idx = L->indices; a.l_val = L->values;
         a.lt_ptr = LT->indptr; a.lt_idx = LT->indices; a.lt_val = LT->values;
     }
@@ -402,6 +441,11 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     a.iters = iters;
     a.status = status;
     a.relres = relres;
+    if (pc_kind == 4) {
+        a.lev_off = ic0_levels[0];
+        a.lev_ptr = ic0_levels[1];
+        a.lev_rows = ic0_levels[2];
+    }
     SPX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "spx_cg_batched memset");
 
     const int cl = cg_cluster_size();

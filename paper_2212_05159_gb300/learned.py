@@ -70,13 +70,19 @@ class Graph:
         self.d = torch.empty(n, dtype=torch.float32, device=dev)
         self.e = torch.empty(max(A.nnz, 1), dtype=torch.float32, device=dev)[: A.nnz]
         self.f = torch.empty(n, F_IN, dtype=torch.float32, device=dev)
-        abi.spx_mpnn_features(A.struct(), self.d, self.e, self.f)
         self.E = A.with_values(self.e)
-        l_ip, l_ix, l_src = abi.spx_tril_pattern(A.struct(), dev)
+        l_ip, l_ix, self.l_src = abi.spx_tril_pattern(A.struct(), dev)
         self.Lpat = CSR(l_ip, l_ix, None, (n, n))
         self.e_low = torch.empty(l_ix.numel(), dtype=torch.float32, device=dev)
-        abi.spx_gather_values(l_src, self.e, self.e_low)
         self.lt_ip, self.lt_ix, self.lt_perm = self.Lpat.transpose_pattern()
+        self.E.plan()
+        self.features()
+
+    def features(self, values: torch.Tensor | None = None):
+        """(Re)computes d, e and the node features for A's values (same pattern)."""
+        abi.spx_mpnn_features(self.A.struct(values), self.d, self.e, self.f)
+        abi.spx_gather_values(self.l_src, self.e, self.e_low)
+        return self
 
     def LT_struct(self, L_values: torch.Tensor, out: torch.Tensor):
         """A^T-pattern view of L with its values gathered into `out`."""

@@ -1,0 +1,180 @@
+"""Learned preconditioner study: train on generated diffusion systems, then time PCG to a
+relative residual of 1e-8 with Jacobi, the learned factor and IC(0) on held-out systems.
+
+Workload (variable-coefficient 2D diffusion, 5-point, log-normal coefficients):
+  training   systems with grid side ~ U{32..128} and sigma ~ U[0.5, 2], drawn fresh for
+             every step (steps x batch systems in total), right-hand sides N(0,1);
+  evaluation held-out 256 x 256 systems (sigma ~ U[0.5, 2], other seeds), N(0,1) rhs.
+Timed per method with CUDA events on the solving stream, from preconditioner set-up
+(network inference and the numeric SpGEMM forming M = L L^T; IC(0) numeric
+factorisation) through convergence; the per-pattern analysis (SpGEMM symbolic, IC(0)
+level schedule, transposes) is set-up outside the timed region and reported separately.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import time
+
+import numpy as np
+import torch
+
+from . import learned, solve
+from .csr import CSR
+
+
+def _gen(nsys, seed, lo, hi, sigma):
+    import synth
+    A, ptr, sides, sig = synth.diffusion_batch(nsys, seed=seed, side_lo=lo, side_hi=hi, sigma=sigma)
+    b = synth.normal(A.m, seed=seed + 7919)
+    return A, ptr, b
+
+
+def train(net: learned.MPNN, steps: int, batch: int = 32, n_it: int = 8, gamma: float = 0.8,
+          lr: float = 2e-3, seed: int = 1, time_budget_s: float | None = None, log=None):
+    """Trains on `steps` fresh batches (steps * batch generated systems)."""
+    tr = learned.Trainer(net, n_it=n_it, gamma=gamma, lr=lr)
+    losses = []
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(_gen, batch, seed * 100003, 32, 128, (0.5, 2.0))
+        for step in range(steps):
+            A, ptr, b = fut.result()
+            if step + 1 < steps:
+                fut = ex.submit(_gen, batch, seed * 100003 + step + 1, 32, 128, (0.5, 2.0))
+            dA = CSR.from_host(A)
+            loss = tr.step(dA, torch.from_numpy(ptr).cuda(), len(ptr) - 1, torch.from_numpy(b).cuda())
+            if step % 20 == 0 or step == steps - 1:
+                losses.append((step, float(loss.mean())))
+                if log:
+                    log(f"step {step} loss {losses[-1][1]:.4f}")
+            if time_budget_s is not None and time.perf_counter() - t0 > time_budget_s:
+                break
+    torch.cuda.synchronize()
+    return {"steps": step + 1, "systems": (step + 1) * batch, "seconds": time.perf_counter() - t0,
+            "loss_history": losses, "n_it": n_it, "gamma": gamma, "lr": lr, "batch": batch}
+
+
+def _timed(fn):
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    out = fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
+
+
+def evaluate(net: learned.MPNN, nsys: int = 128, per_batch: int = 64, side: int = 256, seed: int = 777,
+             tol: float = 1e-8, methods=("jacobi", "learned", "ic0")):
+    """Iterations and wall time to `tol` for each method over `nsys` held-out systems."""
+    res = {m: {"iters": [], "ms": 0.0, "setup_ms": 0.0, "converged": 0, "max_relres": 0.0} for m in methods}
+    analysis_ms = {m: 0.0 for m in methods}
+    done = 0
+    bi = 0
+    while done < nsys:
+        k = min(per_batch, nsys - done)
+        A, ptr, b = _gen(k, seed + bi, side, side, (0.5, 2.0))
+        dA = CSR.from_host(A)
+        batch = solve.SystemBatch(dA, ptr)
+        bt = torch.from_numpy(b).cuda()
+        maxit = 20 * side * side
+        for m in methods:
+            if m == "jacobi":
+                ms, out = _timed(lambda: solve.cg(batch, bt, pc="jacobi", tol=tol, maxit=maxit,
+                                                  values=dA.values))
+                setup = 0.0
+            elif m == "learned":
+                t0 = time.perf_counter()
+                G = learned.Graph(dA)
+                L, _ = net.forward(G)
+                _, plan = learned.explicit_M(G, L)               # pattern of L L^T: per pattern
+                torch.cuda.synchronize()
+                analysis_ms[m] += (time.perf_counter() - t0) * 1e3
+
+                def run():
+                    G.features(dA.values)
+                    L2, _ = net.forward(G)
+                    Mv = plan.numeric(L2, _lt_values(G, L2))
+                    return solve.cg(batch, bt, pc="M", M=plan.C.with_values(Mv), tol=tol, maxit=maxit)
+                ms, out = _timed(run)
+                setup, _ = _timed(lambda: plan.numeric(L, _lt_values(G, L)))
+            else:
+                t0 = time.perf_counter()
+                ic = solve.IC0(batch)
+                torch.cuda.synchronize()
+                analysis_ms[m] += (time.perf_counter() - t0) * 1e3
+
+                def run():
+                    ic.factor()
+                    return solve.cg(batch, bt, pc="ic0", ic0=ic, tol=tol, maxit=maxit)
+                ms, out = _timed(run)
+                setup, _ = _timed(lambda: ic.factor())
+            _, it, st, rr = out
+            r = res[m]
+            r["iters"] += it.cpu().numpy().tolist()
+            r["ms"] += ms
+            r["setup_ms"] += setup
+            r["converged"] += int((st.cpu().numpy() == 0).sum())
+            r["max_relres"] = max(r["max_relres"], float(rr.cpu().numpy().max()))
+        done += k
+        bi += 1
+    out = {"systems": nsys, "side": side, "tol": tol, "per_launch": per_batch}
+    for m in methods:
+        it = np.array(res[m]["iters"])
+        out[m] = {"iters_median": float(np.median(it)), "iters_p90": float(np.percentile(it, 90)),
+                  "iters_mean": float(it.mean()), "total_ms": res[m]["ms"], "ms_per_system": res[m]["ms"] / nsys,
+                  "setup_ms": res[m]["setup_ms"], "analysis_ms_untimed": analysis_ms[m],
+                  "converged": res[m]["converged"], "max_true_relres": res[m]["max_relres"]}
+    if "jacobi" in methods:
+        for m in methods:
+            if m != "jacobi":
+                out[m]["speedup_vs_jacobi"] = out["jacobi"]["total_ms"] / out[m]["total_ms"]
+                out[m]["iter_ratio_vs_jacobi"] = out["jacobi"]["iters_mean"] / out[m]["iters_mean"]
+    return out
+
+
+def _lt_values(G: learned.Graph, L: torch.Tensor):
+    from . import abi
+    out = torch.empty_like(L)
+    abi.spx_gather_values(G.lt_perm, L, out)
+    return out
+
+
+def batch256_jacobi(graph_replay: bool = True, seed: int = 0, reps: int = 3):
+    """The 256-system workload (sides U{32..256}, sigma 1): Jacobi PCG to 1e-8 in one persistent
+    launch, captured once in a CUDA graph and replayed."""
+    import synth
+    A, ptr, sides, _ = synth.diffusion_batch(256, seed=seed, side_lo=32, side_hi=256, sigma=1.0)
+    b = synth.normal(A.m, seed=seed + 1)
+    dA = CSR.from_host(A)
+    batch = solve.SystemBatch(dA, ptr)
+    bt = torch.from_numpy(b).cuda()
+    x = torch.empty(A.m, dtype=torch.float64, device="cuda")
+    batch.dinv()
+    maxit = 10 * 256 * 256
+    solve.cg(batch, bt, pc="jacobi", x=x, maxit=maxit)           # warm-up
+    torch.cuda.synchronize()
+    if graph_replay:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                solve.cg(batch, bt, pc="jacobi", x=x, maxit=maxit)
+        torch.cuda.current_stream().wait_stream(s)
+        run = g.replay
+    else:
+        def run():
+            solve.cg(batch, bt, pc="jacobi", x=x, maxit=maxit)
+    times = []
+    for _ in range(reps):
+        ms, _ = _timed(run)
+        times.append(ms)
+    it = batch.iters.cpu().numpy()
+    st = batch.status.cpu().numpy()
+    rr = batch.relres.cpu().numpy()
+    return {"systems": 256, "rows": int(A.m), "nnz": int(A.nnz), "ms": float(np.median(times)),
+            "graph_replay": graph_replay, "iters_total": int(it.sum()), "iters_max": int(it.max()),
+            "converged": int((st == 0).sum()), "max_true_relres": float(rr.max()),
+            "row_iterations_per_s": float((np.diff(ptr) * it).sum() / (np.median(times) * 1e-3))}

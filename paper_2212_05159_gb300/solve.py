@@ -14,7 +14,7 @@ import torch
 from . import abi
 from .csr import CSR
 
-PC = {"none": 0, "jacobi": 1, "llt": 2, "M": 3}
+PC = {"none": 0, "jacobi": 1, "llt": 2, "M": 3, "ic0": 4}
 
 
 class SystemBatch:
@@ -67,9 +67,39 @@ class Factor:
         return self.L.struct(), lt
 
 
+class IC0:
+    """Zero-fill incomplete Cholesky of every system of a batch (the IC(0) baseline)."""
+
+    def __init__(self, batch: SystemBatch, values: torch.Tensor | None = None):
+        A = batch.A
+        dev = A.device
+        l_ip, l_ix, self.l_src = abi.spx_tril_pattern(A.struct(), dev)
+        self.Lpat = CSR(l_ip, l_ix, None, (A.m, A.m))
+        self.levels = abi.spx_ic0_analyse(self.Lpat.struct(), batch.sys_ptr, batch.nsys, dev)
+        self.values = torch.empty(l_ix.numel(), dtype=torch.float32, device=dev)
+        self.status = torch.empty(batch.nsys, dtype=torch.int32, device=dev)
+        self.t_ip, self.t_ix, self.perm = self.Lpat.transpose_pattern()
+        self.lt_vals = torch.empty_like(self.values)
+        self.batch = batch
+        self.factor(values)
+
+    def factor(self, values: torch.Tensor | None = None):
+        A = self.batch.A
+        v = A.values if values is None else values
+        abi.spx_ic0_factor(self.Lpat.struct(), self.l_src, v, self.batch.nsys, self.levels, self.values,
+                           self.status)
+        abi.spx_gather_values(self.perm, self.values, self.lt_vals)
+        return self
+
+    def structs(self):
+        n = self.batch.A.m
+        return (self.Lpat.struct(self.values),
+                abi.csr_struct(n, n, self.t_ip, self.t_ix, self.lt_vals))
+
+
 def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor | None = None,
        tol: float = 1e-8, maxit: int | None = None, delta: float = 0.1, values: torch.Tensor | None = None,
-       x: torch.Tensor | None = None, M: CSR | None = None):
+       x: torch.Tensor | None = None, M: CSR | None = None, ic0: IC0 | None = None):
     """Solve every system of the batch; returns (x float64, iters, status, relres) tensors.
 
     pc: "none", "jacobi", "llt" (factor: M = L L^T as two products) or "M" (an explicit
@@ -89,8 +119,15 @@ def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor |
         if M is None:
             raise ValueError("pc='M' needs M")
         L = M.struct()
+    levels = None
+    if kind == 4:
+        if ic0 is None:
+            raise ValueError("pc='ic0' needs an IC0")
+        L, LT = ic0.structs()
+        levels = ic0.levels
     abi.spx_cg_batched(A.struct(values), batch.sys_ptr, batch.nsys, batch.order, b.contiguous(), x, kind,
-                       dinv, L, LT, tol, maxit, delta, batch.iters, batch.status, batch.relres, batch.ws)
+                       dinv, L, LT, tol, maxit, delta, batch.iters, batch.status, batch.relres, batch.ws,
+                       ic0_levels=levels)
     return x, batch.iters, batch.status, batch.relres
 
 

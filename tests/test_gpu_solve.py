@@ -148,3 +148,34 @@ def test_full_size_batch_256():
     for s in list(order[:2]) + list(order[-2:]):
         As, a, c = _block(A, ptr, s)
         assert _true_relres(As, xh[a:c], b[a:c]) <= 1e-8
+
+
+def test_ic0_factor_and_pcg_match_oracle(small_batch):
+    A, ptr, batch = small_batch
+    ic = solve.IC0(batch)
+    assert np.all(host(ic.status) == 0)
+    lv = host(ic.values)
+    l_ip = host(ic.Lpat.indptr)
+    b = synth.normal(A.m, seed=9)
+    x, iters, status, relres = solve.cg(batch, dev(b), pc="ic0", ic0=ic, tol=1e-8)
+    x = host(x)
+    assert np.all(host(status) == 0)
+    for s in range(batch.nsys):
+        As, a, c = _block(A, ptr, s)
+        o_ip, o_ix, o_v = oracle.ic0(As)
+        e0, e1 = int(l_ip[a]), int(l_ip[c])
+        np.testing.assert_array_equal(host(ic.Lpat.indices)[e0:e1] - a, o_ix)
+        np.testing.assert_allclose(lv[e0:e1], o_v, rtol=2e-5, atol=1e-6 * np.abs(o_v).max())
+        assert _true_relres(As, x[a:c], b[a:c]) <= 1e-8
+        _, _, it8 = oracle.pcg(As, b[a:c], tol=1e-8, pc="ic0", L=(o_ip, o_ix, o_v))
+        assert host(iters)[s] <= 1.5 * it8 + 5
+
+
+def test_ic0_tridiagonal_one_iteration():
+    """IC(0) of A_N is its exact Cholesky factor: PCG converges in one iteration."""
+    A = synth.poisson1d(300)
+    batch = solve.SystemBatch(spx.CSR.from_host(A), np.array([0, A.m], np.int32))
+    ic = solve.IC0(batch)
+    b = synth.normal(A.m, seed=2)
+    _, it, st, rr = solve.cg(batch, dev(b), pc="ic0", ic0=ic, tol=1e-6)
+    assert host(st)[0] == 0 and host(it)[0] <= 2
