@@ -228,6 +228,26 @@ spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, const spx_csr
                                const int32_t* at_indptr, const int32_t* at_indices,
                                const int32_t* a_perm, void* stream);
 
+/* spx_spmm_t for callers that cannot allocate device memory when they call it -- e.g. a
+ * host framework that owns all device memory through its own pool and forbids other
+ * allocations, or code that must not let an allocation synchronise the device.  The paper
+ * has no counterpart: this is a deployment variant of spx_spmm_t.
+ * Same operation, arguments and results as spx_spmm_t with no workspace and no G slabs,
+ * except that A^T's gathered values are staged in a scratch array built into the library
+ * (16 MiB of device memory per device that loads the library, held until exit), so:
+ *  - AT->nnz must be <= 4,194,304 (2^22); larger sizes return SPX_INVALID_ARG with a
+ *    message, before any device work;
+ *  - it calls no cudaMalloc / cudaFree and allocates nothing;
+ *  - the first call on a device looks the array's device address up once for that
+ *    device (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture;
+ *  - every call shares the one array and leaves its contents behind; each call writes
+ *    all the entries it reads, so nothing needs clearing, but calls whose work overlaps
+ *    on the GPU (other streams, other host threads) race on the array: serialise them. */
+spx_status spx_spmm_t_noalloc(const spx_csr* AT, const int32_t* perm, const float* G,
+                              int64_t ldg, int32_t k, float* gX, int64_t ldgx, float alpha,
+                              float beta, const spx_rowplan* plan, void* stream);
+
 /* dst[e] = src[perm[e]] for e < nnz -- e.g. A^T's values from A's through the
  * permutation of spx_csr_transpose.  Device pointers. */
 spx_status spx_gather_values(int64_t nnz, const int32_t* perm, const float* src, float* dst,

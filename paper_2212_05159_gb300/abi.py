@@ -70,6 +70,7 @@ SIGNATURES = {
     "spx_csr_transpose": [_CSRP, _P, _P, _P, _P, _SZ, _P],
     "spx_spmm_t_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
     "spx_spmm_t": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
+    "spx_spmm_t_noalloc": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P],
     "spx_spgemm_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_spgemm_analyse": [_CSRP, _CSRP, ctypes.POINTER(_I64), _P, _SZ, _P],
     "spx_spgemm_symbolic": [_CSRP, _CSRP, _P, ctypes.POINTER(_I64), _P, _SZ, _P, _SZ, _P],
@@ -251,6 +252,15 @@ def spx_spmm_t_workspace_size(AT: spx_csr, k: int, plan: spx_rowplan | None = No
     _check(lib().spx_spmm_t_workspace_size(ctypes.byref(AT), int(k), _planp(plan), ctypes.byref(sz)),
            "spx_spmm_t_workspace_size")
     return sz.value
+
+
+def spx_spmm_t_noalloc(AT: spx_csr, perm, G, gX, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None):
+    """spx_spmm_t staging A^T's values in the library's built-in scratch (no allocation)."""
+    pg, ldg = _dense(G, "G")
+    px, ldx = _dense(gX, "gX")
+    _check(lib().spx_spmm_t_noalloc(ctypes.byref(AT), ptr(perm), pg, ldg, G.shape[1], px, ldx, float(alpha),
+                                    float(beta), _planp(plan), _stream()), "spx_spmm_t_noalloc")
+    return gX
 
 
 def spx_spmm_t(AT: spx_csr, perm, G, gX, alpha=1.0, beta=0.0, plan: spx_rowplan | None = None,

@@ -25,6 +25,8 @@
 // Every output element is a fixed-order sum: results are deterministic.
 #include <limits.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "scan.cuh"
 #include "slab.cuh"
@@ -445,4 +447,68 @@ extern "C" spx_status spx_gather_values(int64_t nnz, const int32_t* perm, const 
     gather_values_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, as_stream(stream)>>>(nnz, perm, src, dst);
     SPX_CHECK_LAUNCH("spx_gather_values");
     return SPX_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// spx_spmm_t without allocation.
+//
+// Some callers cannot allocate device memory at the moment they need the product: a host
+// framework that owns every byte of device memory through its own pool and forbids side
+// allocations, a callback that must not synchronise the device (cudaMalloc and cudaFree
+// can), or a tight loop that must not touch the allocator at all.  For them this variant
+// stages A^T's gathered values in a scratch array that is part of the library image
+// instead of a caller-provided workspace.  The array is file-scope device memory of a
+// fixed size, held by every device that loads the library until the process exits.
+namespace spx {
+namespace {
+constexpr int64_t NOALLOC_MAX_NNZ = int64_t(1) << 22;          // 4,194,304 entries (16 MiB)
+static __device__ __align__(256) float g_noalloc_values[NOALLOC_MAX_NNZ];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::atomic<float*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array for the current device, looked up once per device.
+spx_status noalloc_scratch(float** out) {
+    int dev = 0;
+    SPX_CUDA(cudaGetDevice(&dev), "spx_spmm_t_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return set_error(SPX_NOT_SUPPORTED, "spx_spmm_t_noalloc: device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
+    float* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* addr = nullptr;
+        SPX_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_values), "spx_spmm_t_noalloc: cudaGetSymbolAddress");
+        p = static_cast<float*>(addr);
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return SPX_OK;
+}
+}  // namespace
+}  // namespace spx
+
+extern "C" spx_status spx_spmm_t_noalloc(const spx_csr* AT, const int32_t* perm, const float* G, int64_t ldg,
+                                         int32_t k, float* gX, int64_t ldgx, float alpha, float beta,
+                                         const spx_rowplan* plan, void* stream) {
+    SPX_TRY(check_csr(AT, true, "spx_spmm_t_noalloc"));
+    if (AT->nnz > NOALLOC_MAX_NNZ)
+        return set_error(SPX_INVALID_ARG,
+                         "spx_spmm_t_noalloc: nnz = %lld exceeds the built-in scratch of %lld entries; "
+                         "use spx_spmm_t with a workspace",
+                         (long long)AT->nnz, (long long)NOALLOC_MAX_NNZ);
+    if (AT->nnz > 0 && !perm) return set_error(SPX_INVALID_ARG, "spx_spmm_t_noalloc: NULL perm");
+    SPX_TRY(check_dense(G, AT->n, ldg, k, "spx_spmm_t_noalloc", "G"));
+    SPX_TRY(check_dense(gX, AT->m, ldgx, k, "spx_spmm_t_noalloc", "gX"));
+    cudaStream_t st = as_stream(stream);
+    if (AT->nnz == 0 || AT->m == 0 || k == 0)
+        return launch_spmm<false>(AT, nullptr, AT->values, G, ldg, k, gX, ldgx, alpha, beta, plan, nullptr, 0, st,
+                                  "spx_spmm_t_noalloc");
+    float* tv = nullptr;
+    SPX_TRY(noalloc_scratch(&tv));
+    // every entry [0, nnz) of the scratch is written here before the product reads it
+    int64_t blocks = (AT->nnz + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    gather_values_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(AT->nnz, perm, AT->values, tv);
+    SPX_CHECK_LAUNCH("spx_spmm_t_noalloc gather");
+    return launch_spmm<false>(AT, nullptr, tv, G, ldg, k, gX, ldgx, alpha, beta, plan, nullptr, 0, st,
+                              "spx_spmm_t_noalloc");
 }
