@@ -333,6 +333,72 @@ def _oracle_pass(A, X, G, rows):
     return sub, time.perf_counter() - t0
 
 
+# ----------------------------------------------------------------------------- SpGEMM / CG
+def _ev_time(fn, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def spgemm_section():
+    """C = A B forward (numeric on a fixed pattern) and both gradients; symbolic timed apart."""
+    import synth
+    import torch
+    import paper_2212_05159_gb300 as spx
+    out = {}
+    cases = {"poisson3d 64^3 squared": lambda: (synth.poisson3d(64),) * 2,
+             "random 8/row n=262144": lambda: (synth.random_k_per_row(262144, 8, seed=1),
+                                               synth.random_k_per_row(262144, 8, seed=2))}
+    for name, mk in cases.items():
+        A, B = mk()
+        A = synth.with_values(A, synth.uniform(A.nnz, seed=3))
+        B = synth.with_values(B, synth.uniform(B.nnz, seed=4))
+        dA, dB = spx.CSR.from_host(A), spx.CSR.from_host(B)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = spx.SpGEMMPlan(dA, dB)
+        torch.cuda.synchronize()
+        sym_ms = (time.perf_counter() - t0) * 1e3
+        dA.transpose_pattern()
+        cv = torch.empty(plan.C.nnz, device="cuda")
+        gc = torch.randn(plan.C.nnz, device="cuda")
+        num_ms = _ev_time(lambda: plan.numeric(out=cv))
+        bwd_ms = _ev_time(lambda: plan.backward(gc))
+        m, nA, nB, nC, P = A.m, A.nnz, B.nnz, plan.C.nnz, plan.products
+        num_bytes = 4 * (m + 1) + 8 * nA + 8 * nA + 8 * P + 4 * (m + 1) + 4 * nC + 4 * nC
+        bwd_bytes = (4 * (m + 1) + 8 * nA + 8 * P + 4 * (m + 1) + 8 * nC + 4 * nA) + \
+                    (4 * (B.m + 1) + 8 * nA + 4 * nA + 8 * nB + 8 * P + 4 * nB)
+        hbm, _ = measured_peaks()
+        out[name] = {"m": m, "nnz_A": nA, "nnz_B": nB, "nnz_C": nC, "products": P,
+                     "symbolic_ms_host_timed": sym_ms, "numeric_ms": num_ms, "backward_ms": bwd_ms,
+                     "numeric_gbs": num_bytes / (num_ms * 1e-3) / 1e9,
+                     "backward_gbs": bwd_bytes / (bwd_ms * 1e-3) / 1e9,
+                     "numeric_frac_of_peak": num_bytes / (num_ms * 1e-3) / 1e9 / hbm,
+                     "bytes_model": "A, B rows per product (index+value), C pattern and values once"}
+    return out
+
+
+def cg_section(args):
+    """CG time to a true relative residual of 1e-8: the 256-system Jacobi batch (one persistent
+    launch replayed from a CUDA graph) and learned vs Jacobi vs IC(0) on held-out 256^2 systems."""
+    from paper_2212_05159_gb300 import learned, pcg_study
+    out = {"batch256_jacobi": pcg_study.batch256_jacobi(graph_replay=True)}
+    net = learned.MPNN(seed=0)
+    steps = 313 if args.cg_full else args.train_steps
+    tr = pcg_study.train(net, steps=steps, batch=32, n_it=8, gamma=0.8, lr=2e-3)
+    tr.pop("loss_history", None)
+    out["training"] = tr
+    out["eval_256x256"] = pcg_study.evaluate(net, nsys=1000 if args.cg_full else args.eval_systems, per_batch=64)
+    return out
+
+
 # ----------------------------------------------------------------------------- main
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -368,6 +434,9 @@ def main():
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cg-full", action="store_true", help="10k training systems, 1k evaluation systems")
+    ap.add_argument("--train-steps", type=int, default=150, help="training batches of 32 systems")
+    ap.add_argument("--eval-systems", type=int, default=128)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -431,6 +500,11 @@ def main():
                               "frac_of_peak": sum(cb2.values()) / (ms2 * 1e-3) / 1e9 / hbm,
                               "per_kernel_ms": per2, "tuning": W.tuning}
         line["extras"] = extras
+    if not args.no_extras and rank == 0:
+        del W
+        torch.cuda.empty_cache()
+        line["spgemm"] = spgemm_section()
+        line["cg"] = cg_section(args)
     if rank == 0 and not args.no_cpu:
         v, desc, cores = cpu_baseline(k=args.k)
         line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}

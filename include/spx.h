@@ -289,6 +289,11 @@ spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys
                           double delta, int32_t* iters, int32_t* status, double* relres,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* Launch shape of spx_cg_batched for this process: threads per block (256, 512 or 1024)
+ * and blocks per cluster (1, 2, 4 or 8); 0 keeps the default (512, 8).  A tuning knob:
+ * results do not depend on it beyond floating-point rounding of the reductions. */
+spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t cluster_size);
+
 /* dinv[i] = 1 / a_ii (0 where the diagonal is absent or zero); device float32[m]. */
 spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream);
 

@@ -25,6 +25,8 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace cg = cooperative_groups;
@@ -32,8 +34,7 @@ namespace cg = cooperative_groups;
 namespace spx {
 namespace {
 
-constexpr int CG_THREADS = 512;
-constexpr int CG_WARPS = CG_THREADS / 32;
+constexpr int CG_MAX_WARPS = 32;
 
 struct CgArgs {
     int32_t nsys;
@@ -89,7 +90,7 @@ __device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + 
 
 // Sums NV values over the cluster: block tree in FP64, then the CL block partials read
 // through DSMEM in rank order.  slot alternates so one barrier per reduction suffices.
-template <int NV>
+template <int NT, int NV>
 __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[NV], double (*red)[4],
                                            double (*part)[4], int& slot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -106,7 +107,7 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[N
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double s = 0.0;
-            for (int w = 0; w < CG_WARPS; ++w) s += red[w][k];
+            for (int w = 0; w < NT / 32; ++w) s += red[w][k];
             part[slot][k] = s;
         }
     }
@@ -122,31 +123,62 @@ __device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[N
     slot ^= 1;
 }
 
+// One row of a sparse product, entries in order; the loads of up to 8 entries are issued
+// together (predicated tail) so that a row costs two dependent round trips, not one per
+// entry.
 __device__ __forceinline__ float spmv_row(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                           const float* __restrict__ val, const float* __restrict__ x, int i) {
+    const int b = ptr[i], e = ptr[i + 1];
     float s = 0.f;
-    for (int e = ptr[i]; e < ptr[i + 1]; ++e) s = fmaf(val[e], x[idx[e]], s);
+    int k = b;
+    for (; k + 8 <= e; k += 8) {
+        int j[8];
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            j[q] = idx[k + q];
+            v[q] = val[k + q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s = fmaf(v[q], x[j[q]], s);
+    }
+    int j[8];
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const bool ok = k + q < e;
+        j[q] = ok ? idx[k + q] : i;
+        v[q] = ok ? val[k + q] : 0.f;
+    }
+    float t[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t[q] = x[j[q]];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (k + q < e) s = fmaf(v[q], t[q], s);
     return s;
 }
 
 // z = M r on rows [lo, hi) of the system (the caller barriers around LLT's two halves)
+template <int NT>
 __device__ __forceinline__ void apply_pc_local(const CgArgs& a, int lo, int hi) {
     if (a.pc == 1) {
-        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) a.z[i] = a.dinv[i] * a.r[i];
+        for (int i = lo + threadIdx.x; i < hi; i += NT) a.z[i] = a.dinv[i] * a.r[i];
     } else if (a.pc == 0) {
-        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) a.z[i] = a.r[i];
+        for (int i = lo + threadIdx.x; i < hi; i += NT) a.z[i] = a.r[i];
     }
 }
 
 // IC(0): z = L^-T L^-1 r with level-scheduled triangular solves, run by the cluster's
 // first block (block barriers between levels) while the others wait at the cluster
 // barrier.  L: lower CSR (diagonal last in each row); LT: its transpose (diagonal first).
+template <int NT>
 __device__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) {
     if (rank != 0) return;
     const int32_t* lp = a.lev_ptr + a.lev_off[sid];
     const int nl = a.lev_off[sid + 1] - a.lev_off[sid] - 1;
     for (int l = 0; l < nl; ++l) {
-        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += CG_THREADS) {
+        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += NT) {
             const int i = a.lev_rows[q];
             const int e1 = a.l_ptr[i + 1] - 1;
             float s = a.r[i];
@@ -156,7 +188,7 @@ __device__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) {
         __syncthreads();
     }
     for (int l = nl - 1; l >= 0; --l) {
-        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += CG_THREADS) {
+        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += NT) {
             const int i = a.lev_rows[q];
             const int e0 = a.lt_ptr[i];
             float s = a.w[i];
@@ -167,31 +199,33 @@ __device__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) {
     }
 }
 
+template <int NT>
 __device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi, unsigned rank, int sid) {
     if (a.pc == 4) {
         cl.sync();                                               // r complete
-        ic0_apply(a, rank, sid);
+        ic0_apply<NT>(a, rank, sid);
         cl.sync();                                               // z complete
     } else if (a.pc == 3) {
         cl.sync();                                               // r complete
-        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
+        for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.r, i);      // z = M r
     } else if (a.pc == 2) {
         cl.sync();                                               // r complete
-        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
+        for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.w[i] = spmv_row(a.lt_ptr, a.lt_idx, a.lt_val, a.r, i);   // w = L^T r
         cl.sync();                                               // w complete
-        for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS)
+        for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.w, i);      // z = L w
     } else {
-        apply_pc_local(a, lo, hi);
+        apply_pc_local<NT>(a, lo, hi);
     }
 }
 
 // r = b - A x in FP64 on [lo, hi); returns the thread's partial of ||r||^2 in FP64.
+template <int NT>
 __device__ __forceinline__ double true_residual(const CgArgs& a, int lo, int hi) {
     double s = 0.0;
-    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+    for (int i = lo + threadIdx.x; i < hi; i += NT) {
         double t = (double)a.b[i];
         for (int e = a.a_ptr[i]; e < a.a_ptr[i + 1]; ++e) t -= (double)a.a_val[e] * a.x[a.a_idx[e]];
         a.r[i] = (float)t;
@@ -200,11 +234,12 @@ __device__ __forceinline__ double true_residual(const CgArgs& a, int lo, int hi)
     return s;
 }
 
-__global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
+template <int NT>
+__global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank();
     const unsigned ncl = cl.num_blocks();
-    __shared__ double red[CG_WARPS][4];
+    __shared__ double red[CG_MAX_WARPS][4];
     __shared__ double part[2][4];
     __shared__ int sys_sh;
     int slot = 0;
@@ -224,7 +259,7 @@ __global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
         double v2[2] = {0.0, 0.0};
         {
             DF bb{0.f, 0.f};
-            for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+            for (int i = lo + threadIdx.x; i < hi; i += NT) {
                 const float bi = a.b[i];
                 a.x[i] = 0.0;
                 a.xp[i] = 0.f;
@@ -233,17 +268,17 @@ __global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
             }
             v2[0] = df_value(bb);
         }
-        apply_pc(a, cl, lo, hi, rank, sid);
+        apply_pc<NT>(a, cl, lo, hi, rank, sid);
         {
             DF rz{0.f, 0.f};
-            for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+            for (int i = lo + threadIdx.x; i < hi; i += NT) {
                 const float zi = a.z[i];
                 a.p[i] = zi;
                 df_add_prod(rz, a.r[i], zi);
             }
             v2[1] = df_value(rz);
         }
-        cluster_sum<2>(cl, v2, red, part, slot);
+        cluster_sum<NT, 2>(cl, v2, red, part, slot);
         const double bnorm = sqrt(v2[0]);
         double rz = v2[1];
         double ref = bnorm;                 // residual norm at the last fold
@@ -263,76 +298,113 @@ __global__ void __launch_bounds__(CG_THREADS) pcg_kernel(CgArgs a) {
                 double v1[1];
                 {
                     DF pq{0.f, 0.f};
-                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
-                        const float qi = spmv_row(a.a_ptr, a.a_idx, a.a_val, a.p, i);
-                        a.q[i] = qi;
-                        df_add_prod(pq, a.p[i], qi);
+                    const float* __restrict__ Pv = a.p;
+                    float* __restrict__ Qv = a.q;
+#pragma unroll 2
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                        const float qi = spmv_row(a.a_ptr, a.a_idx, a.a_val, Pv, i);
+                        Qv[i] = qi;
+                        df_add_prod(pq, Pv[i], qi);
                     }
                     v1[0] = df_value(pq);
                 }
-                cluster_sum<1>(cl, v1, red, part, slot);
+                cluster_sum<NT, 1>(cl, v1, red, part, slot);
                 const double pq = v1[0];
                 if (!isfinite(pq)) { status = SPX_NONFINITE; break; }
                 if (!(pq > 0.0)) { status = SPX_BREAKDOWN; break; }
                 const float alpha = (float)(rz / pq);
-                for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
-                    a.xp[i] = fmaf(alpha, a.p[i], a.xp[i]);
-                    a.r[i] = fmaf(-alpha, a.q[i], a.r[i]);
-                }
                 dirty = true;
                 ++it;
-                apply_pc(a, cl, lo, hi, rank, sid);
-                {
+                if (a.pc <= 1) {
+                    // x_p += alpha p; r -= alpha q; z = M r (local); <r, z>, <r, r> -- one pass
+                    float* __restrict__ XP = a.xp;
+                    float* __restrict__ R = a.r;
+                    float* __restrict__ Z = a.z;
+                    const float* __restrict__ Pv = a.p;
+                    const float* __restrict__ Qv = a.q;
+                    const float* __restrict__ DI = a.dinv;
                     DF rzs{0.f, 0.f}, rrs{0.f, 0.f};
-                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
-                        const float ri = a.r[i];
-                        df_add_prod(rzs, ri, a.z[i]);
+#pragma unroll 2
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                        XP[i] = fmaf(alpha, Pv[i], XP[i]);
+                        const float ri = fmaf(-alpha, Qv[i], R[i]);
+                        R[i] = ri;
+                        const float zi = a.pc == 1 ? DI[i] * ri : ri;
+                        Z[i] = zi;
+                        df_add_prod(rzs, ri, zi);
+                        df_add_prod(rrs, ri, ri);
+                    }
+                    v2[0] = df_value(rzs);
+                    v2[1] = df_value(rrs);
+                } else {
+                    float* __restrict__ XP = a.xp;
+                    float* __restrict__ R = a.r;
+                    const float* __restrict__ Pv = a.p;
+                    const float* __restrict__ Qv = a.q;
+#pragma unroll 2
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                        XP[i] = fmaf(alpha, Pv[i], XP[i]);
+                        R[i] = fmaf(-alpha, Qv[i], R[i]);
+                    }
+                    apply_pc<NT>(a, cl, lo, hi, rank, sid);
+                    DF rzs{0.f, 0.f}, rrs{0.f, 0.f};
+                    const float* __restrict__ Rc = a.r;
+                    const float* __restrict__ Zc = a.z;
+#pragma unroll 2
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                        const float ri = Rc[i];
+                        df_add_prod(rzs, ri, Zc[i]);
                         df_add_prod(rrs, ri, ri);
                     }
                     v2[0] = df_value(rzs);
                     v2[1] = df_value(rrs);
                 }
-                cluster_sum<2>(cl, v2, red, part, slot);
+                cluster_sum<NT, 2>(cl, v2, red, part, slot);
                 double rz_new = v2[0];
                 const double rnorm = sqrt(v2[1]);
                 if (!isfinite(rz_new) || !isfinite(rnorm)) { status = SPX_NONFINITE; break; }
                 if (rnorm <= a.delta * ref || rnorm <= a.tol * bnorm) {
                     // ---- reliable update: fold xp into x (FP64), true residual in FP64
-                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
                         a.x[i] += (double)a.xp[i];
                         a.xp[i] = 0.f;
                     }
                     dirty = false;
                     cl.sync();                                  // x complete
-                    double v64[1] = {true_residual(a, lo, hi)};
-                    cluster_sum<1>(cl, v64, red, part, slot);
+                    double v64[1] = {true_residual<NT>(a, lo, hi)};
+                    cluster_sum<NT, 1>(cl, v64, red, part, slot);
                     const double tn = sqrt(v64[0]);
                     last_true = tn / bnorm;
                     ref = tn;
                     if (!isfinite(tn)) { status = SPX_NONFINITE; break; }
                     if (tn <= a.tol * bnorm) { status = SPX_OK; break; }
-                    apply_pc(a, cl, lo, hi, rank, sid);
+                    apply_pc<NT>(a, cl, lo, hi, rank, sid);
                     DF rzs{0.f, 0.f};
-                    for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) df_add_prod(rzs, a.r[i], a.z[i]);
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) df_add_prod(rzs, a.r[i], a.z[i]);
                     double vz[1] = {df_value(rzs)};
-                    cluster_sum<1>(cl, vz, red, part, slot);
+                    cluster_sum<NT, 1>(cl, vz, red, part, slot);
                     rz_new = vz[0];
                 }
                 if (!(rz_new > 0.0)) { status = SPX_BREAKDOWN; break; }
                 const float beta = (float)(rz_new / rz);
                 rz = rz_new;
-                for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) a.p[i] = fmaf(beta, a.p[i], a.z[i]);
+                {
+                    float* __restrict__ Pv = a.p;
+                    const float* __restrict__ Zc = a.z;
+#pragma unroll 4
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) Pv[i] = fmaf(beta, Pv[i], Zc[i]);
+                }
             }
         }
         if (dirty) {
             // fold the remainder and report the true residual of the returned x
-            for (int i = lo + threadIdx.x; i < hi; i += CG_THREADS) {
+            for (int i = lo + threadIdx.x; i < hi; i += NT) {
                 a.x[i] += (double)a.xp[i];
                 a.xp[i] = 0.f;
             }
             cl.sync();
-            double v64[1] = {true_residual(a, lo, hi)};
-            cluster_sum<1>(cl, v64, red, part, slot);
+            double v64[1] = {true_residual<NT>(a, lo, hi)};
+            cluster_sum<NT, 1>(cl, v64, red, part, slot);
             last_true = bnorm > 0.0 ? sqrt(v64[0]) / bnorm : 0.0;
         }
         if (rank == 0 && threadIdx.x == 0) {
@@ -365,7 +437,9 @@ __global__ void masked_outer_f64_kernel(int32_t m, const int32_t* __restrict__ p
     for (int e = ptr[row] + lane; e < ptr[row + 1]; e += 32) out[e] = (float)(ui * v[idx[e]]);
 }
 
-int cg_cluster_size() { return 8; }
+// Launch shape of the batched PCG (threads per block, blocks per cluster); 0 = default.
+std::atomic<int> g_cg_threads{0};
+std::atomic<int> g_cg_cluster{0};
 
 }  // namespace
 }  // namespace spx
@@ -448,13 +522,15 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     }
     SPX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "spx_cg_batched memset");
 
-    const int cl = cg_cluster_size();
-    int clusters = 2 * num_sms() / cl;
+    const int nt = g_cg_threads.load() > 0 ? g_cg_threads.load() : 512;
+    const int cl = g_cg_cluster.load() > 0 ? g_cg_cluster.load() : 8;
+    const int blocks_per_sm = nt >= 1024 ? 1 : 1024 / nt;      // ~64 registers per thread
+    int clusters = blocks_per_sm * num_sms() / cl;
     if (clusters < 1) clusters = 1;
     if (clusters > nsys) clusters = nsys;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(clusters * cl));
-    cfg.blockDim = dim3(CG_THREADS);
+    cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -464,7 +540,13 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel, a), "spx_cg_batched launch");
+    if (nt == 256) {
+        SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel<256>, a), "spx_cg_batched launch");
+    } else if (nt == 1024) {
+        SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel<1024>, a), "spx_cg_batched launch");
+    } else {
+        SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel<512>, a), "spx_cg_batched launch");
+    }
     return SPX_OK;
 }
 
@@ -487,5 +569,15 @@ extern "C" spx_status spx_masked_outer_f64(const spx_csr* A, const double* u, co
     masked_outer_f64_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, as_stream(stream)>>>(
         A->m, A->indptr, A->indices, u, v, scale, out);
     SPX_CHECK_LAUNCH("spx_masked_outer_f64");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t cluster_size) {
+    if (!(threads_per_block == 0 || threads_per_block == 256 || threads_per_block == 512 ||
+          threads_per_block == 1024) ||
+        !(cluster_size == 0 || cluster_size == 1 || cluster_size == 2 || cluster_size == 4 || cluster_size == 8))
+        return set_error(SPX_INVALID_ARG, "spx_cg_set_launch: threads in {256, 512, 1024}, cluster in {1, 2, 4, 8}");
+    g_cg_threads.store(threads_per_block);
+    g_cg_cluster.store(cluster_size);
     return SPX_OK;
 }

@@ -30,6 +30,11 @@ class SystemBatch:
         # largest systems first: the longest solves start first (load balance)
         self.order = torch.from_numpy(np.argsort(-sizes, kind="stable").astype(np.int32)).to(A.device)
         self.ws = abi.workspace(abi.spx_cg_workspace_size(A.m), A.device)
+        # launch shape: 512-thread blocks, a cluster sized so a block owns ~8192 rows of an
+        # average system (measured best on GB300 for 2D diffusion batches)
+        mean_rows = float(sizes.mean()) if sizes.size else 1.0
+        cl = 2 ** int(round(np.log2(max(mean_rows / 8192.0, 1.0))))
+        self.launch = (512, int(min(8, max(1, cl))))
         self._dinv = None
         self.iters = torch.zeros(self.nsys, dtype=torch.int32, device=A.device)
         self.status = torch.zeros(self.nsys, dtype=torch.int32, device=A.device)
@@ -125,6 +130,7 @@ def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor |
             raise ValueError("pc='ic0' needs an IC0")
         L, LT = ic0.structs()
         levels = ic0.levels
+    abi.spx_cg_set_launch(*batch.launch)
     abi.spx_cg_batched(A.struct(values), batch.sys_ptr, batch.nsys, batch.order, b.contiguous(), x, kind,
                        dinv, L, LT, tol, maxit, delta, batch.iters, batch.status, batch.relres, batch.ws,
                        ic0_levels=levels)
