@@ -202,8 +202,8 @@ class Workload:
         rp = lambda cb: 1 if cb < k else 0  # noqa: E731  (slab repack launch)
         self.launches = (npass(self.plan.col_block) + rp(self.plan.col_block) + npass(self.sddmm_cb)
                          + rp(self.sddmm_cb) + 1 + npass(self.t_plan.col_block) + rp(self.t_plan.col_block))
-        self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group],
-                       "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group],
+        self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine],
+                       "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group, self.t_plan.engine],
                        "sddmm_col_block": self.sddmm_cb}
         self.abi = abi
         self.m, self.n, self.nnz = A.m, A.n, A.nnz

@@ -73,9 +73,18 @@ typedef struct spx_rowplan {
                                  pass per block keeps the gathered slab of the dense
                                  operand resident in L2 */
     int32_t rows_per_group;   /* rows walked by one lane group (0 = default) */
+    int32_t engine;           /* gathers of the dense rows: 0 = loads into registers,
+                                 1 = TMA-engine bulk copies into shared memory (needs k and
+                                 the leading dimensions multiples of 4 and 16-byte aligned
+                                 operands; otherwise 0 is used) */
 } spx_rowplan;
 
 /* ------------------------------------------------------------------ library */
+
+/* Waits for `stream`, then reads and clears the library's device-side error word:
+ * SPX_DEVICE_TIMEOUT if a kernel's bounded wait (e.g. on a TMA copy) ran out since the
+ * last check, else SPX_OK. */
+spx_status spx_check_device(void* stream);
 
 /* Message of the most recent failure on the calling thread ("" if none). */
 const char* spx_last_error(void);

@@ -44,7 +44,7 @@ class spx_csr(ctypes.Structure):
 class spx_rowplan(ctypes.Structure):
     _fields_ = [("long_rows", ctypes.c_void_p), ("n_long", ctypes.c_int32),
                 ("threshold", ctypes.c_int32), ("col_block", ctypes.c_int32),
-                ("rows_per_group", ctypes.c_int32)]
+                ("rows_per_group", ctypes.c_int32), ("engine", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -59,6 +59,7 @@ _PLANP = ctypes.POINTER(spx_rowplan)
 # name -> argtypes (every entry point returns spx_status, an int)
 SIGNATURES = {
     "spx_csr_validate": [_CSRP, _P, _SZ, _P],
+    "spx_check_device": [_P],
     "spx_rowplan_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_rowplan_build": [_CSRP, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
     "spx_spmm_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
@@ -170,6 +171,11 @@ def spx_version() -> int:
     return int(lib().spx_version())
 
 
+def spx_check_device() -> None:
+    """Raises SpxError(SPX_DEVICE_TIMEOUT) if a bounded device-side wait ran out."""
+    _check(lib().spx_check_device(_stream()), "spx_check_device")
+
+
 def spx_csr_validate(A: spx_csr, device) -> None:
     ws = workspace(16, device)
     _check(lib().spx_csr_validate(ctypes.byref(A), ptr(ws), ws.numel(), _stream()),
@@ -186,7 +192,7 @@ def spx_rowplan_build(A: spx_csr, threshold: int, device):
     _check(lib().spx_rowplan_build(ctypes.byref(A), int(threshold), ptr(rows), ctypes.byref(n_long),
                                    ptr(ws), ws.numel(), _stream()), "spx_rowplan_build")
     rows = rows[: n_long.value].clone() if n_long.value > 0 else rows[:0]
-    plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold), 0, 0)
+    plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold), 0, 0, 0)
     return rows, plan
 
 

@@ -7,6 +7,20 @@
 
 namespace spx {
 
+__device__ int g_spx_device_error = 0;
+
+int* device_error_word() {
+    static int* cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!cached[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_spx_device_error) != cudaSuccess) return nullptr;
+        cached[dev] = static_cast<int*>(p);
+    }
+    return cached[dev];
+}
+
 static thread_local char g_msg[512] = "";
 
 spx_status set_error(spx_status st, const char* fmt, ...) {
@@ -120,5 +134,17 @@ extern "C" spx_status spx_csr_validate(const spx_csr* A, void* ws, size_t ws_byt
     SPX_CUDA(cudaStreamSynchronize(st), "spx_csr_validate sync");
     if (h & 1) return set_error(SPX_BAD_PATTERN, "spx_csr_validate: indptr/indices out of range");
     if (h & 2) return set_error(SPX_UNSORTED, "spx_csr_validate: columns not strictly increasing");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_check_device(void* stream) {
+    cudaStream_t st = as_stream(stream);
+    SPX_CUDA(cudaStreamSynchronize(st), "spx_check_device sync");
+    int h = 0, zero = 0;
+    SPX_CUDA(cudaMemcpyFromSymbol(&h, g_spx_device_error, sizeof(int)), "spx_check_device read");
+    if (h) {
+        SPX_CUDA(cudaMemcpyToSymbol(g_spx_device_error, &zero, sizeof(int)), "spx_check_device clear");
+        return set_error(SPX_DEVICE_TIMEOUT, "a bounded device-side wait ran out (flags 0x%x)", h);
+    }
     return SPX_OK;
 }

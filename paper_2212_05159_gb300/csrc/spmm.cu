@@ -204,6 +204,179 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Short rows through the TMA engine.  Each lane group keeps a ring of BK_DEPTH batch slots
+// in shared memory; for every batch (up to 8 entries of one row) the group's lanes issue
+// one cp.async.bulk row copy per entry (X row segment -> slot) counted on the slot's
+// mbarrier, so up to BK_DEPTH batches of row gathers are in flight per group without
+// occupying registers.  The consumer walks the slots in order and accumulates; rows are
+// finished in order, each output a fixed-order sum as in the register path.  A wait that
+// does not complete within 2 s records a device error and ends the group's work.
+constexpr int BK_WARPS = 4;
+constexpr int BK_DEPTH = 4;
+constexpr int BK_WARP_FLOATS = 32 * 4 * BK_DEPTH * BATCH;   // G * D * BATCH * (4 * LPR) = 4096 floats
+
+size_t bulk_smem_bytes() {
+    const size_t bufs = (size_t)BK_WARPS * BK_WARP_FLOATS * 4;            // row slots
+    const size_t vals = (size_t)BK_WARPS * 32 * BK_DEPTH * BATCH * 4;     // <= 32 groups per warp
+    const size_t meta = (size_t)BK_WARPS * 32 * BK_DEPTH * 4 * 4;         // row, count, last, pad
+    const size_t bars = (size_t)BK_WARPS * 32 * BK_DEPTH * 8;
+    return bufs + vals + meta + bars;
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(BK_WARPS * 32) spmm_bulk_kernel(
+    int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+    const float* __restrict__ vals, const float* __restrict__ X, int64_t ldx, int32_t x_shift, int32_t col_begin,
+    int32_t col_end, float* __restrict__ Y, int64_t ldy, float alpha, float beta, int32_t rows_per_group,
+    int32_t threshold, int* __restrict__ err) {
+    constexpr int G = 32 / LPR;
+    constexpr int SLOTS = (BATCH + LPR - 1) / LPR;
+    constexpr int CB = 4 * LPR;                                 // floats per slot row
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / LPR, c = lane % LPR;
+    const unsigned gmask = LPR == 32 ? FULL : (((1u << LPR) - 1u) << (g * LPR));
+    const int gid = warp * G + g;                                // group id within the block
+    float* buf = reinterpret_cast<float*>(smem) + (size_t)gid * BK_DEPTH * BATCH * CB;
+    float* sv = reinterpret_cast<float*>(smem + (size_t)BK_WARPS * BK_WARP_FLOATS * 4) +
+                (size_t)gid * BK_DEPTH * BATCH;
+    int* meta = reinterpret_cast<int*>(smem + (size_t)BK_WARPS * BK_WARP_FLOATS * 4 +
+                                       (size_t)BK_WARPS * 32 * BK_DEPTH * BATCH * 4) +
+                (size_t)gid * BK_DEPTH * 4;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)BK_WARPS * BK_WARP_FLOATS * 4 +
+                                                 (size_t)BK_WARPS * 32 * BK_DEPTH * BATCH * 4 +
+                                                 (size_t)BK_WARPS * 32 * BK_DEPTH * 16) +
+                     (size_t)gid * BK_DEPTH;
+    if (c == 0)
+        for (int s = 0; s < BK_DEPTH; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    fence_mbar_init();
+    __syncthreads();
+
+    const int cbw = col_end - col_begin;                         // floats copied per entry
+    const uint32_t rowbytes = (uint32_t)cbw * 4u;
+    const int col = col_begin + c * 4;
+    const bool colok = col < col_end;
+    const int64_t wglobal = ((int64_t)blockIdx.x * BK_WARPS + warp);
+    const int64_t row0 = (wglobal * G + g) * rows_per_group;
+    const int64_t row_end = row0 + rows_per_group < m ? row0 + rows_per_group : m;
+    const float* Xc = X + (col_begin - x_shift);
+
+    // producer cursor
+    int64_t prow = row0 - 1;
+    int pe = 0, pb = 0;
+    bool pending_empty = false;
+    // advance to the next batch: returns false when the group's rows are exhausted
+    auto next_batch = [&](int64_t& row, int& e0, int& cnt, int& last) -> bool {
+        for (;;) {
+            if (pending_empty) {                      // an empty row still needs its store
+                pending_empty = false;
+                row = prow;
+                e0 = pe;
+                cnt = 0;
+                last = 1;
+                return true;
+            }
+            if (pe < pb) {
+                row = prow;
+                e0 = pe;
+                cnt = pb - pe < BATCH ? pb - pe : BATCH;
+                last = (pe + cnt == pb) ? 1 : 0;
+                pe += cnt;
+                return true;
+            }
+            ++prow;
+            if (prow >= row_end) return false;
+            const int a = indptr[prow], b = indptr[prow + 1];
+            if (b - a > threshold) {                  // a long-row block takes it
+                pe = pb = b;
+                continue;
+            }
+            pe = a;
+            pb = b;
+            if (a == b) pending_empty = true;
+        }
+    };
+    auto produce = [&](int s) -> bool {
+        int64_t row;
+        int e0, cnt, last;
+        if (!next_batch(row, e0, cnt, last)) return false;
+        int jl[SLOTS];
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            const int q = c * SLOTS + t;
+            jl[t] = -1;
+            if (q < cnt) {
+                jl[t] = indices[e0 + q];
+                sv[s * BATCH + q] = vals[e0 + q];
+            }
+        }
+        if (c == 0) {
+            meta[s * 4 + 0] = (int)row;
+            meta[s * 4 + 1] = cnt;
+            meta[s * 4 + 2] = last;
+        }
+        fence_proxy_async();                              // slot reads done before new writes
+        __syncwarp(gmask);
+        if (c == 0) mbar_arrive_expect_tx(smem_u32(&bars[s]), (uint32_t)cnt * rowbytes);
+        __syncwarp(gmask);
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            const int q = c * SLOTS + t;
+            if (q < cnt)
+                bulk_g2s(smem_u32(buf + (size_t)(s * BATCH + q) * CB), Xc + (int64_t)jl[t] * ldx, rowbytes,
+                         smem_u32(&bars[s]));
+        }
+        return true;
+    };
+
+    unsigned phase = 0;                                          // parity bit per slot
+    int filled = 0;
+    for (int s = 0; s < BK_DEPTH; ++s) {
+        if (!produce(s)) break;
+        ++filled;
+    }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int s = 0;
+    bool ok = true;
+    while (filled > 0) {
+        if (ok && !mbar_wait(smem_u32(&bars[s]), (phase >> s) & 1u, 2000000000ull)) {
+            ok = false;
+            if (c == 0 && err) atomicOr(err, 1);
+        }
+        phase ^= 1u << s;
+        --filled;
+        if (ok) {
+            __syncwarp(gmask);
+            const int row = meta[s * 4 + 0], cnt = meta[s * 4 + 1], last = meta[s * 4 + 2];
+            if (colok) {
+                for (int q = 0; q < cnt; ++q) {
+                    const float v = sv[s * BATCH + q];
+                    const float4 x = *reinterpret_cast<const float4*>(buf + (size_t)(s * BATCH + q) * CB + c * 4);
+                    acc[0] = fmaf(v, x.x, acc[0]);
+                    acc[1] = fmaf(v, x.y, acc[1]);
+                    acc[2] = fmaf(v, x.z, acc[2]);
+                    acc[3] = fmaf(v, x.w, acc[3]);
+                }
+                if (last) {
+                    store_row<4>(Y + (int64_t)row * ldy + col, acc, alpha, beta);
+                    acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
+                }
+            }
+            __syncwarp(gmask);
+            if (produce(s)) ++filled;
+        } else {
+            // give the copies already in flight a bounded time to land, then stop
+            for (int r = 0; r < filled; ++r) {
+                const int t = (s + 1 + r) % BK_DEPTH;
+                mbar_wait(smem_u32(&bars[t]), (phase >> t) & 1u, 100000000ull);
+            }
+            break;
+        }
+        s = (s + 1) % BK_DEPTH;
+    }
+}
+
 __global__ void gather_values_kernel(int64_t nnz, const int32_t* __restrict__ perm, const float* __restrict__ vals,
                                      float* __restrict__ out) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -292,6 +465,52 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
     const int64_t grid = short_blocks + long_blocks;
     if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
     if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, sh.cb, slab_ws, st));
+    const bool bulk = !PERM && vec4 && plan && plan->engine == 1 && sh.cb % 4 == 0 && sh.lpr >= 2 &&
+                      sh.lpr * 4 >= sh.cb;
+    if (bulk) {
+        const size_t smem = bulk_smem_bytes();
+        const int64_t rows_per_bblock = (int64_t)BK_WARPS * G * sh.rpg;
+        const int64_t bgrid = ((int64_t)A->m + rows_per_bblock - 1) / rows_per_bblock;
+        if (bgrid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
+        int* err = device_error_word();
+        for (int32_t c0 = 0; c0 < k; c0 += sh.cb) {
+            const int32_t c1 = c0 + sh.cb < k ? c0 + sh.cb : k;
+            const float* Xp = use_slab ? slab_ws + (int64_t)(c0 / sh.cb) * A->n * sh.cb : X;
+            const int64_t ldp = use_slab ? sh.cb : ldx;
+            const int32_t xs = use_slab ? c0 : 0;
+#define SPX_BULK_CASE(L)                                                                                      \
+    case L: {                                                                                                 \
+        static bool attr_set = false;                                                                         \
+        if (!attr_set) {                                                                                      \
+            SPX_CUDA(cudaFuncSetAttribute(spmm_bulk_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                          (int)smem),                                                         \
+                     "spmm bulk attribute");                                                                  \
+            attr_set = true;                                                                                  \
+        }                                                                                                     \
+        spmm_bulk_kernel<L><<<(unsigned)bgrid, BK_WARPS * 32, smem, st>>>(                                    \
+            A->m, A->indptr, A->indices, vals, Xp, ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold, err); \
+        break;                                                                                                \
+    }
+            switch (sh.lpr) {
+                SPX_BULK_CASE(2)
+                SPX_BULK_CASE(4)
+                SPX_BULK_CASE(8)
+                SPX_BULK_CASE(16)
+                SPX_BULK_CASE(32)
+                default: return set_error(SPX_INVALID_ARG, "%s: bulk lane count %d", who, sh.lpr);
+            }
+#undef SPX_BULK_CASE
+            SPX_CHECK_LAUNCH(who);
+            if (long_blocks > 0) {
+                spx_status s = launch_lpr<4, false>(sh.lpr, (unsigned)long_blocks, st, A, perm, vals, Xp, ldp, xs, c0,
+                                                    c1, Y, ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long,
+                                                    long_blocks);
+                if (s != SPX_OK) return s;
+                SPX_CHECK_LAUNCH(who);
+            }
+        }
+        return SPX_OK;
+    }
     for (int32_t c0 = 0; c0 < k; c0 += sh.cb) {
         const int32_t c1 = c0 + sh.cb < k ? c0 + sh.cb : k;
         const float* Xp = use_slab ? slab_ws + (int64_t)(c0 / sh.cb) * A->n * sh.cb : X;

@@ -68,7 +68,7 @@ def _col_blocks(k: int):
 
 
 def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
-    """Best (col_block, rows_per_group) for spx_spmm (or spx_spmm_t when transposed)."""
+    """Best (col_block, rows_per_group, engine) for spx_spmm (or spx_spmm_t when transposed)."""
     kind = "spmm_t" if transposed else "spmm"
     key = _key(A, k, kind)
     with _lock:
@@ -81,9 +81,10 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
     Y = torch.empty(rows_out, k, device=dev)
     base = A.t_plan() if transposed else A.plan()
     best, best_ms, table = None, float("inf"), {}
-    for cb in _col_blocks(k):
-        for rpg in (1, 2, 4):
-            plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg)
+    engines = (0, 1) if k % 4 == 0 else (0,)
+    for cb, rpg, eng in [(cb, rpg, eng) for cb in _col_blocks(k) for rpg in (1, 2, 4) for eng in engines]:
+        if True:
+            plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg, eng)
             if transposed:
                 _, _, perm = A.transpose_pattern()
                 s = A.t_struct()
@@ -95,9 +96,9 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
                 fn = lambda: abi.spx_spmm(s, X, Y, 1.0, 0.0, plan, ws)  # noqa: E731
             ms = _time(fn)
             del ws
-            table[f"{cb},{rpg}"] = ms
+            table[f"{cb},{rpg},{eng}"] = ms
             if ms < best_ms:
-                best, best_ms = (cb, rpg), ms
+                best, best_ms = (cb, rpg, eng), ms
     with _lock:
         _load()[key] = {"best": list(best), "ms": best_ms, "table": table}
         _save()
@@ -131,5 +132,7 @@ def tune_sddmm(A: CSR, k: int, force: bool = False) -> int:
 
 def tuned_plan(A: CSR, k: int, transposed: bool = False):
     base = A.t_plan() if transposed else A.plan()
-    cb, rpg = tune_rows(A, k, transposed)
-    return abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg)
+    best = tune_rows(A, k, transposed)
+    cb, rpg = best[0], best[1]
+    eng = best[2] if len(best) > 2 else 0
+    return abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg, eng)

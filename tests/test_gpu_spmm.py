@@ -183,23 +183,26 @@ def test_full_size_powerlaw_sampled(k):
     np.testing.assert_array_equal(d_perm, perm)
 
 
-@pytest.mark.parametrize("cb,rpg", [(4, 1), (8, 3), (16, 2), (32, 4)])
-def test_tuning_variants_match_oracle(mat, cb, rpg):
-    """Every column-block / rows-per-group setting the autotuner may pick is correct."""
+@pytest.mark.parametrize("cb,rpg,engine", [(4, 1, 0), (8, 3, 0), (16, 2, 0), (32, 4, 0),
+                                           (8, 1, 1), (16, 3, 1), (32, 2, 1)])
+def test_tuning_variants_match_oracle(mat, cb, rpg, engine):
+    """Every column-block / rows-per-group / gather-engine setting the autotuner may pick is
+    correct (engine 1: TMA-engine bulk copies)."""
     from paper_2212_05159_gb300 import abi
     name, A, dA = mat
     k = 32
     X = synth.normal((A.n, k), seed=40)
     G = synth.normal((A.m, k), seed=41)
     base = dA.plan()
-    plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg)
+    plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg, engine)
     Y = torch.empty(A.m, k, device="cuda")
     ws = abi.workspace(abi.spx_spmm_workspace_size(dA.struct(), k, plan), "cuda")
     abi.spx_spmm(dA.struct(), dev(X), Y, 1.0, 0.0, plan, ws)
+    abi.spx_check_device()
     assert_close_normalised(host(Y), oracle.spmm(A, X), oracle.spmm(abs_csr(A), np.abs(X)),
-                            what=f"spmm {name} cb={cb} rpg={rpg}")
+                            what=f"spmm {name} cb={cb} rpg={rpg} engine={engine}")
     tb = dA.t_plan()
-    tplan = abi.spx_rowplan(tb.long_rows, tb.n_long, tb.threshold, cb, rpg)
+    tplan = abi.spx_rowplan(tb.long_rows, tb.n_long, tb.threshold, cb, rpg, engine)
     gX = torch.empty(A.n, k, device="cuda")
     _, _, perm = dA.transpose_pattern()
     abi.spx_spmm_t(dA.t_struct(), perm, dev(G), gX, 1.0, 0.0, tplan, None)   # gather through perm
@@ -207,6 +210,7 @@ def test_tuning_variants_match_oracle(mat, cb, rpg):
                             what=f"spmm_t {name} cb={cb} no workspace")
     abi.spx_spmm_t(dA.t_struct(), perm, dev(G), gX, 1.0, 0.0, tplan,
                    abi.workspace(abi.spx_spmm_t_workspace_size(dA.t_struct(), k, tplan), "cuda"))
+    abi.spx_check_device()
     assert_close_normalised(host(gX), oracle.spmm_t(A, G), oracle.spmm_t(abs_csr(A), np.abs(G)),
                             what=f"spmm_t {name} cb={cb}")
     out = torch.empty(A.nnz, device="cuda")
@@ -214,3 +218,20 @@ def test_tuning_variants_match_oracle(mat, cb, rpg):
                   abi.workspace(abi.spx_sddmm_workspace_size(dA.struct(), k, cb), "cuda"))
     assert_close_normalised(host(out), oracle.sddmm(A, G, X), oracle.sddmm(A, np.abs(G), np.abs(X)),
                             what=f"sddmm {name} cb={cb}")
+
+
+@pytest.mark.parametrize("k", [8, 32, 128])
+def test_bulk_engine_k_widths_and_alpha_beta(mat, k):
+    """TMA-engine gathers at each lane-group width, with alpha / beta and empty rows."""
+    from paper_2212_05159_gb300 import abi
+    name, A, dA = mat
+    X = synth.normal((A.n, k), seed=50 + k)
+    y0 = synth.normal((A.m, k), seed=60 + k)
+    base = dA.plan()
+    plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, k, 2, 1)
+    Y = dev(y0.copy())
+    abi.spx_spmm(dA.struct(), dev(X), Y, 0.5, -1.5, plan, None)
+    abi.spx_check_device()
+    ref = 0.5 * oracle.spmm(A, X) - 1.5 * y0.astype(np.float64)
+    norm = 0.5 * oracle.spmm(abs_csr(A), np.abs(X)) + 1.5 * np.abs(y0)
+    assert_close_normalised(host(Y), ref, norm, what=f"bulk spmm {name} k={k}")
