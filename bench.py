@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sparse fwd+bwd GB/s vs HBM peak"
+NO_TUNE = False
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -189,9 +190,15 @@ class Workload:
         # per-pattern setup (outside timed regions): transpose, row plans, autotuning
         from paper_2212_05159_gb300 import tune
         _, _, self.perm = self.dA.transpose_pattern()
-        self.plan = tune.tuned_plan(self.dA, k)
-        self.t_plan = tune.tuned_plan(self.dA, k, transposed=True)
-        self.sddmm_cb = tune.tune_sddmm(self.dA, k)
+        if NO_TUNE:
+            b, tb = self.dA.plan(), self.dA.t_plan()
+            self.plan = abi.spx_rowplan(b.long_rows, b.n_long, b.threshold, k, 4, 0)
+            self.t_plan = abi.spx_rowplan(tb.long_rows, tb.n_long, tb.threshold, k, 4, 0)
+            self.sddmm_cb = k
+        else:
+            self.plan = tune.tuned_plan(self.dA, k)
+            self.t_plan = tune.tuned_plan(self.dA, k, transposed=True)
+            self.sddmm_cb = tune.tune_sddmm(self.dA, k)
         self.s_A = self.dA.struct()
         self.s_AT = self.dA.t_struct()
         ws = lambda nb: abi.workspace(nb, device) if nb > 0 else None  # noqa: E731
@@ -434,6 +441,10 @@ def main():
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="fixed launch parameters (the tuned choice for this workload) instead of autotuning")
+    ap.add_argument("--sections", default="step,extras,spgemm,cg,cpu",
+                    help="comma list of: step (always), extras, spgemm, cg, cpu")
     ap.add_argument("--cg-full", action="store_true", help="10k training systems, 1k evaluation systems")
     ap.add_argument("--train-steps", type=int, default=150, help="training batches of 32 systems")
     ap.add_argument("--eval-systems", type=int, default=128)
@@ -441,6 +452,13 @@ def main():
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    secs = set(x.strip() for x in args.sections.split(","))
+    if args.no_extras:
+        secs -= {"extras", "spgemm", "cg"}
+    if args.no_cpu:
+        secs.discard("cpu")
+    global NO_TUNE
+    NO_TUNE = args.no_tune
 
     import torch
     if ws > 1:
@@ -488,7 +506,7 @@ def main():
         "gpu_launches": W.launches_per_step() * args.steps,
         "clocks": clk,
     }
-    if not args.no_extras and rank == 0:
+    if "extras" in secs and rank == 0:
         extras = {}
         for kind, k in (("powerlaw", 128), ("poisson3d", 32)):
             del W
@@ -500,12 +518,14 @@ def main():
                               "frac_of_peak": sum(cb2.values()) / (ms2 * 1e-3) / 1e9 / hbm,
                               "per_kernel_ms": per2, "tuning": W.tuning}
         line["extras"] = extras
-    if not args.no_extras and rank == 0:
+    if ("spgemm" in secs or "cg" in secs) and rank == 0:
         del W
         torch.cuda.empty_cache()
-        line["spgemm"] = spgemm_section()
-        line["cg"] = cg_section(args)
-    if rank == 0 and not args.no_cpu:
+        if "spgemm" in secs:
+            line["spgemm"] = spgemm_section()
+        if "cg" in secs:
+            line["cg"] = cg_section(args)
+    if rank == 0 and "cpu" in secs:
         v, desc, cores = cpu_baseline(k=args.k)
         line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:

@@ -178,3 +178,16 @@ def batch256_jacobi(graph_replay: bool = True, seed: int = 0, reps: int = 3):
             "graph_replay": graph_replay, "iters_total": int(it.sum()), "iters_max": int(it.max()),
             "converged": int((st == 0).sum()), "max_true_relres": float(rr.max()),
             "row_iterations_per_s": float((np.diff(ptr) * it).sum() / (np.median(times) * 1e-3))}
+
+
+if __name__ == "__main__":
+    # A small case for profiling the PCG kernel: 32 diffusion systems of side 64..96, Jacobi.
+    import synth
+    A, ptr, _, _ = synth.diffusion_batch(32, seed=5, side_lo=64, side_hi=96, sigma=1.0)
+    dA = CSR.from_host(A)
+    batch = solve.SystemBatch(dA, ptr)
+    b = torch.from_numpy(synth.normal(A.m, seed=6)).cuda()
+    for _ in range(2):
+        _, it, st, rr = solve.cg(batch, b, pc="jacobi")
+    torch.cuda.synchronize()
+    print("pcg profile case:", int(it.sum()), "iterations,", int((st == 0).sum()), "converged")
