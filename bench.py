@@ -192,8 +192,8 @@ class Workload:
         _, _, self.perm = self.dA.transpose_pattern()
         if NO_TUNE:
             b, tb = self.dA.plan(), self.dA.t_plan()
-            self.plan = abi.spx_rowplan(b.long_rows, b.n_long, b.threshold, k, 4, 0)
-            self.t_plan = abi.spx_rowplan(tb.long_rows, tb.n_long, tb.threshold, k, 4, 0)
+            self.plan = b.with_params(k, 4, 0)
+            self.t_plan = tb.with_params(k, 4, 0)
             self.sddmm_cb = k
         else:
             self.plan = tune.tuned_plan(self.dA, k)

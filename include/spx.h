@@ -77,6 +77,10 @@ typedef struct spx_rowplan {
                                  1 = TMA-engine bulk copies into shared memory (needs k and
                                  the leading dimensions multiples of 4 and 16-byte aligned
                                  operands; otherwise 0 is used) */
+    const int32_t* medium_rows; /* device int32[n_medium]: rows with medium_threshold < length
+                                   <= threshold, one warp each (NULL / 0 = none) */
+    int32_t n_medium;
+    int32_t medium_threshold;
 } spx_rowplan;
 
 /* ------------------------------------------------------------------ library */
@@ -118,6 +122,14 @@ spx_status spx_rowplan_build(const spx_csr* A, int32_t threshold, int32_t* long_
  * gathered operand fits the L2 budget, or k is not a multiple of 4). */
 spx_status spx_spmm_workspace_size(const spx_csr* A, int32_t k, const spx_rowplan* plan,
                                    size_t* bytes);
+
+/* Builds the medium-row list of a plan: ids of rows with medium_threshold < length <=
+ * long_threshold, increasing, into medium_rows (device int32[m]), count to
+ * *n_medium_host.  Same workspace as spx_rowplan_build.  Synchronizes `stream`. */
+spx_status spx_rowplan_build_medium(const spx_csr* A, int32_t medium_threshold,
+                                    int32_t long_threshold, int32_t* medium_rows,
+                                    int32_t* n_medium_host, void* workspace,
+                                    size_t workspace_bytes, void* stream);
 
 /* Sparse x dense product (Section 3.1.3; SpMV of Section 3.1.1 when k = 1):
  *   Y = alpha * A X + beta * Y.

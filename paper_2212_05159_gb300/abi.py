@@ -44,7 +44,14 @@ class spx_csr(ctypes.Structure):
 class spx_rowplan(ctypes.Structure):
     _fields_ = [("long_rows", ctypes.c_void_p), ("n_long", ctypes.c_int32),
                 ("threshold", ctypes.c_int32), ("col_block", ctypes.c_int32),
-                ("rows_per_group", ctypes.c_int32), ("engine", ctypes.c_int32)]
+                ("rows_per_group", ctypes.c_int32), ("engine", ctypes.c_int32),
+                ("medium_rows", ctypes.c_void_p), ("n_medium", ctypes.c_int32),
+                ("medium_threshold", ctypes.c_int32)]
+
+    def with_params(self, col_block=0, rows_per_group=0, engine=0):
+        """A copy of this plan (same row lists) with other launch parameters."""
+        return spx_rowplan(self.long_rows, self.n_long, self.threshold, col_block, rows_per_group, engine,
+                           self.medium_rows, self.n_medium, self.medium_threshold)
 
 
 _P = ctypes.c_void_p
@@ -62,6 +69,7 @@ SIGNATURES = {
     "spx_check_device": [_P],
     "spx_rowplan_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_rowplan_build": [_CSRP, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
+    "spx_rowplan_build_medium": [_CSRP, _I32, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
     "spx_spmm_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
     "spx_spmm": [_CSRP, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
     "spx_sddmm_workspace_size": [_CSRP, _I32, _I32, ctypes.POINTER(_SZ)],
@@ -182,8 +190,8 @@ def spx_csr_validate(A: spx_csr, device) -> None:
            "spx_csr_validate")
 
 
-def spx_rowplan_build(A: spx_csr, threshold: int, device):
-    """Returns (long_rows tensor, spx_rowplan)."""
+def spx_rowplan_build(A: spx_csr, threshold: int, device, medium_threshold: int = 0):
+    """Returns (row-list tensors, spx_rowplan); medium_threshold > 0 adds the medium bin."""
     sz = _SZ(0)
     _check(lib().spx_rowplan_workspace_size(A.m, ctypes.byref(sz)), "spx_rowplan_workspace_size")
     ws = workspace(sz.value, device)
@@ -192,8 +200,18 @@ def spx_rowplan_build(A: spx_csr, threshold: int, device):
     _check(lib().spx_rowplan_build(ctypes.byref(A), int(threshold), ptr(rows), ctypes.byref(n_long),
                                    ptr(ws), ws.numel(), _stream()), "spx_rowplan_build")
     rows = rows[: n_long.value].clone() if n_long.value > 0 else rows[:0]
-    plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold), 0, 0, 0)
-    return rows, plan
+    med = rows[:0]
+    n_med = _I32(0)
+    if medium_threshold > 0 and A.m > 0:
+        med = torch.empty(max(A.m, 1), dtype=torch.int32, device=device)
+        _check(lib().spx_rowplan_build_medium(ctypes.byref(A), int(medium_threshold), int(threshold), ptr(med),
+                                              ctypes.byref(n_med), ptr(ws), ws.numel(), _stream()),
+               "spx_rowplan_build_medium")
+        med = med[: n_med.value].clone() if n_med.value > 0 else med[:0]
+    plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold), 0, 0, 0,
+                       med.data_ptr() if n_med.value > 0 else None, n_med.value,
+                       int(medium_threshold) if n_med.value > 0 else 0)
+    return (rows, med), plan
 
 
 def _planp(plan):

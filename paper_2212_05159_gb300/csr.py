@@ -13,6 +13,7 @@ import torch
 from . import abi
 
 LONG_ROW_THRESHOLD = 256
+MEDIUM_ROW_THRESHOLD = 32
 
 
 class CSR:
@@ -67,7 +68,8 @@ class CSR:
     # ------------------------------------------------------------------ caches
     def plan(self):
         if self._plan is None:
-            rows, plan = abi.spx_rowplan_build(self.struct(), LONG_ROW_THRESHOLD, self.device)
+            rows, plan = abi.spx_rowplan_build(self.struct(), LONG_ROW_THRESHOLD, self.device,
+                                               MEDIUM_ROW_THRESHOLD)
             self._plan = (rows, plan)
         return self._plan[1]
 
@@ -87,7 +89,7 @@ class CSR:
         if self._t_plan is None:
             t_ip, t_ix, _ = self.transpose_pattern()
             st = abi.csr_struct(self.n, self.m, t_ip, t_ix, None)
-            self._t_plan = abi.spx_rowplan_build(st, LONG_ROW_THRESHOLD, self.device)
+            self._t_plan = abi.spx_rowplan_build(st, LONG_ROW_THRESHOLD, self.device, MEDIUM_ROW_THRESHOLD)
         return self._t_plan[1]
 
     def __repr__(self):

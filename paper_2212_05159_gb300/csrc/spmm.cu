@@ -16,6 +16,12 @@
 // one is gathered -- and issues the 8 row gathers of X back to back, so each lane has
 // up to 8 independent loads in flight.  One group per row: no cross-lane reduction.
 //
+// Medium rows (the plan's medium list: more than medium_threshold entries, at most the long
+// threshold) are taken by one whole warp each: its lane groups take 8-entry batches
+// round-robin and their partial sums are combined by xor-shuffles in a fixed order.  On a
+// power-law matrix these rows hold a large share of the entries; giving each its own
+// warp keeps the warps of the short-row path evenly loaded.
+//
 // Long rows (more entries than the plan threshold) are taken by whole thread blocks:
 // the block's groups take batches of 8 entries round-robin, then reduce by xor-shuffles
 // inside each warp and through shared memory across warps, in a fixed order.  Those
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
     const float* __restrict__ vals, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t ldx,
     int32_t x_shift, int32_t col_begin, int32_t col_end, float* __restrict__ Y, int64_t ldy, float alpha, float beta,
     int32_t rows_per_group, int32_t threshold, const int32_t* __restrict__ long_rows, int32_t n_long,
-    int32_t long_blocks) {
+    int32_t long_blocks, const int32_t* __restrict__ med_rows, int32_t n_med, int32_t med_blocks) {
     constexpr int G = 32 / LPR;                      // lane groups per warp
     constexpr int SLOTS = (BATCH + LPR - 1) / LPR;
     const int lane = threadIdx.x & 31;
@@ -175,8 +181,42 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
         return;
     }
 
+    if ((int)blockIdx.x < long_blocks + med_blocks) {
+        // ---------------- medium rows: one warp per row, its groups take batches round-robin
+        const int nw = med_blocks * SPMM_WARPS;
+        for (int q = ((int)blockIdx.x - long_blocks) * SPMM_WARPS + warp; q < n_med; q += nw) {
+            const int row = med_rows[q];
+            const int a = indptr[row], b = indptr[row + 1];
+            float acc[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+            int jn[SLOTS];
+            float vn[SLOTS];
+            const int e0 = a + g * BATCH;
+            if (e0 < b) load_batch<LPR, PERM>(jn, vn, e0, b, c, indices, vals, perm, pol_stream);
+            for (int e = e0; e < b; e += G * BATCH) {
+                int jc[SLOTS];
+                float vc[SLOTS];
+#pragma unroll
+                for (int t = 0; t < SLOTS; ++t) {
+                    jc[t] = jn[t];
+                    vc[t] = vn[t];
+                }
+                if (e + G * BATCH < b)
+                    load_batch<LPR, PERM>(jn, vn, e + G * BATCH, b, c, indices, vals, perm, pol_stream);
+                gather_batch<VEC, LPR>(acc, jc, vc, gmask, colok, X, ldx, xcol, pol_keep);
+            }
+#pragma unroll
+            for (int off = LPR; off < 32; off <<= 1)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(FULL, acc[v], off);
+            if (g == 0 && colok) store_row<VEC>(Y + (int64_t)row * ldy + col, acc, alpha, beta);
+        }
+        return;
+    }
+
     // ---------------- short rows: one lane group per row
-    const int64_t wglobal = ((int64_t)(blockIdx.x - long_blocks) * SPMM_THREADS + threadIdx.x) >> 5;
+    const int64_t wglobal = ((int64_t)(blockIdx.x - long_blocks - med_blocks) * SPMM_THREADS + threadIdx.x) >> 5;
     const int64_t row0 = (wglobal * G + g) * rows_per_group;
     for (int p = 0; p < rows_per_group; ++p) {
         const int64_t row = row0 + p;
@@ -396,12 +436,12 @@ template <int VEC, bool PERM>
 spx_status launch_lpr(int lpr, unsigned grid, cudaStream_t st, const spx_csr* A, const int32_t* perm,
                       const float* vals, const float* X, int64_t ldx, int32_t xs, int32_t c0, int32_t c1, float* Y,
                       int64_t ldy, float alpha, float beta, int32_t rpg, int32_t thr, const int32_t* lr,
-                      int32_t n_long, int32_t long_blocks) {
+                      int32_t n_long, int32_t long_blocks, const int32_t* mr, int32_t n_med, int32_t med_blocks) {
 #define SPX_SPMM_CASE(L)                                                                                        \
     case L:                                                                                                     \
         spmm_kernel<VEC, L, PERM><<<grid, SPMM_THREADS, 0, st>>>(A->m, A->indptr, A->indices, vals, perm, X, ldx, \
                                                                  xs, c0, c1, Y, ldy, alpha, beta, rpg, thr, lr,  \
-                                                                 n_long, long_blocks);                           \
+                                                                 n_long, long_blocks, mr, n_med, med_blocks);    \
         break;
     switch (lpr) {
         SPX_SPMM_CASE(1)
@@ -459,10 +499,21 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
         n_long = plan->n_long;
         long_blocks = n_long < 4 * num_sms() ? n_long : 4 * num_sms();
     }
+    const int32_t* med_rows = nullptr;
+    int32_t n_med = 0, med_blocks = 0;
+    if (plan && plan->n_medium > 0) {
+        if (!plan->medium_rows || plan->medium_threshold < 1 || plan->medium_threshold > threshold)
+            return set_error(SPX_INVALID_ARG, "%s: bad medium-row plan", who);
+        med_rows = plan->medium_rows;
+        n_med = plan->n_medium;
+        threshold = plan->medium_threshold;        // short rows stop here
+        const int64_t want = ((int64_t)n_med + 2 * SPMM_WARPS - 1) / (2 * SPMM_WARPS);
+        med_blocks = (int32_t)(want < 8 * num_sms() ? want : 8 * num_sms());
+    }
     const int G = 32 / sh.lpr;
     const int64_t rows_per_block = (int64_t)SPMM_WARPS * G * sh.rpg;
     const int64_t short_blocks = ((int64_t)A->m + rows_per_block - 1) / rows_per_block;
-    const int64_t grid = short_blocks + long_blocks;
+    const int64_t grid = short_blocks + long_blocks + med_blocks;
     if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
     if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, sh.cb, slab_ws, st));
     const bool bulk = !PERM && vec4 && plan && plan->engine == 1 && sh.cb % 4 == 0 && sh.lpr >= 2 &&
@@ -501,10 +552,10 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
             }
 #undef SPX_BULK_CASE
             SPX_CHECK_LAUNCH(who);
-            if (long_blocks > 0) {
-                spx_status s = launch_lpr<4, false>(sh.lpr, (unsigned)long_blocks, st, A, perm, vals, Xp, ldp, xs, c0,
-                                                    c1, Y, ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long,
-                                                    long_blocks);
+            if (long_blocks + med_blocks > 0) {
+                spx_status s = launch_lpr<4, false>(sh.lpr, (unsigned)(long_blocks + med_blocks), st, A, perm, vals,
+                                                    Xp, ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold,
+                                                    long_rows, n_long, long_blocks, med_rows, n_med, med_blocks);
                 if (s != SPX_OK) return s;
                 SPX_CHECK_LAUNCH(who);
             }
@@ -517,19 +568,25 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
         const int64_t ldp = use_slab ? sh.cb : ldx;
         const int32_t xs = use_slab ? c0 : 0;
         spx_status s = vec4 ? launch_lpr<4, PERM>(sh.lpr, (unsigned)grid, st, A, perm, vals, Xp, ldp, xs, c0, c1, Y,
-                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks)
+                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks,
+                                                  med_rows, n_med, med_blocks)
                             : launch_lpr<1, PERM>(sh.lpr, (unsigned)grid, st, A, perm, vals, Xp, ldp, xs, c0, c1, Y,
-                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks);
+                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks,
+                                                  med_rows, n_med, med_blocks);
         if (s != SPX_OK) return s;
         SPX_CHECK_LAUNCH(who);
     }
     return SPX_OK;
 }
 
-__global__ void long_flag_kernel(int32_t m, const int32_t* __restrict__ indptr, int32_t threshold,
+// flags[i] = 1 for rows with lo < length <= hi
+__global__ void long_flag_kernel(int32_t m, const int32_t* __restrict__ indptr, int32_t lo, int32_t hi,
                                  int32_t* __restrict__ flags) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < m) flags[i] = (indptr[i + 1] - indptr[i]) > threshold ? 1 : 0;
+    if (i < m) {
+        const int len = indptr[i + 1] - indptr[i];
+        flags[i] = (len > lo && len <= hi) ? 1 : 0;
+    }
 }
 
 __global__ void long_compact_kernel(int32_t m, const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
@@ -573,7 +630,7 @@ extern "C" spx_status spx_rowplan_build(const spx_csr* A, int32_t threshold, int
     int32_t* pos = (int32_t*)(w + (((size_t)A->m * 4 + 255) & ~size_t(255)));
     int32_t* sws = (int32_t*)((char*)pos + ((((size_t)A->m + 1) * 4 + 255) & ~size_t(255)));
     unsigned blocks = (unsigned)((A->m + 255) / 256);
-    long_flag_kernel<<<blocks, 256, 0, st>>>(A->m, A->indptr, threshold, flags);
+    long_flag_kernel<<<blocks, 256, 0, st>>>(A->m, A->indptr, threshold, INT_MAX, flags);
     SPX_CHECK_LAUNCH("long_flag");
     SPX_TRY((scan_counts<int32_t, int32_t>(flags, pos, A->m, sws, st)));
     long_compact_kernel<<<blocks, 256, 0, st>>>(A->m, flags, pos, long_rows);
@@ -581,6 +638,34 @@ extern "C" spx_status spx_rowplan_build(const spx_csr* A, int32_t threshold, int
     SPX_CUDA(cudaMemcpyAsync(n_long_host, pos + A->m, sizeof(int32_t), cudaMemcpyDeviceToHost, st),
              "spx_rowplan_build copy");
     SPX_CUDA(cudaStreamSynchronize(st), "spx_rowplan_build sync");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_rowplan_build_medium(const spx_csr* A, int32_t medium_threshold, int32_t long_threshold,
+                                               int32_t* medium_rows, int32_t* n_medium_host, void* ws, size_t ws_bytes,
+                                               void* stream) {
+    SPX_TRY(check_csr(A, false, "spx_rowplan_build_medium"));
+    if (!n_medium_host || (A->m > 0 && !medium_rows) || medium_threshold < 1 || long_threshold < medium_threshold)
+        return set_error(SPX_INVALID_ARG, "spx_rowplan_build_medium: bad arguments");
+    size_t need = rowplan_ws(A->m);
+    if (!ws || ws_bytes < need)
+        return set_error(SPX_OOM_WORKSPACE, "spx_rowplan_build_medium: workspace %zu < %zu", ws_bytes, need);
+    *n_medium_host = 0;
+    if (A->m == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    char* w = static_cast<char*>(ws);
+    int32_t* flags = (int32_t*)w;
+    int32_t* pos = (int32_t*)(w + (((size_t)A->m * 4 + 255) & ~size_t(255)));
+    int32_t* sws = (int32_t*)((char*)pos + ((((size_t)A->m + 1) * 4 + 255) & ~size_t(255)));
+    unsigned blocks = (unsigned)((A->m + 255) / 256);
+    long_flag_kernel<<<blocks, 256, 0, st>>>(A->m, A->indptr, medium_threshold, long_threshold, flags);
+    SPX_CHECK_LAUNCH("medium_flag");
+    SPX_TRY((scan_counts<int32_t, int32_t>(flags, pos, A->m, sws, st)));
+    long_compact_kernel<<<blocks, 256, 0, st>>>(A->m, flags, pos, medium_rows);
+    SPX_CHECK_LAUNCH("medium_compact");
+    SPX_CUDA(cudaMemcpyAsync(n_medium_host, pos + A->m, sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+             "spx_rowplan_build_medium copy");
+    SPX_CUDA(cudaStreamSynchronize(st), "spx_rowplan_build_medium sync");
     return SPX_OK;
 }
 

@@ -84,7 +84,7 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
     engines = (0, 1) if k % 4 == 0 else (0,)
     for cb, rpg, eng in [(cb, rpg, eng) for cb in _col_blocks(k) for rpg in (1, 2, 4) for eng in engines]:
         if True:
-            plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg, eng)
+            plan = base.with_params(cb, rpg, eng)
             if transposed:
                 _, _, perm = A.transpose_pattern()
                 s = A.t_struct()
@@ -135,4 +135,4 @@ def tuned_plan(A: CSR, k: int, transposed: bool = False):
     best = tune_rows(A, k, transposed)
     cb, rpg = best[0], best[1]
     eng = best[2] if len(best) > 2 else 0
-    return abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg, eng)
+    return base.with_params(cb, rpg, eng)

@@ -194,7 +194,7 @@ def test_tuning_variants_match_oracle(mat, cb, rpg, engine):
     X = synth.normal((A.n, k), seed=40)
     G = synth.normal((A.m, k), seed=41)
     base = dA.plan()
-    plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, cb, rpg, engine)
+    plan = base.with_params(cb, rpg, engine)
     Y = torch.empty(A.m, k, device="cuda")
     ws = abi.workspace(abi.spx_spmm_workspace_size(dA.struct(), k, plan), "cuda")
     abi.spx_spmm(dA.struct(), dev(X), Y, 1.0, 0.0, plan, ws)
@@ -202,7 +202,7 @@ def test_tuning_variants_match_oracle(mat, cb, rpg, engine):
     assert_close_normalised(host(Y), oracle.spmm(A, X), oracle.spmm(abs_csr(A), np.abs(X)),
                             what=f"spmm {name} cb={cb} rpg={rpg} engine={engine}")
     tb = dA.t_plan()
-    tplan = abi.spx_rowplan(tb.long_rows, tb.n_long, tb.threshold, cb, rpg, engine)
+    tplan = tb.with_params(cb, rpg, engine)
     gX = torch.empty(A.n, k, device="cuda")
     _, _, perm = dA.transpose_pattern()
     abi.spx_spmm_t(dA.t_struct(), perm, dev(G), gX, 1.0, 0.0, tplan, None)   # gather through perm
@@ -228,7 +228,7 @@ def test_bulk_engine_k_widths_and_alpha_beta(mat, k):
     X = synth.normal((A.n, k), seed=50 + k)
     y0 = synth.normal((A.m, k), seed=60 + k)
     base = dA.plan()
-    plan = abi.spx_rowplan(base.long_rows, base.n_long, base.threshold, k, 2, 1)
+    plan = base.with_params(k, 2, 1)
     Y = dev(y0.copy())
     abi.spx_spmm(dA.struct(), dev(X), Y, 0.5, -1.5, plan, None)
     abi.spx_check_device()
