@@ -194,11 +194,12 @@ class Workload:
             b, tb = self.dA.plan(), self.dA.t_plan()
             self.plan = b.with_params(k, 4, 0)
             self.t_plan = tb.with_params(k, 4, 0)
-            self.sddmm_cb = k
+            self.sddmm_cb, self.sddmm_mode = k, "rows"
         else:
             self.plan = tune.tuned_plan(self.dA, k)
             self.t_plan = tune.tuned_plan(self.dA, k, transposed=True)
-            self.sddmm_cb = tune.tune_sddmm(self.dA, k)
+            self.sddmm_cb, self.sddmm_mode = tune.tune_sddmm(self.dA, k)
+        self.sddmm_plan = self.dA.plan().with_params(self.sddmm_cb, 2, 0) if self.sddmm_mode == "rows" else None
         self.s_A = self.dA.struct()
         self.s_AT = self.dA.t_struct()
         ws = lambda nb: abi.workspace(nb, device) if nb > 0 else None  # noqa: E731
@@ -211,7 +212,7 @@ class Workload:
                          + rp(self.sddmm_cb) + 1 + npass(self.t_plan.col_block) + rp(self.t_plan.col_block))
         self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine],
                        "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group, self.t_plan.engine],
-                       "sddmm_col_block": self.sddmm_cb}
+                       "sddmm": [self.sddmm_cb, self.sddmm_mode]}
         self.abi = abi
         self.m, self.n, self.nnz = A.m, A.n, A.nnz
 
@@ -223,7 +224,7 @@ class Workload:
         if which == "spmm":
             a.spx_spmm(self.s_A, self.X, self.Y, 1.0, 0.0, self.plan, self.ws_spmm)
         elif which == "sddmm":
-            a.spx_sddmm(self.s_A, self.G, self.X, self.gA, 1.0, self.sddmm_cb, self.ws_sddmm)
+            a.spx_sddmm(self.s_A, self.G, self.X, self.gA, 1.0, self.sddmm_cb, self.ws_sddmm, plan=self.sddmm_plan)
         else:
             a.spx_spmm_t(self.s_AT, self.perm, self.G, self.gX, 1.0, 0.0, self.t_plan, self.ws_t)
 

@@ -158,10 +158,14 @@ spx_status spx_sddmm_workspace_size(const spx_csr* A, int32_t k, int32_t col_blo
  * G: device float32 m x k (ldg); X: device float32 n x k (ldx); out: device float32[nnz].
  * col_block: dense columns per pass (0 = choose from the sizes); with several passes
  * the partial dot products are added into out in column order.
+ * plan: optional row plan of A (spx_rowplan_build[_medium]); with it rows are binned as in
+ * spx_spmm and each lane group keeps G's row in registers, without it every warp takes an
+ * equal slice of the entries.  Its launch fields (col_block, engine) are not used here.
  * workspace: device scratch of spx_sddmm_workspace_size() bytes, or NULL (as spx_spmm). */
 spx_status spx_sddmm(const spx_csr* A, const float* G, int64_t ldg, const float* X,
                      int64_t ldx, int32_t k, float scale, float* out, int32_t col_block,
-                     void* workspace, size_t workspace_bytes, void* stream);
+                     const spx_rowplan* plan, void* workspace, size_t workspace_bytes,
+                     void* stream);
 
 /* The k = 1 case: out[e] = scale * u[i] * v[j] on mask(A) (Table 1, SpMV row "A";
  * with scale = -1 and u = lambda, v = x it is the SpSolve gradient w.r.t. A).

@@ -73,7 +73,7 @@ SIGNATURES = {
     "spx_spmm_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
     "spx_spmm": [_CSRP, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
     "spx_sddmm_workspace_size": [_CSRP, _I32, _I32, ctypes.POINTER(_SZ)],
-    "spx_sddmm": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, _I32, _P, _SZ, _P],
+    "spx_sddmm": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, _I32, _PLANP, _P, _SZ, _P],
     "spx_masked_outer": [_CSRP, _P, _P, _F, _P, _P],
     "spx_transpose_workspace_size": [_I32, _I32, _I64, ctypes.POINTER(_SZ)],
     "spx_csr_transpose": [_CSRP, _P, _P, _P, _P, _SZ, _P],
@@ -244,11 +244,11 @@ def spx_sddmm_workspace_size(A: spx_csr, k: int, col_block: int = 0) -> int:
     return sz.value
 
 
-def spx_sddmm(A: spx_csr, G, X, out, scale=1.0, col_block=0, ws=None):
+def spx_sddmm(A: spx_csr, G, X, out, scale=1.0, col_block=0, ws=None, plan: spx_rowplan | None = None):
     pg, ldg = _dense(G, "G")
     px, ldx = _dense(X, "X")
     _check(lib().spx_sddmm(ctypes.byref(A), pg, ldg, px, ldx, G.shape[1], float(scale), ptr(out),
-                           int(col_block), *_wsargs(ws), _stream()), "spx_sddmm")
+                           int(col_block), _planp(plan), *_wsargs(ws), _stream()), "spx_sddmm")
     return out
 
 

@@ -107,6 +107,112 @@ __global__ void __launch_bounds__(SDDMM_THREADS) sddmm_kernel(
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// ---------------------------------------------------------------------------------------
+// Row-plan SDDMM (float4 columns).  A lane group of LPR lanes spans the columns of a block;
+// it holds G's row i in registers for the whole row and takes the row's entries LPR at a
+// time: lane c computes the LPR partial dot products of its column slice with the batch's
+// X rows, and a butterfly transpose across the group leaves entry c's total in lane c,
+// which stores it (coalesced).  Rows are binned like the row-wise products: short rows
+// one group each, medium rows one warp each (groups take batches round-robin), long rows
+// one block each.  Outputs are independent, so no cross-group reduction is needed.
+constexpr int SR_THREADS = 256;
+constexpr int SR_WARPS = SR_THREADS / 32;
+
+template <int LPR>
+__device__ __forceinline__ void sddmm_batch(const int32_t* __restrict__ indices, int e, int b, int c, unsigned gmask,
+                                            const float4& gv, bool colok, const float* __restrict__ X, int64_t ldx,
+                                            int xcol, float scale, bool accumulate, float* __restrict__ out,
+                                            uint64_t pol_stream, uint64_t pol_keep) {
+    const int ee = e + c;
+    const int jmine = ee < b ? ld_hint(indices + ee, pol_stream) : -1;
+    float P[LPR];
+#pragma unroll
+    for (int q = 0; q < LPR; ++q) {
+        const int jq = __shfl_sync(gmask, jmine, q, LPR);
+        float acc = 0.f;
+        if (jq >= 0 && colok) {
+            const float4 x = ld_hint4(X + (int64_t)jq * ldx + xcol, pol_keep);
+            acc = fmaf(gv.x, x.x, fmaf(gv.y, x.y, fmaf(gv.z, x.z, gv.w * x.w)));
+        }
+        P[q] = acc;
+    }
+#pragma unroll
+    for (int h = LPR / 2, cnt = LPR / 2; h >= 1; h >>= 1, cnt >>= 1) {
+        const bool upper = (c & h) != 0;
+#pragma unroll
+        for (int q = 0; q < cnt; ++q) {
+            const float send = upper ? P[q] : P[q + cnt];
+            const float keep = upper ? P[q + cnt] : P[q];
+            P[q] = keep + __shfl_xor_sync(gmask, send, h, LPR);
+        }
+    }
+    if (ee < b) {
+        float* o = out + ee;
+        __stcs(o, accumulate ? fmaf(scale, P[0], *o) : scale * P[0]);
+    }
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(SR_THREADS) sddmm_rows_kernel(
+    int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices, const float* __restrict__ G,
+    int64_t ldg, const float* __restrict__ X, int64_t ldx, int32_t x_shift, int32_t col_begin, int32_t col_end,
+    float scale, bool accumulate, float* __restrict__ out, int32_t rows_per_group, int32_t threshold,
+    const int32_t* __restrict__ long_rows, int32_t n_long, int32_t long_blocks, const int32_t* __restrict__ med_rows,
+    int32_t n_med, int32_t med_blocks) {
+    constexpr int G_ = 32 / LPR;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / LPR, c = lane % LPR;
+    const unsigned gmask = LPR == 32 ? FULL : (((1u << LPR) - 1u) << (g * LPR));
+    const int col = col_begin + c * 4;
+    const int xcol = col - x_shift;
+    const bool colok = col < col_end;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    auto grow = [&](int row) {
+        return colok ? __ldg(reinterpret_cast<const float4*>(G + (int64_t)row * ldg + col)) : make_float4(0, 0, 0, 0);
+    };
+    if ((int)blockIdx.x < long_blocks) {
+        const int gid = warp * G_ + g;
+        constexpr int GB = SR_WARPS * G_;
+        for (int q = blockIdx.x; q < n_long; q += long_blocks) {
+            const int row = long_rows[q];
+            const int a = indptr[row], b = indptr[row + 1];
+            const float4 gv = grow(row);
+            for (int e = a + gid * LPR; e < b; e += GB * LPR)
+                sddmm_batch<LPR>(indices, e, b, c, gmask, gv, colok, X, ldx, xcol, scale, accumulate, out, pol_stream,
+                                 pol_keep);
+        }
+        return;
+    }
+    if ((int)blockIdx.x < long_blocks + med_blocks) {
+        const int nw = med_blocks * SR_WARPS;
+        for (int q = ((int)blockIdx.x - long_blocks) * SR_WARPS + warp; q < n_med; q += nw) {
+            const int row = med_rows[q];
+            const int a = indptr[row], b = indptr[row + 1];
+            const float4 gv = grow(row);
+            for (int e = a + g * LPR; e < b; e += G_ * LPR)
+                sddmm_batch<LPR>(indices, e, b, c, gmask, gv, colok, X, ldx, xcol, scale, accumulate, out, pol_stream,
+                                 pol_keep);
+        }
+        return;
+    }
+    const int64_t wglobal = ((int64_t)(blockIdx.x - long_blocks - med_blocks) * SR_THREADS + threadIdx.x) >> 5;
+    const int64_t row0 = (wglobal * G_ + g) * rows_per_group;
+    for (int p = 0; p < rows_per_group; ++p) {
+        const int64_t row = row0 + p;
+        if (row >= m) break;
+        const int a = indptr[row], b = indptr[row + 1];
+        if (b - a > threshold) continue;
+        if (a == b) continue;
+        const float4 gv = grow((int)row);
+        for (int e = a; e < b; e += LPR)
+            sddmm_batch<LPR>(indices, e, b, c, gmask, gv, colok, X, ldx, xcol, scale, accumulate, out, pol_stream,
+                             pol_keep);
+    }
+}
+
+
+
 template <int VEC>
 spx_status launch_lpn(int lpn, dim3 grid, cudaStream_t st, int32_t m, int64_t nnz, const int32_t* ip,
                       const int32_t* ix, const float* G, int64_t ldg, const float* X, int64_t ldx, int32_t xs,
@@ -137,14 +243,69 @@ int32_t sddmm_cb(const spx_csr* A, int32_t k, int32_t col_block, bool vec4) {
     return cb;
 }
 
+spx_status launch_sddmm_rows(const spx_csr* A, const float* G, int64_t ldg, const float* X, int64_t ldx,
+                             int32_t k, float scale, float* out, int32_t cb, const spx_rowplan* plan, float* ws,
+                             bool use_slab, cudaStream_t st) {
+    int lpr = 1;
+    while (lpr * 4 < cb && lpr < 32) lpr <<= 1;
+    int32_t threshold = INT_MAX, n_long = 0, long_blocks = 0, n_med = 0, med_blocks = 0;
+    const int32_t* long_rows = nullptr;
+    const int32_t* med_rows = nullptr;
+    if (plan->n_long > 0) {
+        threshold = plan->threshold;
+        long_rows = plan->long_rows;
+        n_long = plan->n_long;
+        long_blocks = n_long < 4 * num_sms() ? n_long : 4 * num_sms();
+    }
+    if (plan->n_medium > 0) {
+        med_rows = plan->medium_rows;
+        n_med = plan->n_medium;
+        threshold = plan->medium_threshold;
+        const int64_t want = ((int64_t)n_med + 2 * SR_WARPS - 1) / (2 * SR_WARPS);
+        med_blocks = (int32_t)(want < 8 * num_sms() ? want : 8 * num_sms());
+    }
+    const int rpg = plan->rows_per_group > 0 ? plan->rows_per_group : 2;
+    const int64_t rows_per_block = (int64_t)SR_WARPS * (32 / lpr) * rpg;
+    const int64_t grid = ((int64_t)A->m + rows_per_block - 1) / rows_per_block + long_blocks + med_blocks;
+    if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "sddmm: too many rows");
+    if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, cb, ws, st));
+    for (int32_t c0 = 0; c0 < k; c0 += cb) {
+        const int32_t c1 = c0 + cb < k ? c0 + cb : k;
+        const float* Xp = use_slab ? ws + (int64_t)(c0 / cb) * A->n * cb : X;
+        const int64_t ldp = use_slab ? cb : ldx;
+        const int32_t xs = use_slab ? c0 : 0;
+#define SPX_SR_CASE(L)                                                                                         \
+    case L:                                                                                                    \
+        sddmm_rows_kernel<L><<<(unsigned)grid, SR_THREADS, 0, st>>>(A->m, A->indptr, A->indices, G, ldg, Xp, ldp, xs, \
+                                                                     c0, c1, scale, c0 > 0, out, rpg, threshold,   \
+                                                                     long_rows, n_long, long_blocks, med_rows,     \
+                                                                     n_med, med_blocks);                           \
+        break;
+        switch (lpr) {
+            SPX_SR_CASE(2)
+            SPX_SR_CASE(4)
+            SPX_SR_CASE(8)
+            SPX_SR_CASE(16)
+            SPX_SR_CASE(32)
+            default: return set_error(SPX_INVALID_ARG, "sddmm: bad lane count %d", lpr);
+        }
+#undef SPX_SR_CASE
+        SPX_CHECK_LAUNCH("sddmm rows");
+    }
+    return SPX_OK;
+}
+
 spx_status launch_sddmm(const spx_csr* A, const float* G, int64_t ldg, const float* X, int64_t ldx, int32_t k,
-                        float scale, float* out, int32_t col_block, float* ws, size_t ws_bytes, cudaStream_t st) {
+                        float scale, float* out, int32_t col_block, float* ws, size_t ws_bytes, cudaStream_t st,
+                        const spx_rowplan* plan = nullptr) {
     if (A->nnz == 0) return SPX_OK;
     const bool vec4 = (k % 4 == 0) && (ldg % 4 == 0) && (ldx % 4 == 0) && aligned16(G) && aligned16(X);
     const int VEC = vec4 ? 4 : 1;
     const int32_t cb = sddmm_cb(A, k, col_block, vec4);
     const size_t slab = vec4 ? slab_bytes(A->n, k, cb) : 0;
     const bool use_slab = slab > 0 && ws != nullptr && ws_bytes >= slab;
+    if (plan && vec4 && cb >= 8 && cb <= 128)
+        return launch_sddmm_rows(A, G, ldg, X, ldx, k, scale, out, cb, plan, ws, use_slab, st);
     int64_t lanes = (cb + VEC - 1) / VEC;
     int lpn = 1;
     while (lpn < lanes && lpn < 32) lpn <<= 1;
@@ -181,8 +342,8 @@ extern "C" spx_status spx_sddmm_workspace_size(const spx_csr* A, int32_t k, int3
 }
 
 extern "C" spx_status spx_sddmm(const spx_csr* A, const float* G, int64_t ldg, const float* X, int64_t ldx,
-                                int32_t k, float scale, float* out, int32_t col_block, void* ws, size_t ws_bytes,
-                                void* stream) {
+                                int32_t k, float scale, float* out, int32_t col_block, const spx_rowplan* plan,
+                                void* ws, size_t ws_bytes, void* stream) {
     SPX_TRY(check_csr(A, false, "spx_sddmm"));
     if (k < 1 || ldg < k || ldx < k) return set_error(SPX_INVALID_ARG, "spx_sddmm: bad k / leading dims");
     if (A->nnz > 0 && (!G || !X || !out)) return set_error(SPX_INVALID_ARG, "spx_sddmm: NULL operand");
@@ -191,8 +352,10 @@ extern "C" spx_status spx_sddmm(const spx_csr* A, const float* G, int64_t ldg, c
         const size_t need = vec4 ? slab_bytes(A->n, k, sddmm_cb(A, k, col_block, true)) : 0;
         if (ws_bytes < need) return set_error(SPX_OOM_WORKSPACE, "spx_sddmm: workspace %zu < %zu", ws_bytes, need);
     }
+    if (plan && ((plan->n_long > 0 && !plan->long_rows) || (plan->n_medium > 0 && !plan->medium_rows)))
+        return set_error(SPX_INVALID_ARG, "spx_sddmm: plan without rows");
     return launch_sddmm(A, G, ldg, X, ldx, k, scale, out, col_block, static_cast<float*>(ws), ws_bytes,
-                        as_stream(stream));
+                        as_stream(stream), plan);
 }
 
 extern "C" spx_status spx_masked_outer(const spx_csr* A, const float* u, const float* v, float scale, float* out,

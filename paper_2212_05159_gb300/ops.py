@@ -42,7 +42,7 @@ def sddmm(A: CSR, G: torch.Tensor, X: torch.Tensor, scale: float = 1.0, out=None
     else:
         st = A.struct()
         ws = _workspace(abi.spx_sddmm_workspace_size(st, G2.shape[1]), G.device)
-        abi.spx_sddmm(st, G2, X2, o, scale, 0, ws)
+        abi.spx_sddmm(st, G2, X2, o, scale, 0, ws, plan=A.plan())
     return o
 
 

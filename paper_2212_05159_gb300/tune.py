@@ -105,25 +105,28 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
     return best
 
 
-def tune_sddmm(A: CSR, k: int, force: bool = False) -> int:
-    """Best column block for spx_sddmm."""
-    key = _key(A, k, "sddmm")
+def tune_sddmm(A: CSR, k: int, force: bool = False):
+    """Best (column block, "rows" | "chunks") for spx_sddmm."""
+    key = _key(A, k, "sddmm2")
     with _lock:
         c = _load()
         if key in c and not force:
-            return int(c[key]["best"])
+            return tuple(c[key]["best"])
     dev = A.device
     G = torch.randn(A.m, k, device=dev)
     X = torch.randn(A.n, k, device=dev)
     out = torch.empty(A.nnz, device=dev)
     s = A.struct()
     best, best_ms, table = None, float("inf"), {}
+    base = A.plan()
     for cb in _col_blocks(k):
-        ws = abi.workspace(abi.spx_sddmm_workspace_size(s, k, cb), dev)
-        ms = _time(lambda: abi.spx_sddmm(s, G, X, out, 1.0, cb, ws))
-        table[str(cb)] = ms
-        if ms < best_ms:
-            best, best_ms = cb, ms
+        for mode in ("chunks", "rows"):
+            ws = abi.workspace(abi.spx_sddmm_workspace_size(s, k, cb), dev)
+            plan = base.with_params(cb, 2, 0) if mode == "rows" else None
+            ms = _time(lambda: abi.spx_sddmm(s, G, X, out, 1.0, cb, ws, plan=plan))
+            table[f"{cb},{mode}"] = ms
+            if ms < best_ms:
+                best, best_ms = (cb, mode), ms
     with _lock:
         _load()[key] = {"best": best, "ms": best_ms, "table": table}
         _save()

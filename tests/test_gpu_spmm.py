@@ -57,7 +57,7 @@ def test_spmv_1d_and_alpha_beta(mat):
     assert_close_normalised(y, ref, norm, what=f"spmv {name}")
 
 
-@pytest.mark.parametrize("k", [1, 8, 32, 33, 128])
+@pytest.mark.parametrize("k", [1, 8, 12, 32, 33, 128])
 def test_sddmm_matches_oracle(mat, k):
     name, A, dA = mat
     G = synth.normal((A.m, k), seed=10 + k)
@@ -214,10 +214,11 @@ def test_tuning_variants_match_oracle(mat, cb, rpg, engine):
     assert_close_normalised(host(gX), oracle.spmm_t(A, G), oracle.spmm_t(abs_csr(A), np.abs(G)),
                             what=f"spmm_t {name} cb={cb}")
     out = torch.empty(A.nnz, device="cuda")
-    abi.spx_sddmm(dA.struct(), dev(G), dev(X), out, 1.0, cb,
-                  abi.workspace(abi.spx_sddmm_workspace_size(dA.struct(), k, cb), "cuda"))
-    assert_close_normalised(host(out), oracle.sddmm(A, G, X), oracle.sddmm(A, np.abs(G), np.abs(X)),
-                            what=f"sddmm {name} cb={cb}")
+    for p in (None, plan):
+        abi.spx_sddmm(dA.struct(), dev(G), dev(X), out, 1.0, cb,
+                      abi.workspace(abi.spx_sddmm_workspace_size(dA.struct(), k, cb), "cuda"), plan=p)
+        assert_close_normalised(host(out), oracle.sddmm(A, G, X), oracle.sddmm(A, np.abs(G), np.abs(X)),
+                                what=f"sddmm {name} cb={cb} plan={p is not None}")
 
 
 @pytest.mark.parametrize("k", [8, 32, 128])
