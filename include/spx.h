@@ -362,6 +362,15 @@ spx_status spx_dense_forward(int64_t n, const float* X1, int32_t K1, const float
                              const void* W_bf16, const float* bias, int32_t N, int32_t mode,
                              const float* Hin, float* Y, float* U, void* stream);
 
+/* spx_dense_forward on the tensor cores (tcgen05, accumulator in tensor memory): the
+ * activations are rounded to BF16 (round to nearest even) while they are staged, so the
+ * result equals spx_dense_forward applied to BF16-rounded X1, X2 up to the order of the
+ * FP32 accumulation.  N must be a multiple of 16 (16..128), K1 + K2 <= 128.  One
+ * 128-row tile per block.  Device pointers; asynchronous on `stream`. */
+spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K1, const float* X2,
+                                int32_t K2, const void* W_bf16, const float* bias, int32_t N,
+                                int32_t mode, const float* Hin, float* Y, float* U, void* stream);
+
 /* Data gradient [dX1 dX2] = G W^T (or += with accumulate != 0); dX2 may be NULL. */
 spx_status spx_dense_backward_data(int64_t n, const float* G, int32_t N, const void* W_bf16,
                                    int32_t K1, int32_t K2, float* dX1, float* dX2,

@@ -100,6 +100,7 @@ SIGNATURES = {
     "spx_pcg_train": [_CSRP, _P, _I32, _CSRP, _CSRP, _P, _I32, _P, _P, _P, _P, _SZ, _P],
     "spx_mpnn_features": [_CSRP, _P, _P, _P, _P],
     "spx_dense_forward": [_I64, _P, _I32, _P, _I32, _P, _P, _I32, _I32, _P, _P, _P, _P],
+    "spx_dense_forward_tc": [_I64, _P, _I32, _P, _I32, _P, _P, _I32, _I32, _P, _P, _P, _P],
     "spx_dense_backward_data": [_I64, _P, _I32, _P, _I32, _I32, _P, _P, _I32, _P],
     "spx_dense_backward_weight_workspace_size": [_I64, _I32, _I32, ctypes.POINTER(_SZ)],
     "spx_dense_backward_weight": [_I64, _P, _I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P],
@@ -413,6 +414,11 @@ def spx_mpnn_features(A: spx_csr, d, e_vals, feats):
 def spx_dense_forward(n, X1, K1, X2, K2, W16, bias, N, mode, Hin, Y, U=None):
     _check(lib().spx_dense_forward(int(n), ptr(X1), int(K1), ptr(X2), int(K2), ptr(W16), ptr(bias), int(N),
                                    int(mode), ptr(Hin), ptr(Y), ptr(U), _stream()), "spx_dense_forward")
+
+
+def spx_dense_forward_tc(n, X1, K1, X2, K2, W16, bias, N, mode, Hin, Y, U=None):
+    _check(lib().spx_dense_forward_tc(int(n), ptr(X1), int(K1), ptr(X2), int(K2), ptr(W16), ptr(bias), int(N),
+                                      int(mode), ptr(Hin), ptr(Y), ptr(U), _stream()), "spx_dense_forward_tc")
 
 
 def spx_dense_backward_data(n, G, N, W16, K1, K2, dX1, dX2, accumulate):

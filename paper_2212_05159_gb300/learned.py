@@ -140,12 +140,16 @@ class MPNN:
         return self.view(self.grad, name)
 
     # ------------------------------------------------------------------ forward
-    def forward(self, G: Graph):
-        """L values on G.Lpat; returns (L, saved activations)."""
+    def forward(self, G: Graph, tensor_cores: bool = False):
+        """L values on G.Lpat; returns (L, saved activations).
+
+        tensor_cores: run the dense layers on tcgen05 (activations rounded to BF16); the
+        default FP32-activation path is the one the training gradients follow."""
         n, dev = G.n, self.device
         emp = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
+        dense = abi.spx_dense_forward_tc if tensor_cores else abi.spx_dense_forward
         h0 = emp(n, H)
-        abi.spx_dense_forward(n, G.f, F_IN, None, 0, self.p16("W0"), self.p("b0"), H, 1, None, h0)
+        dense(n, G.f, F_IN, None, 0, self.p16("W0"), self.p("b0"), H, 1, None, h0)
         hs, gs, us = [h0], [], []
         Es = G.E.struct()
         plan = G.E.plan()
@@ -155,14 +159,14 @@ class MPNN:
             abi.spx_spmm(Es, h, g, 1.0, 0.0, plan)
             u = emp(n, H)
             hn = emp(n, H)
-            abi.spx_dense_forward(n, h, H, g, H, self.p16(f"W{layer}"), self.p(f"b{layer}"), H, 2, h, hn, u)
+            dense(n, h, H, g, H, self.p16(f"W{layer}"), self.p(f"b{layer}"), H, 2, h, hn, u)
             hs.append(hn)
             gs.append(g)
             us.append(u)
         hL = hs[-1]
         P, Q = emp(n, H), emp(n, H)
-        abi.spx_dense_forward(n, hL, H, None, 0, self.p16("Ua"), None, H, 0, None, P)
-        abi.spx_dense_forward(n, hL, H, None, 0, self.p16("Ub"), None, H, 0, None, Q)
+        dense(n, hL, H, None, 0, self.p16("Ua"), None, H, 0, None, P)
+        dense(n, hL, H, None, 0, self.p16("Ub"), None, H, 0, None, Q)
         L = emp(G.Lpat.nnz)
         abi.spx_edge_forward(G.Lpat.struct(), G.e_low, G.d, P, Q, self.p("u"), self.p("c"), self.p("v"),
                              self.p("bd"), self.p("bo"), L)

@@ -94,7 +94,7 @@ def evaluate(net: learned.MPNN, nsys: int = 128, per_batch: int = 64, side: int 
 
                 def run():
                     G.features(dA.values)
-                    L2, _ = net.forward(G)
+                    L2, _ = net.forward(G, tensor_cores=True)        # inference on tcgen05
                     Mv = plan.numeric(L2, _lt_values(G, L2))
                     return solve.cg(batch, bt, pc="M", M=plan.C.with_values(Mv), tol=tol, maxit=maxit)
                 ms, out = _timed(run)
