@@ -84,18 +84,24 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)                 # the sampler is running before the work starts
         except OSError:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None, load_from=None):
+        """Summary of the samples taken inside `window` (host perf_counter times of the timed
+        region); when the region is too short for 3 samples, the samples from `load_from` (the
+        start of the warm-up under the same load) to its end are used and the window says so."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -104,9 +110,18 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        lines = self.lines
+        used = "whole run"
+        if window is not None:
+            inside = [l for l in lines if window[0] <= l[0] <= window[1]]
+            used = "timed region"
+            if len(inside) < 3 and load_from is not None:
+                inside = [l for l in lines if load_from <= l[0] <= window[1]]
+                used = "warm-up + timed region"
+            lines = inside
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -120,7 +135,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(smax)) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": used}
 
 
 # ----------------------------------------------------------------------------- traffic
@@ -232,8 +247,10 @@ class Workload:
 
 
 def time_workload(W, steps, warmup, ws):
-    """Device-timed steps: returns (ms_per_step, {kernel: avg ms per launch})."""
+    """Device-timed steps: returns (ms_per_step, {kernel: avg ms per launch}); the host times of
+    the warm-up start and of the timed region go to W.windows for the clock sampler."""
     import torch
+    t_load = time.perf_counter()
     for _ in range(warmup):
         for kname in W.KERNELS:
             W.run_kernel(kname)
@@ -244,6 +261,7 @@ def time_workload(W, steps, warmup, ws):
     torch.cuda.synchronize()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
+    t_begin = time.perf_counter()
     start.record(st)
     for s in range(steps):
         ev[s][0].record(st)
@@ -252,7 +270,9 @@ def time_workload(W, steps, warmup, ws):
             ev[s][i + 1].record(st)
     end.record(st)
     torch.cuda.synchronize()
+    t_end = time.perf_counter()
     barrier(ws)
+    W.windows = (t_load, (t_begin, t_end))
     total_ms = start.elapsed_time(end)
     per = {k: 0.0 for k in W.KERNELS}
     for s in range(steps):
@@ -473,7 +493,7 @@ def main():
     clocks = ClockSampler(index=local)
     clocks.start()
     ms, per = time_workload(W, args.steps, args.warmup, ws)
-    clk = clocks.stop()
+    clk = clocks.stop(window=W.windows[1], load_from=W.windows[0])
     ms = max_over_ranks(ms, ws)
     cb = compulsory_bytes(W.m, W.n, W.nnz, W.k)
     gb = gather_bytes(W.m, W.n, W.nnz, W.k)
