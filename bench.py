@@ -207,14 +207,15 @@ class Workload:
         _, _, self.perm = self.dA.transpose_pattern()
         if NO_TUNE:
             b, tb = self.dA.plan(), self.dA.t_plan()
-            self.plan = b.with_params(k, 4, 0)
-            self.t_plan = tb.with_params(k, 4, 0)
-            self.sddmm_cb, self.sddmm_mode = k, "rows"
+            np_ = 1                                              # the tuned choice on GB300
+            self.plan = b.with_params(k, 4, 0, self.dA.parts(np_))
+            self.t_plan = tb.with_params(k, 4, 0, self.dA.t_parts(np_))
+            self.sddmm_cb = k
+            self.sddmm_plan = b.with_params(k, 2, 0, self.dA.parts(np_))
         else:
             self.plan = tune.tuned_plan(self.dA, k)
             self.t_plan = tune.tuned_plan(self.dA, k, transposed=True)
-            self.sddmm_cb, self.sddmm_mode = tune.tune_sddmm(self.dA, k)
-        self.sddmm_plan = self.dA.plan().with_params(self.sddmm_cb, 2, 0) if self.sddmm_mode == "rows" else None
+            self.sddmm_cb, self.sddmm_plan = tune.tuned_sddmm_plan(self.dA, k)
         self.s_A = self.dA.struct()
         self.s_AT = self.dA.t_struct()
         ws = lambda nb: abi.workspace(nb, device) if nb > 0 else None  # noqa: E731
@@ -223,11 +224,17 @@ class Workload:
         self.ws_t = ws(abi.spx_spmm_t_workspace_size(self.s_AT, k, self.t_plan))
         npass = lambda cb: -(-k // cb)  # noqa: E731
         rp = lambda cb: 1 if cb < k else 0  # noqa: E731  (slab repack launch)
-        self.launches = (npass(self.plan.col_block) + rp(self.plan.col_block) + npass(self.sddmm_cb)
-                         + rp(self.sddmm_cb) + 1 + npass(self.t_plan.col_block) + rp(self.t_plan.col_block))
-        self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine],
-                       "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group, self.t_plan.engine],
-                       "sddmm": [self.sddmm_cb, self.sddmm_mode]}
+        nparts = lambda pl: max(1, pl.n_parts) if pl is not None else 1  # noqa: E731
+        sp = self.sddmm_plan
+        self.launches = (npass(self.plan.col_block) * nparts(self.plan) + rp(self.plan.col_block)
+                         + npass(self.sddmm_cb) * nparts(sp) + rp(self.sddmm_cb) + 1
+                         + npass(self.t_plan.col_block) * nparts(self.t_plan) + rp(self.t_plan.col_block))
+        self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine,
+                                nparts(self.plan)],
+                       "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group, self.t_plan.engine,
+                                  nparts(self.t_plan)],
+                       "sddmm": [self.sddmm_cb, "rows" if sp is not None else "chunks", nparts(sp)],
+                       "fields": "col_block, rows_per_group, engine, column parts"}
         self.abi = abi
         self.m, self.n, self.nnz = A.m, A.n, A.nnz
 

@@ -81,6 +81,13 @@ typedef struct spx_rowplan {
                                    <= threshold, one warp each (NULL / 0 = none) */
     int32_t n_medium;
     int32_t medium_threshold;
+    const int32_t* part_ptr;  /* device int32[(n_parts - 1) * m] or NULL: column-range split of
+                                 every row, written by spx_rowplan_build_parts.  With
+                                 n_parts > 1 the products run one pass per range of the dense
+                                 operand's rows (A's columns [p * ceil(n / n_parts), ...)), so
+                                 the part gathered in a pass can stay resident in L2; the
+                                 passes add into the output in range order. */
+    int32_t n_parts;          /* 0 or 1 = one pass over all columns */
 } spx_rowplan;
 
 /* ------------------------------------------------------------------ library */
@@ -117,6 +124,14 @@ spx_status spx_rowplan_workspace_size(int32_t m, size_t* bytes);
 spx_status spx_rowplan_build(const spx_csr* A, int32_t threshold, int32_t* long_rows,
                              int32_t* n_long_host, void* workspace, size_t workspace_bytes,
                              void* stream);
+
+/* Column-range split of A's rows for plans with n_parts > 1 (no counterpart in the paper;
+ * a layout choice for operands larger than L2).  With w = ceil(n / n_parts), writes
+ * part_ptr[(p - 1) * m + i] = the offset of the first entry of row i whose column is
+ * >= p * w, for p = 1 .. n_parts - 1 (rows sorted, so these offsets split each row into
+ * n_parts consecutive segments).  part_ptr: device int32[(n_parts - 1) * m], caller-owned.
+ * Asynchronous on `stream`.  Returns SPX_INVALID_ARG for n_parts < 2 or n_parts > n. */
+spx_status spx_rowplan_build_parts(const spx_csr* A, int32_t n_parts, int32_t* part_ptr, void* stream);
 
 /* Workspace bytes with which spx_spmm repacks X into column-block slabs (0 when the
  * gathered operand fits the L2 budget, or k is not a multiple of 4). */

@@ -46,12 +46,15 @@ class spx_rowplan(ctypes.Structure):
                 ("threshold", ctypes.c_int32), ("col_block", ctypes.c_int32),
                 ("rows_per_group", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("medium_rows", ctypes.c_void_p), ("n_medium", ctypes.c_int32),
-                ("medium_threshold", ctypes.c_int32)]
+                ("medium_threshold", ctypes.c_int32), ("part_ptr", ctypes.c_void_p),
+                ("n_parts", ctypes.c_int32)]
 
-    def with_params(self, col_block=0, rows_per_group=0, engine=0):
-        """A copy of this plan (same row lists) with other launch parameters."""
+    def with_params(self, col_block=0, rows_per_group=0, engine=0, parts=None):
+        """A copy of this plan (same row lists) with other launch parameters; `parts` is a
+        (part_ptr tensor, n_parts) pair from spx_rowplan_build_parts, None for one pass."""
+        pp, np_ = (parts[0].data_ptr(), int(parts[1])) if parts is not None and parts[1] > 1 else (None, 0)
         return spx_rowplan(self.long_rows, self.n_long, self.threshold, col_block, rows_per_group, engine,
-                           self.medium_rows, self.n_medium, self.medium_threshold)
+                           self.medium_rows, self.n_medium, self.medium_threshold, pp, np_)
 
 
 _P = ctypes.c_void_p
@@ -70,6 +73,7 @@ SIGNATURES = {
     "spx_rowplan_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_rowplan_build": [_CSRP, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
     "spx_rowplan_build_medium": [_CSRP, _I32, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
+    "spx_rowplan_build_parts": [_CSRP, _I32, _P, _P],
     "spx_spmm_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
     "spx_spmm": [_CSRP, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
     "spx_sddmm_workspace_size": [_CSRP, _I32, _I32, ctypes.POINTER(_SZ)],
@@ -213,6 +217,14 @@ def spx_rowplan_build(A: spx_csr, threshold: int, device, medium_threshold: int 
                        med.data_ptr() if n_med.value > 0 else None, n_med.value,
                        int(medium_threshold) if n_med.value > 0 else 0)
     return (rows, med), plan
+
+
+def spx_rowplan_build_parts(A: spx_csr, n_parts: int, device):
+    """Column-range split of A's rows into n_parts segments: (part_ptr tensor, n_parts)."""
+    out = torch.empty(max((n_parts - 1) * A.m, 1), dtype=torch.int32, device=device)
+    _check(lib().spx_rowplan_build_parts(ctypes.byref(A), int(n_parts), ptr(out), _stream()),
+           "spx_rowplan_build_parts")
+    return out, int(n_parts)
 
 
 def _planp(plan):

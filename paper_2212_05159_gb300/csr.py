@@ -29,6 +29,8 @@ class CSR:
         self._plan = None
         self._t = None
         self._t_plan = None
+        self._parts = {}
+        self._t_parts = {}
 
     # ------------------------------------------------------------------ construction
     @classmethod
@@ -72,6 +74,26 @@ class CSR:
                                                MEDIUM_ROW_THRESHOLD)
             self._plan = (rows, plan)
         return self._plan[1]
+
+    def parts(self, n_parts: int):
+        """Column-range split of the rows into n_parts segments (cached per count)."""
+        if n_parts <= 1:
+            return None
+        cache = self._parts
+        if n_parts not in cache:
+            cache[n_parts] = abi.spx_rowplan_build_parts(self.struct(), n_parts, self.device)
+        return cache[n_parts]
+
+    def t_parts(self, n_parts: int):
+        """The same split for A^T (rows of A^T split by A's row ranges)."""
+        if n_parts <= 1:
+            return None
+        cache = self._t_parts
+        if n_parts not in cache:
+            t_ip, t_ix, _ = self.transpose_pattern()
+            st = abi.csr_struct(self.n, self.m, t_ip, t_ix, None)
+            cache[n_parts] = abi.spx_rowplan_build_parts(st, n_parts, self.device)
+        return cache[n_parts]
 
     def transpose_pattern(self):
         """(t_indptr, t_indices, perm) of A^T, computed once per pattern."""

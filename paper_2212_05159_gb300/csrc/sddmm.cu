@@ -114,9 +114,15 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 // X rows, and a butterfly transpose across the group leaves entry c's total in lane c,
 // which stores it (coalesced).  Rows are binned like the row-wise products: short rows
 // one group each, medium rows one warp each (groups take batches round-robin), long rows
-// one block each.  Outputs are independent, so no cross-group reduction is needed.
+// one block each.  Outputs are independent, so no cross-group reduction is needed.  With
+// a plan split into column parts, one pass per part takes the entries of each row whose
+// columns lie in that part, so the rows of X gathered in a pass stay resident in L2 (G's
+// row is then read once per part that the row has entries in).
 constexpr int SR_THREADS = 256;
 constexpr int SR_WARPS = SR_THREADS / 32;
+// Resident blocks per SM forced by register capping (latency-bound gathers want warps in
+// flight); measured on GB300: 6 best with 8-lane groups (k = 32), 8 with 32-lane groups.
+constexpr int sr_min_blocks(int lpr) { return lpr >= 32 ? 8 : 6; }
 
 template <int LPR>
 __device__ __forceinline__ void sddmm_batch(const int32_t* __restrict__ indices, int e, int b, int c, unsigned gmask,
@@ -153,8 +159,9 @@ __device__ __forceinline__ void sddmm_batch(const int32_t* __restrict__ indices,
 }
 
 template <int LPR>
-__global__ void __launch_bounds__(SR_THREADS) sddmm_rows_kernel(
-    int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices, const float* __restrict__ G,
+__global__ void __launch_bounds__(SR_THREADS, sr_min_blocks(LPR)) sddmm_rows_kernel(
+    int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ seg_b, const int32_t* __restrict__ seg_e,
+    const int32_t* __restrict__ indices, const float* __restrict__ G,
     int64_t ldg, const float* __restrict__ X, int64_t ldx, int32_t x_shift, int32_t col_begin, int32_t col_end,
     float scale, bool accumulate, float* __restrict__ out, int32_t rows_per_group, int32_t threshold,
     const int32_t* __restrict__ long_rows, int32_t n_long, int32_t long_blocks, const int32_t* __restrict__ med_rows,
@@ -168,6 +175,7 @@ __global__ void __launch_bounds__(SR_THREADS) sddmm_rows_kernel(
     const bool colok = col < col_end;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
+    const bool split = seg_b != indptr || seg_e != indptr + 1;
     auto grow = [&](int row) {
         return colok ? __ldg(reinterpret_cast<const float4*>(G + (int64_t)row * ldg + col)) : make_float4(0, 0, 0, 0);
     };
@@ -176,7 +184,8 @@ __global__ void __launch_bounds__(SR_THREADS) sddmm_rows_kernel(
         constexpr int GB = SR_WARPS * G_;
         for (int q = blockIdx.x; q < n_long; q += long_blocks) {
             const int row = long_rows[q];
-            const int a = indptr[row], b = indptr[row + 1];
+            const int a = seg_b[row], b = seg_e[row];
+            if (a == b) continue;
             const float4 gv = grow(row);
             for (int e = a + gid * LPR; e < b; e += GB * LPR)
                 sddmm_batch<LPR>(indices, e, b, c, gmask, gv, colok, X, ldx, xcol, scale, accumulate, out, pol_stream,
@@ -188,7 +197,8 @@ __global__ void __launch_bounds__(SR_THREADS) sddmm_rows_kernel(
         const int nw = med_blocks * SR_WARPS;
         for (int q = ((int)blockIdx.x - long_blocks) * SR_WARPS + warp; q < n_med; q += nw) {
             const int row = med_rows[q];
-            const int a = indptr[row], b = indptr[row + 1];
+            const int a = seg_b[row], b = seg_e[row];
+            if (a == b) continue;
             const float4 gv = grow(row);
             for (int e = a + g * LPR; e < b; e += G_ * LPR)
                 sddmm_batch<LPR>(indices, e, b, c, gmask, gv, colok, X, ldx, xcol, scale, accumulate, out, pol_stream,
@@ -201,8 +211,12 @@ __global__ void __launch_bounds__(SR_THREADS) sddmm_rows_kernel(
     for (int p = 0; p < rows_per_group; ++p) {
         const int64_t row = row0 + p;
         if (row >= m) break;
-        const int a = indptr[row], b = indptr[row + 1];
+        int a = indptr[row], b = indptr[row + 1];
         if (b - a > threshold) continue;
+        if (split) {
+            a = seg_b[row];
+            b = seg_e[row];
+        }
         if (a == b) continue;
         const float4 gv = grow((int)row);
         for (int e = a; e < b; e += LPR)
@@ -269,28 +283,34 @@ spx_status launch_sddmm_rows(const spx_csr* A, const float* G, int64_t ldg, cons
     const int64_t grid = ((int64_t)A->m + rows_per_block - 1) / rows_per_block + long_blocks + med_blocks;
     if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "sddmm: too many rows");
     if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, cb, ws, st));
+    const int32_t parts = plan->n_parts > 1 && plan->part_ptr ? plan->n_parts : 1;
     for (int32_t c0 = 0; c0 < k; c0 += cb) {
         const int32_t c1 = c0 + cb < k ? c0 + cb : k;
         const float* Xp = use_slab ? ws + (int64_t)(c0 / cb) * A->n * cb : X;
         const int64_t ldp = use_slab ? cb : ldx;
         const int32_t xs = use_slab ? c0 : 0;
-#define SPX_SR_CASE(L)                                                                                         \
-    case L:                                                                                                    \
-        sddmm_rows_kernel<L><<<(unsigned)grid, SR_THREADS, 0, st>>>(A->m, A->indptr, A->indices, G, ldg, Xp, ldp, xs, \
-                                                                     c0, c1, scale, c0 > 0, out, rpg, threshold,   \
-                                                                     long_rows, n_long, long_blocks, med_rows,     \
-                                                                     n_med, med_blocks);                           \
+        for (int32_t p = 0; p < parts; ++p) {
+            // pass p: the entries of each row whose columns lie in range p (disjoint outputs)
+            const int32_t* sb = p == 0 ? A->indptr : plan->part_ptr + (int64_t)(p - 1) * A->m;
+            const int32_t* se = p == parts - 1 ? A->indptr + 1 : plan->part_ptr + (int64_t)p * A->m;
+#define SPX_SR_CASE(L)                                                                                           \
+    case L:                                                                                                      \
+        sddmm_rows_kernel<L><<<(unsigned)grid, SR_THREADS, 0, st>>>(A->m, A->indptr, sb, se, A->indices, G, ldg, Xp, \
+                                                                     ldp, xs, c0, c1, scale, c0 > 0, out, rpg,       \
+                                                                     threshold, long_rows, n_long, long_blocks,      \
+                                                                     med_rows, n_med, med_blocks);                   \
         break;
-        switch (lpr) {
-            SPX_SR_CASE(2)
-            SPX_SR_CASE(4)
-            SPX_SR_CASE(8)
-            SPX_SR_CASE(16)
-            SPX_SR_CASE(32)
-            default: return set_error(SPX_INVALID_ARG, "sddmm: bad lane count %d", lpr);
-        }
+            switch (lpr) {
+                SPX_SR_CASE(2)
+                SPX_SR_CASE(4)
+                SPX_SR_CASE(8)
+                SPX_SR_CASE(16)
+                SPX_SR_CASE(32)
+                default: return set_error(SPX_INVALID_ARG, "sddmm: bad lane count %d", lpr);
+            }
 #undef SPX_SR_CASE
-        SPX_CHECK_LAUNCH("sddmm rows");
+            SPX_CHECK_LAUNCH("sddmm rows");
+        }
     }
     return SPX_OK;
 }

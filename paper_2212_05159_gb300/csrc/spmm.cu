@@ -10,6 +10,12 @@
 // floats) stays resident in L2 while the CSR streams pass through with evict-first
 // loads.  One launch per block, blocks in column order.
 //
+// Column parts.  When the gathered operand is larger than L2 (2^20 x 32 floats is 134 MB),
+// the plan may split every row's entries by column range (A's columns, i.e. X's rows)
+// into n_parts consecutive segments; one pass per range then gathers only from that
+// range's rows of X, which stay resident in L2, and adds into Y (beta = 1 after the first
+// pass).  Each CSR entry is still read once; Y is read and written once more per extra pass.
+//
 // Short rows.  A lane group of LPR lanes spans the block's columns with float4 loads
 // and owns whole rows (rows_per_group consecutive rows per group): it loads the (column,
 // value) pairs of the row 8 at a time -- the next batch is fetched while the current
@@ -43,6 +49,10 @@ namespace {
 constexpr int SPMM_THREADS = 256;
 constexpr int SPMM_WARPS = SPMM_THREADS / 32;
 constexpr int BATCH = 8;                       // entries per gather batch
+// At least 6 resident blocks per SM (registers capped at 40): the gathers are latency-bound,
+// and 48 warps per SM keep more of them in flight than the 40 the uncapped kernel gets
+// (measured on GB300: 15-19 % faster at k = 32 and 128; capping at 32 registers spills).
+constexpr int SPMM_MIN_BLOCKS = 6;
 
 template <int VEC>
 __device__ __forceinline__ void fma_row(float (&acc)[VEC], float v, const float* __restrict__ p, uint64_t pol) {
@@ -123,8 +133,9 @@ __device__ __forceinline__ void gather_batch(float (&acc)[VEC], const int (&j)[(
 }
 
 template <int VEC, int LPR, bool PERM>
-__global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
-    int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+__global__ void __launch_bounds__(SPMM_THREADS, SPMM_MIN_BLOCKS) spmm_kernel(
+    int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ seg_b,
+    const int32_t* __restrict__ seg_e, int32_t accumulate, const int32_t* __restrict__ indices,
     const float* __restrict__ vals, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t ldx,
     int32_t x_shift, int32_t col_begin, int32_t col_end, float* __restrict__ Y, int64_t ldy, float alpha, float beta,
     int32_t rows_per_group, int32_t threshold, const int32_t* __restrict__ long_rows, int32_t n_long,
@@ -141,6 +152,8 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
     const bool colok = col < col_end;
     const uint64_t pol_stream = policy_evict_first();
     const uint64_t pol_keep = policy_evict_last();
+    const float beta_eff = accumulate ? 1.f : beta;     // later column parts add into Y
+    const bool split = seg_b != indptr || seg_e != indptr + 1;
 
     if ((int)blockIdx.x < long_blocks) {
         // ---------------- long rows: all groups of the block on one row
@@ -149,7 +162,8 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
         constexpr int GB = SPMM_WARPS * G;
         for (int q = blockIdx.x; q < n_long; q += long_blocks) {
             const int row = long_rows[q];
-            const int a = indptr[row], b = indptr[row + 1];
+            const int a = seg_b[row], b = seg_e[row];
+            if (accumulate && a == b) continue;         // block-uniform: nothing to add
             float acc[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
@@ -174,7 +188,7 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
                 for (int w = 1; w < SPMM_WARPS; ++w)
 #pragma unroll
                     for (int v = 0; v < VEC; ++v) tot[v] += red[w][c * VEC + v];
-                store_row<VEC>(Y + (int64_t)row * ldy + col, tot, alpha, beta);
+                store_row<VEC>(Y + (int64_t)row * ldy + col, tot, alpha, beta_eff);
             }
             __syncthreads();
         }
@@ -186,7 +200,8 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
         const int nw = med_blocks * SPMM_WARPS;
         for (int q = ((int)blockIdx.x - long_blocks) * SPMM_WARPS + warp; q < n_med; q += nw) {
             const int row = med_rows[q];
-            const int a = indptr[row], b = indptr[row + 1];
+            const int a = seg_b[row], b = seg_e[row];
+            if (accumulate && a == b) continue;         // warp-uniform
             float acc[VEC];
 #pragma unroll
             for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
             for (int off = LPR; off < 32; off <<= 1)
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) acc[v] += __shfl_xor_sync(FULL, acc[v], off);
-            if (g == 0 && colok) store_row<VEC>(Y + (int64_t)row * ldy + col, acc, alpha, beta);
+            if (g == 0 && colok) store_row<VEC>(Y + (int64_t)row * ldy + col, acc, alpha, beta_eff);
         }
         return;
     }
@@ -221,8 +236,13 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
     for (int p = 0; p < rows_per_group; ++p) {
         const int64_t row = row0 + p;
         if (row >= m) break;
-        const int a = indptr[row], b = indptr[row + 1];
+        int a = indptr[row], b = indptr[row + 1];
         if (b - a > threshold) continue;            // a long-row block takes it
+        if (split) {
+            a = seg_b[row];
+            b = seg_e[row];
+            if (accumulate && a == b) continue;     // group-uniform
+        }
         float acc[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
@@ -240,7 +260,7 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_kernel(
             if (e + BATCH < b) load_batch<LPR, PERM>(jn, vn, e + BATCH, b, c, indices, vals, perm, pol_stream);
             gather_batch<VEC, LPR>(acc, jc, vc, gmask, colok, X, ldx, xcol, pol_keep);
         }
-        if (colok) store_row<VEC>(Y + row * ldy + col, acc, alpha, beta);
+        if (colok) store_row<VEC>(Y + row * ldy + col, acc, alpha, beta_eff);
     }
 }
 
@@ -433,13 +453,15 @@ int ilog2_ceil(int64_t x) {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 template <int VEC, bool PERM>
-spx_status launch_lpr(int lpr, unsigned grid, cudaStream_t st, const spx_csr* A, const int32_t* perm,
+spx_status launch_lpr(int lpr, unsigned grid, cudaStream_t st, const spx_csr* A, const int32_t* seg_b,
+                      const int32_t* seg_e, int32_t accumulate, const int32_t* perm,
                       const float* vals, const float* X, int64_t ldx, int32_t xs, int32_t c0, int32_t c1, float* Y,
                       int64_t ldy, float alpha, float beta, int32_t rpg, int32_t thr, const int32_t* lr,
                       int32_t n_long, int32_t long_blocks, const int32_t* mr, int32_t n_med, int32_t med_blocks) {
 #define SPX_SPMM_CASE(L)                                                                                        \
     case L:                                                                                                     \
-        spmm_kernel<VEC, L, PERM><<<grid, SPMM_THREADS, 0, st>>>(A->m, A->indptr, A->indices, vals, perm, X, ldx, \
+        spmm_kernel<VEC, L, PERM><<<grid, SPMM_THREADS, 0, st>>>(A->m, A->indptr, seg_b, seg_e, accumulate,      \
+                                                                 A->indices, vals, perm, X, ldx,                  \
                                                                  xs, c0, c1, Y, ldy, alpha, beta, rpg, thr, lr,  \
                                                                  n_long, long_blocks, mr, n_med, med_blocks);    \
         break;
@@ -516,8 +538,9 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
     const int64_t grid = short_blocks + long_blocks + med_blocks;
     if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
     if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, sh.cb, slab_ws, st));
+    const int32_t parts = plan && plan->n_parts > 1 && plan->part_ptr ? plan->n_parts : 1;
     const bool bulk = !PERM && vec4 && plan && plan->engine == 1 && sh.cb % 4 == 0 && sh.lpr >= 2 &&
-                      sh.lpr * 4 >= sh.cb;
+                      sh.lpr * 4 >= sh.cb && parts == 1;
     if (bulk) {
         const size_t smem = bulk_smem_bytes();
         const int64_t rows_per_bblock = (int64_t)BK_WARPS * G * sh.rpg;
@@ -553,7 +576,8 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
 #undef SPX_BULK_CASE
             SPX_CHECK_LAUNCH(who);
             if (long_blocks + med_blocks > 0) {
-                spx_status s = launch_lpr<4, false>(sh.lpr, (unsigned)(long_blocks + med_blocks), st, A, perm, vals,
+                spx_status s = launch_lpr<4, false>(sh.lpr, (unsigned)(long_blocks + med_blocks), st, A,
+                                                    A->indptr, A->indptr + 1, 0, perm, vals,
                                                     Xp, ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold,
                                                     long_rows, n_long, long_blocks, med_rows, n_med, med_blocks);
                 if (s != SPX_OK) return s;
@@ -567,14 +591,20 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
         const float* Xp = use_slab ? slab_ws + (int64_t)(c0 / sh.cb) * A->n * sh.cb : X;
         const int64_t ldp = use_slab ? sh.cb : ldx;
         const int32_t xs = use_slab ? c0 : 0;
-        spx_status s = vec4 ? launch_lpr<4, PERM>(sh.lpr, (unsigned)grid, st, A, perm, vals, Xp, ldp, xs, c0, c1, Y,
-                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks,
-                                                  med_rows, n_med, med_blocks)
-                            : launch_lpr<1, PERM>(sh.lpr, (unsigned)grid, st, A, perm, vals, Xp, ldp, xs, c0, c1, Y,
-                                                  ldy, alpha, beta, sh.rpg, threshold, long_rows, n_long, long_blocks,
-                                                  med_rows, n_med, med_blocks);
-        if (s != SPX_OK) return s;
-        SPX_CHECK_LAUNCH(who);
+        for (int32_t p = 0; p < parts; ++p) {
+            // pass p: entries [seg_b[i], seg_e[i]) of row i, i.e. columns in range p
+            const int32_t* sb = p == 0 ? A->indptr : plan->part_ptr + (int64_t)(p - 1) * A->m;
+            const int32_t* se = p == parts - 1 ? A->indptr + 1 : plan->part_ptr + (int64_t)p * A->m;
+            const int32_t accum = p > 0 ? 1 : 0;
+            spx_status s = vec4 ? launch_lpr<4, PERM>(sh.lpr, (unsigned)grid, st, A, sb, se, accum, perm, vals, Xp,
+                                                      ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold,
+                                                      long_rows, n_long, long_blocks, med_rows, n_med, med_blocks)
+                                : launch_lpr<1, PERM>(sh.lpr, (unsigned)grid, st, A, sb, se, accum, perm, vals, Xp,
+                                                      ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold,
+                                                      long_rows, n_long, long_blocks, med_rows, n_med, med_blocks);
+            if (s != SPX_OK) return s;
+            SPX_CHECK_LAUNCH(who);
+        }
     }
     return SPX_OK;
 }
@@ -593,6 +623,26 @@ __global__ void long_compact_kernel(int32_t m, const int32_t* __restrict__ flags
                                     int32_t* __restrict__ long_rows) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < m && flags[i]) long_rows[pos[i]] = (int32_t)i;
+}
+
+// part_ptr[(p - 1) * m + i] = first entry of row i with column >= p * w (binary search in
+// the sorted row), p = 1 .. parts - 1
+__global__ void part_split_kernel(int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+                                  int32_t w, int32_t parts, int32_t* __restrict__ part_ptr) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int a = indptr[i], b = indptr[i + 1];
+    int lo = a;
+    for (int p = 1; p < parts; ++p) {
+        const int64_t bound = (int64_t)p * w;
+        int hi = b;                                   // first entry in [lo, b) with column >= bound
+        while (lo < hi) {
+            const int mid = lo + ((hi - lo) >> 1);
+            if ((int64_t)indices[mid] < bound) lo = mid + 1;
+            else hi = mid;
+        }
+        part_ptr[(int64_t)(p - 1) * m + i] = lo;
+    }
 }
 
 size_t rowplan_ws(int32_t m) {
@@ -666,6 +716,19 @@ extern "C" spx_status spx_rowplan_build_medium(const spx_csr* A, int32_t medium_
     SPX_CUDA(cudaMemcpyAsync(n_medium_host, pos + A->m, sizeof(int32_t), cudaMemcpyDeviceToHost, st),
              "spx_rowplan_build_medium copy");
     SPX_CUDA(cudaStreamSynchronize(st), "spx_rowplan_build_medium sync");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_rowplan_build_parts(const spx_csr* A, int32_t n_parts, int32_t* part_ptr, void* stream) {
+    SPX_TRY(check_csr(A, false, "spx_rowplan_build_parts"));
+    if (n_parts < 2 || n_parts > A->n || (A->m > 0 && !part_ptr))
+        return set_error(SPX_INVALID_ARG, "spx_rowplan_build_parts: n_parts = %d (need 2 <= n_parts <= n = %d)",
+                         n_parts, A->n);
+    if (A->m == 0) return SPX_OK;
+    const int32_t w = (int32_t)(((int64_t)A->n + n_parts - 1) / n_parts);
+    part_split_kernel<<<(unsigned)((A->m + 255) / 256), 256, 0, as_stream(stream)>>>(A->m, A->indptr, A->indices, w,
+                                                                                    n_parts, part_ptr);
+    SPX_CHECK_LAUNCH("spx_rowplan_build_parts");
     return SPX_OK;
 }
 

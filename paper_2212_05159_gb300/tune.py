@@ -1,11 +1,13 @@
 """Autotuner for the launch parameters of the row-wise products and of SDDMM.
 
 For a given pattern and dense width k it times the candidate column blocks (columns
-gathered per pass) and rows-per-group settings with CUDA events on the current
-stream and keeps the fastest.  Results are cached per (pattern statistics, k, kind) in
+gathered per pass), rows-per-group settings, gather engines and column-part splits (passes
+over ranges of the dense operand's rows) with CUDA events on the current stream and keeps
+the fastest.  Results are cached per (pattern statistics, k, kind) in
 memory and in ``_build/tune_cache.json``.  Timing only: the kernels computed with any
-candidate give results within the same tolerance (the column split changes only which
-pass adds which columns, never the order of a sum).
+candidate give results within the same tolerance (a column block changes only which pass
+adds which columns; a column-part split sums each output as a fixed sequence of per-part
+partial sums).
 """
 from __future__ import annotations
 
@@ -67,9 +69,18 @@ def _col_blocks(k: int):
     return c
 
 
+PART_COUNTS = (1, 2, 3, 4)
+
+
+def _part_counts(rows_in: int, k: int):
+    """Split counts worth timing: more than one only when the gathered operand exceeds ~32 MB."""
+    return [p for p in PART_COUNTS if p == 1 or rows_in * k * 4 > (32 << 20) * (p - 1)]
+
+
 def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
-    """Best (col_block, rows_per_group, engine) for spx_spmm (or spx_spmm_t when transposed)."""
-    kind = "spmm_t" if transposed else "spmm"
+    """Best (col_block, rows_per_group, engine, n_parts) for spx_spmm (or spx_spmm_t when
+    transposed)."""
+    kind = "spmm_t2" if transposed else "spmm2"
     key = _key(A, k, kind)
     with _lock:
         c = _load()
@@ -82,9 +93,13 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
     base = A.t_plan() if transposed else A.plan()
     best, best_ms, table = None, float("inf"), {}
     engines = (0, 1) if k % 4 == 0 else (0,)
-    for cb, rpg, eng in [(cb, rpg, eng) for cb in _col_blocks(k) for rpg in (1, 2, 4) for eng in engines]:
+    cands = [(cb, rpg, eng, 1) for cb in _col_blocks(k) for rpg in (1, 2, 4) for eng in engines]
+    cands += [(cb, rpg, 0, np_) for cb in _col_blocks(k) for rpg in (1, 2, 4)
+              for np_ in _part_counts(rows_in, min(cb, k)) if np_ > 1]
+    for cb, rpg, eng, np_ in cands:
         if True:
-            plan = base.with_params(cb, rpg, eng)
+            parts = (A.t_parts(np_) if transposed else A.parts(np_)) if np_ > 1 else None
+            plan = base.with_params(cb, rpg, eng, parts)
             if transposed:
                 _, _, perm = A.transpose_pattern()
                 s = A.t_struct()
@@ -96,9 +111,9 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
                 fn = lambda: abi.spx_spmm(s, X, Y, 1.0, 0.0, plan, ws)  # noqa: E731
             ms = _time(fn)
             del ws
-            table[f"{cb},{rpg},{eng}"] = ms
+            table[f"{cb},{rpg},{eng},{np_}"] = ms
             if ms < best_ms:
-                best, best_ms = (cb, rpg, eng), ms
+                best, best_ms = (cb, rpg, eng, np_), ms
     with _lock:
         _load()[key] = {"best": list(best), "ms": best_ms, "table": table}
         _save()
@@ -106,8 +121,8 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
 
 
 def tune_sddmm(A: CSR, k: int, force: bool = False):
-    """Best (column block, "rows" | "chunks") for spx_sddmm."""
-    key = _key(A, k, "sddmm2")
+    """Best (column block, "rows" | "chunks", n_parts) for spx_sddmm."""
+    key = _key(A, k, "sddmm3")
     with _lock:
         c = _load()
         if key in c and not force:
@@ -120,13 +135,13 @@ def tune_sddmm(A: CSR, k: int, force: bool = False):
     best, best_ms, table = None, float("inf"), {}
     base = A.plan()
     for cb in _col_blocks(k):
-        for mode in ("chunks", "rows"):
+        for mode, np_ in [("chunks", 1)] + [("rows", p) for p in _part_counts(A.n, min(cb, k))]:
             ws = abi.workspace(abi.spx_sddmm_workspace_size(s, k, cb), dev)
-            plan = base.with_params(cb, 2, 0) if mode == "rows" else None
+            plan = base.with_params(cb, 2, 0, A.parts(np_)) if mode == "rows" else None
             ms = _time(lambda: abi.spx_sddmm(s, G, X, out, 1.0, cb, ws, plan=plan))
-            table[f"{cb},{mode}"] = ms
+            table[f"{cb},{mode},{np_}"] = ms
             if ms < best_ms:
-                best, best_ms = (cb, mode), ms
+                best, best_ms = (cb, mode, np_), ms
     with _lock:
         _load()[key] = {"best": best, "ms": best_ms, "table": table}
         _save()
@@ -138,4 +153,12 @@ def tuned_plan(A: CSR, k: int, transposed: bool = False):
     best = tune_rows(A, k, transposed)
     cb, rpg = best[0], best[1]
     eng = best[2] if len(best) > 2 else 0
-    return base.with_params(cb, rpg, eng)
+    np_ = best[3] if len(best) > 3 else 1
+    parts = (A.t_parts(np_) if transposed else A.parts(np_)) if np_ > 1 else None
+    return base.with_params(cb, rpg, eng, parts)
+
+
+def tuned_sddmm_plan(A: CSR, k: int):
+    """(column block, plan or None) for spx_sddmm: plan None selects the entry-chunk kernel."""
+    cb, mode, np_ = tune_sddmm(A, k)
+    return cb, (A.plan().with_params(cb, 2, 0, A.parts(np_)) if mode == "rows" else None)

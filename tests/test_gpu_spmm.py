@@ -236,3 +236,54 @@ def test_bulk_engine_k_widths_and_alpha_beta(mat, k):
     ref = 0.5 * oracle.spmm(A, X) - 1.5 * y0.astype(np.float64)
     norm = 0.5 * oracle.spmm(abs_csr(A), np.abs(X)) + 1.5 * np.abs(y0)
     assert_close_normalised(host(Y), ref, norm, what=f"bulk spmm {name} k={k}")
+
+
+@pytest.mark.parametrize("n_parts", [2, 3, 5])
+def test_column_parts_split_offsets(mat, n_parts):
+    """spx_rowplan_build_parts: the offset of the first entry of each row at or past each
+    column boundary, bit-exact against a per-row binary search on the host."""
+    name, A, dA = mat
+    if n_parts > A.n:
+        pytest.skip("more parts than columns")
+    pp, _ = dA.parts(n_parts)
+    got = host(pp)[: (n_parts - 1) * A.m].reshape(n_parts - 1, A.m)
+    w = -(-A.n // n_parts)
+    for p in range(1, n_parts):
+        want = np.array([A.indptr[i] + np.searchsorted(A.indices[A.indptr[i]:A.indptr[i + 1]], p * w)
+                         for i in range(A.m)], dtype=np.int64)
+        np.testing.assert_array_equal(got[p - 1], want, err_msg=f"{name} part {p}")
+
+
+@pytest.mark.parametrize("n_parts,cb,rpg", [(2, 32, 4), (3, 16, 2), (4, 8, 1), (2, 4, 3)])
+def test_column_parts_products_match_oracle(mat, n_parts, cb, rpg):
+    """SpMM, A^T G and SDDMM with the rows split into column parts (one pass per part,
+    later passes adding into the output), with alpha / beta on the forward product."""
+    from paper_2212_05159_gb300 import abi
+    name, A, dA = mat
+    if n_parts > min(A.n, A.m):
+        pytest.skip("more parts than columns")
+    k = 32
+    X = synth.normal((A.n, k), seed=70)
+    G = synth.normal((A.m, k), seed=71)
+    y0 = synth.normal((A.m, k), seed=72)
+    plan = dA.plan().with_params(cb, rpg, 0, dA.parts(n_parts))
+    Y = dev(y0.copy())
+    ws = abi.workspace(abi.spx_spmm_workspace_size(dA.struct(), k, plan), "cuda")
+    abi.spx_spmm(dA.struct(), dev(X), Y, 0.5, -1.5, plan, ws)
+    ref = 0.5 * oracle.spmm(A, X) - 1.5 * y0.astype(np.float64)
+    norm = 0.5 * oracle.spmm(abs_csr(A), np.abs(X)) + 1.5 * np.abs(y0)
+    assert_close_normalised(host(Y), ref, norm, what=f"spmm parts={n_parts} {name} cb={cb}")
+    tplan = dA.t_plan().with_params(cb, rpg, 0, dA.t_parts(n_parts))
+    gX = torch.empty(A.n, k, device="cuda")
+    _, _, perm = dA.transpose_pattern()
+    abi.spx_spmm_t(dA.t_struct(), perm, dev(G), gX, 1.0, 0.0, tplan,
+                   abi.workspace(abi.spx_spmm_t_workspace_size(dA.t_struct(), k, tplan), "cuda"))
+    assert_close_normalised(host(gX), oracle.spmm_t(A, G), oracle.spmm_t(abs_csr(A), np.abs(G)),
+                            what=f"spmm_t parts={n_parts} {name} cb={cb}")
+    out = torch.full((A.nnz,), float("nan"), device="cuda")          # every entry must be written
+    splan = dA.plan().with_params(cb, 2, 0, dA.parts(n_parts))
+    abi.spx_sddmm(dA.struct(), dev(G), dev(X), out, 1.0, cb,
+                  abi.workspace(abi.spx_sddmm_workspace_size(dA.struct(), k, cb), "cuda"), plan=splan)
+    abi.spx_check_device()
+    assert_close_normalised(host(out), oracle.sddmm(A, G, X), oracle.sddmm(A, np.abs(G), np.abs(X)),
+                            what=f"sddmm parts={n_parts} {name} cb={cb}")
