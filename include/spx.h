@@ -69,9 +69,9 @@ typedef struct spx_rowplan {
     const int32_t* long_rows; /* device int32[n_long], increasing row ids */
     int32_t n_long;           /* host-known count */
     int32_t threshold;        /* rows with more than this many entries are "long" */
-    int32_t col_block;        /* dense columns per pass (0 = choose from the sizes); one
-                                 pass per block keeps the gathered slab of the dense
-                                 operand resident in L2 */
+    int32_t col_block;        /* dense columns per pass (0 = all k in one pass); narrower
+                                 blocks gather from column-block slabs of the dense
+                                 operand repacked into the workspace, one pass per block */
     int32_t rows_per_group;   /* rows walked by one lane group (0 = default) */
     int32_t engine;           /* gathers of the dense rows: 0 = loads into registers,
                                  1 = TMA-engine bulk copies into shared memory (needs k and
@@ -171,11 +171,12 @@ spx_status spx_sddmm_workspace_size(const spx_csr* A, int32_t k, int32_t col_blo
  *   out[e] = scale * sum_c G[i,c] * X[j,c]   for every stored entry e = (i, j) of A,
  * i.e. (G X^T) masked to mask(A) -- an SDDMM.  A.values is not read.
  * G: device float32 m x k (ldg); X: device float32 n x k (ldx); out: device float32[nnz].
- * col_block: dense columns per pass (0 = choose from the sizes); with several passes
+ * col_block: dense columns per pass (0 = all k in one pass); with several passes
  * the partial dot products are added into out in column order.
  * plan: optional row plan of A (spx_rowplan_build[_medium]); with it rows are binned as in
  * spx_spmm and each lane group keeps G's row in registers, without it every warp takes an
- * equal slice of the entries.  Its launch fields (col_block, engine) are not used here.
+ * equal slice of the entries; its rows_per_group and n_parts fields apply, its col_block
+ * and engine fields are not used (col_block is the argument).
  * workspace: device scratch of spx_sddmm_workspace_size() bytes, or NULL (as spx_spmm). */
 spx_status spx_sddmm(const spx_csr* A, const float* G, int64_t ldg, const float* X,
                      int64_t ldx, int32_t k, float scale, float* out, int32_t col_block,
@@ -320,8 +321,8 @@ spx_status spx_cg_workspace_size(int32_t n, size_t* bytes);
  *          on the first block of each cluster.  Ignored (may be NULL) for kinds 0-3.
  * iters, status (spx_status per system: OK, MAXITER, BREAKDOWN, NONFINITE): device
  * int32[nsys]; relres: device float64[nsys], the true relative residual of the
- * returned x.  One launch of thread-block clusters (8 blocks per system); capturable
- * in a CUDA graph.  The call's own status reports argument / launch errors only. */
+ * returned x.  One launch of thread-block clusters (one cluster per system at a time,
+ * shape set by spx_cg_set_launch); capturable in a CUDA graph.  The call's own status reports argument / launch errors only. */
 spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
                           const int32_t* order, const float* b, double* x, int32_t pc_kind,
                           const float* pc_diag_inv, const spx_csr* L, const spx_csr* LT,
@@ -329,10 +330,12 @@ spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys
                           double delta, int32_t* iters, int32_t* status, double* relres,
                           void* workspace, size_t workspace_bytes, void* stream);
 
-/* Launch shape of spx_cg_batched for this process: threads per block (256, 512 or 1024)
- * and blocks per cluster (1, 2, 4 or 8); 0 keeps the default (512, 8).  A tuning knob:
- * results do not depend on it beyond floating-point rounding of the reductions. */
-spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t cluster_size);
+/* Launch shape of spx_cg_batched for this process: threads per block (256, 512 or 1024),
+ * blocks per cluster (1, 2, 4, 8, or 16 -- a non-portable cluster size the call opts into)
+ * and the most clusters resident at once (fewer systems in flight keep their vectors in
+ * L2); 0 keeps the default (512 threads, 8 blocks, as many clusters as fit).  A tuning
+ * knob: results do not depend on it beyond floating-point rounding of the reductions. */
+spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t cluster_size, int32_t max_clusters);
 
 /* dinv[i] = 1 / a_ii (0 where the diagonal is absent or zero); device float32[m]. */
 spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream);

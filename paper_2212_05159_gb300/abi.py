@@ -98,7 +98,7 @@ SIGNATURES = {
     "spx_ic0_analyse": [_CSRP, _P, _I32, _P, _P, _P, _P, _SZ, _P],
     "spx_ic0_factor": [_CSRP, _P, _P, _I32, _P, _P, _P, _P, _P, _P],
     "spx_diag_inverse": [_CSRP, _P, _P],
-    "spx_cg_set_launch": [_I32, _I32],
+    "spx_cg_set_launch": [_I32, _I32, _I32],
     "spx_masked_outer_f64": [_CSRP, _P, _P, _D, _P, _P],
     "spx_pcg_train_workspace_size": [_I32, _I32, ctypes.POINTER(_SZ)],
     "spx_pcg_train": [_CSRP, _P, _I32, _CSRP, _CSRP, _P, _I32, _P, _P, _P, _P, _SZ, _P],
@@ -483,5 +483,6 @@ def spx_to_bf16(src, dst):
     _check(lib().spx_to_bf16(int(src.numel()), ptr(src), ptr(dst), _stream()), "spx_to_bf16")
 
 
-def spx_cg_set_launch(threads_per_block: int = 0, cluster_size: int = 0):
-    _check(lib().spx_cg_set_launch(int(threads_per_block), int(cluster_size)), "spx_cg_set_launch")
+def spx_cg_set_launch(threads_per_block: int = 0, cluster_size: int = 0, max_clusters: int = 0):
+    _check(lib().spx_cg_set_launch(int(threads_per_block), int(cluster_size), int(max_clusters)),
+           "spx_cg_set_launch")

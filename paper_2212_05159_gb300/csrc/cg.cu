@@ -6,8 +6,9 @@
 // system at a time from a queue (largest first when an order is given) and runs PCG on
 // it to completion; its blocks split the system's rows.  Dot products are reduced inside
 // each block and then across the cluster through distributed shared memory (one cluster
-// barrier per reduction, partials double-buffered, summed in rank order: deterministic).
-// With few clusters active at once, the vectors of the systems in flight stay in L2.
+// barrier per reduction, partials double-buffered, summed in rank order: deterministic);
+// the scalars of the iteration (alpha, beta, norms, stopping decisions) are then computed
+// once per block by its thread 0 in FP64 and broadcast through shared memory.
 //
 // Precision (GB300 has ~1/60 of its FP32 rate in FP64): the iteration runs in FP32 with
 // "reliable updates" -- the solution accumulates in an FP32 partial that is folded into
@@ -15,7 +16,7 @@
 // at every fold the residual is recomputed in FP64 as b - A x and that true residual
 // decides convergence (||b - A x|| <= tol ||b||).  Inner products accumulate per thread
 // in double-float (an FP32 pair with exact products, ~44 significant bits) and are
-// combined in FP64.  Preconditioners: none, Jacobi (z = D^-1 r), the factored
+// combined in double-float up to the last cross-block sum, which is converted to FP64.  Preconditioners: none, Jacobi (z = D^-1 r), the factored
 // approximate inverse M = L L^T of Section 4.3 (z = L (L^T r), two sparse products), and
 // an explicit sparse M (z = M r, one product; e.g. L L^T formed once by SpGEMM), and
 // IC(0) (z = (L L^T)^-1 r by two level-scheduled triangular solves).
@@ -86,42 +87,78 @@ __device__ __forceinline__ void df_add_prod(DF& s, float a, float b) {
     s.lo += err + pl;
 }
 
-__device__ __forceinline__ double df_value(const DF& s) { return (double)s.hi + (double)s.lo; }
+// a + b in double-float (two-sum of the high parts, low parts added, renormalised)
+__device__ __forceinline__ DF df_add(const DF& a, const DF& b) {
+    const float t = a.hi + b.hi;
+    const float bp = t - a.hi;
+    const float err = (a.hi - (t - bp)) + (b.hi - bp) + (a.lo + b.lo);
+    const float hi = t + err;
+    return DF{hi, err - (hi - t)};
+}
 
-// Sums NV values over the cluster: block tree in FP64, then the CL block partials read
-// through DSMEM in rank order.  slot alternates so one barrier per reduction suffices.
+__device__ __forceinline__ DF df_of(double x) {
+    const float hi = (float)x;
+    return DF{hi, (float)(x - (double)hi)};
+}
+
+__device__ __forceinline__ DF df_shfl_down(const DF& v, int o) {
+    return DF{__shfl_down_sync(FULL, v.hi, o), __shfl_down_sync(FULL, v.lo, o)};
+}
+
+// Sums NV double-float values over the cluster; the totals land in `out` of thread 0 of
+// every block (all blocks add the same partials in the same order, so they agree).  All
+// arithmetic before the last step is FP32 (double-float): GB300's FP64 rate is ~1/64 of its
+// FP32 rate, and a reduction done in FP64 by every thread costs more than the sparse
+// product it follows.  Warp: shuffle tree; block: warp 0 over the warp partials; cluster:
+// lanes of warp 0 read the block partials through DSMEM (rank order), double-buffered so
+// one cluster barrier per reduction suffices.
 template <int NT, int NV>
-__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, double (&v)[NV], double (*red)[4],
-                                           double (*part)[4], int& slot) {
+__device__ __forceinline__ void cluster_sum(cg::cluster_group& cl, DF (&v)[NV], double (&out)[NV], float2 (*red)[4],
+                                           float2 (*part)[4], int& slot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
+        for (int o = 16; o >= 1; o >>= 1) v[k] = df_add(v[k], df_shfl_down(v[k], o));
     }
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+        for (int k = 0; k < NV; ++k) red[warp][k] = make_float2(v[k].hi, v[k].lo);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    const unsigned ncl = cl.num_blocks();
+    if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < NT / 32; ++w) s += red[w][k];
-            part[slot][k] = s;
+            DF t{0.f, 0.f};
+            if (lane < NT / 32) t = DF{red[lane][k].x, red[lane][k].y};
+#pragma unroll
+            for (int o = NT / 64; o >= 1; o >>= 1) t = df_add(t, df_shfl_down(t, o));
+            if (lane == 0) part[slot][k] = make_float2(t.hi, t.lo);
         }
     }
     cl.sync();
-    const unsigned ncl = cl.num_blocks();
+    if (warp == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = 0.0;
-    for (unsigned rk = 0; rk < ncl; ++rk) {
-        const double* rp = cl.map_shared_rank(&part[slot][0], rk);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] += rp[k];
+        for (int k = 0; k < NV; ++k) {
+            DF t{0.f, 0.f};
+            if (lane < (int)ncl) {
+                const float2 pv = *cl.map_shared_rank(&part[slot][k], (unsigned)lane);
+                t = DF{pv.x, pv.y};
+            }
+            for (int o = 16; o >= 1; o >>= 1)
+                if (o < (int)ncl) t = df_add(t, df_shfl_down(t, o));
+            out[k] = (double)t.hi + (double)t.lo;
+        }
     }
     slot ^= 1;
 }
+
+// Scalars of the iteration, decided by thread 0 of each block and read by all its threads.
+struct CgBcast {
+    float alpha, beta;
+    int action;                // ACT_* below
+};
+constexpr int ACT_GO = 0, ACT_STOP = 1, ACT_FOLD = 2;
 
 // One row of a sparse product, entries in order; the loads of up to 8 entries are issued
 // together (predicated tail) so that a row costs two dependent round trips, not one per
@@ -207,13 +244,16 @@ __device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi,
         cl.sync();                                               // z complete
     } else if (a.pc == 3) {
         cl.sync();                                               // r complete
+#pragma unroll 2
         for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.r, i);      // z = M r
     } else if (a.pc == 2) {
         cl.sync();                                               // r complete
+#pragma unroll 2
         for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.w[i] = spmv_row(a.lt_ptr, a.lt_idx, a.lt_val, a.r, i);   // w = L^T r
         cl.sync();                                               // w complete
+#pragma unroll 2
         for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.w, i);      // z = L w
     } else {
@@ -234,18 +274,22 @@ __device__ __forceinline__ double true_residual(const CgArgs& a, int lo, int hi)
     return s;
 }
 
+// Registers capped at 64 (1024 / NT blocks per SM): the launch sizes its grid for that many
+// resident blocks.
 template <int NT>
-__global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
+__global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank();
     const unsigned ncl = cl.num_blocks();
-    __shared__ double red[CG_MAX_WARPS][4];
-    __shared__ double part[2][4];
+    __shared__ float2 red[CG_MAX_WARPS][4];
+    __shared__ float2 part[2][4];
     __shared__ int sys_sh;
+    __shared__ CgBcast bc;
     int slot = 0;
+    const bool t0 = threadIdx.x == 0;
 
     for (;;) {
-        if (rank == 0 && threadIdx.x == 0) sys_sh = atomicAdd(a.queue, 1);
+        if (rank == 0 && t0) sys_sh = atomicAdd(a.queue, 1);
         cl.sync();
         const int s = *cl.map_shared_rank(&sys_sh, 0);
         cl.sync();
@@ -255,66 +299,86 @@ __global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
         const int chunk = (R1 - R0 + (int)ncl - 1) / (int)ncl;
         const int lo = min(R1, R0 + (int)rank * chunk), hi = min(R1, lo + chunk);
 
+        // thread 0 of each block keeps the FP64 scalars; every block computes the same ones
+        double bnorm = 0.0, rz = 0.0, ref = 0.0, last_true = 1.0;
+        int status = SPX_MAXITER;
+
         // ---- x = 0, r = b, z = M r, p = z
-        double v2[2] = {0.0, 0.0};
-        {
-            DF bb{0.f, 0.f};
-            for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                const float bi = a.b[i];
-                a.x[i] = 0.0;
-                a.xp[i] = 0.f;
-                a.r[i] = bi;
-                df_add_prod(bb, bi, bi);
-            }
-            v2[0] = df_value(bb);
+        DF v2[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int i = lo + threadIdx.x; i < hi; i += NT) {
+            const float bi = a.b[i];
+            a.x[i] = 0.0;
+            a.xp[i] = 0.f;
+            a.r[i] = bi;
+            df_add_prod(v2[0], bi, bi);
         }
         apply_pc<NT>(a, cl, lo, hi, rank, sid);
-        {
-            DF rz{0.f, 0.f};
-            for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                const float zi = a.z[i];
-                a.p[i] = zi;
-                df_add_prod(rz, a.r[i], zi);
-            }
-            v2[1] = df_value(rz);
+        for (int i = lo + threadIdx.x; i < hi; i += NT) {
+            const float zi = a.z[i];
+            a.p[i] = zi;
+            df_add_prod(v2[1], a.r[i], zi);
         }
-        cluster_sum<NT, 2>(cl, v2, red, part, slot);
-        const double bnorm = sqrt(v2[0]);
-        double rz = v2[1];
-        double ref = bnorm;                 // residual norm at the last fold
-        double last_true = 1.0;
-        int status = SPX_MAXITER, it = 0;
+        {
+            double o2[2];
+            cluster_sum<NT, 2>(cl, v2, o2, red, part, slot);
+            if (t0) {
+                bnorm = sqrt(o2[0]);
+                rz = o2[1];
+                ref = bnorm;
+                int act = ACT_GO;
+                if (bnorm == 0.0) {
+                    status = SPX_OK;
+                    last_true = 0.0;
+                    act = ACT_STOP;
+                } else if (!isfinite(rz) || !isfinite(bnorm)) {
+                    status = SPX_NONFINITE;
+                    act = ACT_STOP;
+                } else if (!(rz > 0.0)) {
+                    status = SPX_BREAKDOWN;
+                    act = ACT_STOP;
+                }
+                bc.action = act;
+            }
+            __syncthreads();
+        }
+        int it = 0;
         bool dirty = false;                 // xp holds an unfolded part
-        if (bnorm == 0.0) {
-            status = SPX_OK;
-            last_true = 0.0;
-        } else if (!isfinite(rz) || !isfinite(bnorm)) {
-            status = SPX_NONFINITE;
-        } else if (!(rz > 0.0)) {
-            status = SPX_BREAKDOWN;
-        } else {
+        if (bc.action == ACT_GO) {
             while (it < a.maxit) {
-                cl.sync();                                      // p complete
-                double v1[1];
+                cl.sync();                                      // p complete (and bc read by all)
                 {
-                    DF pq{0.f, 0.f};
+                    DF v1[1] = {{0.f, 0.f}};
                     const float* __restrict__ Pv = a.p;
                     float* __restrict__ Qv = a.q;
 #pragma unroll 2
                     for (int i = lo + threadIdx.x; i < hi; i += NT) {
                         const float qi = spmv_row(a.a_ptr, a.a_idx, a.a_val, Pv, i);
                         Qv[i] = qi;
-                        df_add_prod(pq, Pv[i], qi);
+                        df_add_prod(v1[0], Pv[i], qi);
                     }
-                    v1[0] = df_value(pq);
+                    double o1[1];
+                    cluster_sum<NT, 1>(cl, v1, o1, red, part, slot);
+                    if (t0) {
+                        const double pq = o1[0];
+                        int act = ACT_GO;
+                        if (!isfinite(pq)) {
+                            status = SPX_NONFINITE;
+                            act = ACT_STOP;
+                        } else if (!(pq > 0.0)) {
+                            status = SPX_BREAKDOWN;
+                            act = ACT_STOP;
+                        } else {
+                            bc.alpha = (float)(rz / pq);
+                        }
+                        bc.action = act;
+                    }
+                    __syncthreads();
                 }
-                cluster_sum<NT, 1>(cl, v1, red, part, slot);
-                const double pq = v1[0];
-                if (!isfinite(pq)) { status = SPX_NONFINITE; break; }
-                if (!(pq > 0.0)) { status = SPX_BREAKDOWN; break; }
-                const float alpha = (float)(rz / pq);
+                if (bc.action == ACT_STOP) break;
+                const float alpha = bc.alpha;
                 dirty = true;
                 ++it;
+                DF v2n[2] = {{0.f, 0.f}, {0.f, 0.f}};
                 if (a.pc <= 1) {
                     // x_p += alpha p; r -= alpha q; z = M r (local); <r, z>, <r, r> -- one pass
                     float* __restrict__ XP = a.xp;
@@ -323,7 +387,6 @@ __global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
                     const float* __restrict__ Pv = a.p;
                     const float* __restrict__ Qv = a.q;
                     const float* __restrict__ DI = a.dinv;
-                    DF rzs{0.f, 0.f}, rrs{0.f, 0.f};
 #pragma unroll 2
                     for (int i = lo + threadIdx.x; i < hi; i += NT) {
                         XP[i] = fmaf(alpha, Pv[i], XP[i]);
@@ -331,11 +394,31 @@ __global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
                         R[i] = ri;
                         const float zi = a.pc == 1 ? DI[i] * ri : ri;
                         Z[i] = zi;
-                        df_add_prod(rzs, ri, zi);
-                        df_add_prod(rrs, ri, ri);
+                        df_add_prod(v2n[0], ri, zi);
+                        df_add_prod(v2n[1], ri, ri);
                     }
-                    v2[0] = df_value(rzs);
-                    v2[1] = df_value(rrs);
+                } else if (a.pc == 3) {
+                    // explicit M: update, barrier, then z = M r with the dots in the same pass
+                    float* __restrict__ XP = a.xp;
+                    float* __restrict__ R = a.r;
+                    const float* __restrict__ Pv = a.p;
+                    const float* __restrict__ Qv = a.q;
+#pragma unroll 2
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                        XP[i] = fmaf(alpha, Pv[i], XP[i]);
+                        R[i] = fmaf(-alpha, Qv[i], R[i]);
+                    }
+                    cl.sync();                                  // r complete
+                    const float* __restrict__ Rc = a.r;
+                    float* __restrict__ Z = a.z;
+#pragma unroll 2
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                        const float zi = spmv_row(a.l_ptr, a.l_idx, a.l_val, Rc, i);
+                        Z[i] = zi;
+                        const float ri = Rc[i];
+                        df_add_prod(v2n[0], ri, zi);
+                        df_add_prod(v2n[1], ri, ri);
+                    }
                 } else {
                     float* __restrict__ XP = a.xp;
                     float* __restrict__ R = a.r;
@@ -347,23 +430,41 @@ __global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
                         R[i] = fmaf(-alpha, Qv[i], R[i]);
                     }
                     apply_pc<NT>(a, cl, lo, hi, rank, sid);
-                    DF rzs{0.f, 0.f}, rrs{0.f, 0.f};
                     const float* __restrict__ Rc = a.r;
                     const float* __restrict__ Zc = a.z;
 #pragma unroll 2
                     for (int i = lo + threadIdx.x; i < hi; i += NT) {
                         const float ri = Rc[i];
-                        df_add_prod(rzs, ri, Zc[i]);
-                        df_add_prod(rrs, ri, ri);
+                        df_add_prod(v2n[0], ri, Zc[i]);
+                        df_add_prod(v2n[1], ri, ri);
                     }
-                    v2[0] = df_value(rzs);
-                    v2[1] = df_value(rrs);
                 }
-                cluster_sum<NT, 2>(cl, v2, red, part, slot);
-                double rz_new = v2[0];
-                const double rnorm = sqrt(v2[1]);
-                if (!isfinite(rz_new) || !isfinite(rnorm)) { status = SPX_NONFINITE; break; }
-                if (rnorm <= a.delta * ref || rnorm <= a.tol * bnorm) {
+                double rz_new = 0.0;
+                {
+                    double o2[2];
+                    cluster_sum<NT, 2>(cl, v2n, o2, red, part, slot);
+                    if (t0) {
+                        rz_new = o2[0];
+                        const double rnorm = sqrt(o2[1]);
+                        int act = ACT_GO;
+                        if (!isfinite(rz_new) || !isfinite(rnorm)) {
+                            status = SPX_NONFINITE;
+                            act = ACT_STOP;
+                        } else if (rnorm <= a.delta * ref || rnorm <= a.tol * bnorm) {
+                            act = ACT_FOLD;
+                        } else if (!(rz_new > 0.0)) {
+                            status = SPX_BREAKDOWN;
+                            act = ACT_STOP;
+                        } else {
+                            bc.beta = (float)(rz_new / rz);
+                            rz = rz_new;
+                        }
+                        bc.action = act;
+                    }
+                    __syncthreads();
+                }
+                if (bc.action == ACT_STOP) break;
+                if (bc.action == ACT_FOLD) {
                     // ---- reliable update: fold xp into x (FP64), true residual in FP64
                     for (int i = lo + threadIdx.x; i < hi; i += NT) {
                         a.x[i] += (double)a.xp[i];
@@ -371,23 +472,48 @@ __global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
                     }
                     dirty = false;
                     cl.sync();                                  // x complete
-                    double v64[1] = {true_residual<NT>(a, lo, hi)};
-                    cluster_sum<NT, 1>(cl, v64, red, part, slot);
-                    const double tn = sqrt(v64[0]);
-                    last_true = tn / bnorm;
-                    ref = tn;
-                    if (!isfinite(tn)) { status = SPX_NONFINITE; break; }
-                    if (tn <= a.tol * bnorm) { status = SPX_OK; break; }
+                    {
+                        DF v64[1] = {df_of(true_residual<NT>(a, lo, hi))};
+                        double o1[1];
+                        cluster_sum<NT, 1>(cl, v64, o1, red, part, slot);
+                        if (t0) {
+                            const double tn = sqrt(o1[0]);
+                            last_true = tn / bnorm;
+                            ref = tn;
+                            int act = ACT_GO;
+                            if (!isfinite(tn)) {
+                                status = SPX_NONFINITE;
+                                act = ACT_STOP;
+                            } else if (tn <= a.tol * bnorm) {
+                                status = SPX_OK;
+                                act = ACT_STOP;
+                            }
+                            bc.action = act;
+                        }
+                        __syncthreads();
+                    }
+                    if (bc.action == ACT_STOP) break;
                     apply_pc<NT>(a, cl, lo, hi, rank, sid);
-                    DF rzs{0.f, 0.f};
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) df_add_prod(rzs, a.r[i], a.z[i]);
-                    double vz[1] = {df_value(rzs)};
-                    cluster_sum<NT, 1>(cl, vz, red, part, slot);
-                    rz_new = vz[0];
+                    DF vz[1] = {{0.f, 0.f}};
+                    for (int i = lo + threadIdx.x; i < hi; i += NT) df_add_prod(vz[0], a.r[i], a.z[i]);
+                    double o1[1];
+                    cluster_sum<NT, 1>(cl, vz, o1, red, part, slot);
+                    if (t0) {
+                        rz_new = o1[0];
+                        int act = ACT_GO;
+                        if (!(rz_new > 0.0)) {
+                            status = SPX_BREAKDOWN;
+                            act = ACT_STOP;
+                        } else {
+                            bc.beta = (float)(rz_new / rz);
+                            rz = rz_new;
+                        }
+                        bc.action = act;
+                    }
+                    __syncthreads();
+                    if (bc.action == ACT_STOP) break;
                 }
-                if (!(rz_new > 0.0)) { status = SPX_BREAKDOWN; break; }
-                const float beta = (float)(rz_new / rz);
-                rz = rz_new;
+                const float beta = bc.beta;
                 {
                     float* __restrict__ Pv = a.p;
                     const float* __restrict__ Zc = a.z;
@@ -403,11 +529,12 @@ __global__ void __launch_bounds__(NT) pcg_kernel(CgArgs a) {
                 a.xp[i] = 0.f;
             }
             cl.sync();
-            double v64[1] = {true_residual<NT>(a, lo, hi)};
-            cluster_sum<NT, 1>(cl, v64, red, part, slot);
-            last_true = bnorm > 0.0 ? sqrt(v64[0]) / bnorm : 0.0;
+            DF v64[1] = {df_of(true_residual<NT>(a, lo, hi))};
+            double o1[1];
+            cluster_sum<NT, 1>(cl, v64, o1, red, part, slot);
+            if (t0) last_true = bnorm > 0.0 ? sqrt(o1[0]) / bnorm : 0.0;
         }
-        if (rank == 0 && threadIdx.x == 0) {
+        if (rank == 0 && t0) {
             a.iters[sid] = it;
             a.status[sid] = status;
             a.relres[sid] = last_true;
@@ -440,6 +567,7 @@ __global__ void masked_outer_f64_kernel(int32_t m, const int32_t* __restrict__ p
 // Launch shape of the batched PCG (threads per block, blocks per cluster); 0 = default.
 std::atomic<int> g_cg_threads{0};
 std::atomic<int> g_cg_cluster{0};
+std::atomic<int> g_cg_max_clusters{0};
 
 }  // namespace
 }  // namespace spx
@@ -524,8 +652,10 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
 
     const int nt = g_cg_threads.load() > 0 ? g_cg_threads.load() : 512;
     const int cl = g_cg_cluster.load() > 0 ? g_cg_cluster.load() : 8;
-    const int blocks_per_sm = nt >= 1024 ? 1 : 1024 / nt;      // ~64 registers per thread
+    const int blocks_per_sm = nt >= 1024 ? 1 : 1024 / nt;      // 64 registers per thread
     int clusters = blocks_per_sm * num_sms() / cl;
+    const int maxc = g_cg_max_clusters.load();
+    if (maxc > 0 && clusters > maxc) clusters = maxc;
     if (clusters < 1) clusters = 1;
     if (clusters > nsys) clusters = nsys;
     cudaLaunchConfig_t cfg{};
@@ -540,14 +670,16 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (nt == 256) {
-        SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel<256>, a), "spx_cg_batched launch");
-    } else if (nt == 1024) {
-        SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel<1024>, a), "spx_cg_batched launch");
-    } else {
-        SPX_CUDA(cudaLaunchKernelEx(&cfg, pcg_kernel<512>, a), "spx_cg_batched launch");
-    }
-    return SPX_OK;
+    auto launch = [&](auto kern) -> spx_status {
+        if (cl > 8)   // 16 blocks per cluster is beyond the portable size: opt in once
+            SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+                     "spx_cg_batched cluster attribute");
+        SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, a), "spx_cg_batched launch");
+        return SPX_OK;
+    };
+    if (nt == 256) return launch(pcg_kernel<256>);
+    if (nt == 1024) return launch(pcg_kernel<1024>);
+    return launch(pcg_kernel<512>);
 }
 
 extern "C" spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream) {
@@ -572,12 +704,17 @@ extern "C" spx_status spx_masked_outer_f64(const spx_csr* A, const double* u, co
     return SPX_OK;
 }
 
-extern "C" spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t cluster_size) {
+extern "C" spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t cluster_size, int32_t max_clusters) {
     if (!(threads_per_block == 0 || threads_per_block == 256 || threads_per_block == 512 ||
           threads_per_block == 1024) ||
-        !(cluster_size == 0 || cluster_size == 1 || cluster_size == 2 || cluster_size == 4 || cluster_size == 8))
-        return set_error(SPX_INVALID_ARG, "spx_cg_set_launch: threads in {256, 512, 1024}, cluster in {1, 2, 4, 8}");
+        !(cluster_size == 0 || cluster_size == 1 || cluster_size == 2 || cluster_size == 4 || cluster_size == 8 ||
+          cluster_size == 16) ||
+        max_clusters < 0)
+        return set_error(SPX_INVALID_ARG,
+                         "spx_cg_set_launch: threads in {256, 512, 1024}, cluster in {1, 2, 4, 8, 16}, "
+                         "max_clusters >= 0");
     g_cg_threads.store(threads_per_block);
     g_cg_cluster.store(cluster_size);
+    g_cg_max_clusters.store(max_clusters);
     return SPX_OK;
 }

@@ -251,7 +251,7 @@ spx_status launch_lpn(int lpn, dim3 grid, cudaStream_t st, int32_t m, int64_t nn
 }
 
 int32_t sddmm_cb(const spx_csr* A, int32_t k, int32_t col_block, bool vec4) {
-    int32_t cb = col_block > 0 ? col_block : slab_col_block(A->n, k);
+    int32_t cb = col_block > 0 ? col_block : k;       // default: one pass over all columns
     if (cb > k) cb = k;
     if (vec4 && cb % 4 != 0) cb = (cb + 3) / 4 * 4;
     return cb;

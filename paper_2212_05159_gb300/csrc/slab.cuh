@@ -3,28 +3,18 @@
 // A gather kernel that reads rows of a dense n x k operand at random keeps the touched
 // data in L2 only if the data is dense in cache lines: L2 allocates whole 128-byte lines,
 // so a column block of a row-major array (a few sectors per row) costs as much L2 as the
-// full array.  When the operand is larger than the L2 budget it is repacked once into
-// column-block-major slabs -- slab b holds columns [b*cb, b*cb + cb) of every row,
-// contiguously, row stride cb -- and each pass of the gather kernel reads one slab.
+// full array.  When a caller asks for column blocks narrower than k, the operand is
+// repacked once into column-block-major slabs -- slab b holds columns [b*cb, b*cb + cb) of
+// every row, contiguously, row stride cb -- and each pass of the gather kernel reads one
+// slab.  On GB300 one pass over all k columns was the fastest choice on every workload
+// measured (power-law and stencil matrices, k = 32 to 128), so blocks are opt-in: the
+// default is one pass.
 #pragma once
 
 #include "common.cuh"
 
 namespace spx {
 namespace {  // internal linkage: every translation unit gets its own copy
-
-// L2 bytes a gathered slab may occupy (the L2 of a GB300 is ~126 MB; leave room for the
-// streams and the output).
-constexpr int64_t SLAB_L2_BUDGET = 64ll << 20;
-
-// Columns per pass for an operand of `rows` rows and k columns; k when it fits in L2.
-inline int32_t slab_col_block(int64_t rows, int32_t k) {
-    if (rows * (int64_t)k * 4 <= SLAB_L2_BUDGET || k % 4 != 0) return k;
-    int64_t fit = SLAB_L2_BUDGET / (rows * 4);
-    int32_t p = 4;
-    while ((int64_t)p * 2 <= fit && p * 2 < k) p *= 2;
-    return p;
-}
 
 // Number of slabs and bytes of the repacked copy (0 when no repacking applies).
 inline int32_t slab_count(int32_t k, int32_t cb) { return (k + cb - 1) / cb; }

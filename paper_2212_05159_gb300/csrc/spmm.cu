@@ -490,7 +490,7 @@ SpmmShape spmm_shape(const spx_csr* A, int32_t k, const spx_rowplan* plan, bool 
     SpmmShape sh{};
     sh.vec4 = vec4;
     const int VEC = vec4 ? 4 : 1;
-    int32_t cb = plan && plan->col_block > 0 ? plan->col_block : slab_col_block(A->n, k);
+    int32_t cb = plan && plan->col_block > 0 ? plan->col_block : k;   // default: one pass
     if (cb > k) cb = k;
     if (vec4 && cb % 4 != 0) cb = (cb + 3) / 4 * 4;
     if (cb > 32 * VEC) cb = 32 * VEC;

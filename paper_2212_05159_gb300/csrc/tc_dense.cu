@@ -3,15 +3,19 @@
 // BF16 operands (activations rounded to BF16 while staged, BF16 weights), FP32
 // accumulation in tensor memory.
 //
-// One CTA of 128 threads per 128-row tile:
-//   * all threads stage the tile's activations (FP32 -> BF16) and W^T into shared memory
-//     in the canonical no-swizzle K-major layout: 8-row x 16-byte core matrices, the core
-//     matrices of one 8-row group contiguous along K (leading byte offset 128), groups
-//     (K/8) * 128 bytes apart (stride byte offset);
+// One CTA of 128 threads per 128-row tile (the layer is memory-bound: K, N <= 128):
+//   * the threads stage the tile's activations with coalesced float4 loads (consecutive
+//     threads read consecutive 16-byte pieces of a row), convert them to BF16 and store
+//     them in the canonical no-swizzle K-major layout: 8-row x 16-byte core matrices, the
+//     core matrices of one 8-row group contiguous along K (leading byte offset 128), groups
+//     (K/8) * 128 bytes apart (stride byte offset); W^T the same way;
 //   * warp 0 allocates N columns of tensor memory; one thread issues K/16 tcgen05.mma
 //     (M = 128, N, K = 16 each) and commits them to an mbarrier;
-//   * after a bounded wait each warp reads its 32 accumulator lanes with tcgen05.ld and
-//     applies the epilogue; warp 0 frees the tensor memory.
+//   * after a bounded wait each warp reads its 32 accumulator lanes (rows) with tcgen05.ld,
+//     adds the bias and parks the rows in shared memory (the operand tiles are free once
+//     the MMAs have completed); the warp then writes its rows back with coalesced float4
+//     accesses, reading Hin and writing U for the residual epilogue; warp 0 frees the
+//     tensor memory.
 // A wait that does not complete within 2 s records a device error; the kernel still frees
 // its tensor memory before returning.
 #include <cuda_bf16.h>
@@ -25,6 +29,9 @@ constexpr int TC_M = 128;
 constexpr int TC_THREADS = 128;
 constexpr int TC_KMAX = 128;
 constexpr int TC_NMAX = 128;
+constexpr int TC_TILES = TC_M * TC_KMAX * 2 + TC_NMAX * TC_KMAX * 2;  // A and B^T tiles: 64 KB
+constexpr int TC_STAGE = TC_M * (TC_NMAX + 4) * 4;                    // epilogue rows: 66 KB
+constexpr int TC_SMEM = TC_TILES > TC_STAGE ? TC_TILES : TC_STAGE;
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
@@ -50,6 +57,37 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// Stages rows [row0, row0 + 128) of X (n x K, row stride K, K % 4 == 0) into columns
+// [kbase, kbase + K) of the A tile; rows past n are zero.  Loads are issued STAGE_BATCH at a
+// time per thread before any is converted, so enough bytes are in flight to cover the
+// memory latency (the layer is bandwidth-bound).
+constexpr int STAGE_BATCH = 8;
+
+__device__ __forceinline__ void stage_rows(unsigned char* sA, const float* __restrict__ X, int K, int kbase, int kpad,
+                                           int64_t row0, int64_t n) {
+    const int q4 = K >> 2;                                   // float4 pieces per row
+    const int total = TC_M * q4;
+    for (int t0 = threadIdx.x; t0 < total; t0 += STAGE_BATCH * TC_THREADS) {
+        float4 v[STAGE_BATCH];
+#pragma unroll
+        for (int u = 0; u < STAGE_BATCH; ++u) {
+            const int t = t0 + u * TC_THREADS;
+            const int r = t / q4, kq = t - r * q4;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < total && row0 + r < n) v[u] = __ldcs(reinterpret_cast<const float4*>(X + (row0 + r) * K) + kq);
+        }
+#pragma unroll
+        for (int u = 0; u < STAGE_BATCH; ++u) {
+            const int t = t0 + u * TC_THREADS;
+            if (t < total) {
+                const int r = t / q4, kq = t - r * q4;
+                const uint2 pk = make_uint2(pack_bf16x2(v[u].x, v[u].y), pack_bf16x2(v[u].z, v[u].w));
+                *reinterpret_cast<uint2*>(sA + core_off(r, kbase + kq * 4, kpad)) = pk;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const float* __restrict__ X1, int K1,
                                                               const float* __restrict__ X2, int K2,
                                                               const __nv_bfloat16* __restrict__ W,
@@ -67,39 +105,21 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     const int64_t row0 = (int64_t)blockIdx.x * TC_M;
     const int ncols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
 
-    // ---- stage A: 8-element chunks (16 bytes) of the tile rows, FP32 -> BF16
-    const int kch = kpad >> 3;
-    for (int t = threadIdx.x; t < TC_M * kch; t += TC_THREADS) {
-        const int r = t / kch, kc = t % kch;
-        const int64_t row = row0 + r;
-        float v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = kc * 8 + q;
-            float x = 0.f;
-            if (row < n) {
-                if (k < K1) x = X1[row * K1 + k];
-                else if (k < K) x = X2[row * K2 + (k - K1)];
-            }
-            v[q] = x;
+    // ---- stage A = [X1 X2] (FP32 -> BF16) and its zero padding up to kpad
+    stage_rows(sA, X1, K1, 0, kpad, row0, n);
+    if (K2 > 0) stage_rows(sA, X2, K2, K1, kpad, row0, n);
+    if (kpad > K) {
+        const int pq = (kpad - K) >> 2;                        // K % 4 == 0: padding in 4-column pieces
+        for (int t = threadIdx.x; t < TC_M * pq; t += TC_THREADS) {
+            const int r = t / pq, kq = t - r * pq;
+            *reinterpret_cast<uint2*>(sA + core_off(r, K + kq * 4, kpad)) = make_uint2(0u, 0u);
         }
-        uint4 pk = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                              pack_bf16x2(v[6], v[7]));
-        *reinterpret_cast<uint4*>(sA + core_off(r, kc * 8, kpad)) = pk;
     }
-    // ---- stage B = W^T (N rows, K-major)
-    for (int t = threadIdx.x; t < N * kch; t += TC_THREADS) {
-        const int nn = t / kch, kc = t % kch;
-        unsigned short h[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int k = kc * 8 + q;
-            __nv_bfloat16 w = k < K ? W[k * N + nn] : __float2bfloat16(0.f);
-            h[q] = *reinterpret_cast<unsigned short*>(&w);
-        }
-        uint4 pk = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16), h[4] | ((uint32_t)h[5] << 16),
-                              h[6] | ((uint32_t)h[7] << 16));
-        *reinterpret_cast<uint4*>(sB + core_off(nn, kc * 8, kpad)) = pk;
+    // ---- stage B = W^T (N rows, K-major); consecutive threads read consecutive columns of W
+    for (int t = threadIdx.x; t < N * kpad; t += TC_THREADS) {
+        const int k = t / N, nn = t - k * N;
+        const __nv_bfloat16 w = k < K ? W[k * N + nn] : __float2bfloat16(0.f);
+        *reinterpret_cast<__nv_bfloat16*>(sB + core_off(nn, k, kpad)) = w;
     }
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&mbar), 1);
@@ -120,7 +140,7 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     if (threadIdx.x == 0) {
         const uint32_t idesc = instr_desc(TC_M, N);
         const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        const uint32_t sbo = (uint32_t)kch * 128u;
+        const uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
         for (int s = 0; s < kpad / 16; ++s) {
             const uint64_t ad = smem_desc(a0 + s * 256u, 128u, sbo);
             const uint64_t bd = smem_desc(b0 + s * 256u, 128u, sbo);
@@ -140,9 +160,11 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     if (!ok) {
         if (threadIdx.x == 0 && err) atomicOr(err, 2);
     } else {
-        // ---- epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
-        const int r = warp * 32 + lane;
-        const int64_t row = row0 + r;
+        // ---- epilogue 1: accumulator lanes of this warp (rows 32w .. 32w + 31) -> shared
+        // memory, bias added.  The MMAs have completed (mbarrier), so the operand tiles are
+        // free; each warp reuses its own slice: 32 rows x (N + 4) floats.
+        const int ldst = N + 4;                                      // padded row stride (floats)
+        float* stage = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * ldst;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
         for (int c0 = 0; c0 < N; c0 += 16) {
             uint32_t v[16];
@@ -153,21 +175,37 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < n) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int c = c0 + q;
-                    if (c >= N) break;
-                    const float pre = __uint_as_float(v[q]) + (bias ? bias[c] : 0.f);
-                    if (mode == 0) {
-                        Y[row * N + c] = pre;
-                    } else if (mode == 1) {
-                        Y[row * N + c] = fmaxf(pre, 0.f);
-                    } else {
-                        U[row * N + c] = pre;
-                        Y[row * N + c] = Hin[row * N + c] + fmaxf(pre, 0.f);
-                    }
-                }
+            for (int q = 0; q < 16; q += 4) {
+                float4 o;
+                o.x = __uint_as_float(v[q + 0]) + (bias ? bias[c0 + q + 0] : 0.f);
+                o.y = __uint_as_float(v[q + 1]) + (bias ? bias[c0 + q + 1] : 0.f);
+                o.z = __uint_as_float(v[q + 2]) + (bias ? bias[c0 + q + 2] : 0.f);
+                o.w = __uint_as_float(v[q + 3]) + (bias ? bias[c0 + q + 3] : 0.f);
+                *reinterpret_cast<float4*>(stage + lane * ldst + c0 + q) = o;
+            }
+        }
+        __syncwarp();
+        // ---- epilogue 2: the warp's 32 rows to global memory, float4 pieces in row order
+        const int n4 = N >> 2;
+#pragma unroll 4
+        for (int t = lane; t < 32 * n4; t += 32) {
+            const int r = t / n4, cq = t - r * n4;
+            const int64_t row = row0 + warp * 32 + r;
+            if (row >= n) break;                                 // rows only grow with t
+            const float4 pre = *reinterpret_cast<const float4*>(stage + r * ldst + cq * 4);
+            const int64_t o = row * N + cq * 4;
+            if (mode == 0) {
+                __stcs(reinterpret_cast<float4*>(Y + o), pre);
+            } else if (mode == 1) {
+                __stcs(reinterpret_cast<float4*>(Y + o),
+                       make_float4(fmaxf(pre.x, 0.f), fmaxf(pre.y, 0.f), fmaxf(pre.z, 0.f), fmaxf(pre.w, 0.f)));
+            } else {
+                const float4 h = __ldcs(reinterpret_cast<const float4*>(Hin + o));
+                __stcs(reinterpret_cast<float4*>(U + o), pre);
+                __stcs(reinterpret_cast<float4*>(Y + o),
+                       make_float4(h.x + fmaxf(pre.x, 0.f), h.y + fmaxf(pre.y, 0.f), h.z + fmaxf(pre.z, 0.f),
+                                   h.w + fmaxf(pre.w, 0.f)));
             }
         }
     }
@@ -179,7 +217,9 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     }
 }
 
-size_t tc_smem_bytes() { return (size_t)TC_M * TC_KMAX * 2 + (size_t)TC_NMAX * TC_KMAX * 2; }
+size_t tc_smem_bytes() { return (size_t)TC_SMEM; }
+
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 }  // namespace
 }  // namespace spx
@@ -194,6 +234,9 @@ extern "C" spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K
         return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: sizes (K <= 128, N in 16..128, N %% 16 == 0)");
     if (n > 0 && (!X1 || (K2 > 0 && !X2) || !W_bf16 || !Y || (mode == 2 && (!Hin || !U))))
         return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: NULL operand");
+    if (K1 % 4 != 0 || K2 % 4 != 0 || !al16(X1) || (K2 > 0 && !al16(X2)) || !al16(Y) ||
+        (mode == 2 && (!al16(Hin) || !al16(U))))
+        return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: K1, K2 multiples of 4 and 16-byte aligned rows needed");
     if (n == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
     const size_t smem = tc_smem_bytes();

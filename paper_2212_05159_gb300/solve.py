@@ -30,15 +30,25 @@ class SystemBatch:
         # largest systems first: the longest solves start first (load balance)
         self.order = torch.from_numpy(np.argsort(-sizes, kind="stable").astype(np.int32)).to(A.device)
         self.ws = abi.workspace(abi.spx_cg_workspace_size(A.m), A.device)
-        # launch shape: 512-thread blocks, a cluster sized so a block owns ~8192 rows of an
-        # average system (measured best on GB300 for 2D diffusion batches)
-        mean_rows = float(sizes.mean()) if sizes.size else 1.0
-        cl = 2 ** int(round(np.log2(max(mean_rows / 8192.0, 1.0))))
-        self.launch = (512, int(min(8, max(1, cl))))
+        self.mean_rows = float(sizes.mean()) if sizes.size else 1.0
+        self.launch = None          # (threads, cluster, max clusters); None = launch_for()
         self._dinv = None
         self.iters = torch.zeros(self.nsys, dtype=torch.int32, device=A.device)
         self.status = torch.zeros(self.nsys, dtype=torch.int32, device=A.device)
         self.relres = torch.zeros(self.nsys, dtype=torch.float64, device=A.device)
+
+    def launch_for(self, kind: int):
+        """Launch shape of spx_cg_batched: 1024-thread blocks and a cluster (power of two, at
+        most 16) giving each thread ~8 rows of an average system (~4 with a sparse M or
+        L L^T, whose extra product is the longer dependent chain).  Measured on GB300 with
+        2D diffusion batches: 64 systems of 256^2 run fastest at 8 blocks with Jacobi and
+        16 with the learned M; 256 systems of 32^2..256^2 at 4 blocks."""
+        if self.launch is not None:
+            return self.launch
+        rows_per_thread = 4.0 if kind in (2, 3) else 8.0
+        want = self.mean_rows / rows_per_thread / 1024.0
+        cl = 2 ** int(round(np.log2(max(want, 1.0))))
+        return (1024, int(min(16, max(1, cl))), 0)
 
     def dinv(self, values=None):
         if values is not None:
@@ -130,7 +140,7 @@ def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor |
             raise ValueError("pc='ic0' needs an IC0")
         L, LT = ic0.structs()
         levels = ic0.levels
-    abi.spx_cg_set_launch(*batch.launch)
+    abi.spx_cg_set_launch(*batch.launch_for(kind))
     abi.spx_cg_batched(A.struct(values), batch.sys_ptr, batch.nsys, batch.order, b.contiguous(), x, kind,
                        dinv, L, LT, tol, maxit, delta, batch.iters, batch.status, batch.relres, batch.ws,
                        ic0_levels=levels)
