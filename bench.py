@@ -426,11 +426,11 @@ def cg_section(args):
     from paper_2212_05159_gb300 import learned, pcg_study
     out = {"batch256_jacobi": pcg_study.batch256_jacobi(graph_replay=True)}
     net = learned.MPNN(seed=0)
-    steps = 313 if args.cg_full else args.train_steps
-    tr = pcg_study.train(net, steps=steps, batch=32, n_it=8, gamma=0.8, lr=2e-3)
+    tr = pcg_study.train(net, steps=args.train_steps, batch=32, n_it=8, gamma=0.8, lr=2e-3)
     tr.pop("loss_history", None)
     out["training"] = tr
-    out["eval_256x256"] = pcg_study.evaluate(net, nsys=1000 if args.cg_full else args.eval_systems, per_batch=64)
+    out["eval_256x256"] = pcg_study.evaluate(net, nsys=args.eval_systems, per_batch=64,
+                                             ic0_systems=min(args.ic0_systems, args.eval_systems))
     return out
 
 
@@ -473,9 +473,11 @@ def main():
                     help="fixed launch parameters (the tuned choice for this workload) instead of autotuning")
     ap.add_argument("--sections", default="step,extras,spgemm,cg,cpu",
                     help="comma list of: step (always), extras, spgemm, cg, cpu")
-    ap.add_argument("--cg-full", action="store_true", help="10k training systems, 1k evaluation systems")
-    ap.add_argument("--train-steps", type=int, default=150, help="training batches of 32 systems")
-    ap.add_argument("--eval-systems", type=int, default=128)
+    ap.add_argument("--train-steps", type=int, default=313,
+                    help="training batches of 32 generated systems (313: the 10k-system training set)")
+    ap.add_argument("--eval-systems", type=int, default=1000, help="held-out 256^2 systems")
+    ap.add_argument("--ic0-systems", type=int, default=128,
+                    help="the first this many held-out systems are also solved with IC(0) (~50 ms each)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
