@@ -9,6 +9,10 @@ The arithmetic lives in ``spx_oracle.c`` (plain serial C loops in double precisi
 compiled with gcc by :func:`build`); this module only marshals numpy arrays.  Inputs
 arrive as float32 (what the GPU consumes) and are promoted exactly to float64.
 
+Submodules: ``pcg_unrolled`` (the unrolled-PCG loss of Section 4.3 and its reverse),
+``mpnn`` (the learned-preconditioner network), ``spai`` (Section 4.6: SPAI by gradient
+descent and the static-pattern SPAI).
+
 Parity pins: every function here is checked by ``tests/test_oracle_*.py`` against
 dense linear algebra, closed forms of the model problems, finite differences or
 brute force on tiny inputs (see the test files for which pin covers which routine).
