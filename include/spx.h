@@ -269,6 +269,34 @@ spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, const spx_csr
                                const int32_t* at_indptr, const int32_t* at_indices,
                                const int32_t* a_perm, void* stream);
 
+/* ------------------------------ sparse approximate inverse by descent (Section 4.6) */
+
+/* The residual of the SPAI loss ||I - M A||_F^2 on the pattern of C = M A (formed by the
+ * SpGEMM entry points): out[e] = scale * ([i == j] - C.values[e]) for every stored entry
+ * e = (i, j) of C; scale = -2 gives the gradient of the loss w.r.t. C's values, to be passed
+ * to spx_spgemm_backward for the gradient w.r.t. M.  diag_count (device int32, may be NULL)
+ * receives the number of diagonal entries stored in C (each missing one adds 1 to the
+ * loss).  C: device CSR with values; out: device float32[C.nnz].  Asynchronous. */
+spx_status spx_spai_residual(const spx_csr* C, float scale, float* out, int32_t* diag_count,
+                             void* stream);
+
+/* Workspace bytes of spx_dot for vectors of n entries. */
+spx_status spx_dot_workspace_size(int64_t n, size_t* bytes);
+
+/* *out = sum_i x[i] y[i] (device float32 inputs, device double output), accumulated in
+ * double-float per thread and FP64 across threads and blocks in a fixed order, so the
+ * result is reproducible bit for bit.  workspace: device, spx_dot_workspace_size bytes.
+ * Asynchronous; the result stays on the device. */
+spx_status spx_dot(int64_t n, const float* x, const float* y, double* out, void* workspace,
+                   size_t workspace_bytes, void* stream);
+
+/* The exact line-search step of the SPAI descent: m[e] -= eta * g[e] with
+ * eta = (1/2) *gg / *dada, where gg = <g, g> and dada = <g A, g A> are device doubles (from
+ * spx_dot).  The loss is quadratic in M, so eta minimises it along -g.  No step is taken
+ * when dada is not positive and finite.  m, g: device float32[nnz].  Asynchronous. */
+spx_status spx_spai_update(int64_t nnz, float* m, const float* g, const double* gg,
+                           const double* dada, void* stream);
+
 /* spx_spmm_t for callers that cannot allocate device memory when they call it -- e.g. a
  * host framework that owns all device memory through its own pool and forbids other
  * allocations, or code that must not let an allocation synchronise the device.  The paper

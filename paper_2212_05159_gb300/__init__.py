@@ -4,8 +4,8 @@ differentiation of CSR operations (arXiv 2212.05159).
 The compute lives in the in-tree CUDA library ``_build/libspx.so`` (C ABI in
 ``include/spx.h``); this package is its thin Python binding plus autograd glue.
 """
-from . import abi
+from . import abi, spai
 from .csr import CSR
 from .ops import SpGEMMPlan, masked_outer, sddmm, spgemm, spmm, spmm_t
 
-__all__ = ["abi", "CSR", "spmm", "sddmm", "spmm_t", "masked_outer", "spgemm", "SpGEMMPlan"]
+__all__ = ["abi", "CSR", "spmm", "sddmm", "spmm_t", "masked_outer", "spgemm", "SpGEMMPlan", "spai"]

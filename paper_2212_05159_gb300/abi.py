@@ -117,6 +117,10 @@ SIGNATURES = {
                           _SZ, _P],
     "spx_adam_step": [_I64, _P, _P, _P, _P, _I32, _F, _F, _F, _F, _P, _P],
     "spx_to_bf16": [_I64, _P, _P, _P],
+    "spx_spai_residual": [_CSRP, _F, _P, _P, _P],
+    "spx_dot_workspace_size": [_I64, ctypes.POINTER(_SZ)],
+    "spx_dot": [_I64, _P, _P, _P, _P, _SZ, _P],
+    "spx_spai_update": [_I64, _P, _P, _P, _P, _P],
 }
 
 
@@ -481,6 +485,29 @@ def spx_adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-
 
 def spx_to_bf16(src, dst):
     _check(lib().spx_to_bf16(int(src.numel()), ptr(src), ptr(dst), _stream()), "spx_to_bf16")
+
+
+def spx_spai_residual(C: spx_csr, scale: float, out, diag_count=None):
+    _check(lib().spx_spai_residual(ctypes.byref(C), float(scale), ptr(out), ptr(diag_count), _stream()),
+           "spx_spai_residual")
+    return out
+
+
+def spx_dot_workspace_size(n: int) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_dot_workspace_size(int(n), ctypes.byref(sz)), "spx_dot_workspace_size")
+    return sz.value
+
+
+def spx_dot(x, y, out, ws):
+    """out (device float64 scalar tensor) = <x, y>."""
+    _check(lib().spx_dot(int(x.numel()), ptr(x), ptr(y), ptr(out), ptr(ws), ws.numel(), _stream()), "spx_dot")
+    return out
+
+
+def spx_spai_update(m, g, gg, dada):
+    _check(lib().spx_spai_update(int(m.numel()), ptr(m), ptr(g), ptr(gg), ptr(dada), _stream()),
+           "spx_spai_update")
 
 
 def spx_cg_set_launch(threads_per_block: int = 0, cluster_size: int = 0, max_clusters: int = 0):
