@@ -412,6 +412,37 @@ def spai_section():
             "setup_ms_host_timed": setup_ms}
 
 
+def spadd_section():
+    """C = A - 0.5 B for two n = 2^20 power-law matrices (Section 3.1.4): numeric and backward
+    on the union pattern, device-timed; the pattern and maps are per-pair set-up."""
+    import synth
+    import torch
+    import paper_2212_05159_gb300 as spx
+    A = synth.powerlaw_csr(1 << 20, seed=0)
+    B = synth.powerlaw_csr(1 << 20, seed=3)
+    dA, dB = spx.CSR.from_host(A), spx.CSR.from_host(B)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = spx.SpAddPlan(dA, dB)
+    torch.cuda.synchronize()
+    sym_ms = (time.perf_counter() - t0) * 1e3
+    nC = plan.C.nnz
+    cv = torch.empty(nC, device="cuda")
+    gc = torch.randn(nC, device="cuda")
+    ga = torch.empty(A.nnz, device="cuda")
+    gb = torch.empty(B.nnz, device="cuda")
+    num_ms = _ev_time(lambda: plan.numeric(1.0, -0.5, out=cv))
+    bwd_ms = _ev_time(lambda: spx.abi.spx_spadd_backward(1.0, -0.5, gc, plan.pos_a, plan.pos_b, ga, gb))
+    num_bytes = 8 * nC + 4 * (A.nnz + B.nnz) + 4 * nC           # maps, values of A and B, C
+    bwd_bytes = 4 * nC + 8 * (A.nnz + B.nnz)                     # gc, maps and outputs
+    hbm, _ = measured_peaks()
+    return {"nnz_A": A.nnz, "nnz_B": B.nnz, "nnz_C": nC, "symbolic_ms_host_timed": sym_ms,
+            "numeric_ms": num_ms, "backward_ms": bwd_ms, "numeric_gbs": num_bytes / (num_ms * 1e-3) / 1e9,
+            "backward_gbs": bwd_bytes / (bwd_ms * 1e-3) / 1e9,
+            "numeric_frac_of_peak": num_bytes / (num_ms * 1e-3) / 1e9 / hbm,
+            "bytes_model": "numeric: src maps + A, B values + C; backward: gc + pos maps + gA, gB"}
+
+
 def spgemm_section():
     """C = A B forward (numeric on a fixed pattern) and both gradients; symbolic timed apart."""
     import synth
@@ -584,6 +615,7 @@ def main():
         if "spgemm" in secs:
             line["spgemm"] = spgemm_section()
             line["spai"] = spai_section()
+            line["spadd"] = spadd_section()
         if "cg" in secs:
             line["cg"] = cg_section(args)
     if rank == 0 and "cpu" in secs:

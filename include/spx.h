@@ -269,6 +269,40 @@ spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, const spx_csr
                                const int32_t* at_indptr, const int32_t* at_indices,
                                const int32_t* a_perm, void* stream);
 
+/* ------------------------------------------------- sparse + sparse (Section 3.1.4) */
+
+/* Workspace bytes of spx_spadd_symbolic for m rows. */
+spx_status spx_spadd_workspace_size(int32_t m, size_t* bytes);
+
+/* Row offsets of C = alpha A + beta B, whose pattern is the union of A's and B's stored
+ * patterns row by row (structural: entries that cancel stay).  A, B: device CSR patterns of
+ * the same shape (sorted, unique columns).  c_indptr: device int32[m + 1] (written);
+ * *nnz_c: host, nnz of C.  Synchronizes `stream` (the count returns to the host);
+ * SPX_INVALID_ARG when nnz(C) does not fit int32. */
+spx_status spx_spadd_symbolic(const spx_csr* A, const spx_csr* B, int32_t* c_indptr, int64_t* nnz_c,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
+/* Columns of C and the maps between the patterns: src_a[e] / src_b[e] = the entry of A / B
+ * that entry e of C takes its value from (-1 if none); pos_a[e] / pos_b[e] = the position in
+ * C of entry e of A / B.  c_indices, src_a, src_b: device int32[nnz_c]; pos_a: int32[nnz(A)];
+ * pos_b: int32[nnz(B)].  Asynchronous. */
+spx_status spx_spadd_fill(const spx_csr* A, const spx_csr* B, const int32_t* c_indptr,
+                          int32_t* c_indices, int32_t* src_a, int32_t* src_b, int32_t* pos_a,
+                          int32_t* pos_b, void* stream);
+
+/* c_vals[e] = alpha a_vals[src_a[e]] + beta b_vals[src_b[e]] (absent terms skipped), each
+ * value written once.  Device float32 arrays.  Asynchronous. */
+spx_status spx_spadd_numeric(int64_t nnz_c, float alpha, const float* a_vals, const int32_t* src_a,
+                             float beta, const float* b_vals, const int32_t* src_b, float* c_vals,
+                             void* stream);
+
+/* Gradients of C = alpha A + beta B (Table 1, Sp + Sp): ga[e] = alpha gc[pos_a[e]] on
+ * mask(A), gb[e] = beta gc[pos_b[e]] on mask(B), gc given on mask(C).  ga or gb may be NULL
+ * (not computed).  Asynchronous. */
+spx_status spx_spadd_backward(int64_t nnz_a, int64_t nnz_b, float alpha, float beta, const float* gc,
+                              const int32_t* pos_a, const int32_t* pos_b, float* ga, float* gb,
+                              void* stream);
+
 /* ------------------------------ sparse approximate inverse by descent (Section 4.6) */
 
 /* The residual of the SPAI loss ||I - M A||_F^2 on the pattern of C = M A (formed by the

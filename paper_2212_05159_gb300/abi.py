@@ -118,6 +118,11 @@ SIGNATURES = {
     "spx_adam_step": [_I64, _P, _P, _P, _P, _I32, _F, _F, _F, _F, _P, _P],
     "spx_to_bf16": [_I64, _P, _P, _P],
     "spx_spai_residual": [_CSRP, _F, _P, _P, _P],
+    "spx_spadd_workspace_size": [_I32, ctypes.POINTER(_SZ)],
+    "spx_spadd_symbolic": [_CSRP, _CSRP, _P, ctypes.POINTER(_I64), _P, _SZ, _P],
+    "spx_spadd_fill": [_CSRP, _CSRP, _P, _P, _P, _P, _P, _P, _P],
+    "spx_spadd_numeric": [_I64, _F, _P, _P, _F, _P, _P, _P, _P],
+    "spx_spadd_backward": [_I64, _I64, _F, _F, _P, _P, _P, _P, _P, _P],
     "spx_dot_workspace_size": [_I64, ctypes.POINTER(_SZ)],
     "spx_dot": [_I64, _P, _P, _P, _P, _SZ, _P],
     "spx_spai_update": [_I64, _P, _P, _P, _P, _P],
@@ -485,6 +490,32 @@ def spx_adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-
 
 def spx_to_bf16(src, dst):
     _check(lib().spx_to_bf16(int(src.numel()), ptr(src), ptr(dst), _stream()), "spx_to_bf16")
+
+
+def spx_spadd_symbolic(A: spx_csr, B: spx_csr, c_indptr, device) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_spadd_workspace_size(A.m, ctypes.byref(sz)), "spx_spadd_workspace_size")
+    ws = workspace(sz.value, device)
+    nnz = _I64(0)
+    _check(lib().spx_spadd_symbolic(ctypes.byref(A), ctypes.byref(B), ptr(c_indptr), ctypes.byref(nnz), ptr(ws),
+                                    ws.numel(), _stream()), "spx_spadd_symbolic")
+    return nnz.value
+
+
+def spx_spadd_fill(A: spx_csr, B: spx_csr, c_indptr, c_indices, src_a, src_b, pos_a, pos_b):
+    _check(lib().spx_spadd_fill(ctypes.byref(A), ctypes.byref(B), ptr(c_indptr), ptr(c_indices), ptr(src_a),
+                                ptr(src_b), ptr(pos_a), ptr(pos_b), _stream()), "spx_spadd_fill")
+
+
+def spx_spadd_numeric(alpha, a_vals, src_a, beta, b_vals, src_b, c_vals):
+    _check(lib().spx_spadd_numeric(int(c_vals.numel()), float(alpha), ptr(a_vals), ptr(src_a), float(beta),
+                                   ptr(b_vals), ptr(src_b), ptr(c_vals), _stream()), "spx_spadd_numeric")
+    return c_vals
+
+
+def spx_spadd_backward(alpha, beta, gc, pos_a, pos_b, ga=None, gb=None):
+    _check(lib().spx_spadd_backward(int(pos_a.numel()), int(pos_b.numel()), float(alpha), float(beta), ptr(gc),
+                                    ptr(pos_a), ptr(pos_b), ptr(ga), ptr(gb), _stream()), "spx_spadd_backward")
 
 
 def spx_spai_residual(C: spx_csr, scale: float, out, diag_count=None):

@@ -50,3 +50,18 @@ class SpGEMM(torch.autograd.Function):
         a_values, b_values = ctx.saved_tensors
         ga, gb = ctx.plan.backward(gc, a_values, b_values, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
         return ga, gb, None
+
+
+class SpAdd(torch.autograd.Function):
+    """values of C = alpha A + beta B on the plan's (union) pattern.  VJPs (Table 1,
+    Sp + Sp): dL/dA = alpha V masked to A,  dL/dB = beta V masked to B."""
+
+    @staticmethod
+    def forward(ctx, a_values, b_values, plan, alpha: float, beta: float):
+        ctx.plan, ctx.alpha, ctx.beta = plan, alpha, beta
+        return plan.numeric(alpha, beta, a_values, b_values)
+
+    @staticmethod
+    def backward(ctx, gc):
+        ga, gb = ctx.plan.backward(gc, ctx.alpha, ctx.beta, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return ga, gb, None, None, None

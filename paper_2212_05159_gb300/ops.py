@@ -103,6 +103,49 @@ class SpGEMMPlan:
         return ga, gb
 
 
+class SpAddPlan:
+    """Pattern of C = alpha A + beta B -- the union of the stored patterns, row by row
+    (Section 3.1.4) -- and the maps between the three patterns, built once per pair."""
+
+    def __init__(self, A: CSR, B: CSR):
+        if A.shape != B.shape:
+            raise ValueError("shapes differ")
+        self.A, self.B = A, B
+        dev = A.device
+        i32 = dict(dtype=torch.int32, device=dev)
+        c_ip = torch.empty(A.m + 1, **i32)
+        nnz = abi.spx_spadd_symbolic(A.struct(), B.struct(), c_ip, dev)
+        c_ix = torch.empty(max(nnz, 1), **i32)
+        self.src_a = torch.empty(max(nnz, 1), **i32)
+        self.src_b = torch.empty(max(nnz, 1), **i32)
+        self.pos_a = torch.empty(max(A.nnz, 1), **i32)
+        self.pos_b = torch.empty(max(B.nnz, 1), **i32)
+        abi.spx_spadd_fill(A.struct(), B.struct(), c_ip, c_ix, self.src_a, self.src_b, self.pos_a, self.pos_b)
+        self.src_a, self.src_b = self.src_a[:nnz], self.src_b[:nnz]
+        self.pos_a, self.pos_b = self.pos_a[:A.nnz], self.pos_b[:B.nnz]
+        self.C = CSR(c_ip, c_ix[:nnz], None, A.shape)
+
+    def numeric(self, alpha=1.0, beta=1.0, a_values=None, b_values=None, out=None) -> torch.Tensor:
+        a = self.A.values if a_values is None else a_values
+        b = self.B.values if b_values is None else b_values
+        o = out if out is not None else torch.empty(self.C.nnz, dtype=torch.float32, device=self.A.device)
+        abi.spx_spadd_numeric(alpha, a, self.src_a, beta, b, self.src_b, o)
+        return o
+
+    def backward(self, gc: torch.Tensor, alpha=1.0, beta=1.0, need_a=True, need_b=True):
+        dev = self.A.device
+        ga = torch.empty(self.A.nnz, dtype=torch.float32, device=dev) if need_a else None
+        gb = torch.empty(self.B.nnz, dtype=torch.float32, device=dev) if need_b else None
+        abi.spx_spadd_backward(alpha, beta, gc.contiguous(), self.pos_a, self.pos_b, ga, gb)
+        return ga, gb
+
+
+def spadd(A: CSR, B: CSR, alpha: float = 1.0, beta: float = 1.0) -> CSR:
+    """C = alpha A + beta B with the union pattern (Section 3.1.4)."""
+    plan = SpAddPlan(A, B)
+    return plan.C.with_values(plan.numeric(alpha, beta))
+
+
 def spgemm(A: CSR, B: CSR) -> CSR:
     """C = A B with the structural pattern (Section 3.1.2)."""
     plan = SpGEMMPlan(A, B)
