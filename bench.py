@@ -443,6 +443,41 @@ def spadd_section():
             "bytes_model": "numeric: src maps + A, B values + C; backward: gc + pos maps + gA, gB"}
 
 
+def spx_csr_from_host(A):
+    import paper_2212_05159_gb300 as spx
+    return spx.CSR.from_host(A)
+
+
+def sptrsv_section():
+    """Batched triangular solves (Section 3.1.5) with the IC(0) factors of the 256-system
+    diffusion batch (sides 32..256, 6.8 M rows): the forward solve and the VJP (transposed
+    solve + masked outer product), device-timed; one block per system, level by level."""
+    import synth
+    import torch
+    from paper_2212_05159_gb300 import solve
+    from paper_2212_05159_gb300.autograd import SpTRSV
+    from paper_2212_05159_gb300.ops import TriangularSolver
+    A, ptr, _, _ = synth.diffusion_batch(256, seed=0, side_lo=32, side_hi=256, sigma=1.0)
+    dA = spx_csr_from_host(A)
+    batch = solve.SystemBatch(dA, ptr)
+    ic = solve.IC0(batch)
+    L = ic.Lpat.with_values(ic.values)
+    tsolver = TriangularSolver(L, batch.sys_ptr)
+    b = torch.from_numpy(synth.normal(A.m, seed=1)).cuda()
+    v = torch.from_numpy(synth.normal(A.m, seed=2)).cuda()
+    x = torch.empty_like(b)
+    fwd_ms = _ev_time(lambda: tsolver.solve(b, out=x))
+    lv = L.values.clone().requires_grad_(True)
+
+    def vjp():
+        return torch.autograd.grad(SpTRSV.apply(lv, b, tsolver), (lv,), grad_outputs=v)
+    vjp_ms = _ev_time(vjp)
+    levels = int(tsolver.levels[0][-1].item()) - tsolver.nsys      # sum over systems of their level counts
+    return {"systems": 256, "rows": A.m, "nnz_L": L.nnz, "levels_total": levels,
+            "forward_ms": fwd_ms, "forward_plus_vjp_ms": vjp_ms,
+            "status_ok": int((tsolver.status == 0).sum())}
+
+
 def spgemm_section():
     """C = A B forward (numeric on a fixed pattern) and both gradients; symbolic timed apart."""
     import synth
@@ -616,6 +651,7 @@ def main():
             line["spgemm"] = spgemm_section()
             line["spai"] = spai_section()
             line["spadd"] = spadd_section()
+            line["sptrsv"] = sptrsv_section()
         if "cg" in secs:
             line["cg"] = cg_section(args)
     if rank == 0 and "cpu" in secs:

@@ -269,6 +269,21 @@ spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, const spx_csr
                                const int32_t* at_indptr, const int32_t* at_indices,
                                const int32_t* a_perm, void* stream);
 
+/* ------------------------------------------ sparse triangular solve (Section 3.1.5) */
+
+/* Solves T x = b for every system of a block-diagonal batch of triangular systems.
+ * upper = 0: T is lower triangular with the diagonal stored as the last entry of each row
+ * (sorted columns); upper = 1: T is the CSR of L^T for such an L (upper triangular, the
+ * diagonal first in each row), which gives the transposed solve L^T x = b of the VJP
+ * (grad_b = L^-T v; grad_L = -(L^-T v) x^T on mask(L), i.e. spx_masked_outer with scale -1).
+ * {sys_lev_off, lev_ptr, lev_rows}: the level schedule of L's pattern from spx_ic0_analyse
+ * (used in reverse order for upper = 1).  b, x: device float32[n]; status: device
+ * int32[nsys] (SPX_OK, or SPX_BREAKDOWN for a zero, missing or non-finite pivot) or NULL.
+ * One thread block per system, one block barrier per level.  Asynchronous. */
+spx_status spx_sptrsv(const spx_csr* T, int32_t upper, int32_t nsys, const int32_t* sys_lev_off,
+                      const int32_t* lev_ptr, const int32_t* lev_rows, const float* b, float* x,
+                      int32_t* status, void* stream);
+
 /* ------------------------------------------------- sparse + sparse (Section 3.1.4) */
 
 /* Workspace bytes of spx_spadd_symbolic for m rows. */

@@ -6,6 +6,6 @@ The compute lives in the in-tree CUDA library ``_build/libspx.so`` (C ABI in
 """
 from . import abi, spai
 from .csr import CSR
-from .ops import SpAddPlan, SpGEMMPlan, masked_outer, sddmm, spadd, spgemm, spmm, spmm_t
+from .ops import SpAddPlan, SpGEMMPlan, TriangularSolver, masked_outer, sddmm, spadd, spgemm, spmm, spmm_t
 
-__all__ = ["abi", "CSR", "spmm", "sddmm", "spmm_t", "masked_outer", "spgemm", "SpGEMMPlan", "spadd", "SpAddPlan", "spai"]
+__all__ = ["abi", "CSR", "spmm", "sddmm", "spmm_t", "masked_outer", "spgemm", "SpGEMMPlan", "spadd", "SpAddPlan", "TriangularSolver", "spai"]

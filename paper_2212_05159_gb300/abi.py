@@ -118,6 +118,7 @@ SIGNATURES = {
     "spx_adam_step": [_I64, _P, _P, _P, _P, _I32, _F, _F, _F, _F, _P, _P],
     "spx_to_bf16": [_I64, _P, _P, _P],
     "spx_spai_residual": [_CSRP, _F, _P, _P, _P],
+    "spx_sptrsv": [_CSRP, _I32, _I32, _P, _P, _P, _P, _P, _P, _P],
     "spx_spadd_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_spadd_symbolic": [_CSRP, _CSRP, _P, ctypes.POINTER(_I64), _P, _SZ, _P],
     "spx_spadd_fill": [_CSRP, _CSRP, _P, _P, _P, _P, _P, _P, _P],
@@ -490,6 +491,13 @@ def spx_adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-
 
 def spx_to_bf16(src, dst):
     _check(lib().spx_to_bf16(int(src.numel()), ptr(src), ptr(dst), _stream()), "spx_to_bf16")
+
+
+def spx_sptrsv(T: spx_csr, upper: bool, nsys: int, levels, b, x, status=None):
+    off, lp, rows = levels
+    _check(lib().spx_sptrsv(ctypes.byref(T), int(bool(upper)), int(nsys), ptr(off), ptr(lp), ptr(rows), ptr(b),
+                            ptr(x), ptr(status), _stream()), "spx_sptrsv")
+    return x
 
 
 def spx_spadd_symbolic(A: spx_csr, B: spx_csr, c_indptr, device) -> int:

@@ -65,3 +65,22 @@ class SpAdd(torch.autograd.Function):
     def backward(ctx, gc):
         ga, gb = ctx.plan.backward(gc, ctx.alpha, ctx.beta, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
         return ga, gb, None, None, None
+
+
+class SpTRSV(torch.autograd.Function):
+    """x = L^-1 b for a batch of lower-triangular systems.  VJPs (Section 3.1.5, Table 1
+    SpSolve rule): grad_b = L^-T v,  grad_L = -(L^-T v) x^T masked to mask(L)."""
+
+    @staticmethod
+    def forward(ctx, l_values, b, solver):
+        x = solver.solve(b, l_values)
+        ctx.solver = solver
+        ctx.save_for_backward(l_values, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, v):
+        l_values, x = ctx.saved_tensors
+        lam = ctx.solver.solve(v.contiguous(), l_values, transpose=True)
+        g_l = ops.masked_outer(ctx.solver.L, lam, x, -1.0) if ctx.needs_input_grad[0] else None
+        return g_l, lam, None

@@ -103,6 +103,36 @@ class SpGEMMPlan:
         return ga, gb
 
 
+class TriangularSolver:
+    """Level schedule and transpose of a block-diagonal batch of lower-triangular patterns
+    (Section 3.1.5), built once per pattern; solves L x = b and L^T y = v on the device."""
+
+    def __init__(self, L: CSR, sys_ptr):
+        if L.m != L.n:
+            raise ValueError("L must be square")
+        self.L = L
+        dev = L.device
+        ptr_t = sys_ptr if isinstance(sys_ptr, torch.Tensor) else torch.as_tensor(sys_ptr, dtype=torch.int32)
+        self.sys_ptr = ptr_t.to(device=dev, dtype=torch.int32)
+        self.nsys = int(self.sys_ptr.numel()) - 1
+        self.levels = abi.spx_ic0_analyse(L.struct(), self.sys_ptr, self.nsys, dev)
+        self.t_ip, self.t_ix, self.perm = L.transpose_pattern()
+        self.status = torch.zeros(self.nsys, dtype=torch.int32, device=dev)
+
+    def solve(self, b: torch.Tensor, values: torch.Tensor | None = None, transpose: bool = False,
+              out: torch.Tensor | None = None) -> torch.Tensor:
+        v = self.L.values if values is None else values
+        x = out if out is not None else torch.empty_like(b)
+        if transpose:
+            lt = torch.empty_like(v)
+            abi.spx_gather_values(self.perm, v, lt)
+            T = abi.csr_struct(self.L.n, self.L.m, self.t_ip, self.t_ix, lt)
+        else:
+            T = self.L.struct(v)
+        abi.spx_sptrsv(T, transpose, self.nsys, self.levels, b.contiguous(), x, self.status)
+        return x
+
+
 class SpAddPlan:
     """Pattern of C = alpha A + beta B -- the union of the stored patterns, row by row
     (Section 3.1.4) -- and the maps between the three patterns, built once per pair."""
