@@ -291,38 +291,96 @@ def time_workload(W, steps, warmup, ws):
 
 
 def time_e2e(W, steps, warmup):
-    """Same step through host buffers: pinned H2D of values, X, G; D2H of Y, gA, gX."""
+    """The step end to end through host buffers: every step copies its inputs (A's values, X,
+    G) from pinned host memory and its results (Y, gA, gX) back.  Streamed the way a user
+    feeds batches: two device buffer sets, copies in on one stream, the three products on a
+    second, copies out on a third, so step s + 1's inputs travel while step s computes and
+    step s - 1's results travel back (the link is full duplex).  Returns (ms per step,
+    H2D bytes per step, D2H bytes per step, ms per step with everything on one stream)."""
     import torch
+    from paper_2212_05159_gb300 import abi
     hv = torch.from_numpy(W.host.values).pin_memory()
     hX = W.X.cpu().pin_memory()
     hG = W.G.cpu().pin_memory()
     oY = torch.empty_like(W.Y, device="cpu").pin_memory()
     oA = torch.empty_like(W.gA, device="cpu").pin_memory()
     oX = torch.empty_like(W.gX, device="cpu").pin_memory()
-    vals = W.dA.values
+    slots = [dict(v=W.dA.values, X=W.X, G=W.G, Y=W.Y, gA=W.gA, gX=W.gX)]
+    slots.append({k: torch.empty_like(t) for k, t in slots[0].items()})
+    for sl in slots:
+        sl["sA"] = W.dA.struct(sl["v"])
+        sl["sAT"] = W.dA.t_struct(sl["v"])
 
-    def step():
-        vals.copy_(hv, non_blocking=True)
-        W.X.copy_(hX, non_blocking=True)
-        W.G.copy_(hG, non_blocking=True)
-        for kname in W.KERNELS:
-            W.run_kernel(kname)
-        oY.copy_(W.Y, non_blocking=True)
-        oA.copy_(W.gA, non_blocking=True)
-        oX.copy_(W.gX, non_blocking=True)
+    def compute(sl):
+        abi.spx_spmm(sl["sA"], sl["X"], sl["Y"], 1.0, 0.0, W.plan, W.ws_spmm)
+        abi.spx_sddmm(sl["sA"], sl["G"], sl["X"], sl["gA"], 1.0, W.sddmm_cb, W.ws_sddmm, plan=W.sddmm_plan)
+        abi.spx_spmm_t(sl["sAT"], W.perm, sl["G"], sl["gX"], 1.0, 0.0, W.t_plan, W.ws_t)
+
+    def h2d(sl):
+        sl["v"].copy_(hv, non_blocking=True)
+        sl["X"].copy_(hX, non_blocking=True)
+        sl["G"].copy_(hG, non_blocking=True)
+
+    def d2h(sl):
+        oY.copy_(sl["Y"], non_blocking=True)
+        oA.copy_(sl["gA"], non_blocking=True)
+        oX.copy_(sl["gX"], non_blocking=True)
+
+    # one stream, no overlap (reported beside the streamed figure)
+    def serial_step():
+        h2d(slots[0])
+        compute(slots[0])
+        d2h(slots[0])
     for _ in range(warmup):
-        step()
+        serial_step()
     torch.cuda.synchronize()
-    st = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
+    a.record()
     for _ in range(steps):
-        step()
-    b.record(st)
+        serial_step()
+    b.record()
     torch.cuda.synchronize()
-    h2d = hv.numel() * 4 + hX.numel() * 4 + hG.numel() * 4
-    d2h = oY.numel() * 4 + oA.numel() * 4 + oX.numel() * 4
-    return a.elapsed_time(b) / steps, h2d, d2h
+    serial_ms = a.elapsed_time(b) / steps
+
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    done_in = [ev(), ev()]
+    done_cmp = [ev(), ev()]
+    done_out = [ev(), ev()]
+    used = [False, False]
+
+    def streamed(n):
+        for step in range(n):
+            k = step % 2
+            with torch.cuda.stream(s_in):
+                if used[k]:
+                    s_in.wait_event(done_cmp[k])           # slot k's inputs consumed
+                h2d(slots[k])
+                done_in[k].record(s_in)
+            with torch.cuda.stream(s_cmp):
+                s_cmp.wait_event(done_in[k])
+                if used[k]:
+                    s_cmp.wait_event(done_out[k])          # slot k's results copied out
+                compute(slots[k])
+                done_cmp[k].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(done_cmp[k])
+                d2h(slots[k])
+                done_out[k].record(s_out)
+            used[k] = True
+    streamed(max(warmup, 2))
+    torch.cuda.synchronize()
+    used[0] = used[1] = False
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(s_in)
+    streamed(steps)
+    s_out.wait_stream(s_in)
+    s_out.wait_stream(s_cmp)
+    t1.record(s_out)
+    torch.cuda.synchronize()
+    h2d_b = hv.numel() * 4 + hX.numel() * 4 + hG.numel() * 4
+    d2h_b = oY.numel() * 4 + oA.numel() * 4 + oX.numel() * 4
+    return t0.elapsed_time(t1) / steps, h2d_b, d2h_b, serial_ms
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -614,7 +672,7 @@ def main():
                 "traffic": ncu_traffic(f"{dom}_powerlaw_k{W.k}", src_path),
                 "algorithmic_bytes": cb[dom], "bytes_model": "compulsory",
                 "gather_model_frac": gb[dom] / (per[dom] * 1e-3) / 1e9 / hbm}
-    e2e_ms, h2d, d2h = time_e2e(W, max(3, args.steps // 2), 2)
+    e2e_ms, h2d, d2h, e2e_serial_ms = time_e2e(W, max(3, args.steps // 2), 2)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -628,7 +686,9 @@ def main():
         "per_kernel_gbs_compulsory": {k: cb[k] / (per[k] * 1e-3) / 1e9 for k in per},
         "roofline": roofline,
         "e2e": {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "mode": "streamed: inputs, products and results on three streams, two buffer sets",
+                "serial_ms_per_step": e2e_serial_ms},
         "gpu_launches": W.launches_per_step() * args.steps,
         "clocks": clk,
     }
