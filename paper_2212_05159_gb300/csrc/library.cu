@@ -112,7 +112,7 @@ extern "C" const char* spx_status_name(int s) {
     }
 }
 
-extern "C" int32_t spx_version(void) { return 100; }
+extern "C" int32_t spx_version(void) { return 200; }
 
 extern "C" spx_status spx_csr_validate(const spx_csr* A, void* ws, size_t ws_bytes,
                                        void* stream) {
