@@ -583,7 +583,7 @@ def cg_section(args):
     tr = pcg_study.train(net, steps=args.train_steps, batch=32, n_it=8, gamma=0.8, lr=2e-3)
     tr.pop("loss_history", None)
     out["training"] = tr
-    out["eval_256x256"] = pcg_study.evaluate(net, nsys=args.eval_systems, per_batch=64,
+    out["eval_256x256"] = pcg_study.evaluate(net, nsys=args.eval_systems, per_batch=args.eval_batch,
                                              ic0_systems=min(args.ic0_systems, args.eval_systems))
     return out
 
@@ -630,6 +630,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=313,
                     help="training batches of 32 generated systems (313: the 10k-system training set)")
     ap.add_argument("--eval-systems", type=int, default=1000, help="held-out 256^2 systems")
+    ap.add_argument("--eval-batch", type=int, default=256, help="held-out systems per PCG launch")
     ap.add_argument("--ic0-systems", type=int, default=128,
                     help="the first this many held-out systems are also solved with IC(0) (~50 ms each)")
     args = ap.parse_args()
