@@ -68,6 +68,82 @@ def gather_bytes(m, n, nnz, k):
 
 
 # ----------------------------------------------------------------------------- clocks
+class NvmlClockSampler:
+    """Reads the SM clock and the clock-event (throttle) reasons through NVML every ~0.5 ms
+    on a host thread while the timed region runs (read-only queries; no setting is changed).
+    The timed region of the step is tens of milliseconds, too short for nvidia-smi's loop."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.ok = False
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+                return
+            self.reasons_fn = None
+            for nm in ("nvmlDeviceGetCurrentClocksEventReasons", "nvmlDeviceGetCurrentClocksThrottleReasons"):
+                try:
+                    self.reasons_fn = getattr(self.lib, nm)
+                    break
+                except AttributeError:
+                    continue
+            mx = ctypes.c_uint(0)
+            self.max_mhz = None
+            if self.lib.nvmlDeviceGetMaxClockInfo(self.h, ctypes.c_int(1), ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self.ok = True
+        except OSError:
+            self.ok = False
+
+    def _one(self):
+        mhz = ctypes.c_uint(0)
+        rs = ctypes.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetClockInfo(self.h, ctypes.c_int(1), ctypes.byref(mhz)) != 0:
+            return None
+        if self.reasons_fn is not None:
+            self.reasons_fn(self.h, ctypes.byref(rs))
+        return time.perf_counter(), float(mhz.value), int(rs.value)
+
+    def start(self):
+        self.stop_flag = False
+
+        def loop():
+            while not self.stop_flag:
+                smp = self._one()
+                if smp:
+                    self.samples.append(smp)
+                time.sleep(0.0005)
+        self.thread = threading.Thread(target=loop, daemon=True)
+        self.thread.start()
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 2.0:
+            time.sleep(0.001)
+
+    def stop(self, window=None, load_from=None):
+        self.stop_flag = True
+        self.thread.join(timeout=2)
+        smp = self.samples
+        used = "whole run"
+        if window is not None:
+            inside = [x for x in smp if window[0] <= x[0] <= window[1]]
+            used = "timed region"
+            if len(inside) < 3 and load_from is not None:
+                inside = [x for x in smp if load_from <= x[0] <= window[1]]
+                used = "warm-up + timed region"
+            smp = inside
+        reasons = sorted({nm for _, _, r in smp for bit, nm in self.REASONS.items() if r & bit})
+        sm = [m for _, m, _ in smp]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(sm), "window": used, "source": "nvml"}
+
+
 class ClockSampler:
     """Samples nvidia-smi during the timed region (SM clock, throttle reasons)."""
 
@@ -654,7 +730,9 @@ def main():
     import paper_2212_05159_gb300  # noqa: F401  (fails loudly without the CUDA library)
 
     W = Workload("powerlaw", k=args.k)
-    clocks = ClockSampler(index=local)
+    clocks = NvmlClockSampler(index=local)
+    if not clocks.ok:
+        clocks = ClockSampler(index=local)
     clocks.start()
     ms, per = time_workload(W, args.steps, args.warmup, ws)
     clk = clocks.stop(window=W.windows[1], load_from=W.windows[0])
