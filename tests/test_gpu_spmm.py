@@ -152,6 +152,34 @@ def test_validate_rejects_bad_patterns():
         spx.CSR.from_host(oob).validate()
 
 
+@pytest.mark.parametrize("kind,k", [("powerlaw", 32), ("powerlaw", 128), ("poisson3d", 32)])
+def test_full_size_bench_configuration_sampled(kind, k):
+    """The benchmark's own workloads (power-law n = 2^20 at k = 32 and 128, 3D Poisson 128^3 at
+    k = 32), built and autotuned exactly as bench.py does and run through its launch calls;
+    sampled rows of Y, gA and gX against the oracle computed on those rows alone."""
+    import bench
+    W = bench.Workload(kind, k=k)
+    for kname in W.KERNELS:
+        W.run_kernel(kname)
+    torch.cuda.synchronize()
+    A = W.host
+    X, G = host(W.X).astype(np.float64), host(W.G).astype(np.float64)
+    Y, gA, gX = host(W.Y), host(W.gA), host(W.gX)
+    rng = np.random.default_rng(1)
+    lens = A.row_lengths()
+    rows = np.concatenate([rng.choice(A.m, 300, replace=False), np.argsort(lens)[-10:]])
+    S, take = sub_rows(A, rows)
+    assert_close_normalised(Y[rows], oracle.spmm(S, X), oracle.spmm(abs_csr(S), np.abs(X)), what=f"Y {kind}")
+    Gs = G[rows]
+    assert_close_normalised(gA[take], oracle.sddmm(S, Gs, X), oracle.sddmm(S, np.abs(Gs), np.abs(X)),
+                            what=f"gA {kind}")
+    t_ip, t_ix, perm = oracle.transpose(A)
+    AT = synth.CSR(A.n, A.m, t_ip, t_ix, A.values[perm])
+    cols = rng.choice(A.n, 300, replace=False)
+    ST, _ = sub_rows(AT, cols)
+    assert_close_normalised(gX[cols], oracle.spmm(ST, G), oracle.spmm(abs_csr(ST), np.abs(G)), what=f"gX {kind}")
+
+
 @pytest.mark.parametrize("k", [32])
 def test_full_size_powerlaw_sampled(k):
     """The n = 2^20 power-law workload in the benchmark's launch configuration, checked
