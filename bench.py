@@ -752,6 +752,8 @@ def main():
                 "algorithmic_bytes": cb[dom], "bytes_model": "compulsory",
                 "gather_model_frac": gb[dom] / (per[dom] * 1e-3) / 1e9 / hbm}
     e2e_ms, h2d, d2h, e2e_serial_ms = time_e2e(W, max(3, args.steps // 2), 2)
+    e2e_ms = max_over_ranks(e2e_ms, ws)
+    e2e_serial_ms = max_over_ranks(e2e_serial_ms, ws)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -793,7 +795,7 @@ def main():
             line["sptrsv"] = sptrsv_section()
         if "cg" in secs:
             line["cg"] = cg_section(args)
-    if rank == 0 and "cpu" in secs:
+    if rank == 0 and ws == 1 and "cpu" in secs:            # the CPU baseline: one process, N = 1 only
         v, desc, cores = cpu_baseline(k=args.k)
         line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
