@@ -15,13 +15,16 @@
 //   numeric   per row, C_ij = sum over k in A_i (in A's order) of A_ik B_kj: the row's
 //             accumulator is walked k by k; within one k the columns of B_k are distinct,
 //             so lanes never collide and the order of every sum is fixed (deterministic).
-// Reverse:
+//             (Four 8-lane groups with private accumulator rows, as in the reverse kernels,
+//             measured slower here: the extra shared memory halves the resident warps.)
+// Reverse (8-lane groups as well, four stored entries of the output in flight per warp):
 //   gA[(i,k)] = sum_{j in B_k} V[i,j] B[k,j]: one warp per row i, C_i's columns and V's
-//             values staged in shared memory, one lane per stored (i,k), binary search
-//             of each j in C_i.
+//             values staged in shared memory; a group per stored (i,k), its lanes over
+//             B_k's entries (binary search of j in C_i), then a fixed shuffle tree.
 //   gB[(k,j)] = sum_{i in A^T_k} A[i,k] V[i,j]: the "SpGEMM on the columns of A" of
-//             Section 3.1.2 -- one warp per row k of B over the transposed pattern of A,
-//             lanes over B_k's entries, binary search of j in C_i, i in increasing order.
+//             Section 3.1.2 -- one warp per row k of B over the transposed pattern of A; a
+//             group per stored (k,j), its lanes over A^T_k (binary search of j in C_i),
+//             then a fixed shuffle tree.
 // All integer work is exact; every floating-point sum has a fixed order.
 #include <limits.h>
 
@@ -34,6 +37,8 @@ namespace {
 constexpr int WARP_CAP = 512;          // products per row handled by one warp
 constexpr int SYM_WARPS = 8;           // warps per block, symbolic / fill
 constexpr int NUM_WARPS = 4;           // warps per block, numeric
+constexpr int GRP = 8;                 // lanes per group in the value kernels
+constexpr int NGRP = 32 / GRP;         // groups per warp
 constexpr int BIG_THREADS = 512;
 constexpr int BITMAP_WORDS = 8192;     // 32 KB shared bitmap: 262144 columns per chunk
 
@@ -288,6 +293,13 @@ __global__ void __launch_bounds__(BIG_THREADS) numeric_big_kernel(
 }
 
 // ------------------------------------------------------------------ backward
+// sum over the GRP lanes of a group, a fixed xor tree (the same order on every run)
+__device__ __forceinline__ float group_sum(float v, unsigned gmask) {
+#pragma unroll
+    for (int o = GRP / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(gmask, v, o, GRP);
+    return v;
+}
+
 // gA[(i,k)] = sum_{f in B_k} V[i, B_idx[f]] * B_val[f]   (V on C's pattern)
 __global__ void __launch_bounds__(NUM_WARPS * 32) grad_a_kernel(
     int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
@@ -296,6 +308,8 @@ __global__ void __launch_bounds__(NUM_WARPS * 32) grad_a_kernel(
     __shared__ int cols_all[NUM_WARPS][WARP_CAP];
     __shared__ float v_all[NUM_WARPS][WARP_CAP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / GRP, w = lane % GRP;
+    const unsigned gmask = ((1u << GRP) - 1u) << (g * GRP);
     const int64_t row = (int64_t)blockIdx.x * NUM_WARPS + warp;
     if (row >= m) return;
     const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
@@ -309,19 +323,25 @@ __global__ void __launch_bounds__(NUM_WARPS * 32) grad_a_kernel(
         }
     }
     __syncwarp();
-    for (int e = a_ptr[row] + lane; e < a_ptr[row + 1]; e += 32) {
-        const int k = a_idx[e];
+    const int a0 = a_ptr[row], a1 = a_ptr[row + 1];
+    // the groups take the row's entries round-robin; every lane of a group runs the same trips
+    for (int e0 = a0; e0 < a1; e0 += NGRP) {
+        const int e = e0 + g;
         float s = 0.f;
-        for (int f = b_ptr[k]; f < b_ptr[k + 1]; ++f) {
-            const int j = b_idx[f];
-            const int pos = lower_bound_i32(cols, nc, j);
-            if (pos < nc && cols[pos] == j) s = fmaf(v[pos], b_val[f], s);
+        if (e < a1) {
+            const int k = a_idx[e];
+            for (int f = b_ptr[k] + w; f < b_ptr[k + 1]; f += GRP) {
+                const int j = b_idx[f];
+                const int pos = lower_bound_i32(cols, nc, j);
+                if (pos < nc && cols[pos] == j) s = fmaf(v[pos], b_val[f], s);
+            }
         }
-        ga[e] = s;
+        s = group_sum(s, gmask);
+        if (e < a1 && w == 0) ga[e] = s;
     }
 }
 
-// gB[(k,j)] = sum_{i in A^T_k, increasing} A[i,k] * V[i,j]
+// gB[(k,j)] = sum_{i in A^T_k} A[i,k] * V[i,j]: a group per stored (k,j), lanes over A^T_k
 __global__ void __launch_bounds__(256) grad_b_kernel(
     int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
     const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
@@ -329,19 +349,26 @@ __global__ void __launch_bounds__(256) grad_b_kernel(
     const float* __restrict__ gc, float* __restrict__ gb) {
     const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    const int g = lane / GRP, w = lane % GRP;
+    const unsigned gmask = ((1u << GRP) - 1u) << (g * GRP);
     if (k >= kb) return;
     const int ia = at_ptr[k], ib = at_ptr[k + 1];
-    for (int f = b_ptr[k] + lane; f < b_ptr[k + 1]; f += 32) {
-        const int j = b_idx[f];
+    const int f1 = b_ptr[k + 1];
+    for (int f0 = b_ptr[k]; f0 < f1; f0 += NGRP) {
+        const int f = f0 + g;
         float s = 0.f;
-        for (int t = ia; t < ib; ++t) {
-            const int i = at_idx[t];
-            const float aik = a_val[a_perm[t]];
-            const int c0 = c_ptr[i], nc = c_ptr[i + 1] - c0;
-            const int pos = lower_bound_i32(c_idx + c0, nc, j);
-            if (pos < nc && c_idx[c0 + pos] == j) s = fmaf(aik, gc[c0 + pos], s);
+        if (f < f1) {
+            const int j = b_idx[f];
+            for (int t = ia + w; t < ib; t += GRP) {
+                const int i = at_idx[t];
+                const float aik = a_val[a_perm[t]];
+                const int c0 = c_ptr[i], nc = c_ptr[i + 1] - c0;
+                const int pos = lower_bound_i32(c_idx + c0, nc, j);
+                if (pos < nc && c_idx[c0 + pos] == j) s = fmaf(aik, gc[c0 + pos], s);
+            }
         }
-        gb[f] = s;
+        s = group_sum(s, gmask);
+        if (f < f1 && w == 0) gb[f] = s;
     }
 }
 
