@@ -12,11 +12,12 @@
 //             bitmap of the column space (chunked), which yields the columns already
 //             sorted.  mask(C) is structural: no numerical-zero dropping.
 //   fill      copies the unique columns into C_indices.
-//   numeric   per row, C_ij = sum over k in A_i (in A's order) of A_ik B_kj: the row's
-//             accumulator is walked k by k; within one k the columns of B_k are distinct,
-//             so lanes never collide and the order of every sum is fixed (deterministic).
-//             (Four 8-lane groups with private accumulator rows, as in the reverse kernels,
-//             measured slower here: the extra shared memory halves the resident warps.)
+//   numeric   per row, C_ij = sum over k in A_i of A_ik B_kj.  Rows with at most 128
+//             columns: four 8-lane groups, group g takes the entries k = g, g+4, ... of A_i
+//             (in A's order) into a private slice of the row's accumulator (the four slices
+//             fit the space one wide row needs), its lanes over B_k's columns (distinct within
+//             a k, so lanes never collide); the slices are added in group order.  Wider rows:
+//             the whole warp on one k at a time.  Every sum has a fixed order.
 // Reverse (8-lane groups as well, four stored entries of the output in flight per warp):
 //   gA[(i,k)] = sum_{j in B_k} V[i,j] B[k,j]: one warp per row i, C_i's columns and V's
 //             values staged in shared memory; a group per stored (i,k), its lanes over
@@ -252,12 +253,41 @@ __global__ void __launch_bounds__(NUM_WARPS * 32) numeric_warp_kernel(
     int* cols = cols_all[warp];
     float* acc = acc_all[warp];
     const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
+    const int a0 = a_ptr[row], a1 = a_ptr[row + 1];
+    if (nc * NGRP <= WARP_CAP) {
+        // four 8-lane groups, each with a private accumulator slice of the row: group g takes
+        // the entries k = g, g+4, ... of A_i in order; the slices are added in group order
+        for (int t = lane; t < nc; t += 32) cols[t] = c_idx[c0 + t];
+        for (int t = lane; t < nc * NGRP; t += 32) acc[t] = 0.f;
+        __syncwarp();
+        const int g = lane / GRP, w = lane % GRP;
+        const unsigned gmask = ((1u << GRP) - 1u) << (g * GRP);
+        float* mine = acc + g * nc;
+        for (int e = a0 + g; e < a1; e += NGRP) {
+            const int k = a_idx[e];
+            const float av = a_val[e];
+            for (int f = b_ptr[k] + w; f < b_ptr[k + 1]; f += GRP) {
+                const int pos = lower_bound_i32(cols, nc, b_idx[f]);
+                mine[pos] = fmaf(av, b_val[f], mine[pos]);
+            }
+            __syncwarp(gmask);                      // the group's next k may hit the same columns
+        }
+        __syncwarp();
+        for (int t = lane; t < nc; t += 32) {
+            float sum = acc[t];
+#pragma unroll
+            for (int q = 1; q < NGRP; ++q) sum += acc[q * nc + t];
+            c_val[c0 + t] = sum;
+        }
+        return;
+    }
+    // wider rows: the whole warp on one k at a time, one accumulator
     for (int t = lane; t < nc; t += 32) {
         cols[t] = c_idx[c0 + t];
         acc[t] = 0.f;
     }
     __syncwarp();
-    for (int e = a_ptr[row]; e < a_ptr[row + 1]; ++e) {
+    for (int e = a0; e < a1; ++e) {
         const int k = a_idx[e];
         const float av = a_val[e];
         for (int f = b_ptr[k] + lane; f < b_ptr[k + 1]; f += 32) {
