@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/spx.h"
 
 namespace spx {
@@ -131,3 +133,21 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
         spx_status s_ = (call);                                        \
         if (s_ != SPX_OK) return s_;                                   \
     } while (0)
+
+namespace spx {
+
+// Raises the dynamic shared-memory limit of `kern` to `bytes` once per device (the attribute
+// belongs to the device's context); `done` holds one bit per device id below 64 and makes
+// concurrent first calls from several threads harmless (the attribute call is idempotent).
+template <typename K>
+inline spx_status ensure_smem_attr(K kern, int bytes, std::atomic<unsigned long long>& done, const char* who) {
+    int dev = 0;
+    SPX_CUDA(cudaGetDevice(&dev), who);
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return SPX_OK;
+    SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes), who);
+    if (bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return SPX_OK;
+}
+
+}  // namespace spx

@@ -554,13 +554,8 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
             const int32_t xs = use_slab ? c0 : 0;
 #define SPX_BULK_CASE(L)                                                                                      \
     case L: {                                                                                                 \
-        static bool attr_set = false;                                                                         \
-        if (!attr_set) {                                                                                      \
-            SPX_CUDA(cudaFuncSetAttribute(spmm_bulk_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                          (int)smem),                                                         \
-                     "spmm bulk attribute");                                                                  \
-            attr_set = true;                                                                                  \
-        }                                                                                                     \
+        static std::atomic<unsigned long long> attr_done{0};                                                  \
+        SPX_TRY(ensure_smem_attr(spmm_bulk_kernel<L>, (int)smem, attr_done, "spmm bulk attribute"));           \
         spmm_bulk_kernel<L><<<(unsigned)bgrid, BK_WARPS * 32, smem, st>>>(                                    \
             A->m, A->indptr, A->indices, vals, Xp, ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold, err); \
         break;                                                                                                \

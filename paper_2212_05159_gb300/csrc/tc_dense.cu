@@ -240,12 +240,8 @@ extern "C" spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K
     if (n == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
     const size_t smem = tc_smem_bytes();
-    static bool attr = false;
-    if (!attr) {
-        SPX_CUDA(cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                 "spx_dense_forward_tc attribute");
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    SPX_TRY(ensure_smem_attr(dense_tc_kernel, (int)smem, attr_done, "spx_dense_forward_tc attribute"));
     const int64_t tiles = (n + TC_M - 1) / TC_M;
     dense_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, st>>>(n, X1, K1, X2, K2,
                                                               static_cast<const __nv_bfloat16*>(W_bf16), bias, N, mode,
