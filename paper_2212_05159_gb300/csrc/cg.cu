@@ -29,6 +29,7 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "trisolve.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -197,11 +198,11 @@ __device__ __forceinline__ float spmv_row(const int32_t* __restrict__ ptr, const
 }
 
 // z = M r on rows [lo, hi) of the system (the caller barriers around LLT's two halves)
-template <int NT>
+template <int NT, int PC>
 __device__ __forceinline__ void apply_pc_local(const CgArgs& a, int lo, int hi) {
-    if (a.pc == 1) {
+    if constexpr (PC == 1) {
         for (int i = lo + threadIdx.x; i < hi; i += NT) a.z[i] = a.dinv[i] * a.r[i];
-    } else if (a.pc == 0) {
+    } else if constexpr (PC == 0) {
         for (int i = lo + threadIdx.x; i < hi; i += NT) a.z[i] = a.r[i];
     }
 }
@@ -209,45 +210,55 @@ __device__ __forceinline__ void apply_pc_local(const CgArgs& a, int lo, int hi) 
 // IC(0): z = L^-T L^-1 r with level-scheduled triangular solves, run by the cluster's
 // first block (block barriers between levels) while the others wait at the cluster
 // barrier.  L: lower CSR (diagonal last in each row); LT: its transpose (diagonal first).
+// The first NT rows of the next level are fetched (row ids, bounds, entries, pivot, right-
+// hand side) while the current level computes, so a level costs one round trip for the
+// solution entries it reads plus the barrier; rows beyond NT in a level are fetched in place.
 template <int NT>
-__device__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) {
+__device__ __noinline__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) {
     if (rank != 0) return;
     const int32_t* lp = a.lev_ptr + a.lev_off[sid];
     const int nl = a.lev_off[sid + 1] - a.lev_off[sid] - 1;
+    const int tid = threadIdx.x;
+    // forward: L w = r, levels ascending
+    TriRow cur = nl > 0 ? fetch_tri_row(true, lp[0] + tid, lp[1], a.lev_rows, a.l_ptr, a.l_idx, a.l_val, a.r) : TriRow{};
     for (int l = 0; l < nl; ++l) {
-        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += NT) {
-            const int i = a.lev_rows[q];
-            const int e1 = a.l_ptr[i + 1] - 1;
-            float s = a.r[i];
-            for (int e = a.l_ptr[i]; e < e1; ++e) s = fmaf(-a.l_val[e], a.w[a.l_idx[e]], s);
-            a.w[i] = s / a.l_val[e1];
-        }
+        TriRow nxt;
+        if (l + 1 < nl) nxt = fetch_tri_row(true, lp[l + 1] + tid, lp[l + 2], a.lev_rows, a.l_ptr, a.l_idx, a.l_val, a.r);
+        solve_tri_row(cur, a.l_idx, a.l_val, a.w);
+        for (int q = lp[l] + NT + tid; q < lp[l + 1]; q += NT)
+            solve_tri_row(fetch_tri_row(true, q, lp[l + 1], a.lev_rows, a.l_ptr, a.l_idx, a.l_val, a.r), a.l_idx,
+                          a.l_val, a.w);
         __syncthreads();
+        cur = nxt;
     }
+    // backward: L^T z = w, levels descending
+    cur = nl > 0 ? fetch_tri_row(false, lp[nl - 1] + tid, lp[nl], a.lev_rows, a.lt_ptr, a.lt_idx, a.lt_val, a.w)
+                 : TriRow{};
     for (int l = nl - 1; l >= 0; --l) {
-        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += NT) {
-            const int i = a.lev_rows[q];
-            const int e0 = a.lt_ptr[i];
-            float s = a.w[i];
-            for (int e = e0 + 1; e < a.lt_ptr[i + 1]; ++e) s = fmaf(-a.lt_val[e], a.z[a.lt_idx[e]], s);
-            a.z[i] = s / a.lt_val[e0];
-        }
+        TriRow nxt;
+        // the right-hand side of a row is w[i], final since the forward sweep ended
+        if (l > 0) nxt = fetch_tri_row(false, lp[l - 1] + tid, lp[l], a.lev_rows, a.lt_ptr, a.lt_idx, a.lt_val, a.w);
+        solve_tri_row(cur, a.lt_idx, a.lt_val, a.z);
+        for (int q = lp[l] + NT + tid; q < lp[l + 1]; q += NT)
+            solve_tri_row(fetch_tri_row(false, q, lp[l + 1], a.lev_rows, a.lt_ptr, a.lt_idx, a.lt_val, a.w), a.lt_idx,
+                          a.lt_val, a.z);
         __syncthreads();
+        cur = nxt;
     }
 }
 
-template <int NT>
+template <int NT, int PC>
 __device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi, unsigned rank, int sid) {
-    if (a.pc == 4) {
+    if constexpr (PC == 4) {
         cl.sync();                                               // r complete
         ic0_apply<NT>(a, rank, sid);
         cl.sync();                                               // z complete
-    } else if (a.pc == 3) {
+    } else if constexpr (PC == 3) {
         cl.sync();                                               // r complete
 #pragma unroll 2
         for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.r, i);      // z = M r
-    } else if (a.pc == 2) {
+    } else if constexpr (PC == 2) {
         cl.sync();                                               // r complete
 #pragma unroll 2
         for (int i = lo + threadIdx.x; i < hi; i += NT)
@@ -257,7 +268,7 @@ __device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi,
         for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.w, i);      // z = L w
     } else {
-        apply_pc_local<NT>(a, lo, hi);
+        apply_pc_local<NT, PC>(a, lo, hi);
     }
 }
 
@@ -276,7 +287,7 @@ __device__ __forceinline__ double true_residual(const CgArgs& a, int lo, int hi)
 
 // Registers capped at 64 (1024 / NT blocks per SM): the launch sizes its grid for that many
 // resident blocks.
-template <int NT>
+template <int NT, int PC>
 __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank();
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
             a.r[i] = bi;
             df_add_prod(v2[0], bi, bi);
         }
-        apply_pc<NT>(a, cl, lo, hi, rank, sid);
+        apply_pc<NT, PC>(a, cl, lo, hi, rank, sid);
         for (int i = lo + threadIdx.x; i < hi; i += NT) {
             const float zi = a.z[i];
             a.p[i] = zi;
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
                 dirty = true;
                 ++it;
                 DF v2n[2] = {{0.f, 0.f}, {0.f, 0.f}};
-                if (a.pc <= 1) {
+                if constexpr (PC <= 1) {
                     // x_p += alpha p; r -= alpha q; z = M r (local); <r, z>, <r, r> -- one pass
                     float* __restrict__ XP = a.xp;
                     float* __restrict__ R = a.r;
@@ -392,12 +403,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
                         XP[i] = fmaf(alpha, Pv[i], XP[i]);
                         const float ri = fmaf(-alpha, Qv[i], R[i]);
                         R[i] = ri;
-                        const float zi = a.pc == 1 ? DI[i] * ri : ri;
+                        const float zi = PC == 1 ? DI[i] * ri : ri;
                         Z[i] = zi;
                         df_add_prod(v2n[0], ri, zi);
                         df_add_prod(v2n[1], ri, ri);
                     }
-                } else if (a.pc == 3) {
+                } else if constexpr (PC == 3) {
                     // explicit M: update, barrier, then z = M r with the dots in the same pass
                     float* __restrict__ XP = a.xp;
                     float* __restrict__ R = a.r;
@@ -429,7 +440,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
                         XP[i] = fmaf(alpha, Pv[i], XP[i]);
                         R[i] = fmaf(-alpha, Qv[i], R[i]);
                     }
-                    apply_pc<NT>(a, cl, lo, hi, rank, sid);
+                    apply_pc<NT, PC>(a, cl, lo, hi, rank, sid);
                     const float* __restrict__ Rc = a.r;
                     const float* __restrict__ Zc = a.z;
 #pragma unroll 2
@@ -493,7 +504,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
                         __syncthreads();
                     }
                     if (bc.action == ACT_STOP) break;
-                    apply_pc<NT>(a, cl, lo, hi, rank, sid);
+                    apply_pc<NT, PC>(a, cl, lo, hi, rank, sid);
                     DF vz[1] = {{0.f, 0.f}};
                     for (int i = lo + threadIdx.x; i < hi; i += NT) df_add_prod(vz[0], a.r[i], a.z[i]);
                     double o1[1];
@@ -677,9 +688,21 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
         SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, a), "spx_cg_batched launch");
         return SPX_OK;
     };
-    if (nt == 256) return launch(pcg_kernel<256>);
-    if (nt == 1024) return launch(pcg_kernel<1024>);
-    return launch(pcg_kernel<512>);
+    auto by_pc = [&](auto k0, auto k1, auto k2, auto k3, auto k4) -> spx_status {
+        switch (pc_kind) {
+            case 0: return launch(k0);
+            case 1: return launch(k1);
+            case 2: return launch(k2);
+            case 3: return launch(k3);
+            default: return launch(k4);
+        }
+    };
+    if (nt == 256)
+        return by_pc(pcg_kernel<256, 0>, pcg_kernel<256, 1>, pcg_kernel<256, 2>, pcg_kernel<256, 3>, pcg_kernel<256, 4>);
+    if (nt == 1024)
+        return by_pc(pcg_kernel<1024, 0>, pcg_kernel<1024, 1>, pcg_kernel<1024, 2>, pcg_kernel<1024, 3>,
+                     pcg_kernel<1024, 4>);
+    return by_pc(pcg_kernel<512, 0>, pcg_kernel<512, 1>, pcg_kernel<512, 2>, pcg_kernel<512, 3>, pcg_kernel<512, 4>);
 }
 
 extern "C" spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream) {

@@ -6,34 +6,23 @@
 // lower pattern (spx_ic0_analyse) are walked by one thread block per system, rows of a level
 // in parallel, one block barrier between levels -- no thread ever waits on a flag written by
 // another block.  The transposed solve walks the same levels in reverse order on the CSR of
-// L^T (upper triangular).  Each row's sum is accumulated in double-float (FP32 pair) before
-// the division by the pivot.  A zero, non-finite or missing pivot sets the system's status
+// L^T (upper triangular).  The rows of the next level are fetched while a level solves
+// (trisolve.cuh); each row's sum is accumulated in double-float (FP32 pair) before the
+// division by the pivot.  A zero, non-finite or missing pivot sets the system's status
 // to SPX_BREAKDOWN (its solution is then not meaningful).
 #include <math.h>
 
 #include "common.cuh"
+#include "trisolve.cuh"
 
 namespace spx {
 namespace {
 
 constexpr int TRSV_THREADS = 512;
 
-struct DFt {
-    float hi, lo;
-};
-
-__device__ __forceinline__ void dft_add_prod(DFt& s, float a, float b) {
-    const float ph = a * b;
-    const float pl = fmaf(a, b, -ph);
-    const float t = s.hi + ph;
-    const float bp = t - s.hi;
-    const float err = (s.hi - (t - bp)) + (ph - bp);
-    s.hi = t;
-    s.lo += err + pl;
-}
-
 // upper = 0: T is lower with the diagonal last in each row, levels ascending;
 // upper = 1: T is upper (the CSR of L^T) with the diagonal first, levels descending.
+// The first TRSV_THREADS rows of the next level are fetched while the current level solves.
 __global__ void __launch_bounds__(TRSV_THREADS) sptrsv_kernel(int32_t nsys, int32_t upper,
                                                               const int32_t* __restrict__ tp,
                                                               const int32_t* __restrict__ ti,
@@ -50,20 +39,28 @@ __global__ void __launch_bounds__(TRSV_THREADS) sptrsv_kernel(int32_t nsys, int3
     __syncthreads();
     const int32_t* lp = lev_ptr + off[s];
     const int nl = off[s + 1] - off[s] - 1;
+    const bool lower = upper == 0;
+    const int tid = threadIdx.x;
+    auto level = [&](int t) { return upper ? nl - 1 - t : t; };
+    auto check = [&](const TriRow& r) {
+        if (r.i >= 0 && (r.piv == 0.f || !isfinite(r.piv))) atomicOr(&bad, 1);
+    };
+    TriRow cur;
+    if (nl > 0) cur = fetch_tri_row(lower, lp[level(0)] + tid, lp[level(0) + 1], lev_rows, tp, ti, tv, b);
     for (int t = 0; t < nl; ++t) {
-        const int l = upper ? nl - 1 - t : t;
-        for (int q = lp[l] + threadIdx.x; q < lp[l + 1]; q += TRSV_THREADS) {
-            const int i = lev_rows[q];
-            const int a = tp[i], e = tp[i + 1];
-            const int d = upper ? a : e - 1;                       // pivot position
-            DFt acc{b[i], 0.f};
-            const int o0 = upper ? a + 1 : a, o1 = upper ? e : e - 1;
-            for (int k = o0; k < o1; ++k) dft_add_prod(acc, -tv[k], x[ti[k]]);
-            const float piv = (e > a && ti[d] == i) ? tv[d] : 0.f;
-            if (piv == 0.f || !isfinite(piv)) atomicOr(&bad, 1);
-            x[i] = (acc.hi + acc.lo) / piv;
+        const int l = level(t);
+        TriRow nxt;
+        if (t + 1 < nl)
+            nxt = fetch_tri_row(lower, lp[level(t + 1)] + tid, lp[level(t + 1) + 1], lev_rows, tp, ti, tv, b);
+        check(cur);
+        solve_tri_row_df(cur, ti, tv, x);
+        for (int q = lp[l] + TRSV_THREADS + tid; q < lp[l + 1]; q += TRSV_THREADS) {
+            const TriRow r = fetch_tri_row(lower, q, lp[l + 1], lev_rows, tp, ti, tv, b);
+            check(r);
+            solve_tri_row_df(r, ti, tv, x);
         }
         __syncthreads();
+        cur = nxt;
     }
     if (threadIdx.x == 0 && status) status[s] = bad ? SPX_BREAKDOWN : SPX_OK;
 }
