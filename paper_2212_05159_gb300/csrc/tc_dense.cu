@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     const int K = K1 + K2;
     const int kpad = (K + 15) & ~15;
     unsigned char* sA = smem;                                   // 128 x kpad bf16
-    unsigned char* sB = smem + TC_M * TC_KMAX * 2;              // N x kpad bf16
+    unsigned char* sB = smem + TC_M * kpad * 2;                 // N x kpad bf16, after A
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = (int64_t)blockIdx.x * TC_M;
     const int ncols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
@@ -217,7 +217,14 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     }
 }
 
-size_t tc_smem_bytes() { return (size_t)TC_SMEM; }
+// Shared memory one launch needs: the A and B^T tiles for its K, or the epilogue rows for its
+// N, whichever is larger (smaller layers fit more blocks per SM).
+size_t tc_smem_bytes(int K, int N) {
+    const size_t kpad = (size_t)((K + 15) & ~15);
+    const size_t tiles = (size_t)TC_M * kpad * 2 + (size_t)N * kpad * 2;
+    const size_t stage = (size_t)TC_M * (N + 4) * 4;
+    return tiles > stage ? tiles : stage;
+}
 
 bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
@@ -239,9 +246,9 @@ extern "C" spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K
         return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: K1, K2 multiples of 4 and 16-byte aligned rows needed");
     if (n == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
-    const size_t smem = tc_smem_bytes();
+    const size_t smem = tc_smem_bytes(K1 + K2, N);
     static std::atomic<unsigned long long> attr_done{0};
-    SPX_TRY(ensure_smem_attr(dense_tc_kernel, (int)smem, attr_done, "spx_dense_forward_tc attribute"));
+    SPX_TRY(ensure_smem_attr(dense_tc_kernel, TC_SMEM, attr_done, "spx_dense_forward_tc attribute"));
     const int64_t tiles = (n + TC_M - 1) / TC_M;
     dense_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, st>>>(n, X1, K1, X2, K2,
                                                               static_cast<const __nv_bfloat16*>(W_bf16), bias, N, mode,
