@@ -5,7 +5,7 @@ one statement per step of the architecture below; gradients come from torch auto
 
 The network maps an SPD matrix A (CSR) to the values of a lower-triangular L on the
 pattern of tril(A), used as the factored approximate inverse M = L L^T of Section 4.3.
-The architecture is this build's (the paper gives none for this use; the closest is
+The architecture is chosen here (the paper gives none for this use; the closest is
 the GNN of Section 4.5); parity of the trained weights themselves is unpinned.
 
   scale-free inputs   d_i = a_ii^(-1/2),  e_ij = d_i a_ij d_j  (e_ii = 1)
