@@ -269,6 +269,45 @@ spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, const spx_csr
                                const int32_t* at_indptr, const int32_t* at_indices,
                                const int32_t* a_perm, void* stream);
 
+/* ------------------------------------------------------- solver conveniences */
+
+/* z = M r for the preconditioners of spx_cg_batched, applied outside the solver (e.g. to
+ * use a learned M elsewhere): pc_kind 0 z = r; 1 z = pc_diag_inv .* r; 2 z = L (LT r) with
+ * LT the CSR of L^T with values (tmp: device float32[n]); 3 z = L r for an explicit M passed
+ * as L; 4 (IC(0)) z = L^-T (L^-1 r) by two spx_sptrsv solves with the level schedule
+ * ic0_levels of nsys systems (tmp: device float32[n]).  r, z: device float32[n], distinct.
+ * Asynchronous. */
+spx_status spx_precond_apply(int32_t pc_kind, int64_t n, const float* r, float* z,
+                             const float* pc_diag_inv, const spx_csr* L, const spx_csr* LT,
+                             int32_t nsys, const int32_t* const* ic0_levels, float* tmp, void* stream);
+
+/* The SpSolve VJP of Table 1 in one call, for a batch solved with spx_cg_batched: lambda =
+ * A^-T g (A symmetric, so the same PCG with right-hand side g; lambda: device float64[n],
+ * = grad_b), then grad_A = -(lambda x^T) on mask(A) (device float32[nnz], or NULL to skip;
+ * x: the forward solution, device float64[n]).  The remaining arguments are those of
+ * spx_cg_batched and have the same meaning; iters / status / relres describe the adjoint
+ * solve.  Asynchronous. */
+spx_status spx_cg_adjoint(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
+                          const int32_t* order, const double* x, const float* g, double* lambda,
+                          float* grad_A, int32_t pc_kind, const float* pc_diag_inv,
+                          const spx_csr* L, const spx_csr* LT, const int32_t* const* ic0_levels,
+                          double tol, int32_t maxit, double delta, int32_t* iters, int32_t* status,
+                          double* relres, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Chooses the launch parameters of spx_spmm for A and width k by timing on `stream`: rows
+ * per lane group 1, 2, 4, 8 and both gather engines (when the operands allow the TMA
+ * engine), one pass over all k columns; keeps the plan's row lists and column parts.  X, Y:
+ * the operands to time with (Y is overwritten).  Writes the fastest into *plan and its time
+ * (ms per call) into *best_ms.  Synchronizes `stream`. */
+spx_status spx_spmm_autotune(const spx_csr* A, const float* X, int64_t ldx, int32_t k, float* Y,
+                             int64_t ldy, spx_rowplan* plan, float* best_ms, void* stream);
+
+/* Copies n status words (e.g. the per-system status of spx_cg_batched) from the device to
+ * status_host after the work queued on `stream`, checks the device error word like
+ * spx_check_device, and returns SPX_OK if every word is SPX_OK, else the first one that is
+ * not (with its index in spx_last_error()).  Synchronizes `stream`. */
+spx_status spx_sync_status(const int32_t* status_dev, int32_t n, int32_t* status_host, void* stream);
+
 /* ------------------------------------------ sparse triangular solve (Section 3.1.5) */
 
 /* Solves T x = b for every system of a block-diagonal batch of triangular systems.

@@ -118,6 +118,11 @@ SIGNATURES = {
     "spx_adam_step": [_I64, _P, _P, _P, _P, _I32, _F, _F, _F, _F, _P, _P],
     "spx_to_bf16": [_I64, _P, _P, _P],
     "spx_spai_residual": [_CSRP, _F, _P, _P, _P],
+    "spx_precond_apply": [_I32, _I64, _P, _P, _P, _CSRP, _CSRP, _I32, _P, _P, _P],
+    "spx_cg_adjoint": [_CSRP, _P, _I32, _P, _P, _P, _P, _P, _I32, _P, _CSRP, _CSRP, _P, _D, _I32, _D, _P, _P, _P,
+                       _P, _SZ, _P],
+    "spx_spmm_autotune": [_CSRP, _P, _I64, _I32, _P, _I64, _PLANP, ctypes.POINTER(_F), _P],
+    "spx_sync_status": [_P, _I32, _P, _P],
     "spx_sptrsv": [_CSRP, _I32, _I32, _P, _P, _P, _P, _P, _P, _P],
     "spx_spadd_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_spadd_symbolic": [_CSRP, _CSRP, _P, ctypes.POINTER(_I64), _P, _SZ, _P],
@@ -498,6 +503,51 @@ def spx_sptrsv(T: spx_csr, upper: bool, nsys: int, levels, b, x, status=None):
     _check(lib().spx_sptrsv(ctypes.byref(T), int(bool(upper)), int(nsys), ptr(off), ptr(lp), ptr(rows), ptr(b),
                             ptr(x), ptr(status), _stream()), "spx_sptrsv")
     return x
+
+
+def _levels_arg(levels):
+    if levels is None:
+        return None
+    arr = (ctypes.c_void_p * 3)(*[t.data_ptr() for t in levels])
+    return ctypes.cast(arr, ctypes.c_void_p), arr            # keep arr alive with the pointer
+
+
+def spx_precond_apply(kind: int, r, z, dinv=None, L: spx_csr | None = None, LT: spx_csr | None = None,
+                      nsys: int = 0, levels=None, tmp=None):
+    lv = _levels_arg(levels)
+    _check(lib().spx_precond_apply(int(kind), int(r.numel()), ptr(r), ptr(z), ptr(dinv),
+                                   ctypes.byref(L) if L is not None else None,
+                                   ctypes.byref(LT) if LT is not None else None, int(nsys),
+                                   lv[0] if lv else None, ptr(tmp), _stream()), "spx_precond_apply")
+    return z
+
+
+def spx_cg_adjoint(A: spx_csr, sys_ptr, nsys, order, x, g, lam, grad_A, pc_kind, dinv, L, LT, tol, maxit, delta,
+                   iters, status, relres, ws, ic0_levels=None):
+    lv = _levels_arg(ic0_levels)
+    _check(lib().spx_cg_adjoint(ctypes.byref(A), ptr(sys_ptr), int(nsys), ptr(order), ptr(x), ptr(g), ptr(lam),
+                                ptr(grad_A), int(pc_kind), ptr(dinv), ctypes.byref(L) if L is not None else None,
+                                ctypes.byref(LT) if LT is not None else None, lv[0] if lv else None, float(tol),
+                                int(maxit), float(delta), ptr(iters), ptr(status), ptr(relres), ptr(ws), ws.numel(),
+                                _stream()), "spx_cg_adjoint")
+
+
+def spx_spmm_autotune(A: spx_csr, X, Y, plan: spx_rowplan):
+    """Times spx_spmm's launch parameters on the device; returns (plan, ms per call)."""
+    px, ldx = _dense(X, "X")
+    py, ldy = _dense(Y, "Y")
+    p = spx_rowplan.from_buffer_copy(plan)
+    ms = _F(0.0)
+    _check(lib().spx_spmm_autotune(ctypes.byref(A), px, ldx, int(X.shape[1]), py, ldy, ctypes.byref(p),
+                                   ctypes.byref(ms), _stream()), "spx_spmm_autotune")
+    return p, float(ms.value)
+
+
+def spx_sync_status(status_dev):
+    """Host copy of the status words; raises SpxError on the first one that is not SPX_OK."""
+    out = (ctypes.c_int32 * max(int(status_dev.numel()), 1))()
+    _check(lib().spx_sync_status(ptr(status_dev), int(status_dev.numel()), out, _stream()), "spx_sync_status")
+    return list(out)[: int(status_dev.numel())]
 
 
 def spx_spadd_symbolic(A: spx_csr, B: spx_csr, c_indptr, device) -> int:

@@ -179,3 +179,82 @@ def test_ic0_tridiagonal_one_iteration():
     b = synth.normal(A.m, seed=2)
     _, it, st, rr = solve.cg(batch, dev(b), pc="ic0", ic0=ic, tol=1e-6)
     assert host(st)[0] == 0 and host(it)[0] <= 2
+
+
+def test_cg_adjoint_entry_point_matches_autograd_and_oracle(small_batch):
+    """spx_cg_adjoint (one C call) gives the autograd Solve's gradients bit for bit, and the
+    oracle's within tolerance."""
+    from paper_2212_05159_gb300 import abi
+    A, ptr, batch = small_batch
+    b = synth.normal(A.m, seed=12)
+    g = synth.normal(A.m, seed=13)
+    x, _, st, _ = solve.cg(batch, dev(b), pc="jacobi", tol=1e-10)
+    x = x.clone()
+    lam = torch.empty(A.m, dtype=torch.float64, device="cuda")
+    gA = torch.empty(A.nnz, dtype=torch.float32, device="cuda")
+    iters = torch.empty(batch.nsys, dtype=torch.int32, device="cuda")
+    status = torch.empty_like(iters)
+    relres = torch.empty(batch.nsys, dtype=torch.float64, device="cuda")
+    abi.spx_cg_set_launch(*batch.launch_for(1))
+    abi.spx_cg_adjoint(batch.A.struct(), batch.sys_ptr, batch.nsys, batch.order, x, dev(g), lam, gA, 1,
+                       batch.dinv(), None, None, 1e-10, 20 * A.m, 0.1, iters, status, relres, batch.ws)
+    assert abi.spx_sync_status(status) == [0] * batch.nsys
+    vals = batch.A.values.clone().requires_grad_(True)
+    bt = dev(b).requires_grad_(True)
+    xx = solve.Solve.apply(vals, bt, batch, "jacobi", 1e-10)
+    xx.backward(dev(g.astype(np.float64)))
+    np.testing.assert_array_equal(host(gA), host(vals.grad))
+    np.testing.assert_array_equal(host(lam).astype(np.float32), host(bt.grad))
+    xh = host(x)
+    for s in range(batch.nsys):
+        As, a, c = _block(A, ptr, s)
+        lam_o, _ = oracle.solve_adjoint(As, xh[a:c], g[a:c])
+        np.testing.assert_allclose(host(lam)[a:c], lam_o, rtol=0, atol=1e-6 * np.abs(lam_o).max())
+
+
+def test_sync_status_reports_the_first_failure():
+    from paper_2212_05159_gb300.abi import SpxError, spx_sync_status
+    A, ptr = synth.block_diag([synth.poisson2d(8), synth.poisson2d(12)])
+    batch = solve.SystemBatch(spx.CSR.from_host(A), ptr)
+    b = synth.normal(A.m, seed=1)
+    _, _, st, _ = solve.cg(batch, dev(b), pc="jacobi", tol=1e-12, maxit=3)
+    with pytest.raises(SpxError, match="MAXITER"):
+        spx_sync_status(st)
+    _, _, st, _ = solve.cg(batch, dev(b), pc="jacobi")
+    assert spx_sync_status(st) == [0, 0]
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
+def test_precond_apply_matches_oracle(small_batch, kind):
+    """z = M r outside the solver for every preconditioner kind of the PCG."""
+    from paper_2212_05159_gb300 import abi
+    from paper_2212_05159_gb300.csr import CSR
+    A, ptr, batch = small_batch
+    r = synth.normal(A.m, seed=21)
+    z = torch.empty(A.m, device="cuda")
+    tmp = torch.empty(A.m, device="cuda")
+    diag = oracle.diagonal(A)
+    l_ip, l_ix, l_v = oracle.ic0(A)                       # a lower factor with the IC(0) pattern
+    Lh = synth.CSR(A.m, A.m, l_ip, l_ix, l_v.astype(np.float32))
+    dL = CSR.from_host(Lh)
+    t_ip, t_ix, perm = dL.transpose_pattern()
+    lt = dL.values[perm.long()].contiguous()
+    sL = dL.struct()
+    sLT = abi.csr_struct(A.m, A.m, t_ip, t_ix, lt)
+    if kind == 0:
+        abi.spx_precond_apply(0, dev(r), z)
+        ref = r.astype(np.float64)
+    elif kind == 1:
+        abi.spx_precond_apply(1, dev(r), z, dinv=dev((1.0 / diag).astype(np.float32)))
+        ref = r / diag.astype(np.float32).astype(np.float64)
+    elif kind == 2:
+        abi.spx_precond_apply(2, dev(r), z, L=sL, LT=sLT, tmp=tmp)
+        ref = oracle.spmm(Lh, oracle.spmm_t(Lh, r))
+    elif kind == 3:
+        abi.spx_precond_apply(3, dev(r), z, L=batch.A.struct())
+        ref = oracle.spmm(A, r)
+    else:
+        levels = abi.spx_ic0_analyse(sL, batch.sys_ptr, batch.nsys, "cuda")
+        abi.spx_precond_apply(4, dev(r), z, L=sL, LT=sLT, nsys=batch.nsys, levels=levels, tmp=tmp)
+        ref = oracle.trsv_lower_t(l_ip, l_ix, Lh.values, oracle.trsv_lower(l_ip, l_ix, Lh.values, r))
+    np.testing.assert_allclose(host(z), ref, rtol=2e-5, atol=2e-5 * np.abs(ref).max())

@@ -315,3 +315,19 @@ def test_column_parts_products_match_oracle(mat, n_parts, cb, rpg):
     abi.spx_check_device()
     assert_close_normalised(host(out), oracle.sddmm(A, G, X), oracle.sddmm(A, np.abs(G), np.abs(X)),
                             what=f"sddmm parts={n_parts} {name} cb={cb}")
+
+
+def test_spmm_autotune_entry_point(mat):
+    """spx_spmm_autotune picks launch parameters by timing; the chosen plan computes A X."""
+    from paper_2212_05159_gb300 import abi
+    name, A, dA = mat
+    k = 32
+    X = synth.normal((A.n, k), seed=80)
+    Y = torch.empty(A.m, k, device="cuda")
+    plan, ms = abi.spx_spmm_autotune(dA.struct(), dev(X), Y, dA.plan())
+    assert ms > 0 and plan.rows_per_group in (1, 2, 4, 8) and plan.engine in (0, 1)
+    Y.zero_()
+    abi.spx_spmm(dA.struct(), dev(X), Y, 1.0, 0.0, plan, None)
+    abi.spx_check_device()
+    assert_close_normalised(host(Y), oracle.spmm(A, X), oracle.spmm(abs_csr(A), np.abs(X)),
+                            what=f"spmm {name} autotuned rpg={plan.rows_per_group} engine={plan.engine}")
