@@ -505,10 +505,36 @@ spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K1, const fl
                                 int32_t K2, const void* W_bf16, const float* bias, int32_t N,
                                 int32_t mode, const float* Hin, float* Y, float* U, void* stream);
 
+/* spx_dense_backward_data on the tensor cores (tcgen05, accumulator in tensor memory): G is
+ * rounded to BF16 while staged, so the result equals spx_dense_backward_data applied to a
+ * BF16-rounded G up to the order of the FP32 accumulation.  N, K1, K2 multiples of 4,
+ * N <= 128, K1 + K2 <= 128; G, dX1, dX2 16-byte aligned.  Asynchronous. */
+spx_status spx_dense_backward_data_tc(int64_t n, const float* G, int32_t N, const void* W_bf16,
+                                      int32_t K1, int32_t K2, float* dX1, float* dX2,
+                                      int32_t accumulate, void* stream);
+
 /* Data gradient [dX1 dX2] = G W^T (or += with accumulate != 0); dX2 may be NULL. */
 spx_status spx_dense_backward_data(int64_t n, const float* G, int32_t N, const void* W_bf16,
                                    int32_t K1, int32_t K2, float* dX1, float* dX2,
                                    int32_t accumulate, void* stream);
+
+/* Workspace bytes of spx_dense_backward_weight_tc: one (K + 1) x N float32 partial per CTA
+ * (at most one CTA per SM of the current device).  K = K1 + K2 <= 128, K % 4 == 0;
+ * N in {16, 32, 64, 128}. */
+spx_status spx_dense_backward_weight_tc_workspace_size(int64_t n, int32_t K, int32_t N,
+                                                       size_t* bytes);
+
+/* spx_dense_backward_weight on the tensor cores (tcgen05): dW = [X1 X2]^T G with X and G
+ * rounded to BF16 while staged and the products summed in FP32 in tensor memory; db = the
+ * column sums of G in FP32 (or NULL).  Overwrites dW (K x N row-major) and db.  K1 >= 4,
+ * K1, K2 multiples of 4, K1 + K2 <= 128, N in {16, 32, 64, 128}; X1, X2, G, workspace
+ * 16-byte aligned.  Deterministic: per-CTA partials (fixed row tiles per CTA) added in CTA
+ * order.  A tensor-core completion wait that exceeds 2 s records a device error
+ * (spx_check_device).  Asynchronous. */
+spx_status spx_dense_backward_weight_tc(int64_t n, const float* X1, int32_t K1, const float* X2,
+                                        int32_t K2, const float* G, int32_t N, float* dW,
+                                        float* db, void* workspace, size_t workspace_bytes,
+                                        void* stream);
 
 /* Workspace bytes of spx_dense_backward_weight ((K + 1) * N <= 8448). */
 spx_status spx_dense_backward_weight_workspace_size(int64_t n, int32_t K, int32_t N,

@@ -118,6 +118,9 @@ SIGNATURES = {
     "spx_adam_step": [_I64, _P, _P, _P, _P, _I32, _F, _F, _F, _F, _P, _P],
     "spx_to_bf16": [_I64, _P, _P, _P],
     "spx_spai_residual": [_CSRP, _F, _P, _P, _P],
+    "spx_dense_backward_data_tc": [_I64, _P, _I32, _P, _I32, _I32, _P, _P, _I32, _P],
+    "spx_dense_backward_weight_tc_workspace_size": [_I64, _I32, _I32, ctypes.POINTER(_SZ)],
+    "spx_dense_backward_weight_tc": [_I64, _P, _I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P],
     "spx_precond_apply": [_I32, _I64, _P, _P, _P, _CSRP, _CSRP, _I32, _P, _P, _P],
     "spx_cg_adjoint": [_CSRP, _P, _I32, _P, _P, _P, _P, _P, _I32, _P, _CSRP, _CSRP, _P, _D, _I32, _D, _P, _P, _P,
                        _P, _SZ, _P],
@@ -451,6 +454,17 @@ def spx_dense_forward_tc(n, X1, K1, X2, K2, W16, bias, N, mode, Hin, Y, U=None):
 def spx_dense_backward_data(n, G, N, W16, K1, K2, dX1, dX2, accumulate):
     _check(lib().spx_dense_backward_data(int(n), ptr(G), int(N), ptr(W16), int(K1), int(K2), ptr(dX1), ptr(dX2),
                                          int(accumulate), _stream()), "spx_dense_backward_data")
+
+
+def spx_dense_backward_data_tc(n, G, N, W16, K1, K2, dX1, dX2, accumulate):
+    _check(lib().spx_dense_backward_data_tc(int(n), ptr(G), int(N), ptr(W16), int(K1), int(K2), ptr(dX1),
+                                            ptr(dX2), int(accumulate), _stream()), "spx_dense_backward_data_tc")
+
+
+def spx_dense_backward_weight_tc(n, X1, K1, X2, K2, G, N, dW, db, ws):
+    _check(lib().spx_dense_backward_weight_tc(int(n), ptr(X1), int(K1), ptr(X2), int(K2), ptr(G), int(N), ptr(dW),
+                                              ptr(db), ptr(ws), ws.numel(), _stream()),
+           "spx_dense_backward_weight_tc")
 
 
 def spx_dense_backward_weight(n, X1, K1, X2, K2, G, N, dW, db, ws):

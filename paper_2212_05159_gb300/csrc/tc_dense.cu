@@ -217,6 +217,361 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Data gradient of the layer on the tensor cores: [dX1 dX2] (+)= G W^T with G: n x N (FP32,
+// rounded to BF16 while staged) and W: (K1 + K2) x N (BF16).  The same tile scheme as the
+// forward kernel with the roles swapped: A = G's 128-row tile (K-major over N), B = W's rows
+// (one per output column, K-major over N), M = 128, the MMA's N = K1 + K2 rounded up to 16;
+// the epilogue writes (or adds into) dX1's and dX2's columns with coalesced float4 accesses.
+__global__ void __launch_bounds__(TC_THREADS) dense_tc_bwd_data_kernel(int64_t n, const float* __restrict__ G, int N,
+                                                                       const __nv_bfloat16* __restrict__ W, int K1,
+                                                                       int K2, float* __restrict__ dX1,
+                                                                       float* __restrict__ dX2, int accumulate,
+                                                                       int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int K = K1 + K2;                                      // output columns
+    const int kout = (K + 15) & ~15;                            // the MMA's N
+    const int npad = (N + 15) & ~15;                            // reduction extent
+    unsigned char* sA = smem;                                   // 128 x npad bf16 (rows of G)
+    unsigned char* sB = smem + TC_M * npad * 2;                 // kout x npad bf16 (rows of W)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
+    const int ncols = kout <= 32 ? 32 : (kout <= 64 ? 64 : 128);
+
+    stage_rows(sA, G, N, 0, npad, row0, n);
+    if (npad > N) {
+        const int pq = (npad - N) >> 2;
+        for (int t = threadIdx.x; t < TC_M * pq; t += TC_THREADS) {
+            const int r = t / pq, kq = t - r * pq;
+            *reinterpret_cast<uint2*>(sA + core_off(r, N + kq * 4, npad)) = make_uint2(0u, 0u);
+        }
+    }
+    // B row kk = W's row kk (consecutive threads read consecutive entries of a row)
+    for (int t = threadIdx.x; t < kout * npad; t += TC_THREADS) {
+        const int kk = t / npad, c = t - kk * npad;
+        const __nv_bfloat16 w = (kk < K && c < N) ? W[kk * N + c] : __float2bfloat16(0.f);
+        *reinterpret_cast<__nv_bfloat16*>(sB + core_off(kk, c, npad)) = w;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&mbar), 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = instr_desc(TC_M, kout);
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        const uint32_t sbo = (uint32_t)(npad >> 3) * 128u;
+        for (int s = 0; s < npad / 16; ++s) {
+            const uint64_t ad = smem_desc(a0 + s * 256u, 128u, sbo);
+            const uint64_t bd = smem_desc(b0 + s * 256u, 128u, sbo);
+            const uint32_t acc = s > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&mbar))
+                     : "memory");
+    }
+    const bool ok = __all_sync(FULL, mbar_wait(smem_u32(&mbar), 0, 2000000000ull));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+        if (threadIdx.x == 0 && err) atomicOr(err, 2);
+    } else {
+        const int ldst = kout + 4;
+        float* stage = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * ldst;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < kout; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+                *reinterpret_cast<float4*>(stage + lane * ldst + c0 + q) =
+                    make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]), __uint_as_float(v[q + 2]),
+                                __uint_as_float(v[q + 3]));
+        }
+        __syncwarp();
+        const int k4 = K >> 2;                                   // K1, K2 multiples of 4
+#pragma unroll 4
+        for (int t = lane; t < 32 * k4; t += 32) {
+            const int r = t / k4, cq = t - r * k4;
+            const int64_t row = row0 + warp * 32 + r;
+            if (row >= n) break;
+            const int c = cq * 4;
+            float* dst;
+            if (c < K1) dst = dX1 + row * K1 + c;
+            else if (dX2) dst = dX2 + row * K2 + (c - K1);
+            else continue;
+            float4 val = *reinterpret_cast<const float4*>(stage + r * ldst + c);
+            if (accumulate) {
+                const float4 o = *reinterpret_cast<const float4*>(dst);
+                val = make_float4(o.x + val.x, o.y + val.y, o.z + val.z, o.w + val.w);
+            }
+            *reinterpret_cast<float4*>(dst) = val;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Weight gradient of the layer on the tensor cores: dW = [X1 X2]^T G (K x N) and db = the
+// column sums of G.  The reduction runs over the rows, so the operands are the transposes
+// of the row tiles: A (M = 128 rows of dW, the K inputs zero-padded to 128) holds X^T and
+// B (the MMA's N = N) holds G^T, both K-major over 128 rows of the tile.  Each thread
+// loads two rows of a 4-column piece (two float4, consecutive threads on consecutive
+// pieces) and stores four BF16 pairs (row r, r + 1) of the transposed operand.
+//
+// One persistent CTA per SM walks the row tiles with a stride of the grid, two staging
+// buffers in turn: while the tensor cores run tile t's 8 MMAs (K = 16 rows each, the FP32
+// accumulator stays in tensor memory across all of the CTA's tiles), the threads stage
+// tile t + 1.  A buffer is restaged only after the mbarrier of the commit that read it has
+// completed (bounded wait).  db is summed in FP32 by the threads from the values they
+// load (each thread owns one 4-column piece of G).  Each CTA writes its partial (K + 1) x N
+// block (dW rows, then db) to the workspace; a second kernel adds the partials in block
+// order, so the result does not depend on timing.
+constexpr int TW_THREADS = 256;
+constexpr int TW_BATCH = 8;                                    // row-pair items in flight per thread
+constexpr int TW_A = TC_M * TC_M * 2;                           // A buffer: 128 x 128 BF16
+__host__ __device__ constexpr int tw_buf_bytes(int N) { return TW_A + N * TC_M * 2; }
+
+// Stages rows [row0, row0 + 128) of the sources into the transposed operand: column c of
+// source s becomes operand row mbase_s + c.  nq1, nq2: 4-column pieces of the sources.
+// When sum != nullptr (only for a single source whose pieces divide TW_THREADS) the thread
+// adds the values of its piece into sum.
+__device__ __forceinline__ void stage_transposed(unsigned char* buf, const float* __restrict__ S1, int nq1,
+                                                 const float* __restrict__ S2, int nq2, int64_t row0, int64_t n,
+                                                 float4* sum) {
+    const int nq = nq1 + nq2;
+    const int total = (TC_M / 2) * nq;                          // (row pair, piece) items
+    for (int t0 = threadIdx.x; t0 < total; t0 += TW_BATCH * TW_THREADS) {
+        float4 lo[TW_BATCH], hi[TW_BATCH];
+#pragma unroll
+        for (int u = 0; u < TW_BATCH; ++u) {
+            const int t = t0 + u * TW_THREADS;
+            lo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            hi[u] = lo[u];
+            if (t < total) {
+                const int p = t / nq, q = t - p * nq;
+                const int64_t r = row0 + 2 * p;
+                const float* src = q < nq1 ? S1 + r * (4 * nq1) + 4 * q : S2 + r * (4 * nq2) + 4 * (q - nq1);
+                const int64_t step = q < nq1 ? 4 * nq1 : 4 * nq2;
+                if (r < n) lo[u] = __ldcs(reinterpret_cast<const float4*>(src));
+                if (r + 1 < n) hi[u] = __ldcs(reinterpret_cast<const float4*>(src + step));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < TW_BATCH; ++u) {
+            const int t = t0 + u * TW_THREADS;
+            if (t < total) {
+                const int p = t / nq, q = t - p * nq;
+                const int m = 4 * q;                            // operand row of the piece's first column
+                const int kr = 2 * p;
+                *reinterpret_cast<uint32_t*>(buf + core_off(m + 0, kr, TC_M)) = pack_bf16x2(lo[u].x, hi[u].x);
+                *reinterpret_cast<uint32_t*>(buf + core_off(m + 1, kr, TC_M)) = pack_bf16x2(lo[u].y, hi[u].y);
+                *reinterpret_cast<uint32_t*>(buf + core_off(m + 2, kr, TC_M)) = pack_bf16x2(lo[u].z, hi[u].z);
+                *reinterpret_cast<uint32_t*>(buf + core_off(m + 3, kr, TC_M)) = pack_bf16x2(lo[u].w, hi[u].w);
+                if (sum) {
+                    sum->x += lo[u].x + hi[u].x;
+                    sum->y += lo[u].y + hi[u].y;
+                    sum->z += lo[u].z + hi[u].z;
+                    sum->w += lo[u].w + hi[u].w;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TW_THREADS, 1) dense_tc_bwd_weight_kernel(int64_t n, const float* __restrict__ X1,
+                                                                            int K1, const float* __restrict__ X2,
+                                                                            int K2, const float* __restrict__ G, int N,
+                                                                            float* __restrict__ part,
+                                                                            int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int K = K1 + K2;
+    const int bufb = tw_buf_bytes(N);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+    const int64_t tiles = (n + TC_M - 1) / TC_M;
+
+    // operand rows K..127 of A stay zero in both buffers (the staging never writes them)
+    if (K < TC_M) {
+        const int zq = (TC_M - K) * (TC_M / 8);                 // 16-byte pieces: (rows) x (128 / 8)
+        for (int t = threadIdx.x; t < 2 * zq; t += TW_THREADS) {
+            const int b = t / zq, z = t - b * zq;
+            const int m = K + z / (TC_M / 8), k8 = (z % (TC_M / 8)) * 8;
+            *reinterpret_cast<uint4*>(smem + b * bufb + core_off(m, k8, TC_M)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = instr_desc(TC_M, N);
+    const uint32_t sbo = (uint32_t)(TC_M >> 3) * 128u;
+
+    float4 dbs = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool failed = false;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+        const int b = it & 1;
+        unsigned char* sA = smem + b * bufb;
+        unsigned char* sB = sA + TW_A;
+        if (it >= 2) {                                          // the MMAs of tile it - 2 read this buffer
+            const bool ok = mbar_wait(smem_u32(&mbar[b]), (uint32_t)(((it - 2) >> 1) & 1), 2000000000ull);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        const int64_t row0 = tile * TC_M;
+        stage_transposed(sA, X1, K1 >> 2, X2, K2 >> 2, row0, n, nullptr);
+        stage_transposed(sB, G, N >> 2, nullptr, 0, row0, n, &dbs);
+        fence_proxy_async();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0) {
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (int s = 0; s < TC_M / 16; ++s) {
+                const uint64_t ad = smem_desc(a0 + s * 256u, 128u, sbo);
+                const uint64_t bd = smem_desc(b0 + s * 256u, 128u, sbo);
+                const uint32_t acc = (it > 0 || s > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar[b]))
+                         : "memory");
+        }
+    }
+    // the last commit covers every MMA this CTA issued
+    if (!failed && it > 0) {
+        const int last = it - 1;
+        const bool ok = mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), 2000000000ull);
+        failed = __syncthreads_or(!ok);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float* pblk = part + (size_t)blockIdx.x * (size_t)(K + 1) * N;
+    if (failed) {
+        if (threadIdx.x == 0 && err) atomicOr(err, 2);
+    } else {
+        // dW rows: warp w (< 4) reads accumulator lanes 32 w .. 32 w + 31 (operand rows = inputs)
+        if (warp < 4) {
+            const int m = warp * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t v[16];
+                if (it > 0) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(taddr + (uint32_t)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = 0u;
+                }
+                if (m < K) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4*>(pblk + (size_t)m * N + c0 + q) =
+                            make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]), __uint_as_float(v[q + 2]),
+                                        __uint_as_float(v[q + 3]));
+                }
+            }
+        }
+        // db row: the threads owning piece q (threadIdx.x = q mod N/4) added in thread order
+        float4* red = reinterpret_cast<float4*>(smem);
+        red[threadIdx.x] = dbs;
+        __syncthreads();
+        const int nq = N >> 2;
+        if (threadIdx.x < N) {
+            const int q = threadIdx.x >> 2, comp = threadIdx.x & 3;
+            float s = 0.f;
+            for (int t = q; t < TW_THREADS; t += nq) {
+                const float4 v = red[t];
+                s += comp == 0 ? v.x : (comp == 1 ? v.y : (comp == 2 ? v.z : v.w));
+            }
+            pblk[(size_t)K * N + threadIdx.x] = s;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// dW and db from the per-CTA partials: 32 outputs per block, 8 interleaved slices of the
+// partials summed by 8 threads each, then the 8 slice sums added in slice order.
+constexpr int TWR_SLICES = 8;
+__global__ void __launch_bounds__(256) tc_wgrad_reduce_kernel(int nparts, int K, int N, const float* __restrict__ part,
+                                                             float* __restrict__ dW, float* __restrict__ db) {
+    __shared__ float s[TWR_SLICES][32];
+    const int outs = (K + 1) * N;
+    const int o = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int slice = threadIdx.x >> 5;
+    float acc = 0.f;
+    if (o < outs)
+        for (int b = slice; b < nparts; b += TWR_SLICES) acc += part[(size_t)b * outs + o];
+    s[slice][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32 && o < outs) {
+        float t = 0.f;
+#pragma unroll
+        for (int j = 0; j < TWR_SLICES; ++j) t += s[j][threadIdx.x];
+        if (o < K * N) dW[o] = t;
+        else if (db) db[o - K * N] = t;
+    }
+}
+
 // Shared memory one launch needs: the A and B^T tiles for its K, or the epilogue rows for its
 // N, whichever is larger (smaller layers fit more blocks per SM).
 size_t tc_smem_bytes(int K, int N) {
@@ -254,5 +609,72 @@ extern "C" spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K
                                                               static_cast<const __nv_bfloat16*>(W_bf16), bias, N, mode,
                                                               Hin, Y, U, device_error_word());
     SPX_CHECK_LAUNCH("spx_dense_forward_tc");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_dense_backward_data_tc(int64_t n, const float* G, int32_t N, const void* W_bf16,
+                                                 int32_t K1, int32_t K2, float* dX1, float* dX2, int32_t accumulate,
+                                                 void* stream) {
+    if (n < 0 || N < 4 || N > TC_KMAX || N % 4 != 0 || K1 < 4 || K2 < 0 || K1 % 4 != 0 || K2 % 4 != 0 ||
+        K1 + K2 > TC_NMAX)
+        return set_error(SPX_INVALID_ARG,
+                         "spx_dense_backward_data_tc: sizes (N <= 128, K1 + K2 <= 128, all multiples of 4)");
+    if (n > 0 && (!G || !W_bf16 || !dX1)) return set_error(SPX_INVALID_ARG, "spx_dense_backward_data_tc: NULL operand");
+    if (n > 0 && (!al16(G) || !al16(dX1) || (dX2 && !al16(dX2))))
+        return set_error(SPX_INVALID_ARG, "spx_dense_backward_data_tc: 16-byte aligned rows needed");
+    if (n == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    const int kout = ((K1 + K2) + 15) & ~15;
+    const size_t smem = tc_smem_bytes(N, kout);                 // tiles over N, epilogue over the outputs
+    static std::atomic<unsigned long long> attr_done{0};
+    SPX_TRY(ensure_smem_attr(dense_tc_bwd_data_kernel, TC_SMEM, attr_done, "spx_dense_backward_data_tc attribute"));
+    const int64_t tiles = (n + TC_M - 1) / TC_M;
+    dense_tc_bwd_data_kernel<<<(unsigned)tiles, TC_THREADS, smem, st>>>(
+        n, G, N, static_cast<const __nv_bfloat16*>(W_bf16), K1, K2, dX1, dX2, accumulate, device_error_word());
+    SPX_CHECK_LAUNCH("spx_dense_backward_data_tc");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_dense_backward_weight_tc_workspace_size(int64_t n, int32_t K, int32_t N, size_t* bytes) {
+    if (!bytes || n < 0 || K < 4 || K > TC_M || K % 4 != 0 || (N != 16 && N != 32 && N != 64 && N != 128))
+        return set_error(SPX_INVALID_ARG,
+                         "spx_dense_backward_weight_tc_workspace_size: sizes (K <= 128, K %% 4 == 0, N in 16/32/64/128)");
+    const int64_t tiles = (n + TC_M - 1) / TC_M;
+    const int64_t parts = tiles < num_sms() ? tiles : num_sms();
+    *bytes = (size_t)(parts > 0 ? parts : 1) * (size_t)(K + 1) * N * 4 + 256;
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_dense_backward_weight_tc(int64_t n, const float* X1, int32_t K1, const float* X2, int32_t K2,
+                                                   const float* G, int32_t N, float* dW, float* db, void* ws,
+                                                   size_t ws_bytes, void* stream) {
+    if (K1 < 4 || K1 % 4 != 0 || K2 < 0 || K2 % 4 != 0)
+        return set_error(SPX_INVALID_ARG, "spx_dense_backward_weight_tc: K1, K2 multiples of 4, K1 >= 4");
+    const int32_t K = K1 + K2;
+    size_t need = 0;
+    SPX_TRY(spx_dense_backward_weight_tc_workspace_size(n, K, N, &need));
+    if (!ws || ws_bytes < need) return set_error(SPX_OOM_WORKSPACE, "spx_dense_backward_weight_tc: workspace too small");
+    if (!dW || (n > 0 && (!X1 || (K2 > 0 && !X2) || !G)))
+        return set_error(SPX_INVALID_ARG, "spx_dense_backward_weight_tc: NULL operand");
+    if (n > 0 && (!al16(X1) || (K2 > 0 && !al16(X2)) || !al16(G) || !al16(ws)))
+        return set_error(SPX_INVALID_ARG, "spx_dense_backward_weight_tc: 16-byte aligned rows needed");
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) {
+        SPX_CUDA(cudaMemsetAsync(dW, 0, sizeof(float) * (size_t)K * N, st), "spx_dense_backward_weight_tc memset");
+        if (db) SPX_CUDA(cudaMemsetAsync(db, 0, sizeof(float) * (size_t)N, st), "spx_dense_backward_weight_tc memset");
+        return SPX_OK;
+    }
+    const int64_t tiles = (n + TC_M - 1) / TC_M;
+    const int parts = (int)(tiles < num_sms() ? tiles : num_sms());
+    static std::atomic<unsigned long long> attr_done{0};
+    SPX_TRY(ensure_smem_attr(dense_tc_bwd_weight_kernel, 2 * tw_buf_bytes(TC_NMAX), attr_done,
+                             "spx_dense_backward_weight_tc attribute"));
+    float* partial = static_cast<float*>(ws);
+    dense_tc_bwd_weight_kernel<<<(unsigned)parts, TW_THREADS, 2 * tw_buf_bytes(N), st>>>(n, X1, K1, X2, K2, G, N,
+                                                                                       partial, device_error_word());
+    SPX_CHECK_LAUNCH("spx_dense_backward_weight_tc");
+    const int outs = (K + 1) * N;
+    tc_wgrad_reduce_kernel<<<(unsigned)((outs + 31) / 32), 256, 0, st>>>(parts, K, N, partial, dW, db);
+    SPX_CHECK_LAUNCH("spx_dense_backward_weight_tc reduce");
     return SPX_OK;
 }

@@ -144,7 +144,7 @@ class MPNN:
         """L values on G.Lpat; returns (L, saved activations).
 
         tensor_cores: run the dense layers on tcgen05 (activations rounded to BF16); the
-        default FP32-activation path is the one the training gradients follow."""
+        default keeps FP32 activations (CUDA-core kernels)."""
         n, dev = G.n, self.device
         emp = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
         dense = abi.spx_dense_forward_tc if tensor_cores else abi.spx_dense_forward
@@ -173,9 +173,14 @@ class MPNN:
         return L, {"hs": hs, "gs": gs, "us": us, "P": P, "Q": Q}
 
     # ------------------------------------------------------------------ reverse
-    def backward(self, G: Graph, saved, gL: torch.Tensor):
-        """Accumulates d loss / d params into self.grad (overwritten) from gL on G.Lpat."""
+    def backward(self, G: Graph, saved, gL: torch.Tensor, tensor_cores: bool = False):
+        """Accumulates d loss / d params into self.grad (overwritten) from gL on G.Lpat.
+
+        tensor_cores: the data gradients G W^T and the weight gradients X^T G of the dense
+        layers run on tcgen05 (operands rounded to BF16, FP32 accumulation; bias gradients
+        summed in FP32)."""
         n, dev = G.n, self.device
+        bdata = abi.spx_dense_backward_data_tc if tensor_cores else abi.spx_dense_backward_data
         emp = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
         hs, gs, us, P, Q = saved["hs"], saved["gs"], saved["us"], saved["P"], saved["Q"]
         gP, gQ = emp(n, H), emp(n, H)
@@ -190,16 +195,17 @@ class MPNN:
         self.g("bo").copy_(gpar[3 * H + 1:3 * H + 2])
 
         def wgrad(X1, K1, X2, K2, Gm, N, dW, db):
-            ws = abi.workspace(abi._size("spx_dense_backward_weight_workspace_size", int(n), int(K1 + K2),
+            sfx = "_tc" if tensor_cores else ""
+            ws = abi.workspace(abi._size(f"spx_dense_backward_weight{sfx}_workspace_size", int(n), int(K1 + K2),
                                          int(N)), dev)
-            abi.spx_dense_backward_weight(n, X1, K1, X2, K2, Gm, N, dW, db, ws)
+            getattr(abi, f"spx_dense_backward_weight{sfx}")(n, X1, K1, X2, K2, Gm, N, dW, db, ws)
 
         hL = hs[-1]
         wgrad(hL, H, None, 0, gP, H, self.g("Ua"), None)
         wgrad(hL, H, None, 0, gQ, H, self.g("Ub"), None)
         gh = emp(n, H)
-        abi.spx_dense_backward_data(n, gP, H, self.p16("Ua"), H, 0, gh, None, 0)
-        abi.spx_dense_backward_data(n, gQ, H, self.p16("Ub"), H, 0, gh, None, 1)
+        bdata(n, gP, H, self.p16("Ua"), H, 0, gh, None, 0)
+        bdata(n, gQ, H, self.p16("Ub"), H, 0, gh, None, 1)
         Es = G.E.struct()
         plan = G.E.plan()
         for layer in range(LAYERS, 0, -1):
@@ -209,7 +215,7 @@ class MPNN:
             wgrad(h_in, H, g, H, gu, H, self.g(f"W{layer}"), self.g(f"b{layer}"))
             gg = torch.zeros(n, H, dtype=torch.float32, device=dev)
             # h_out = h_in + relu(u): gh_in = gh_out + (gu W^T)[:, :H]; gg = (gu W^T)[:, H:]
-            abi.spx_dense_backward_data(n, gu, H, self.p16(f"W{layer}"), H, H, gh, gg, 1)
+            bdata(n, gu, H, self.p16(f"W{layer}"), H, H, gh, gg, 1)
             # g = E h_in  ->  gh_in += E^T gg  (E is symmetric for symmetric A)
             abi.spx_spmm(Es, gg, gh, 1.0, 1.0, plan)
         gu0 = emp(n, H)
@@ -226,14 +232,15 @@ class MPNN:
 class Trainer:
     """Unrolled-PCG training of the network on block-diagonal batches of systems."""
 
-    def __init__(self, net: MPNN, n_it: int = 4, gamma: float = 0.6, lr: float = 1e-3):
+    def __init__(self, net: MPNN, n_it: int = 4, gamma: float = 0.6, lr: float = 1e-3, tensor_cores: bool = False):
         self.net, self.n_it, self.gamma, self.lr = net, n_it, gamma, lr
+        self.tensor_cores = tensor_cores
         self.wts = torch.from_numpy(loss_weights(n_it, gamma)).to(net.device)
 
     def loss_and_grad(self, A: CSR, sys_ptr: torch.Tensor, nsys: int, b: torch.Tensor, G: Graph | None = None):
         """Mean loss over the systems and the L gradient (the network is not updated)."""
         G = G or Graph(A)
-        L, saved = self.net.forward(G)
+        L, saved = self.net.forward(G, tensor_cores=self.tensor_cores)
         lt_vals = torch.empty_like(L)
         LT = G.LT_struct(L, lt_vals)
         Ls = abi.csr_struct(G.n, G.n, G.Lpat.indptr, G.Lpat.indices, L)
@@ -245,7 +252,7 @@ class Trainer:
 
     def step(self, A: CSR, sys_ptr: torch.Tensor, nsys: int, b: torch.Tensor):
         loss, gL, L, G, saved = self.loss_and_grad(A, sys_ptr, nsys, b)
-        self.net.backward(G, saved, gL)
+        self.net.backward(G, saved, gL, tensor_cores=self.tensor_cores)
         self.net.adam(self.lr)
         return loss
 

@@ -56,3 +56,114 @@ def test_tc_network_forward_close_to_fp32_path():
     a, t = L32.cpu().numpy(), Ltc.cpu().numpy()
     # BF16 activations: agreement to a few BF16 ulps of the output scale
     assert np.abs(a - t).max() <= 3e-2 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("n", [1, 127, 300, 4096])
+@pytest.mark.parametrize("N,K1,K2,acc", [(64, 64, 64, 1), (64, 64, 0, 0), (64, 64, 0, 1), (32, 16, 16, 0),
+                                         (128, 64, 0, 0), (64, 4, 0, 0)])
+def test_tc_backward_data_matches_fp32_kernel(n, N, K1, K2, acc):
+    """[dX1 dX2] (+)= G W^T on the tensor cores against the FP32 kernel on a BF16-rounded G."""
+    g = torch.Generator().manual_seed(n * 7 + N + K1 + K2 + acc)
+    G = torch.randn(n, N, generator=g).cuda()
+    W = (torch.randn(K1 + K2, N, generator=g) * 0.2).to(torch.bfloat16).cuda()
+    d1 = torch.randn(n, K1, generator=g).cuda()
+    d2 = torch.randn(n, K2, generator=g).cuda() if K2 else None
+    r1, r2 = d1.clone(), (d2.clone() if K2 else None)
+    abi.spx_dense_backward_data_tc(n, G, N, W, K1, K2, d1, d2, acc)
+    abi.spx_check_device()
+    abi.spx_dense_backward_data(n, _bf16(G), N, W, K1, K2, r1, r2, acc)
+    torch.cuda.synchronize()
+    norm = (_bf16(G).abs().double() @ W.float().abs().double().t()).cpu().numpy()
+    got = torch.cat([d1, d2], 1) if K2 else d1
+    ref = torch.cat([r1, r2], 1) if K2 else r1
+    if acc:
+        norm = norm + ref.abs().double().cpu().numpy()
+    assert_close_normalised(got.cpu().numpy(), ref.cpu().numpy(), norm, what=f"tc dX n={n} N={N} K={K1}+{K2}")
+
+
+def test_tc_network_backward_close_to_fp32_path():
+    """Reverse pass of the network with the data gradients G W^T on the tensor cores (incoming
+    gradients rounded to BF16) against the FP32 path, on the same saved activations; then
+    forward and reverse both on the tensor cores.  Relative Frobenius error per parameter."""
+    import synth
+    from paper_2212_05159_gb300 import learned
+    A, ptr, _, _ = synth.diffusion_batch(4, seed=4, side_lo=20, side_hi=40, sigma=1.0)
+    rng = np.random.default_rng(1)
+    net = learned.MPNN(seed=0)
+    p = net.get_params()
+    for k in p:
+        p[k] = (p[k] + rng.normal(0, 0.1, p[k].shape)).astype(np.float32)
+    net.set_params(p)
+    G = learned.Graph(spx.CSR.from_host(A))
+    L32, s32 = net.forward(G)
+    gL = torch.from_numpy(rng.normal(0, 1, L32.numel()).astype(np.float32)).cuda()
+    g32 = net.backward(G, s32, gL).clone()
+    gbw = net.backward(G, s32, gL, tensor_cores=True).clone()
+    _, stc = net.forward(G, tensor_cores=True)
+    gtc = net.backward(G, stc, gL, tensor_cores=True).clone()
+    worst = {}
+    for name, _, _ in learned.PARAMS:
+        a = net.view(g32, name).double()
+        nrm = max(float(a.norm()), 1e-12)
+        rb = float((net.view(gbw, name).double() - a).norm()) / nrm
+        rt = float((net.view(gtc, name).double() - a).norm()) / nrm
+        worst[name] = (round(rb, 5), round(rt, 5))
+    print("relative errors (backward on tc, all on tc):", worst)
+    for name, (rb, rt) in worst.items():
+        assert rb <= 1e-2, name      # BF16 rounding of the incoming gradient (2^-9 relative)
+        assert rt <= 5e-2, name      # plus BF16 activations through every layer
+
+
+@pytest.mark.parametrize("n", [1, 127, 300, 4096, 100003])
+@pytest.mark.parametrize("K1,K2,N,with_db", [(64, 64, 64, True), (64, 0, 64, False), (4, 0, 64, True),
+                                             (16, 16, 32, True), (60, 0, 16, True), (64, 64, 128, False)])
+def test_tc_backward_weight_matches_fp64_product(n, K1, K2, N, with_db):
+    """dW = [X1 X2]^T G on the tensor cores against an FP64 product of the BF16-rounded X and G
+    (the BF16 products are exact in FP32; only the rounding of the sums differs); db against
+    the FP64 column sums of the unrounded G.  n = 100003 gives every CTA several row tiles,
+    so both staging buffers are reused."""
+    g = torch.Generator().manual_seed(n + 3 * K1 + 5 * K2 + N)
+    X1 = torch.randn(n, K1, generator=g).cuda()
+    X2 = torch.randn(n, K2, generator=g).cuda() if K2 else None
+    G = torch.randn(n, N, generator=g).cuda()
+    K = K1 + K2
+    dW = torch.full((K, N), float("nan"), device="cuda")
+    db = torch.full((N,), float("nan"), device="cuda") if with_db else None
+    ws = abi.workspace(abi._size("spx_dense_backward_weight_tc_workspace_size", n, K, N), "cuda")
+    abi.spx_dense_backward_weight_tc(n, X1, K1, X2, K2, G, N, dW, db, ws)
+    abi.spx_check_device()
+    X1r, Gr = _bf16(X1).cpu().double(), _bf16(G).cpu().double()
+    Xr = torch.cat([X1r, _bf16(X2).cpu().double()], 1) if K2 else X1r
+    dWr = (Xr.t() @ Gr).numpy()
+    norm = (Xr.abs().t() @ Gr.abs()).numpy()
+    assert_close_normalised(dW.cpu().numpy(), dWr, norm, what=f"tc dW n={n} K={K1}+{K2} N={N}")
+    if with_db:
+        Gd = G.double()
+        assert_close_normalised(db.cpu().numpy(), Gd.sum(0).cpu().numpy(), Gd.abs().sum(0).cpu().numpy(),
+                                what="tc db")
+
+
+def test_tc_backward_weight_is_deterministic():
+    g = torch.Generator().manual_seed(9)
+    n, K, N = 50000, 128, 64
+    X = torch.randn(n, K, generator=g).cuda()
+    G = torch.randn(n, N, generator=g).cuda()
+    ws = abi.workspace(abi._size("spx_dense_backward_weight_tc_workspace_size", n, K, N), "cuda")
+    outs = []
+    for _ in range(3):
+        dW, db = torch.empty(K, N, device="cuda"), torch.empty(N, device="cuda")
+        abi.spx_dense_backward_weight_tc(n, X, K, None, 0, G, N, dW, db, ws)
+        outs.append((dW.cpu(), db.cpu()))
+    for dW, db in outs[1:]:
+        assert torch.equal(dW, outs[0][0]) and torch.equal(db, outs[0][1])
+
+
+def test_tc_backward_weight_rejects_bad_sizes():
+    ws = abi.workspace(1 << 20, "cuda")
+    X = torch.zeros(8, 8, device="cuda")
+    Gm = torch.zeros(8, 48, device="cuda")
+    dW = torch.zeros(8, 48, device="cuda")
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_backward_weight_tc(8, X, 8, None, 0, Gm, 48, dW, None, ws)      # N not a power of two
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_backward_weight_tc(8, X, 6, None, 0, Gm[:, :16], 16, dW, None, ws)  # K1 % 4
