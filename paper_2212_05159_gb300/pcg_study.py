@@ -12,7 +12,9 @@ level schedule, transposes) is set-up outside the timed region and reported sepa
 """
 from __future__ import annotations
 
+import collections
 import concurrent.futures as cf
+import multiprocessing
 import time
 
 import numpy as np
@@ -24,34 +26,51 @@ from .csr import CSR
 
 def _gen(nsys, seed, lo, hi, sigma):
     import synth
-    A, ptr, sides, sig = synth.diffusion_batch(nsys, seed=seed, side_lo=lo, side_hi=hi, sigma=sigma)
-    b = synth.normal(A.m, seed=seed + 7919)
-    return A, ptr, b
+    return synth.diffusion_system_batch(nsys, seed, lo, hi, sigma)
 
 
 def train(net: learned.MPNN, steps: int, batch: int = 32, n_it: int = 8, gamma: float = 0.8,
-          lr: float = 2e-3, seed: int = 1, time_budget_s: float | None = None, log=None):
-    """Trains on `steps` fresh batches (steps * batch generated systems)."""
-    tr = learned.Trainer(net, n_it=n_it, gamma=gamma, lr=lr)
-    losses = []
+          lr: float = 2e-3, seed: int = 1, time_budget_s: float | None = None, log=None,
+          tensor_cores: bool = True, workers: int = 4, depth: int = 8):
+    """Trains on `steps` fresh batches (steps * batch generated systems).  tensor_cores: the
+    network's dense products forward and backward on tcgen05, the numerics of inference.
+    Reports the wall time and the GPU time of the training steps (CUDA events)."""
+    tr = learned.Trainer(net, n_it=n_it, gamma=gamma, lr=lr, tensor_cores=tensor_cores)
+    import synth
+    losses, events = [], []
     t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(1) as ex:
-        fut = ex.submit(_gen, batch, seed * 100003, 32, 128, (0.5, 2.0))
+    # batches are generated on the host by `workers` spawned processes, `depth` ahead
+    ctx = multiprocessing.get_context("spawn")
+    st = torch.cuda.current_stream()
+    step = -1
+    with cf.ProcessPoolExecutor(workers, mp_context=ctx) as ex:
+        args = lambda i: (batch, seed * 100003 + i, 32, 128, (0.5, 2.0))  # noqa: E731
+        futs = collections.deque(ex.submit(synth.diffusion_system_batch, *args(i))
+                                 for i in range(min(depth, steps)))
         for step in range(steps):
-            A, ptr, b = fut.result()
-            if step + 1 < steps:
-                fut = ex.submit(_gen, batch, seed * 100003 + step + 1, 32, 128, (0.5, 2.0))
+            A, ptr, b = futs.popleft().result()
+            if step + len(futs) + 1 < steps:
+                futs.append(ex.submit(synth.diffusion_system_batch, *args(step + len(futs) + 1)))
             dA = CSR.from_host(A)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
             loss = tr.step(dA, torch.from_numpy(ptr).cuda(), len(ptr) - 1, torch.from_numpy(b).cuda())
+            e1.record(st)
+            events.append((e0, e1))
             if step % 20 == 0 or step == steps - 1:
                 losses.append((step, float(loss.mean())))
                 if log:
                     log(f"step {step} loss {losses[-1][1]:.4f}")
             if time_budget_s is not None and time.perf_counter() - t0 > time_budget_s:
+                for f in futs:
+                    f.cancel()
                 break
     torch.cuda.synchronize()
+    gpu_ms = sum(a.elapsed_time(b) for a, b in events)
     return {"steps": step + 1, "systems": (step + 1) * batch, "seconds": time.perf_counter() - t0,
-            "loss_history": losses, "n_it": n_it, "gamma": gamma, "lr": lr, "batch": batch}
+            "gpu_seconds": gpu_ms * 1e-3, "generator_processes": workers,
+            "loss_history": losses, "n_it": n_it, "gamma": gamma, "lr": lr, "batch": batch,
+            "tensor_cores": tensor_cores}
 
 
 def _leading(A, ptr, b, k):

@@ -289,3 +289,11 @@ def diffusion_batch(nsys: int, seed: int, side_lo: int = 32, side_hi: int = 256,
     mats = [diffusion2d(int(s), float(sg), int(sd)) for s, sg, sd in zip(sides, sigmas, seeds)]
     A, ptr = block_diag(mats)
     return A, ptr, sides, sigmas
+
+
+def diffusion_system_batch(nsys: int, seed: int, side_lo: int, side_hi: int, sigma=(0.5, 2.0)):
+    """A block-diagonal batch of diffusion systems with N(0,1) right-hand sides:
+    (CSR, sys_ptr int32[B+1], b float32[m]).  A plain function of its arguments, so it can
+    run in a worker process."""
+    A, ptr, _, _ = diffusion_batch(nsys, seed=seed, side_lo=side_lo, side_hi=side_hi, sigma=sigma)
+    return A, ptr, normal(A.m, seed=seed + 7919)

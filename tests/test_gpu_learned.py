@@ -123,12 +123,14 @@ def test_initial_network_is_jacobi():
     assert np.all(Lh[~on] == 0)
 
 
-def test_training_beats_the_untrained_start():
+@pytest.mark.parametrize("tensor_cores", [False, True])
+def test_training_beats_the_untrained_start(tensor_cores):
     """A short training run on small diffusion systems must cut held-out PCG iterations
-    below the untrained network's (M = D^-1, i.e. Jacobi)."""
+    below the untrained network's (M = D^-1, i.e. Jacobi); with FP32 activations and with
+    every dense product on the tensor cores."""
     torch.manual_seed(0)
     net = learned.MPNN(seed=0)
-    tr = learned.Trainer(net, n_it=8, gamma=0.8, lr=3e-3)
+    tr = learned.Trainer(net, n_it=8, gamma=0.8, lr=3e-3, tensor_cores=tensor_cores)
     for step in range(150):
         A, ptr, _, _ = synth.diffusion_batch(16, seed=100 + step, side_lo=12, side_hi=32, sigma=(0.5, 2.0))
         b = synth.normal(A.m, seed=1000 + step)
@@ -140,7 +142,7 @@ def test_training_beats_the_untrained_start():
     _, it_j, st_j, _ = solve.cg(batch, b, pc="jacobi", tol=1e-8)
     it_j = host(it_j).copy()
     G = learned.Graph(dA)
-    L, _ = net.forward(G)
+    L, _ = net.forward(G, tensor_cores=tensor_cores)
     M, _ = learned.explicit_M(G, L)
     _, it_l, st_l, rr = solve.cg(batch, b, pc="M", M=M, tol=1e-8)
     it_l = host(it_l)
