@@ -453,6 +453,14 @@ spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys
  * knob: results do not depend on it beyond floating-point rounding of the reductions. */
 spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t cluster_size, int32_t max_clusters);
 
+/* Where spx_cg_batched keeps the vectors a block reads only on its own rows (x's FP32
+ * partial, A p, z, D^-1, r when the preconditioner does not gather it, and a copy of p):
+ * 1 (default) in shared memory whenever a system's rows per block are at most 8 x the
+ * threads per block (preconditioner kinds 0, 1 and 3); 0 always in the global workspace.
+ * p (gathered by the sparse product) always lives in the workspace.  The arithmetic and
+ * its order are the same either way: results are bitwise identical. */
+spx_status spx_cg_set_vector_residency(int32_t shared_memory);
+
 /* dinv[i] = 1 / a_ii (0 where the diagonal is absent or zero); device float32[m]. */
 spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream);
 

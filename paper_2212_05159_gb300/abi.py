@@ -99,6 +99,7 @@ SIGNATURES = {
     "spx_ic0_factor": [_CSRP, _P, _P, _I32, _P, _P, _P, _P, _P, _P],
     "spx_diag_inverse": [_CSRP, _P, _P],
     "spx_cg_set_launch": [_I32, _I32, _I32],
+    "spx_cg_set_vector_residency": [_I32],
     "spx_masked_outer_f64": [_CSRP, _P, _P, _D, _P, _P],
     "spx_pcg_train_workspace_size": [_I32, _I32, ctypes.POINTER(_SZ)],
     "spx_pcg_train": [_CSRP, _P, _I32, _CSRP, _CSRP, _P, _I32, _P, _P, _P, _P, _SZ, _P],
@@ -611,6 +612,10 @@ def spx_dot(x, y, out, ws):
 def spx_spai_update(m, g, gg, dada):
     _check(lib().spx_spai_update(int(m.numel()), ptr(m), ptr(g), ptr(gg), ptr(dada), _stream()),
            "spx_spai_update")
+
+
+def spx_cg_set_vector_residency(shared_memory: int = 1):
+    _check(lib().spx_cg_set_vector_residency(int(shared_memory)), "spx_cg_set_vector_residency")
 
 
 def spx_cg_set_launch(threads_per_block: int = 0, cluster_size: int = 0, max_clusters: int = 0):

@@ -10,6 +10,13 @@
 // the scalars of the iteration (alpha, beta, norms, stopping decisions) are then computed
 // once per block by its thread 0 in FP64 and broadcast through shared memory.
 //
+// Every loop gives row i of a block's range to the same thread, so the vectors that are
+// read only on a thread's own rows (x's FP32 partial, A p, z, D^-1, r unless M gathers it,
+// and a copy of p) never cross threads: when a block's rows fit 8 per thread they live in
+// the block's shared memory (192 KB at 1024 threads) instead of the workspace, and only p
+// (and r for an explicit M), which the sparse products gather, goes through L2.  The
+// arithmetic is the same either way.
+//
 // Precision (GB300 has ~1/60 of its FP32 rate in FP64): the iteration runs in FP32 with
 // "reliable updates" -- the solution accumulates in an FP32 partial that is folded into
 // the FP64 x whenever the recurrence residual has dropped by `delta` (and at the end);
@@ -37,6 +44,12 @@ namespace spx {
 namespace {
 
 constexpr int CG_MAX_WARPS = 32;
+
+// Private vector rows per block kept in shared memory: 8 per thread (6 vectors, 192 bytes
+// per thread: 192 KB for 1024 threads, within the 227 KB a block may use; with fewer
+// threads the blocks that share an SM split the same budget).
+constexpr int CG_SMEM_ROWS_PER_THREAD = 8;
+constexpr int CG_SMEM_VECTORS = 6;
 
 struct CgArgs {
     int32_t nsys;
@@ -71,6 +84,22 @@ struct CgArgs {
     const int32_t* lev_off;   // IC(0): per-system offsets into lev_ptr
     const int32_t* lev_ptr;   // IC(0): level l of a system = lev_rows[lev_ptr[l] .. lev_ptr[l+1])
     const int32_t* lev_rows;
+    int32_t smem_rows;        // rows of a block's private vectors that fit in shared memory (0: none)
+};
+
+// The vectors a thread reads only on its own rows, as seen by one system: in shared memory
+// (element i at [i - off]) when the block's rows fit, else the global workspace (off = 0).
+// p is written to both (other blocks gather it from global memory); r lives in global
+// memory when the preconditioner gathers it (explicit M).
+struct Vecs {
+    float* xp;
+    float* q;
+    float* z;
+    float* r;
+    const float* di;
+    float* po;        // the thread's own entries of p
+    int off;
+    bool sm;
 };
 
 // ---------------------------------------------------------------- double-float sums
@@ -199,11 +228,11 @@ __device__ __forceinline__ float spmv_row(const int32_t* __restrict__ ptr, const
 
 // z = M r on rows [lo, hi) of the system (the caller barriers around LLT's two halves)
 template <int NT, int PC>
-__device__ __forceinline__ void apply_pc_local(const CgArgs& a, int lo, int hi) {
+__device__ __forceinline__ void apply_pc_local(const Vecs& v, int lo, int hi) {
     if constexpr (PC == 1) {
-        for (int i = lo + threadIdx.x; i < hi; i += NT) a.z[i] = a.dinv[i] * a.r[i];
+        for (int i = lo + threadIdx.x; i < hi; i += NT) v.z[i - v.off] = v.di[i - v.off] * v.r[i - v.off];
     } else if constexpr (PC == 0) {
-        for (int i = lo + threadIdx.x; i < hi; i += NT) a.z[i] = a.r[i];
+        for (int i = lo + threadIdx.x; i < hi; i += NT) v.z[i - v.off] = v.r[i - v.off];
     }
 }
 
@@ -248,7 +277,8 @@ __device__ __noinline__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) 
 }
 
 template <int NT, int PC>
-__device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi, unsigned rank, int sid) {
+__device__ void apply_pc(const CgArgs& a, const Vecs& v, cg::cluster_group& cl, int lo, int hi, unsigned rank,
+                         int sid) {
     if constexpr (PC == 4) {
         cl.sync();                                               // r complete
         ic0_apply<NT>(a, rank, sid);
@@ -257,7 +287,7 @@ __device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi,
         cl.sync();                                               // r complete
 #pragma unroll 2
         for (int i = lo + threadIdx.x; i < hi; i += NT)
-            a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.r, i);      // z = M r
+            v.z[i - v.off] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.r, i);      // z = M r
     } else if constexpr (PC == 2) {
         cl.sync();                                               // r complete
 #pragma unroll 2
@@ -268,25 +298,300 @@ __device__ void apply_pc(const CgArgs& a, cg::cluster_group& cl, int lo, int hi,
         for (int i = lo + threadIdx.x; i < hi; i += NT)
             a.z[i] = spmv_row(a.l_ptr, a.l_idx, a.l_val, a.w, i);      // z = L w
     } else {
-        apply_pc_local<NT, PC>(a, lo, hi);
+        apply_pc_local<NT, PC>(v, lo, hi);
     }
 }
 
 // r = b - A x in FP64 on [lo, hi); returns the thread's partial of ||r||^2 in FP64.
 template <int NT>
-__device__ __forceinline__ double true_residual(const CgArgs& a, int lo, int hi) {
+__device__ __forceinline__ double true_residual(const CgArgs& a, const Vecs& v, int lo, int hi) {
     double s = 0.0;
     for (int i = lo + threadIdx.x; i < hi; i += NT) {
         double t = (double)a.b[i];
         for (int e = a.a_ptr[i]; e < a.a_ptr[i + 1]; ++e) t -= (double)a.a_val[e] * a.x[a.a_idx[e]];
-        a.r[i] = (float)t;
+        v.r[i - v.off] = (float)t;
         s += t * t;
     }
     return s;
 }
 
+// The vectors of one system for a block (shared memory when SM, else the workspace).
+template <int NT, int PC, bool SM>
+__device__ __forceinline__ Vecs make_vecs(const CgArgs& a, float* sv, int lo, int hi) {
+    constexpr int cap = CG_SMEM_ROWS_PER_THREAD * NT;
+    if constexpr (SM) {
+        if constexpr (PC == 1)
+            for (int i = lo + threadIdx.x; i < hi; i += NT) sv[4 * cap + i - lo] = a.dinv[i];
+        // element i of every view is at [i - lo]: the global r (gathered by M r) is shifted to match
+        return Vecs{sv, sv + cap, sv + 2 * cap, PC <= 1 ? sv + 3 * cap : a.r + lo,
+                    PC <= 1 ? sv + 4 * cap : nullptr, sv + 5 * cap, lo, true};
+    } else {
+        return Vecs{a.xp, a.q, a.z, a.r, a.dinv, a.p, 0, false};
+    }
+}
+
+// PCG on rows [lo, hi) of system sid by this block (its cluster runs the other rows).
+template <int NT, int PC, bool SM>
+__device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& cl, unsigned rank, int sid, int lo,
+                                           int hi, float* sv, float2 (&red)[CG_MAX_WARPS][4], float2 (&part)[2][4],
+                                           CgBcast& bc, int& slot) {
+    const bool t0 = threadIdx.x == 0;
+    const Vecs v = make_vecs<NT, PC, SM>(a, sv, lo, hi);
+    // thread 0 of each block keeps the FP64 scalars; every block computes the same ones
+    double bnorm = 0.0, rz = 0.0, ref = 0.0, last_true = 1.0;
+    int status = SPX_MAXITER;
+
+    // ---- x = 0, r = b, z = M r, p = z
+    DF v2[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+        const float bi = a.b[i];
+        a.x[i] = 0.0;
+        v.xp[i - v.off] = 0.f;
+        v.r[i - v.off] = bi;
+        df_add_prod(v2[0], bi, bi);
+    }
+    apply_pc<NT, PC>(a, v, cl, lo, hi, rank, sid);
+    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+        const float zi = v.z[i - v.off];
+        a.p[i] = zi;
+        if (v.sm) v.po[i - v.off] = zi;
+        df_add_prod(v2[1], v.r[i - v.off], zi);
+    }
+    {
+        double o2[2];
+        cluster_sum<NT, 2>(cl, v2, o2, red, part, slot);
+        if (t0) {
+            bnorm = sqrt(o2[0]);
+            rz = o2[1];
+            ref = bnorm;
+            int act = ACT_GO;
+            if (bnorm == 0.0) {
+                status = SPX_OK;
+                last_true = 0.0;
+                act = ACT_STOP;
+            } else if (!isfinite(rz) || !isfinite(bnorm)) {
+                status = SPX_NONFINITE;
+                act = ACT_STOP;
+            } else if (!(rz > 0.0)) {
+                status = SPX_BREAKDOWN;
+                act = ACT_STOP;
+            }
+            bc.action = act;
+        }
+        __syncthreads();
+    }
+    int it = 0;
+    bool dirty = false;                 // xp holds an unfolded part
+    if (bc.action == ACT_GO) {
+        while (it < a.maxit) {
+            cl.sync();                                      // p complete (and bc read by all)
+            {
+                DF v1[1] = {{0.f, 0.f}};
+                const float* __restrict__ Pv = a.p;
+#pragma unroll 2
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    const float qi = spmv_row(a.a_ptr, a.a_idx, a.a_val, Pv, i);
+                    v.q[i - v.off] = qi;
+                    df_add_prod(v1[0], v.po[i - v.off], qi);
+                }
+                double o1[1];
+                cluster_sum<NT, 1>(cl, v1, o1, red, part, slot);
+                if (t0) {
+                    const double pq = o1[0];
+                    int act = ACT_GO;
+                    if (!isfinite(pq)) {
+                        status = SPX_NONFINITE;
+                        act = ACT_STOP;
+                    } else if (!(pq > 0.0)) {
+                        status = SPX_BREAKDOWN;
+                        act = ACT_STOP;
+                    } else {
+                        bc.alpha = (float)(rz / pq);
+                    }
+                    bc.action = act;
+                }
+                __syncthreads();
+            }
+            if (bc.action == ACT_STOP) break;
+            const float alpha = bc.alpha;
+            dirty = true;
+            ++it;
+            DF v2n[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            if constexpr (PC <= 1) {
+                // x_p += alpha p; r -= alpha q; z = M r (local); <r, z>, <r, r> -- one pass
+                float* __restrict__ XP = v.xp - v.off;
+                float* __restrict__ R = v.r - v.off;
+                float* __restrict__ Z = v.z - v.off;
+                const float* __restrict__ Pv = v.po - v.off;
+                const float* __restrict__ Qv = v.q - v.off;
+                const float* __restrict__ DI = v.di - v.off;
+#pragma unroll 2
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    XP[i] = fmaf(alpha, Pv[i], XP[i]);
+                    const float ri = fmaf(-alpha, Qv[i], R[i]);
+                    R[i] = ri;
+                    const float zi = PC == 1 ? DI[i] * ri : ri;
+                    Z[i] = zi;
+                    df_add_prod(v2n[0], ri, zi);
+                    df_add_prod(v2n[1], ri, ri);
+                }
+            } else if constexpr (PC == 3) {
+                // explicit M: update, barrier, then z = M r with the dots in the same pass
+                float* __restrict__ XP = v.xp - v.off;
+                float* __restrict__ R = a.r;
+                const float* __restrict__ Pv = v.po - v.off;
+                const float* __restrict__ Qv = v.q - v.off;
+#pragma unroll 2
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    XP[i] = fmaf(alpha, Pv[i], XP[i]);
+                    R[i] = fmaf(-alpha, Qv[i], R[i]);
+                }
+                cl.sync();                                  // r complete
+                const float* __restrict__ Rc = a.r;
+                float* __restrict__ Z = v.z - v.off;
+#pragma unroll 2
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    const float zi = spmv_row(a.l_ptr, a.l_idx, a.l_val, Rc, i);
+                    Z[i] = zi;
+                    const float ri = Rc[i];
+                    df_add_prod(v2n[0], ri, zi);
+                    df_add_prod(v2n[1], ri, ri);
+                }
+            } else {
+                float* __restrict__ XP = v.xp - v.off;
+                float* __restrict__ R = v.r - v.off;
+                const float* __restrict__ Pv = v.po - v.off;
+                const float* __restrict__ Qv = v.q - v.off;
+#pragma unroll 2
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    XP[i] = fmaf(alpha, Pv[i], XP[i]);
+                    R[i] = fmaf(-alpha, Qv[i], R[i]);
+                }
+                apply_pc<NT, PC>(a, v, cl, lo, hi, rank, sid);
+                const float* __restrict__ Rc = v.r - v.off;
+                const float* __restrict__ Zc = v.z - v.off;
+#pragma unroll 2
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    const float ri = Rc[i];
+                    df_add_prod(v2n[0], ri, Zc[i]);
+                    df_add_prod(v2n[1], ri, ri);
+                }
+            }
+            double rz_new = 0.0;
+            {
+                double o2[2];
+                cluster_sum<NT, 2>(cl, v2n, o2, red, part, slot);
+                if (t0) {
+                    rz_new = o2[0];
+                    const double rnorm = sqrt(o2[1]);
+                    int act = ACT_GO;
+                    if (!isfinite(rz_new) || !isfinite(rnorm)) {
+                        status = SPX_NONFINITE;
+                        act = ACT_STOP;
+                    } else if (rnorm <= a.delta * ref || rnorm <= a.tol * bnorm) {
+                        act = ACT_FOLD;
+                    } else if (!(rz_new > 0.0)) {
+                        status = SPX_BREAKDOWN;
+                        act = ACT_STOP;
+                    } else {
+                        bc.beta = (float)(rz_new / rz);
+                        rz = rz_new;
+                    }
+                    bc.action = act;
+                }
+                __syncthreads();
+            }
+            if (bc.action == ACT_STOP) break;
+            if (bc.action == ACT_FOLD) {
+                // ---- reliable update: fold xp into x (FP64), true residual in FP64
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    a.x[i] += (double)v.xp[i - v.off];
+                    v.xp[i - v.off] = 0.f;
+                }
+                dirty = false;
+                cl.sync();                                  // x complete
+                {
+                    DF v64[1] = {df_of(true_residual<NT>(a, v, lo, hi))};
+                    double o1[1];
+                    cluster_sum<NT, 1>(cl, v64, o1, red, part, slot);
+                    if (t0) {
+                        const double tn = sqrt(o1[0]);
+                        last_true = tn / bnorm;
+                        ref = tn;
+                        int act = ACT_GO;
+                        if (!isfinite(tn)) {
+                            status = SPX_NONFINITE;
+                            act = ACT_STOP;
+                        } else if (tn <= a.tol * bnorm) {
+                            status = SPX_OK;
+                            act = ACT_STOP;
+                        }
+                        bc.action = act;
+                    }
+                    __syncthreads();
+                }
+                if (bc.action == ACT_STOP) break;
+                apply_pc<NT, PC>(a, v, cl, lo, hi, rank, sid);
+                DF vz[1] = {{0.f, 0.f}};
+                for (int i = lo + threadIdx.x; i < hi; i += NT) df_add_prod(vz[0], v.r[i - v.off], v.z[i - v.off]);
+                double o1[1];
+                cluster_sum<NT, 1>(cl, vz, o1, red, part, slot);
+                if (t0) {
+                    rz_new = o1[0];
+                    int act = ACT_GO;
+                    if (!(rz_new > 0.0)) {
+                        status = SPX_BREAKDOWN;
+                        act = ACT_STOP;
+                    } else {
+                        bc.beta = (float)(rz_new / rz);
+                        rz = rz_new;
+                    }
+                    bc.action = act;
+                }
+                __syncthreads();
+                if (bc.action == ACT_STOP) break;
+            }
+            const float beta = bc.beta;
+            if (v.sm) {
+                float* __restrict__ Pg = a.p;
+                float* __restrict__ PO = v.po - v.off;
+                const float* __restrict__ Zc = v.z - v.off;
+#pragma unroll 4
+                for (int i = lo + threadIdx.x; i < hi; i += NT) {
+                    const float pi = fmaf(beta, PO[i], Zc[i]);
+                    PO[i] = pi;
+                    Pg[i] = pi;
+                }
+            } else {
+                float* __restrict__ Pv = a.p;
+                const float* __restrict__ Zc = a.z;
+#pragma unroll 4
+                for (int i = lo + threadIdx.x; i < hi; i += NT) Pv[i] = fmaf(beta, Pv[i], Zc[i]);
+            }
+        }
+    }
+    if (dirty) {
+        // fold the remainder and report the true residual of the returned x
+        for (int i = lo + threadIdx.x; i < hi; i += NT) {
+            a.x[i] += (double)v.xp[i - v.off];
+            v.xp[i - v.off] = 0.f;
+        }
+        cl.sync();
+        DF v64[1] = {df_of(true_residual<NT>(a, v, lo, hi))};
+        double o1[1];
+        cluster_sum<NT, 1>(cl, v64, o1, red, part, slot);
+        if (t0) last_true = bnorm > 0.0 ? sqrt(o1[0]) / bnorm : 0.0;
+    }
+    if (rank == 0 && t0) {
+        a.iters[sid] = it;
+        a.status[sid] = status;
+        a.relres[sid] = last_true;
+    }
+}
+
 // Registers capped at 64 (1024 / NT blocks per SM): the launch sizes its grid for that many
-// resident blocks.
+// resident blocks.  A system whose rows per block fit CG_SMEM_ROWS_PER_THREAD x NT keeps
+// the block's private vectors in shared memory (dynamic, 6 x that many floats).
 template <int NT, int PC>
 __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
     cg::cluster_group cl = cg::this_cluster();
@@ -296,6 +601,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
     __shared__ float2 part[2][4];
     __shared__ int sys_sh;
     __shared__ CgBcast bc;
+    extern __shared__ float sv[];
     int slot = 0;
     const bool t0 = threadIdx.x == 0;
 
@@ -309,247 +615,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
         const int R0 = a.sys_ptr[sid], R1 = a.sys_ptr[sid + 1];
         const int chunk = (R1 - R0 + (int)ncl - 1) / (int)ncl;
         const int lo = min(R1, R0 + (int)rank * chunk), hi = min(R1, lo + chunk);
-
-        // thread 0 of each block keeps the FP64 scalars; every block computes the same ones
-        double bnorm = 0.0, rz = 0.0, ref = 0.0, last_true = 1.0;
-        int status = SPX_MAXITER;
-
-        // ---- x = 0, r = b, z = M r, p = z
-        DF v2[2] = {{0.f, 0.f}, {0.f, 0.f}};
-        for (int i = lo + threadIdx.x; i < hi; i += NT) {
-            const float bi = a.b[i];
-            a.x[i] = 0.0;
-            a.xp[i] = 0.f;
-            a.r[i] = bi;
-            df_add_prod(v2[0], bi, bi);
-        }
-        apply_pc<NT, PC>(a, cl, lo, hi, rank, sid);
-        for (int i = lo + threadIdx.x; i < hi; i += NT) {
-            const float zi = a.z[i];
-            a.p[i] = zi;
-            df_add_prod(v2[1], a.r[i], zi);
-        }
-        {
-            double o2[2];
-            cluster_sum<NT, 2>(cl, v2, o2, red, part, slot);
-            if (t0) {
-                bnorm = sqrt(o2[0]);
-                rz = o2[1];
-                ref = bnorm;
-                int act = ACT_GO;
-                if (bnorm == 0.0) {
-                    status = SPX_OK;
-                    last_true = 0.0;
-                    act = ACT_STOP;
-                } else if (!isfinite(rz) || !isfinite(bnorm)) {
-                    status = SPX_NONFINITE;
-                    act = ACT_STOP;
-                } else if (!(rz > 0.0)) {
-                    status = SPX_BREAKDOWN;
-                    act = ACT_STOP;
-                }
-                bc.action = act;
-            }
-            __syncthreads();
-        }
-        int it = 0;
-        bool dirty = false;                 // xp holds an unfolded part
-        if (bc.action == ACT_GO) {
-            while (it < a.maxit) {
-                cl.sync();                                      // p complete (and bc read by all)
-                {
-                    DF v1[1] = {{0.f, 0.f}};
-                    const float* __restrict__ Pv = a.p;
-                    float* __restrict__ Qv = a.q;
-#pragma unroll 2
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                        const float qi = spmv_row(a.a_ptr, a.a_idx, a.a_val, Pv, i);
-                        Qv[i] = qi;
-                        df_add_prod(v1[0], Pv[i], qi);
-                    }
-                    double o1[1];
-                    cluster_sum<NT, 1>(cl, v1, o1, red, part, slot);
-                    if (t0) {
-                        const double pq = o1[0];
-                        int act = ACT_GO;
-                        if (!isfinite(pq)) {
-                            status = SPX_NONFINITE;
-                            act = ACT_STOP;
-                        } else if (!(pq > 0.0)) {
-                            status = SPX_BREAKDOWN;
-                            act = ACT_STOP;
-                        } else {
-                            bc.alpha = (float)(rz / pq);
-                        }
-                        bc.action = act;
-                    }
-                    __syncthreads();
-                }
-                if (bc.action == ACT_STOP) break;
-                const float alpha = bc.alpha;
-                dirty = true;
-                ++it;
-                DF v2n[2] = {{0.f, 0.f}, {0.f, 0.f}};
-                if constexpr (PC <= 1) {
-                    // x_p += alpha p; r -= alpha q; z = M r (local); <r, z>, <r, r> -- one pass
-                    float* __restrict__ XP = a.xp;
-                    float* __restrict__ R = a.r;
-                    float* __restrict__ Z = a.z;
-                    const float* __restrict__ Pv = a.p;
-                    const float* __restrict__ Qv = a.q;
-                    const float* __restrict__ DI = a.dinv;
-#pragma unroll 2
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                        XP[i] = fmaf(alpha, Pv[i], XP[i]);
-                        const float ri = fmaf(-alpha, Qv[i], R[i]);
-                        R[i] = ri;
-                        const float zi = PC == 1 ? DI[i] * ri : ri;
-                        Z[i] = zi;
-                        df_add_prod(v2n[0], ri, zi);
-                        df_add_prod(v2n[1], ri, ri);
-                    }
-                } else if constexpr (PC == 3) {
-                    // explicit M: update, barrier, then z = M r with the dots in the same pass
-                    float* __restrict__ XP = a.xp;
-                    float* __restrict__ R = a.r;
-                    const float* __restrict__ Pv = a.p;
-                    const float* __restrict__ Qv = a.q;
-#pragma unroll 2
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                        XP[i] = fmaf(alpha, Pv[i], XP[i]);
-                        R[i] = fmaf(-alpha, Qv[i], R[i]);
-                    }
-                    cl.sync();                                  // r complete
-                    const float* __restrict__ Rc = a.r;
-                    float* __restrict__ Z = a.z;
-#pragma unroll 2
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                        const float zi = spmv_row(a.l_ptr, a.l_idx, a.l_val, Rc, i);
-                        Z[i] = zi;
-                        const float ri = Rc[i];
-                        df_add_prod(v2n[0], ri, zi);
-                        df_add_prod(v2n[1], ri, ri);
-                    }
-                } else {
-                    float* __restrict__ XP = a.xp;
-                    float* __restrict__ R = a.r;
-                    const float* __restrict__ Pv = a.p;
-                    const float* __restrict__ Qv = a.q;
-#pragma unroll 2
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                        XP[i] = fmaf(alpha, Pv[i], XP[i]);
-                        R[i] = fmaf(-alpha, Qv[i], R[i]);
-                    }
-                    apply_pc<NT, PC>(a, cl, lo, hi, rank, sid);
-                    const float* __restrict__ Rc = a.r;
-                    const float* __restrict__ Zc = a.z;
-#pragma unroll 2
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                        const float ri = Rc[i];
-                        df_add_prod(v2n[0], ri, Zc[i]);
-                        df_add_prod(v2n[1], ri, ri);
-                    }
-                }
-                double rz_new = 0.0;
-                {
-                    double o2[2];
-                    cluster_sum<NT, 2>(cl, v2n, o2, red, part, slot);
-                    if (t0) {
-                        rz_new = o2[0];
-                        const double rnorm = sqrt(o2[1]);
-                        int act = ACT_GO;
-                        if (!isfinite(rz_new) || !isfinite(rnorm)) {
-                            status = SPX_NONFINITE;
-                            act = ACT_STOP;
-                        } else if (rnorm <= a.delta * ref || rnorm <= a.tol * bnorm) {
-                            act = ACT_FOLD;
-                        } else if (!(rz_new > 0.0)) {
-                            status = SPX_BREAKDOWN;
-                            act = ACT_STOP;
-                        } else {
-                            bc.beta = (float)(rz_new / rz);
-                            rz = rz_new;
-                        }
-                        bc.action = act;
-                    }
-                    __syncthreads();
-                }
-                if (bc.action == ACT_STOP) break;
-                if (bc.action == ACT_FOLD) {
-                    // ---- reliable update: fold xp into x (FP64), true residual in FP64
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                        a.x[i] += (double)a.xp[i];
-                        a.xp[i] = 0.f;
-                    }
-                    dirty = false;
-                    cl.sync();                                  // x complete
-                    {
-                        DF v64[1] = {df_of(true_residual<NT>(a, lo, hi))};
-                        double o1[1];
-                        cluster_sum<NT, 1>(cl, v64, o1, red, part, slot);
-                        if (t0) {
-                            const double tn = sqrt(o1[0]);
-                            last_true = tn / bnorm;
-                            ref = tn;
-                            int act = ACT_GO;
-                            if (!isfinite(tn)) {
-                                status = SPX_NONFINITE;
-                                act = ACT_STOP;
-                            } else if (tn <= a.tol * bnorm) {
-                                status = SPX_OK;
-                                act = ACT_STOP;
-                            }
-                            bc.action = act;
-                        }
-                        __syncthreads();
-                    }
-                    if (bc.action == ACT_STOP) break;
-                    apply_pc<NT, PC>(a, cl, lo, hi, rank, sid);
-                    DF vz[1] = {{0.f, 0.f}};
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) df_add_prod(vz[0], a.r[i], a.z[i]);
-                    double o1[1];
-                    cluster_sum<NT, 1>(cl, vz, o1, red, part, slot);
-                    if (t0) {
-                        rz_new = o1[0];
-                        int act = ACT_GO;
-                        if (!(rz_new > 0.0)) {
-                            status = SPX_BREAKDOWN;
-                            act = ACT_STOP;
-                        } else {
-                            bc.beta = (float)(rz_new / rz);
-                            rz = rz_new;
-                        }
-                        bc.action = act;
-                    }
-                    __syncthreads();
-                    if (bc.action == ACT_STOP) break;
-                }
-                const float beta = bc.beta;
-                {
-                    float* __restrict__ Pv = a.p;
-                    const float* __restrict__ Zc = a.z;
-#pragma unroll 4
-                    for (int i = lo + threadIdx.x; i < hi; i += NT) Pv[i] = fmaf(beta, Pv[i], Zc[i]);
-                }
-            }
-        }
-        if (dirty) {
-            // fold the remainder and report the true residual of the returned x
-            for (int i = lo + threadIdx.x; i < hi; i += NT) {
-                a.x[i] += (double)a.xp[i];
-                a.xp[i] = 0.f;
-            }
-            cl.sync();
-            DF v64[1] = {df_of(true_residual<NT>(a, lo, hi))};
-            double o1[1];
-            cluster_sum<NT, 1>(cl, v64, o1, red, part, slot);
-            if (t0) last_true = bnorm > 0.0 ? sqrt(o1[0]) / bnorm : 0.0;
-        }
-        if (rank == 0 && t0) {
-            a.iters[sid] = it;
-            a.status[sid] = status;
-            a.relres[sid] = last_true;
-        }
+        bool in_smem = false;
+        if constexpr (PC == 0 || PC == 1 || PC == 3)
+            in_smem = a.smem_rows >= CG_SMEM_ROWS_PER_THREAD * NT && chunk <= CG_SMEM_ROWS_PER_THREAD * NT;
+        if (in_smem)                                            // uniform across the cluster
+            pcg_system<NT, PC, true>(a, cl, rank, sid, lo, hi, sv, red, part, bc, slot);
+        else
+            pcg_system<NT, PC, false>(a, cl, rank, sid, lo, hi, sv, red, part, bc, slot);
         cl.sync();                                              // finish before the next system
     }
 }
@@ -579,6 +651,8 @@ __global__ void masked_outer_f64_kernel(int32_t m, const int32_t* __restrict__ p
 std::atomic<int> g_cg_threads{0};
 std::atomic<int> g_cg_cluster{0};
 std::atomic<int> g_cg_max_clusters{0};
+std::atomic<int> g_cg_smem_vectors{1};
+
 
 }  // namespace
 }  // namespace spx
@@ -669,10 +743,13 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     if (maxc > 0 && clusters > maxc) clusters = maxc;
     if (clusters < 1) clusters = 1;
     if (clusters > nsys) clusters = nsys;
+    const bool smem_vecs = g_cg_smem_vectors.load() != 0 && (pc_kind == 0 || pc_kind == 1 || pc_kind == 3);
+    a.smem_rows = smem_vecs ? CG_SMEM_ROWS_PER_THREAD * nt : 0;
+    const size_t smem = (size_t)a.smem_rows * CG_SMEM_VECTORS * sizeof(float);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(clusters * cl));
     cfg.blockDim = dim3(nt);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -682,9 +759,12 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     auto launch = [&](auto kern) -> spx_status {
-        if (cl > 8)   // 16 blocks per cluster is beyond the portable size: opt in once
+        if (cl > 8)   // 16 blocks per cluster is beyond the portable size: opt in
             SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
                      "spx_cg_batched cluster attribute");
+        if (smem > 0)
+            SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                     "spx_cg_batched shared memory attribute");
         SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, a), "spx_cg_batched launch");
         return SPX_OK;
     };
@@ -739,5 +819,12 @@ extern "C" spx_status spx_cg_set_launch(int32_t threads_per_block, int32_t clust
     g_cg_threads.store(threads_per_block);
     g_cg_cluster.store(cluster_size);
     g_cg_max_clusters.store(max_clusters);
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_cg_set_vector_residency(int32_t shared_memory) {
+    if (shared_memory != 0 && shared_memory != 1)
+        return set_error(SPX_INVALID_ARG, "spx_cg_set_vector_residency: 0 or 1");
+    g_cg_smem_vectors.store(shared_memory);
     return SPX_OK;
 }

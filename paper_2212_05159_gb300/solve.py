@@ -31,6 +31,7 @@ class SystemBatch:
         self.order = torch.from_numpy(np.argsort(-sizes, kind="stable").astype(np.int32)).to(A.device)
         self.ws = abi.workspace(abi.spx_cg_workspace_size(A.m), A.device)
         self.mean_rows = float(sizes.mean()) if sizes.size else 1.0
+        self.max_rows = float(sizes.max()) if sizes.size else 1.0
         self.launch = None          # (threads, cluster, max clusters); None = launch_for()
         self._dinv = None
         self.iters = torch.zeros(self.nsys, dtype=torch.int32, device=A.device)
@@ -39,15 +40,22 @@ class SystemBatch:
 
     def launch_for(self, kind: int):
         """Launch shape of spx_cg_batched: 1024-thread blocks and a cluster (power of two, at
-        most 16) giving each thread ~8 rows of an average system (~4 with a sparse M or
-        L L^T, whose extra product is the longer dependent chain).  Measured on GB300 with
-        2D diffusion batches: 64 systems of 256^2 run fastest at 8 blocks with Jacobi and
-        16 with the learned M; 256 systems of 32^2..256^2 at 4 blocks."""
+        most 16).  With no preconditioner, Jacobi or an explicit M the cluster is the
+        smallest whose blocks hold the largest system's private vectors in shared memory
+        (8 rows per thread); measured on GB300 with 2D diffusion batches, 64 systems of
+        256^2 run at 70 ms (Jacobi) and 102 ms (explicit M) with 8 blocks against 94 and
+        133 ms with the vectors in global memory, and 256 systems of 32^2..256^2 at 105 ms
+        against 127 ms.  The triangular preconditioners keep ~8 (IC(0)) or ~4 (L L^T, the
+        longer dependent chain) rows of an average system per thread."""
         if self.launch is not None:
             return self.launch
-        rows_per_thread = 4.0 if kind in (2, 3) else 8.0
-        want = self.mean_rows / rows_per_thread / 1024.0
-        cl = 2 ** int(round(np.log2(max(want, 1.0))))
+        if kind in (0, 1, 3):
+            want = self.max_rows / (8.0 * 1024.0)
+            cl = 2 ** int(np.ceil(np.log2(max(want, 1.0))))
+        else:
+            rows_per_thread = 4.0 if kind == 2 else 8.0
+            want = self.mean_rows / rows_per_thread / 1024.0
+            cl = 2 ** int(round(np.log2(max(want, 1.0))))
         return (1024, int(min(16, max(1, cl))), 0)
 
     def dinv(self, values=None):

@@ -258,3 +258,48 @@ def test_precond_apply_matches_oracle(small_batch, kind):
         abi.spx_precond_apply(4, dev(r), z, L=sL, LT=sLT, nsys=batch.nsys, levels=levels, tmp=tmp)
         ref = oracle.trsv_lower_t(l_ip, l_ix, Lh.values, oracle.trsv_lower(l_ip, l_ix, Lh.values, r))
     np.testing.assert_allclose(host(z), ref, rtol=2e-5, atol=2e-5 * np.abs(ref).max())
+
+
+def _spd_band(A, ptr):
+    """A symmetric, strictly diagonally dominant M on each system's rows: 2 on the diagonal,
+    -0.5 between rows i and i + 1 of the same system (a sparse product that gathers r)."""
+    rows, cols, vals = [], [], []
+    for s in range(len(ptr) - 1):
+        a, c = int(ptr[s]), int(ptr[s + 1])
+        for i in range(a, c):
+            for j, v in ((i - 1, -0.5), (i, 2.0), (i + 1, -0.5)):
+                if a <= j < c:
+                    rows.append(i)
+                    cols.append(j)
+                    vals.append(v)
+    ip = np.zeros(A.m + 1, np.int64)
+    np.add.at(ip, np.asarray(rows) + 1, 1)
+    return spx.CSR.from_host(synth.CSR(A.m, A.m, np.cumsum(ip), np.asarray(cols), np.asarray(vals, np.float32)))
+
+
+@pytest.mark.parametrize("pc", ["none", "jacobi", "M"])
+@pytest.mark.parametrize("launch", [(256, 1, 0), (1024, 2, 0)])
+def test_vector_residency_is_bitwise_neutral(pc, launch):
+    """Private PCG vectors in shared memory or in the workspace: the same arithmetic in the
+    same order, so x, iterations, status and residuals agree bit for bit.  With 256-thread
+    blocks of one (shared memory for 2048 rows per block) the batch mixes systems that fit
+    (sides 8..45) with systems that do not (sides 46..70) in one launch."""
+    A, ptr, _, _ = synth.diffusion_batch(10, seed=11, side_lo=8, side_hi=70, sigma=1.0)
+    batch = solve.SystemBatch(spx.CSR.from_host(A), ptr)
+    batch.launch = launch
+    M = _spd_band(A, ptr) if pc == "M" else None
+    b = dev(synth.normal(A.m, seed=12))
+    out = []
+    try:
+        for res in (1, 0):
+            spx.abi.spx_cg_set_vector_residency(res)
+            x, it, st, rr = solve.cg(batch, b, pc=pc, M=M, tol=1e-8)
+            out.append((host(x).copy(), host(it).copy(), host(st).copy(), host(rr).copy()))
+    finally:
+        spx.abi.spx_cg_set_vector_residency(1)
+    assert np.all(out[0][2] == 0)
+    for u, w in zip(out[0], out[1]):
+        np.testing.assert_array_equal(u, w)
+    sides = np.sqrt(np.diff(ptr)).astype(int)
+    if launch[0] == 256:
+        assert (sides * sides <= 2048).any() and (sides * sides > 2048).any()
