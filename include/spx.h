@@ -527,7 +527,7 @@ spx_status spx_dense_backward_data(int64_t n, const float* G, int32_t N, const v
                                    int32_t accumulate, void* stream);
 
 /* Workspace bytes of spx_dense_backward_weight_tc: one (K + 1) x N float32 partial per CTA
- * (at most one CTA per SM of the current device).  K = K1 + K2 <= 128, K % 4 == 0;
+ * (at most two CTAs per SM of the current device).  K = K1 + K2 <= 128, K % 4 == 0;
  * N in {16, 32, 64, 128}. */
 spx_status spx_dense_backward_weight_tc_workspace_size(int64_t n, int32_t K, int32_t N,
                                                        size_t* bytes);

@@ -61,7 +61,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // [kbase, kbase + K) of the A tile; rows past n are zero.  Loads are issued STAGE_BATCH at a
 // time per thread before any is converted, so enough bytes are in flight to cover the
 // memory latency (the layer is bandwidth-bound).
-constexpr int STAGE_BATCH = 8;
+constexpr int STAGE_BATCH = 16;
+constexpr int EPI_BATCH = 8;                                 // epilogue loads in flight per thread
 
 __device__ __forceinline__ void stage_rows(unsigned char* sA, const float* __restrict__ X, int K, int kbase, int kpad,
                                            int64_t row0, int64_t n) {
@@ -186,26 +187,42 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
             }
         }
         __syncwarp();
-        // ---- epilogue 2: the warp's 32 rows to global memory, float4 pieces in row order
+        // ---- epilogue 2: the warp's valid rows to global memory, float4 pieces in row order;
+        // the residual's Hin pieces are loaded EPI_BATCH at a time before any is used
         const int n4 = N >> 2;
-#pragma unroll 4
-        for (int t = lane; t < 32 * n4; t += 32) {
-            const int r = t / n4, cq = t - r * n4;
-            const int64_t row = row0 + warp * 32 + r;
-            if (row >= n) break;                                 // rows only grow with t
-            const float4 pre = *reinterpret_cast<const float4*>(stage + r * ldst + cq * 4);
-            const int64_t o = row * N + cq * 4;
-            if (mode == 0) {
-                __stcs(reinterpret_cast<float4*>(Y + o), pre);
-            } else if (mode == 1) {
-                __stcs(reinterpret_cast<float4*>(Y + o),
-                       make_float4(fmaxf(pre.x, 0.f), fmaxf(pre.y, 0.f), fmaxf(pre.z, 0.f), fmaxf(pre.w, 0.f)));
-            } else {
-                const float4 h = __ldcs(reinterpret_cast<const float4*>(Hin + o));
-                __stcs(reinterpret_cast<float4*>(U + o), pre);
-                __stcs(reinterpret_cast<float4*>(Y + o),
-                       make_float4(h.x + fmaxf(pre.x, 0.f), h.y + fmaxf(pre.y, 0.f), h.z + fmaxf(pre.z, 0.f),
-                                   h.w + fmaxf(pre.w, 0.f)));
+        const int64_t wrow0 = row0 + warp * 32;
+        const int nv = n - wrow0 >= 32 ? 32 : (n > wrow0 ? (int)(n - wrow0) : 0);
+        const int total = nv * n4;
+        for (int t0 = lane; t0 < total; t0 += EPI_BATCH * 32) {
+            float4 h[EPI_BATCH];
+            if (mode == 2) {
+#pragma unroll
+                for (int u = 0; u < EPI_BATCH; ++u) {
+                    const int t = t0 + u * 32;
+                    if (t < total) {
+                        const int r = t / n4, cq = t - r * n4;
+                        h[u] = __ldcs(reinterpret_cast<const float4*>(Hin + (wrow0 + r) * N + cq * 4));
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < EPI_BATCH; ++u) {
+                const int t = t0 + u * 32;
+                if (t >= total) break;
+                const int r = t / n4, cq = t - r * n4;
+                const float4 pre = *reinterpret_cast<const float4*>(stage + r * ldst + cq * 4);
+                const int64_t o = (wrow0 + r) * N + cq * 4;
+                if (mode == 0) {
+                    __stcs(reinterpret_cast<float4*>(Y + o), pre);
+                } else if (mode == 1) {
+                    __stcs(reinterpret_cast<float4*>(Y + o),
+                           make_float4(fmaxf(pre.x, 0.f), fmaxf(pre.y, 0.f), fmaxf(pre.z, 0.f), fmaxf(pre.w, 0.f)));
+                } else {
+                    __stcs(reinterpret_cast<float4*>(U + o), pre);
+                    __stcs(reinterpret_cast<float4*>(Y + o),
+                           make_float4(h[u].x + fmaxf(pre.x, 0.f), h[u].y + fmaxf(pre.y, 0.f),
+                                       h[u].z + fmaxf(pre.z, 0.f), h[u].w + fmaxf(pre.w, 0.f)));
+                }
             }
         }
     }
@@ -312,23 +329,40 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_bwd_data_kernel(int64_t n
                                 __uint_as_float(v[q + 3]));
         }
         __syncwarp();
-        const int k4 = K >> 2;                                   // K1, K2 multiples of 4
-#pragma unroll 4
-        for (int t = lane; t < 32 * k4; t += 32) {
-            const int r = t / k4, cq = t - r * k4;
-            const int64_t row = row0 + warp * 32 + r;
-            if (row >= n) break;
-            const int c = cq * 4;
-            float* dst;
-            if (c < K1) dst = dX1 + row * K1 + c;
-            else if (dX2) dst = dX2 + row * K2 + (c - K1);
-            else continue;
-            float4 val = *reinterpret_cast<const float4*>(stage + r * ldst + c);
+        // the warp's valid rows, float4 pieces in row order (K1, K2 multiples of 4: a piece
+        // never straddles dX1 and dX2); with accumulate the old pieces are loaded EPI_BATCH
+        // at a time before any is added
+        const int k4 = K >> 2;
+        const int64_t wrow0 = row0 + warp * 32;
+        const int nv = n - wrow0 >= 32 ? 32 : (n > wrow0 ? (int)(n - wrow0) : 0);
+        const int total = nv * k4;
+        auto dst_of = [&](int t) -> float* {
+            const int r = t / k4, c = (t - r * k4) * 4;
+            if (c < K1) return dX1 + (wrow0 + r) * K1 + c;
+            return dX2 ? dX2 + (wrow0 + r) * K2 + (c - K1) : nullptr;
+        };
+        for (int t0 = lane; t0 < total; t0 += EPI_BATCH * 32) {
+            float4 old[EPI_BATCH];
             if (accumulate) {
-                const float4 o = *reinterpret_cast<const float4*>(dst);
-                val = make_float4(o.x + val.x, o.y + val.y, o.z + val.z, o.w + val.w);
+#pragma unroll
+                for (int u = 0; u < EPI_BATCH; ++u) {
+                    const int t = t0 + u * 32;
+                    float* d = t < total ? dst_of(t) : nullptr;
+                    old[u] = d ? *reinterpret_cast<const float4*>(d) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
-            *reinterpret_cast<float4*>(dst) = val;
+#pragma unroll
+            for (int u = 0; u < EPI_BATCH; ++u) {
+                const int t = t0 + u * 32;
+                if (t >= total) break;
+                float* d = dst_of(t);
+                if (!d) continue;
+                const int r = t / k4;
+                float4 val = *reinterpret_cast<const float4*>(stage + r * ldst + (t - r * k4) * 4);
+                if (accumulate)
+                    val = make_float4(old[u].x + val.x, old[u].y + val.y, old[u].z + val.z, old[u].w + val.w);
+                *reinterpret_cast<float4*>(d) = val;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -347,15 +381,16 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_bwd_data_kernel(int64_t n
 // loads two rows of a 4-column piece (two float4, consecutive threads on consecutive
 // pieces) and stores four BF16 pairs (row r, r + 1) of the transposed operand.
 //
-// One persistent CTA per SM walks the row tiles with a stride of the grid, two staging
-// buffers in turn: while the tensor cores run tile t's 8 MMAs (K = 16 rows each, the FP32
-// accumulator stays in tensor memory across all of the CTA's tiles), the threads stage
-// tile t + 1.  A buffer is restaged only after the mbarrier of the commit that read it has
+// Two persistent CTAs per SM (one's loads in flight while the other converts) walk the row
+// tiles with a stride of the grid, each with two staging buffers in turn: while the tensor
+// cores run tile t's 8 MMAs (K = 16 rows each, the FP32 accumulator stays in tensor memory
+// across all of the CTA's tiles), the threads stage tile t + 1.  A buffer is restaged only after the mbarrier of the commit that read it has
 // completed (bounded wait).  db is summed in FP32 by the threads from the values they
 // load (each thread owns one 4-column piece of G).  Each CTA writes its partial (K + 1) x N
 // block (dW rows, then db) to the workspace; a second kernel adds the partials in block
 // order, so the result does not depend on timing.
 constexpr int TW_THREADS = 256;
+constexpr int TW_CTAS_PER_SM = 2;                               // two staging pipelines per SM
 constexpr int TW_BATCH = 8;                                    // row-pair items in flight per thread
 constexpr int TW_A = TC_M * TC_M * 2;                           // A buffer: 128 x 128 BF16
 __host__ __device__ constexpr int tw_buf_bytes(int N) { return TW_A + N * TC_M * 2; }
@@ -407,7 +442,7 @@ __device__ __forceinline__ void stage_transposed(unsigned char* buf, const float
     }
 }
 
-__global__ void __launch_bounds__(TW_THREADS, 1) dense_tc_bwd_weight_kernel(int64_t n, const float* __restrict__ X1,
+__global__ void __launch_bounds__(TW_THREADS, TW_CTAS_PER_SM) dense_tc_bwd_weight_kernel(int64_t n, const float* __restrict__ X1,
                                                                             int K1, const float* __restrict__ X2,
                                                                             int K2, const float* __restrict__ G, int N,
                                                                             float* __restrict__ part,
@@ -640,7 +675,7 @@ extern "C" spx_status spx_dense_backward_weight_tc_workspace_size(int64_t n, int
         return set_error(SPX_INVALID_ARG,
                          "spx_dense_backward_weight_tc_workspace_size: sizes (K <= 128, K %% 4 == 0, N in 16/32/64/128)");
     const int64_t tiles = (n + TC_M - 1) / TC_M;
-    const int64_t parts = tiles < num_sms() ? tiles : num_sms();
+    const int64_t parts = tiles < TW_CTAS_PER_SM * num_sms() ? tiles : TW_CTAS_PER_SM * num_sms();
     *bytes = (size_t)(parts > 0 ? parts : 1) * (size_t)(K + 1) * N * 4 + 256;
     return SPX_OK;
 }
@@ -665,7 +700,7 @@ extern "C" spx_status spx_dense_backward_weight_tc(int64_t n, const float* X1, i
         return SPX_OK;
     }
     const int64_t tiles = (n + TC_M - 1) / TC_M;
-    const int parts = (int)(tiles < num_sms() ? tiles : num_sms());
+    const int parts = (int)(tiles < TW_CTAS_PER_SM * num_sms() ? tiles : TW_CTAS_PER_SM * num_sms());
     static std::atomic<unsigned long long> attr_done{0};
     SPX_TRY(ensure_smem_attr(dense_tc_bwd_weight_kernel, 2 * tw_buf_bytes(TC_NMAX), attr_done,
                              "spx_dense_backward_weight_tc attribute"));
