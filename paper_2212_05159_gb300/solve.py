@@ -45,16 +45,19 @@ class SystemBatch:
         (8 rows per thread); measured on GB300 with 2D diffusion batches, 64 systems of
         256^2 run at 70 ms (Jacobi) and 102 ms (explicit M) with 8 blocks against 94 and
         133 ms with the vectors in global memory, and 256 systems of 32^2..256^2 at 105 ms
-        against 127 ms.  The triangular preconditioners keep ~8 (IC(0)) or ~4 (L L^T, the
-        longer dependent chain) rows of an average system per thread."""
+        against 127 ms.  IC(0) runs its triangular solves on one block per system while
+        the cluster's other blocks wait, so it takes one block per system (128 systems of
+        256^2: 1.15 s against 6.2 s with 8 blocks); L L^T keeps ~4 rows of an average
+        system per thread."""
         if self.launch is not None:
             return self.launch
         if kind in (0, 1, 3):
             want = self.max_rows / (8.0 * 1024.0)
             cl = 2 ** int(np.ceil(np.log2(max(want, 1.0))))
+        elif kind == 4:
+            cl = 1
         else:
-            rows_per_thread = 4.0 if kind == 2 else 8.0
-            want = self.mean_rows / rows_per_thread / 1024.0
+            want = self.mean_rows / 4.0 / 1024.0
             cl = 2 ** int(round(np.log2(max(want, 1.0))))
         return (1024, int(min(16, max(1, cl))), 0)
 
