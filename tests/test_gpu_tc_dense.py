@@ -17,7 +17,7 @@ def _bf16(t):
 
 @pytest.mark.parametrize("n", [1, 127, 300, 4096])
 @pytest.mark.parametrize("K1,K2,N,mode", [(4, 0, 64, 1), (64, 64, 64, 2), (64, 0, 64, 0), (64, 0, 128, 0),
-                                           (32, 16, 32, 1)])
+                                           (32, 16, 32, 1), (12, 8, 16, 1), (60, 68, 128, 0)])
 def test_tc_dense_matches_fp32_kernel(n, K1, K2, N, mode):
     g = torch.Generator().manual_seed(n * 1000 + K1 + K2 + N + mode)
     X1 = torch.randn(n, K1, generator=g).cuda()
@@ -60,7 +60,8 @@ def test_tc_network_forward_close_to_fp32_path():
 
 @pytest.mark.parametrize("n", [1, 127, 300, 4096])
 @pytest.mark.parametrize("N,K1,K2,acc", [(64, 64, 64, 1), (64, 64, 0, 0), (64, 64, 0, 1), (32, 16, 16, 0),
-                                         (128, 64, 0, 0), (64, 4, 0, 0)])
+                                         (128, 64, 0, 0), (64, 4, 0, 0), (4, 16, 0, 0), (20, 8, 12, 1),
+                                         (128, 60, 68, 1)])
 def test_tc_backward_data_matches_fp32_kernel(n, N, K1, K2, acc):
     """[dX1 dX2] (+)= G W^T on the tensor cores against the FP32 kernel on a BF16-rounded G."""
     g = torch.Generator().manual_seed(n * 7 + N + K1 + K2 + acc)
