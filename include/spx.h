@@ -438,7 +438,7 @@ spx_status spx_cg_workspace_size(int32_t n, size_t* bytes);
  * iters, status (spx_status per system: OK, MAXITER, BREAKDOWN, NONFINITE): device
  * int32[nsys]; relres: device float64[nsys], the true relative residual of the
  * returned x.  One launch of thread-block clusters (one cluster per system at a time,
- * shape set by spx_cg_set_launch; for kinds 0, 1 and 3 each block takes 24 bytes of
+ * shape set by spx_cg_set_launch; for kinds 0, 1 and 3 each block takes 192 bytes of
  * dynamic shared memory per thread for its private vectors, see
  * spx_cg_set_vector_residency); capturable in a CUDA graph.  The call's own status reports argument / launch errors only. */
 spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
