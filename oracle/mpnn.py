@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain PyTorch CPU float64
 one statement per step of the architecture below; gradients come from torch autograd.
 
 The network maps an SPD matrix A (CSR) to the values of a lower-triangular L on the
-pattern of tril(A), used as the factored approximate inverse M = L L^T of Section 4.3.
+pattern of tril(A) -- or, as a richer factor, of tril(A + A^2) (the structural pattern of
+the product, every entry any k reaches, plus A's own) -- used as the factored approximate
+inverse M = L L^T of Section 4.3.
 The architecture is chosen here (the paper gives none for this use; the closest is
 the GNN of Section 4.5); parity of the trained weights themselves is unpinned.
 
@@ -14,7 +16,8 @@ the GNN of Section 4.5); parity of the trained weights themselves is unpinned.
   encoder             h = relu(f W0 + b0)                          (4 -> 64)
   3 layers            g = E h  (sparse product on A's pattern with values e)
                       h = h + relu([h, g] Wl + bl)                 (128 -> 64)
-  edge head, tril(A)  t_e = relu(h_i Ua + h_j Ub + e_ij u + c)     (e = (i, j), j <= i)
+  edge head, tril(S)  t_e = relu(h_i Ua + h_j Ub + e_ij u + c)     (e = (i, j), j <= i; S = A or A + A^2,
+                                                                   e_ij = 0 where A has no entry)
                       o_e = t_e . v + (bd if i == j else bo)
   factor              Lhat_e = softplus(o_e) if i == j else o_e;   L_e = d_i Lhat_e
 With v = 0, bo = 0 and softplus(bd) = 1 the factor is L = D^(-1/2): M = D^(-1) (Jacobi).
@@ -61,8 +64,23 @@ def _rows(indptr):
     return np.repeat(np.arange(len(ip) - 1), np.diff(ip))
 
 
-def forward(A, params: dict, want_graph=False):
-    """L values (float64 torch tensor on tril(A)'s pattern) and the tril pattern.
+def square_pattern(A):
+    """Per-row sorted columns of the structural pattern of A + A^2: j is stored in row i when
+    a_ij is stored or a_ik and a_kj are stored for some k (no cancellation)."""
+    ip = np.asarray(A.indptr, np.int64)
+    ix = np.asarray(A.indices, np.int64)
+    rows = []
+    for i in range(A.m):
+        cols = set(ix[ip[i]:ip[i + 1]].tolist())
+        for k in ix[ip[i]:ip[i + 1]]:
+            cols.update(ix[ip[k]:ip[k + 1]].tolist())
+        rows.append(sorted(cols))
+    return rows
+
+
+def forward(A, params: dict, want_graph=False, pattern: str = "A"):
+    """L values (float64 torch tensor on the pattern of tril(A), or of tril(A + A^2) with
+    pattern="A2") and that pattern as (rows, cols).
 
     params: dict of torch float64 tensors (requires_grad as the caller wishes)."""
     n = A.m
@@ -88,9 +106,24 @@ def forward(A, params: dict, want_graph=False):
     for layer in range(1, N_LAYERS + 1):
         g = torch.zeros(n, H, dtype=torch.float64).index_add(0, rows, e[:, None] * h[cols])
         h = h + torch.relu(torch.cat([h, g], dim=1) @ params[f"W{layer}"] + params[f"b{layer}"])
-    # edge head on tril(A)
-    low = cols <= rows
-    ri, ci, el = rows[low], cols[low], e[low]
+    # edge head on tril(A) or tril(A + A^2)
+    if pattern == "A":
+        low = cols <= rows
+        ri, ci, el = rows[low], cols[low], e[low]
+    elif pattern == "A2":
+        pos = {(int(r), int(c)): k for k, (r, c) in enumerate(zip(rows.tolist(), cols.tolist()))}
+        pr, pc = [], []
+        for i, cs in enumerate(square_pattern(A)):
+            for j in cs:
+                if j <= i:
+                    pr.append(i)
+                    pc.append(j)
+        ri = torch.tensor(pr, dtype=torch.int64)
+        ci = torch.tensor(pc, dtype=torch.int64)
+        src = torch.tensor([pos.get((r, c), -1) for r, c in zip(pr, pc)], dtype=torch.int64)
+        el = torch.where(src >= 0, e[src.clamp(min=0)], torch.zeros((), dtype=torch.float64))
+    else:
+        raise ValueError(f"unknown pattern {pattern!r}")
     P = h @ params["Ua"]
     Q = h @ params["Ub"]
     t = torch.relu(P[ri] + Q[ci] + el[:, None] * params["u"] + params["c"])
