@@ -655,11 +655,17 @@ def cg_section(args):
     launch replayed from a CUDA graph) and learned vs Jacobi vs IC(0) on held-out 256^2 systems."""
     from paper_2212_05159_gb300 import learned, pcg_study
     out = {"batch256_jacobi": pcg_study.batch256_jacobi(graph_replay=True)}
-    net = learned.MPNN(seed=0)
-    tr = pcg_study.train(net, steps=args.train_steps, batch=32, n_it=8, gamma=0.8, lr=2e-3)
-    tr.pop("loss_history", None)
-    out["training"] = tr
-    out["eval_256x256"] = pcg_study.evaluate(net, nsys=args.eval_systems, per_batch=args.eval_batch,
+    nets = {}
+    for pattern in args.learned_patterns.split(","):
+        net = learned.MPNN(seed=0)
+        tr = pcg_study.train(net, steps=args.train_steps, batch=32, n_it=8, gamma=0.8, lr=2e-3, workers=4,
+                             pattern=pattern)
+        tr.pop("loss_history", None)
+        name = "learned" if pattern == "A" else f"learned_{pattern}"
+        out["training" if pattern == "A" else f"training_{pattern}"] = tr
+        nets[name] = (net, pattern)
+    out["eval_256x256"] = pcg_study.evaluate(None, nsys=args.eval_systems, per_batch=args.eval_batch,
+                                             methods=("jacobi", *nets, "ic0"), learned_nets=nets,
                                              ic0_systems=min(args.ic0_systems, args.eval_systems))
     return out
 
@@ -705,6 +711,8 @@ def main():
                     help="comma list of: step (always), extras, spgemm, cg, cpu")
     ap.add_argument("--train-steps", type=int, default=313,
                     help="training batches of 32 generated systems (313: the 10k-system training set)")
+    ap.add_argument("--learned-patterns", default="A,A2",
+                    help="factor patterns to train and evaluate: A = tril(A), A2 = tril(A + A^2)")
     ap.add_argument("--eval-systems", type=int, default=1000, help="held-out 256^2 systems")
     ap.add_argument("--eval-batch", type=int, default=256, help="held-out systems per PCG launch")
     ap.add_argument("--ic0-systems", type=int, default=128,

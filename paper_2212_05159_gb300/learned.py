@@ -24,7 +24,7 @@ import torch
 
 from . import abi
 from .csr import CSR
-from .ops import SpGEMMPlan
+from .ops import SpAddPlan, SpGEMMPlan
 
 H = 64
 F_IN = 4
@@ -60,18 +60,33 @@ def default_init(seed: int) -> dict:
 
 
 class Graph:
-    """Per-batch inputs of the network: features, e on A and on tril(A), tril patterns."""
+    """Per-batch inputs of the network: features, e on A and on the factor's pattern.
 
-    def __init__(self, A: CSR):
+    pattern "A": L on tril(A); "A2": L on tril(A + A^2), the structural pattern of the
+    product plus A's own (built with the library's SpGEMM symbolic phase and sparse add),
+    with e_ij = 0 where A has no entry."""
+
+    def __init__(self, A: CSR, pattern: str = "A"):
         dev = A.device
         self.A = A
         n = A.m
         self.n = n
+        self.pattern = pattern
         self.d = torch.empty(n, dtype=torch.float32, device=dev)
         self.e = torch.empty(max(A.nnz, 1), dtype=torch.float32, device=dev)[: A.nnz]
         self.f = torch.empty(n, F_IN, dtype=torch.float32, device=dev)
         self.E = A.with_values(self.e)
-        l_ip, l_ix, self.l_src = abi.spx_tril_pattern(A.struct(), dev)
+        if pattern == "A":
+            base, self._eplan = A, None
+        elif pattern == "A2":
+            sq = SpGEMMPlan(A, A).C
+            self._zeros = torch.zeros(max(sq.nnz, 1), dtype=torch.float32, device=dev)[: sq.nnz]
+            self._eplan = SpAddPlan(self.E, sq.with_values(self._zeros))
+            base = self._eplan.C
+            self._e_base = torch.empty(max(base.nnz, 1), dtype=torch.float32, device=dev)[: base.nnz]
+        else:
+            raise ValueError(f"unknown factor pattern {pattern!r}")
+        l_ip, l_ix, self.l_src = abi.spx_tril_pattern(base.struct(), dev)
         self.Lpat = CSR(l_ip, l_ix, None, (n, n))
         self.e_low = torch.empty(l_ix.numel(), dtype=torch.float32, device=dev)
         self.lt_ip, self.lt_ix, self.lt_perm = self.Lpat.transpose_pattern()
@@ -81,7 +96,11 @@ class Graph:
     def features(self, values: torch.Tensor | None = None):
         """(Re)computes d, e and the node features for A's values (same pattern)."""
         abi.spx_mpnn_features(self.A.struct(values), self.d, self.e, self.f)
-        abi.spx_gather_values(self.l_src, self.e, self.e_low)
+        if self._eplan is None:
+            abi.spx_gather_values(self.l_src, self.e, self.e_low)
+        else:
+            self._eplan.numeric(1.0, 0.0, a_values=self.e, b_values=self._zeros, out=self._e_base)
+            abi.spx_gather_values(self.l_src, self._e_base, self.e_low)
         return self
 
     def LT_struct(self, L_values: torch.Tensor, out: torch.Tensor):
@@ -232,14 +251,16 @@ class MPNN:
 class Trainer:
     """Unrolled-PCG training of the network on block-diagonal batches of systems."""
 
-    def __init__(self, net: MPNN, n_it: int = 4, gamma: float = 0.6, lr: float = 1e-3, tensor_cores: bool = False):
+    def __init__(self, net: MPNN, n_it: int = 4, gamma: float = 0.6, lr: float = 1e-3, tensor_cores: bool = False,
+                 pattern: str = "A"):
         self.net, self.n_it, self.gamma, self.lr = net, n_it, gamma, lr
         self.tensor_cores = tensor_cores
+        self.pattern = pattern
         self.wts = torch.from_numpy(loss_weights(n_it, gamma)).to(net.device)
 
     def loss_and_grad(self, A: CSR, sys_ptr: torch.Tensor, nsys: int, b: torch.Tensor, G: Graph | None = None):
         """Mean loss over the systems and the L gradient (the network is not updated)."""
-        G = G or Graph(A)
+        G = G or Graph(A, self.pattern)
         L, saved = self.net.forward(G, tensor_cores=self.tensor_cores)
         lt_vals = torch.empty_like(L)
         LT = G.LT_struct(L, lt_vals)

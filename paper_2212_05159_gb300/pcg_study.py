@@ -31,19 +31,23 @@ def _gen(nsys, seed, lo, hi, sigma):
 
 def train(net: learned.MPNN, steps: int, batch: int = 32, n_it: int = 8, gamma: float = 0.8,
           lr: float = 2e-3, seed: int = 1, time_budget_s: float | None = None, log=None,
-          tensor_cores: bool = True, workers: int = 4, depth: int = 8):
+          tensor_cores: bool = True, workers: int = 0, depth: int = 8, pattern: str = "A"):
     """Trains on `steps` fresh batches (steps * batch generated systems).  tensor_cores: the
     network's dense products forward and backward on tcgen05, the numerics of inference.
-    Reports the wall time and the GPU time of the training steps (CUDA events)."""
-    tr = learned.Trainer(net, n_it=n_it, gamma=gamma, lr=lr, tensor_cores=tensor_cores)
+    Reports the wall time and the GPU time of the training steps (CUDA events).  pattern: the
+    factor's pattern, tril(A) ("A") or tril(A + A^2) ("A2").  The batches are generated on the
+    host `depth` steps ahead, by one background thread (workers = 0) or by `workers` spawned
+    processes (the calling script must then guard its entry point with
+    `if __name__ == "__main__"`, as spawned processes import it)."""
+    tr = learned.Trainer(net, n_it=n_it, gamma=gamma, lr=lr, tensor_cores=tensor_cores, pattern=pattern)
     import synth
     losses, events = [], []
     t0 = time.perf_counter()
-    # batches are generated on the host by `workers` spawned processes, `depth` ahead
-    ctx = multiprocessing.get_context("spawn")
     st = torch.cuda.current_stream()
     step = -1
-    with cf.ProcessPoolExecutor(workers, mp_context=ctx) as ex:
+    pool = (cf.ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) if workers > 0
+            else cf.ThreadPoolExecutor(1))
+    with pool as ex:
         args = lambda i: (batch, seed * 100003 + i, 32, 128, (0.5, 2.0))  # noqa: E731
         futs = collections.deque(ex.submit(synth.diffusion_system_batch, *args(i))
                                  for i in range(min(depth, steps)))
@@ -70,7 +74,7 @@ def train(net: learned.MPNN, steps: int, batch: int = 32, n_it: int = 8, gamma: 
     return {"steps": step + 1, "systems": (step + 1) * batch, "seconds": time.perf_counter() - t0,
             "gpu_seconds": gpu_ms * 1e-3, "generator_processes": workers,
             "loss_history": losses, "n_it": n_it, "gamma": gamma, "lr": lr, "batch": batch,
-            "tensor_cores": tensor_cores}
+            "tensor_cores": tensor_cores, "pattern": pattern}
 
 
 def _leading(A, ptr, b, k):
@@ -94,9 +98,13 @@ def _timed(fn):
 
 
 def evaluate(net: learned.MPNN, nsys: int = 128, per_batch: int = 64, side: int = 256, seed: int = 777,
-             tol: float = 1e-8, methods=("jacobi", "learned", "ic0"), ic0_systems: int | None = None):
+             tol: float = 1e-8, methods=("jacobi", "learned", "ic0"), ic0_systems: int | None = None,
+             learned_nets: dict | None = None):
     """Iterations and wall time to `tol` for each method over `nsys` held-out systems (IC(0),
-    whose triangular solves are ~20x slower per system, over the first `ic0_systems` only)."""
+    whose triangular solves are ~20x slower per system, over the first `ic0_systems` only).
+    learned_nets: method name -> (network, factor pattern); by default "learned" is `net`
+    on tril(A)."""
+    nets = learned_nets if learned_nets is not None else {"learned": (net, "A")}
     ic0_systems = nsys if ic0_systems is None else ic0_systems
     res = {m: {"iters": [], "ms": 0.0, "setup_ms": 0.0, "converged": 0, "max_relres": 0.0, "systems": 0}
            for m in methods}
@@ -117,9 +125,10 @@ def evaluate(net: learned.MPNN, nsys: int = 128, per_batch: int = 64, side: int 
                 ms, out = _timed(lambda: solve.cg(batch, bt, pc="jacobi", tol=tol, maxit=maxit,
                                                   values=dA.values))
                 setup = 0.0
-            elif m == "learned":
+            elif m in nets:
+                net_m, pattern = nets[m]
                 t0 = time.perf_counter()
-                G = learned.Graph(dA)
+                G = learned.Graph(dA, pattern)
                 ones = torch.ones(G.Lpat.nnz, dtype=torch.float32, device=dA.device)
                 _, plan = learned.explicit_M(G, ones)            # pattern of L L^T: per pattern
                 torch.cuda.synchronize()
@@ -128,7 +137,7 @@ def evaluate(net: learned.MPNN, nsys: int = 128, per_batch: int = 64, side: int 
 
                 def run():
                     G.features(dA.values)
-                    L2, _ = net.forward(G, tensor_cores=True)        # inference on tcgen05
+                    L2, _ = net_m.forward(G, tensor_cores=True)      # inference on tcgen05
                     held["L"] = L2
                     Mv = plan.numeric(L2, _lt_values(G, L2))
                     return solve.cg(batch, bt, pc="M", M=plan.C.with_values(Mv), tol=tol, maxit=maxit)

@@ -86,15 +86,18 @@ def _rand_params(seed):
     return _bf16_round(p)
 
 
-def test_mpnn_forward_backward_match_oracle():
+@pytest.mark.parametrize("pattern", ["A", "A2"])
+def test_mpnn_forward_backward_match_oracle(pattern):
+    """L on tril(A) or tril(A + A^2): pattern bit-exact, values and every parameter
+    gradient against the FP64 oracle."""
     A, ptr = _batch([6, 11, 8], seed=5, sigma=1.5)
     p = _rand_params(7)
     net = learned.MPNN(params=p)
     dA = spx.CSR.from_host(A)
-    G = learned.Graph(dA)
+    G = learned.Graph(dA, pattern)
     L, saved = net.forward(G)
     tp = ompnn.params_to_torch(p)
-    Lo, (ri, ci) = ompnn.forward(A, tp)
+    Lo, (ri, ci) = ompnn.forward(A, tp, pattern=pattern)
     l_ip = host(G.Lpat.indptr)
     rows = np.repeat(np.arange(A.m), np.diff(l_ip))
     np.testing.assert_array_equal(rows, ri)
@@ -123,14 +126,14 @@ def test_initial_network_is_jacobi():
     assert np.all(Lh[~on] == 0)
 
 
-@pytest.mark.parametrize("tensor_cores", [False, True])
-def test_training_beats_the_untrained_start(tensor_cores):
+@pytest.mark.parametrize("tensor_cores,pattern", [(False, "A"), (True, "A"), (True, "A2")])
+def test_training_beats_the_untrained_start(tensor_cores, pattern):
     """A short training run on small diffusion systems must cut held-out PCG iterations
     below the untrained network's (M = D^-1, i.e. Jacobi); with FP32 activations and with
     every dense product on the tensor cores."""
     torch.manual_seed(0)
     net = learned.MPNN(seed=0)
-    tr = learned.Trainer(net, n_it=8, gamma=0.8, lr=3e-3, tensor_cores=tensor_cores)
+    tr = learned.Trainer(net, n_it=8, gamma=0.8, lr=3e-3, tensor_cores=tensor_cores, pattern=pattern)
     for step in range(150):
         A, ptr, _, _ = synth.diffusion_batch(16, seed=100 + step, side_lo=12, side_hi=32, sigma=(0.5, 2.0))
         b = synth.normal(A.m, seed=1000 + step)
@@ -141,7 +144,7 @@ def test_training_beats_the_untrained_start(tensor_cores):
     b = dev(synth.normal(A.m, seed=5))
     _, it_j, st_j, _ = solve.cg(batch, b, pc="jacobi", tol=1e-8)
     it_j = host(it_j).copy()
-    G = learned.Graph(dA)
+    G = learned.Graph(dA, pattern)
     L, _ = net.forward(G, tensor_cores=tensor_cores)
     M, _ = learned.explicit_M(G, L)
     _, it_l, st_l, rr = solve.cg(batch, b, pc="M", M=M, tol=1e-8)
