@@ -303,3 +303,29 @@ def test_vector_residency_is_bitwise_neutral(pc, launch):
     sides = np.sqrt(np.diff(ptr)).astype(int)
     if launch[0] == 256:
         assert (sides * sides <= 2048).any() and (sides * sides > 2048).any()
+
+
+@pytest.mark.parametrize("pc", ["none", "jacobi", "M"])
+@pytest.mark.parametrize("residency", [1, 0])
+def test_empty_and_one_row_systems(pc, residency):
+    """A batch holding an empty system (repeated offset) and a 1 x 1 system between two
+    grids: the empty one reports OK after 0 iterations with residual 0, the 1 x 1 one
+    x = b / a in one iteration, the grids converge as usual."""
+    one = synth.CSR(1, 1, np.array([0, 1]), np.array([0]), np.array([2.0], np.float32))
+    A, ptr = synth.block_diag([synth.diffusion2d(5, 1.0, 1), one, synth.diffusion2d(4, 1.0, 2)])
+    ptr = np.array([0, 25, 25, 26, 42], np.int32)
+    batch = solve.SystemBatch(spx.CSR.from_host(A), ptr)
+    M = _spd_band(A, ptr) if pc == "M" else None
+    b = synth.normal(A.m, seed=3)
+    try:
+        spx.abi.spx_cg_set_vector_residency(residency)
+        x, it, st, rr = solve.cg(batch, dev(b), pc=pc, M=M, tol=1e-8)
+    finally:
+        spx.abi.spx_cg_set_vector_residency(1)
+    x, it, st, rr = host(x), host(it), host(st), host(rr)
+    assert list(st) == [0, 0, 0, 0]
+    assert it[1] == 0 and rr[1] == 0.0
+    assert it[2] == 1 and abs(x[25] - b[25] / 2.0) <= 1e-7 * abs(b[25] / 2.0)
+    for s in (0, 3):
+        As, a, c = _block(A, ptr, s)
+        assert _true_relres(As, x[a:c], b[a:c]) <= 1e-8
