@@ -46,7 +46,7 @@ namespace {
 constexpr int CG_MAX_WARPS = 32;
 // Rows up to this long are multiplied two at a time (spmv_row2).  Five covers the 5-point
 // stencil: 4-6 % faster PCG on 2D diffusion batches than one row at a time; wider paths
-// spill under the 64-register cap (6: no gain, 8: several hundred bytes of spills).
+// spill under the 64-register cap (a 7-entry pair for the explicit M: 9 % slower).
 constexpr int CG_ROW2_W = 5;
 
 // Private vector rows per block kept in shared memory: 8 per thread (6 vectors, 192 bytes
@@ -193,6 +193,13 @@ struct CgBcast {
     int action;                // ACT_* below
 };
 constexpr int ACT_GO = 0, ACT_STOP = 1, ACT_FOLD = 2;
+
+// The FP64 state of one system, kept by thread 0 of each block in shared memory (no other
+// thread reads it, so it holds no registers of the others through the iteration).
+struct CgScal {
+    double bnorm, rz, ref, last_true;
+    int status;
+};
 
 // One row of a sparse product, entries in order; the loads of up to 8 entries are issued
 // together (predicated tail) so that a row costs two dependent round trips, not one per
@@ -379,12 +386,22 @@ __device__ __forceinline__ Vecs make_vecs(const CgArgs& a, float* sv, int lo, in
 template <int NT, int PC, bool SM>
 __device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& cl, unsigned rank, int sid, int lo,
                                            int hi, float* sv, float2 (&red)[CG_MAX_WARPS][4], float2 (&part)[2][4],
-                                           CgBcast& bc, int& slot) {
+                                           CgBcast& bc, CgScal& sc, int& slot) {
     const bool t0 = threadIdx.x == 0;
     const Vecs v = make_vecs<NT, PC, SM>(a, sv, lo, hi);
     // thread 0 of each block keeps the FP64 scalars; every block computes the same ones
-    double bnorm = 0.0, rz = 0.0, ref = 0.0, last_true = 1.0;
-    int status = SPX_MAXITER;
+    double& bnorm = sc.bnorm;
+    double& rz = sc.rz;
+    double& ref = sc.ref;
+    double& last_true = sc.last_true;
+    int& status = sc.status;
+    if (t0) {
+        bnorm = 0.0;
+        rz = 0.0;
+        ref = 0.0;
+        last_true = 1.0;
+        status = SPX_MAXITER;
+    }
 
     // ---- x = 0, r = b, z = M r, p = z
     DF v2[2] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -652,6 +669,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
     __shared__ float2 part[2][4];
     __shared__ int sys_sh;
     __shared__ CgBcast bc;
+    __shared__ CgScal sc;
     extern __shared__ float sv[];
     int slot = 0;
     const bool t0 = threadIdx.x == 0;
@@ -670,9 +688,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
         if constexpr (PC == 0 || PC == 1 || PC == 3)
             in_smem = a.smem_rows >= CG_SMEM_ROWS_PER_THREAD * NT && chunk <= CG_SMEM_ROWS_PER_THREAD * NT;
         if (in_smem)                                            // uniform across the cluster
-            pcg_system<NT, PC, true>(a, cl, rank, sid, lo, hi, sv, red, part, bc, slot);
+            pcg_system<NT, PC, true>(a, cl, rank, sid, lo, hi, sv, red, part, bc, sc, slot);
         else
-            pcg_system<NT, PC, false>(a, cl, rank, sid, lo, hi, sv, red, part, bc, slot);
+            pcg_system<NT, PC, false>(a, cl, rank, sid, lo, hi, sv, red, part, bc, sc, slot);
         cl.sync();                                              // finish before the next system
     }
 }
