@@ -168,3 +168,31 @@ def test_tc_backward_weight_rejects_bad_sizes():
         abi.spx_dense_backward_weight_tc(8, X, 8, None, 0, Gm, 48, dW, None, ws)      # N not a power of two
     with pytest.raises(abi.SpxError):
         abi.spx_dense_backward_weight_tc(8, X, 6, None, 0, Gm[:, :16], 16, dW, None, ws)  # K1 % 4
+
+
+def test_tc_kernels_reject_unaligned_or_unsupported_operands():
+    """The tensor-core entry points check their layout before any launch: rows that do not
+    start on 16 bytes, and sizes outside the supported tiles, are argument errors."""
+    n, K, N = 64, 64, 64
+    buf = torch.zeros(n * K + 1, device="cuda")
+    X_bad = buf[1:].view(n, K)                       # 4-byte offset: not 16-byte aligned
+    X = torch.zeros(n, K, device="cuda")
+    G = torch.zeros(n, N, device="cuda")
+    W = torch.zeros(K, N, dtype=torch.bfloat16, device="cuda")
+    Y = torch.zeros(n, N, device="cuda")
+    dX = torch.zeros(n, K, device="cuda")
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_forward_tc(n, X_bad, K, None, 0, W, None, N, 0, None, Y, None)
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_forward_tc(n, X, K, None, 0, W, None, 40, 0, None, Y, None)      # N % 16
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_backward_data_tc(n, G, N, W, K, 0, X_bad, None, 0)
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_backward_data_tc(n, G, N, W, 6, 0, dX, None, 0)                 # K1 % 4
+    ws = abi.workspace(abi._size("spx_dense_backward_weight_tc_workspace_size", n, K, N), "cuda")
+    dW = torch.zeros(K, N, device="cuda")
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_backward_weight_tc(n, X_bad, K, None, 0, G, N, dW, None, ws)
+    with pytest.raises(abi.SpxError):
+        abi.spx_dense_backward_weight_tc(n, X, K, None, 0, G, N, dW, None, ws[:16])   # workspace too small
+    abi.spx_check_device()
