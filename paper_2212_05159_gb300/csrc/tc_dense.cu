@@ -63,6 +63,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // memory latency (the layer is bandwidth-bound).
 constexpr int STAGE_BATCH = 16;
 constexpr int EPI_BATCH = 8;                                 // epilogue loads in flight per thread
+constexpr int TD_EPI_COLS = 64;                              // data-gradient epilogue part width
 
 __device__ __forceinline__ void stage_rows(unsigned char* sA, const float* __restrict__ X, int K, int kbase, int kpad,
                                            int64_t row0, int64_t n) {
@@ -310,59 +311,66 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_bwd_data_kernel(int64_t n
     if (!ok) {
         if (threadIdx.x == 0 && err) atomicOr(err, 2);
     } else {
-        const int ldst = kout + 4;
+        // epilogue in parts of TD_EPI_COLS accumulator columns, so the staged rows take a
+        // quarter of the 128-column layer's shared memory and more blocks stay resident
+        const int ldst = (kout < TD_EPI_COLS ? kout : TD_EPI_COLS) + 4;
         float* stage = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * ldst;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < kout; c0 += 16) {
-            uint32_t v[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int q = 0; q < 16; q += 4)
-                *reinterpret_cast<float4*>(stage + lane * ldst + c0 + q) =
-                    make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]), __uint_as_float(v[q + 2]),
-                                __uint_as_float(v[q + 3]));
-        }
-        __syncwarp();
-        // the warp's valid rows, float4 pieces in row order (K1, K2 multiples of 4: a piece
-        // never straddles dX1 and dX2); with accumulate the old pieces are loaded EPI_BATCH
-        // at a time before any is added
-        const int k4 = K >> 2;
         const int64_t wrow0 = row0 + warp * 32;
         const int nv = n - wrow0 >= 32 ? 32 : (n > wrow0 ? (int)(n - wrow0) : 0);
-        const int total = nv * k4;
-        auto dst_of = [&](int t) -> float* {
-            const int r = t / k4, c = (t - r * k4) * 4;
-            if (c < K1) return dX1 + (wrow0 + r) * K1 + c;
-            return dX2 ? dX2 + (wrow0 + r) * K2 + (c - K1) : nullptr;
-        };
-        for (int t0 = lane; t0 < total; t0 += EPI_BATCH * 32) {
-            float4 old[EPI_BATCH];
-            if (accumulate) {
+        for (int h = 0; h < K; h += TD_EPI_COLS) {
+            const int hw = kout - h < TD_EPI_COLS ? kout - h : TD_EPI_COLS;     // multiple of 16
+            for (int c0 = 0; c0 < hw; c0 += 16) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr + (uint32_t)(h + c0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 16; q += 4)
+                    *reinterpret_cast<float4*>(stage + lane * ldst + c0 + q) =
+                        make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]), __uint_as_float(v[q + 2]),
+                                    __uint_as_float(v[q + 3]));
+            }
+            __syncwarp();
+            // the warp's valid rows, float4 pieces of output columns [h, h + kh * 4) in row
+            // order (K1, K2 multiples of 4: a piece never straddles dX1 and dX2); with
+            // accumulate the old pieces are loaded EPI_BATCH at a time before any is added
+            const int kh = (K - h < TD_EPI_COLS ? K - h : TD_EPI_COLS) >> 2;
+            const int total = nv * kh;
+            auto dst_of = [&](int t) -> float* {
+                const int r = t / kh, c = h + (t - r * kh) * 4;
+                if (c < K1) return dX1 + (wrow0 + r) * K1 + c;
+                return dX2 ? dX2 + (wrow0 + r) * K2 + (c - K1) : nullptr;
+            };
+            for (int t0 = lane; t0 < total; t0 += EPI_BATCH * 32) {
+                float4 old[EPI_BATCH];
+                if (accumulate) {
+#pragma unroll
+                    for (int u = 0; u < EPI_BATCH; ++u) {
+                        const int t = t0 + u * 32;
+                        float* d = t < total ? dst_of(t) : nullptr;
+                        old[u] = d ? *reinterpret_cast<const float4*>(d) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
 #pragma unroll
                 for (int u = 0; u < EPI_BATCH; ++u) {
                     const int t = t0 + u * 32;
-                    float* d = t < total ? dst_of(t) : nullptr;
-                    old[u] = d ? *reinterpret_cast<const float4*>(d) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (t >= total) break;
+                    float* d = dst_of(t);
+                    if (!d) continue;
+                    const int r = t / kh;
+                    float4 val = *reinterpret_cast<const float4*>(stage + r * ldst + (t - r * kh) * 4);
+                    if (accumulate)
+                        val = make_float4(old[u].x + val.x, old[u].y + val.y, old[u].z + val.z, old[u].w + val.w);
+                    *reinterpret_cast<float4*>(d) = val;
                 }
             }
-#pragma unroll
-            for (int u = 0; u < EPI_BATCH; ++u) {
-                const int t = t0 + u * 32;
-                if (t >= total) break;
-                float* d = dst_of(t);
-                if (!d) continue;
-                const int r = t / k4;
-                float4 val = *reinterpret_cast<const float4*>(stage + r * ldst + (t - r * k4) * 4);
-                if (accumulate)
-                    val = make_float4(old[u].x + val.x, old[u].y + val.y, old[u].z + val.z, old[u].w + val.w);
-                *reinterpret_cast<float4*>(d) = val;
-            }
+            __syncwarp();                                       // stage read before the next part
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -616,6 +624,15 @@ size_t tc_smem_bytes(int K, int N) {
     return tiles > stage ? tiles : stage;
 }
 
+// Shared memory of the data-gradient kernel: G's and W's tiles over N, or the epilogue rows
+// of one part of at most TD_EPI_COLS columns.
+size_t td_smem_bytes(int N, int kout) {
+    const size_t npad = (size_t)((N + 15) & ~15);
+    const size_t tiles = (size_t)TC_M * npad * 2 + (size_t)kout * npad * 2;
+    const size_t stage = (size_t)TC_M * ((kout < TD_EPI_COLS ? kout : TD_EPI_COLS) + 4) * 4;
+    return tiles > stage ? tiles : stage;
+}
+
 bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 }  // namespace
@@ -660,7 +677,7 @@ extern "C" spx_status spx_dense_backward_data_tc(int64_t n, const float* G, int3
     if (n == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
     const int kout = ((K1 + K2) + 15) & ~15;
-    const size_t smem = tc_smem_bytes(N, kout);                 // tiles over N, epilogue over the outputs
+    const size_t smem = td_smem_bytes(N, kout);
     static std::atomic<unsigned long long> attr_done{0};
     SPX_TRY(ensure_smem_attr(dense_tc_bwd_data_kernel, TC_SMEM, attr_done, "spx_dense_backward_data_tc attribute"));
     const int64_t tiles = (n + TC_M - 1) / TC_M;
