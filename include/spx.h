@@ -405,6 +405,18 @@ spx_status spx_spmm_t_noalloc(const spx_csr* AT, const int32_t* perm, const floa
                               int64_t ldg, int32_t k, float* gX, int64_t ldgx, float alpha,
                               float beta, const spx_rowplan* plan, void* stream);
 
+/* Diagonal of A (the paper's A.diagonal(), Section 4.1): for i < min(m, n),
+ * diag[i] = a_ii, or 0 where row i stores no diagonal entry, and pos[i] = the index of
+ * entry (i, i) in A's indices / values, or -1.  Either output may be NULL (diag needs
+ * A's values).  Binary search per row (columns sorted).  Device pointers; asynchronous. */
+spx_status spx_csr_diagonal(const spx_csr* A, float* diag, int32_t* pos, void* stream);
+
+/* VJP of spx_csr_diagonal w.r.t. A's values (a gradient on A's pattern):
+ * g_values[pos[i]] += g_diag[i] for i < nd with pos[i] >= 0 (positions are distinct, so
+ * no two threads touch one entry).  g_values: device float32[nnz], typically zeroed. */
+spx_status spx_diagonal_backward(int32_t nd, const int32_t* pos, const float* g_diag,
+                                 float* g_values, void* stream);
+
 /* dst[e] = src[perm[e]] for e < nnz -- e.g. A^T's values from A's through the
  * permutation of spx_csr_transpose.  Device pointers. */
 spx_status spx_gather_values(int64_t nnz, const int32_t* perm, const float* src, float* dst,

@@ -91,6 +91,8 @@ SIGNATURES = {
     "spx_spgemm_numeric": [_CSRP, _CSRP, _CSRP, _P, _P, _SZ, _P],
     "spx_spgemm_backward": [_CSRP, _CSRP, _CSRP, _P, _P, _P, _P, _P, _P, _P],
     "spx_gather_values": [_I64, _P, _P, _P, _P],
+    "spx_csr_diagonal": [_CSRP, _P, _P, _P],
+    "spx_diagonal_backward": [_I32, _P, _P, _P, _P],
     "spx_cg_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_cg_batched": [_CSRP, _P, _I32, _P, _P, _P, _I32, _P, _CSRP, _CSRP, ctypes.POINTER(_P), _D, _I32, _D,
                        _P, _P, _P, _P, _SZ, _P],
@@ -369,6 +371,15 @@ def spx_spgemm_backward(A: spx_csr, B: spx_csr, C: spx_csr, gc, ga, gb, at_indpt
 
 
 # ------------------------------------------------------------------ solve
+def spx_csr_diagonal(A: spx_csr, diag, pos):
+    _check(lib().spx_csr_diagonal(ctypes.byref(A), ptr(diag), ptr(pos), _stream()), "spx_csr_diagonal")
+
+
+def spx_diagonal_backward(pos, g_diag, g_values):
+    _check(lib().spx_diagonal_backward(int(pos.numel()), ptr(pos), ptr(g_diag), ptr(g_values), _stream()),
+           "spx_diagonal_backward")
+
+
 def spx_gather_values(perm, src, dst):
     _check(lib().spx_gather_values(int(perm.numel()), ptr(perm), ptr(src), ptr(dst), _stream()),
            "spx_gather_values")

@@ -7,7 +7,7 @@ from __future__ import annotations
 
 import torch
 
-from . import ops
+from . import abi, ops
 from .csr import CSR
 
 
@@ -84,3 +84,40 @@ class SpTRSV(torch.autograd.Function):
         lam = ctx.solver.solve(v.contiguous(), l_values, transpose=True)
         g_l = ops.masked_outer(ctx.solver.L, lam, x, -1.0) if ctx.needs_input_grad[0] else None
         return g_l, lam, None
+
+
+class Permute(torch.autograd.Function):
+    """out = values[perm] (e.g. A^T's values in A^T's order); the VJP gathers the gradient
+    back through the inverse permutation."""
+
+    @staticmethod
+    def forward(ctx, values, perm, inv):
+        ctx.inv = inv
+        out = torch.empty_like(values)
+        abi.spx_gather_values(perm, values.contiguous(), out)
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        gv = torch.empty_like(g)
+        abi.spx_gather_values(ctx.inv, g.contiguous(), gv)
+        return gv, None, None
+
+
+class Diagonal(torch.autograd.Function):
+    """d_i = a_ii (0 where absent); the VJP puts g_i on the stored entry (i, i)."""
+
+    @staticmethod
+    def forward(ctx, values, A: CSR):
+        pos = A.diagonal_positions()
+        ctx.pos, ctx.nnz = pos, values.numel()
+        nd = pos.numel()
+        d = torch.empty(max(nd, 1), dtype=torch.float32, device=values.device)[:nd]
+        abi.spx_csr_diagonal(A.struct(values.contiguous()), d, None)
+        return d
+
+    @staticmethod
+    def backward(ctx, g):
+        gv = torch.zeros(ctx.nnz, dtype=torch.float32, device=g.device)
+        abi.spx_diagonal_backward(ctx.pos, g.contiguous(), gv)
+        return gv, None

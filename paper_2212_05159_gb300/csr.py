@@ -114,5 +114,55 @@ class CSR:
             self._t_plan = abi.spx_rowplan_build(st, LONG_ROW_THRESHOLD, self.device, MEDIUM_ROW_THRESHOLD)
         return self._t_plan[1]
 
+    def diagonal_positions(self) -> torch.Tensor:
+        """int32[min(m, n)]: index of entry (i, i) in indices / values, -1 if absent (cached)."""
+        if getattr(self, "_diag_pos", None) is None:
+            nd = min(self.m, self.n)
+            pos = torch.empty(max(nd, 1), dtype=torch.int32, device=self.device)[:nd]
+            abi.spx_csr_diagonal(abi.csr_struct(self.m, self.n, self.indptr, self.indices, None), None, pos)
+            self._diag_pos = pos
+        return self._diag_pos
+
+    def inverse_transpose_perm(self) -> torch.Tensor:
+        """The inverse of transpose_pattern()'s permutation: A.values = A^T.values[inv]."""
+        if getattr(self, "_t_inv", None) is None:
+            t_ip, t_ix, _ = self.transpose_pattern()
+            _, _, inv = abi.spx_csr_transpose(abi.csr_struct(self.n, self.m, t_ip, t_ix, None), self.device)
+            self._t_inv = inv
+        return self._t_inv
+
+    # ------------------------------------------------------------------ the paper's operator syntax
+    def __matmul__(self, other):
+        """A @ X for a dense 1-D or 2-D X (Section 3.1.1 / 3.1.3, differentiable in A's values
+        and X) or A @ B for a CSR B (Section 3.1.2: the structural pattern, differentiable in
+        both value arrays; the pattern is analysed on every call -- keep an ops.SpGEMMPlan to
+        reuse it)."""
+        from . import autograd
+        if isinstance(other, CSR):
+            from .ops import SpGEMMPlan
+            plan = SpGEMMPlan(self, other)
+            return plan.C.with_values(autograd.SpGEMM.apply(self.values, other.values, plan))
+        return autograd.spmm(self, other)
+
+    @property
+    def T(self) -> "CSR":
+        """A^T: the cached transposed pattern with A's values gathered through its
+        permutation (differentiable: the gradient returns through the inverse permutation)."""
+        from . import autograd
+        t_ip, t_ix, perm = self.transpose_pattern()
+        inv = self.inverse_transpose_perm()
+        out = CSR(t_ip, t_ix, None, (self.n, self.m))
+        out._t = (self.indptr, self.indices, inv)
+        out._t_inv = perm
+        if self.values is not None:
+            out.values = autograd.Permute.apply(self.values, perm, inv)
+        return out
+
+    def diagonal(self) -> torch.Tensor:
+        """The diagonal, length min(m, n), 0 where a row stores no diagonal entry;
+        differentiable in A's values (the gradient lands on the stored entries (i, i))."""
+        from . import autograd
+        return autograd.Diagonal.apply(self.values, self)
+
     def __repr__(self):
         return f"CSR({self.m}x{self.n}, nnz={self.nnz}, device={self.device})"
