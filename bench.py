@@ -14,7 +14,12 @@ The headline value is compulsory bytes per step (each CSR array, X, G and the ou
 moved once) divided by the step time: an effective GB/s that earns no credit for
 extra traffic.  The JSON line also carries a roofline object for the dominant kernel,
 a CPU baseline of the FP64 oracle on a bounded sample, an end-to-end number through
-host buffers, sampled SM clocks and extra workloads (k = 128, 3D Poisson 128^3).
+host buffers, sampled SM clocks and extra sections: k = 128 and 3D Poisson 128^3,
+SpGEMM forward and backward, sparse add, the batched triangular solve, SPAI descent, and
+"cg": the 256-system Jacobi batch replayed from a CUDA graph, training of the learned
+factor (tril(A) and tril(A + A^2)) on 10,016 generated systems, and PCG to a true
+relative residual of 1e-8 on 1000 held-out 256^2 systems with Jacobi, each learned
+factor and IC(0) (the first 128).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
