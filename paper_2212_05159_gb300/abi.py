@@ -47,14 +47,16 @@ class spx_rowplan(ctypes.Structure):
                 ("rows_per_group", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("medium_rows", ctypes.c_void_p), ("n_medium", ctypes.c_int32),
                 ("medium_threshold", ctypes.c_int32), ("part_ptr", ctypes.c_void_p),
-                ("n_parts", ctypes.c_int32)]
+                ("n_parts", ctypes.c_int32), ("short_rows", ctypes.c_void_p), ("n_short", ctypes.c_int32)]
 
-    def with_params(self, col_block=0, rows_per_group=0, engine=0, parts=None):
+    def with_params(self, col_block=0, rows_per_group=0, engine=0, parts=None, short_order=True):
         """A copy of this plan (same row lists) with other launch parameters; `parts` is a
-        (part_ptr tensor, n_parts) pair from spx_rowplan_build_parts, None for one pass."""
+        (part_ptr tensor, n_parts) pair from spx_rowplan_build_parts, None for one pass;
+        short_order=False walks the short rows in natural order instead of the plan's."""
         pp, np_ = (parts[0].data_ptr(), int(parts[1])) if parts is not None and parts[1] > 1 else (None, 0)
+        sr, ns = (self.short_rows, self.n_short) if short_order else (None, 0)
         return spx_rowplan(self.long_rows, self.n_long, self.threshold, col_block, rows_per_group, engine,
-                           self.medium_rows, self.n_medium, self.medium_threshold, pp, np_)
+                           self.medium_rows, self.n_medium, self.medium_threshold, pp, np_, sr, ns)
 
 
 _P = ctypes.c_void_p
@@ -72,6 +74,7 @@ SIGNATURES = {
     "spx_check_device": [_P],
     "spx_rowplan_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_rowplan_build": [_CSRP, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
+    "spx_rowplan_build_short": [_CSRP, _I32, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P, _SZ, _P],
     "spx_rowplan_build_medium": [_CSRP, _I32, _I32, _P, ctypes.POINTER(_I32), _P, _SZ, _P],
     "spx_rowplan_build_parts": [_CSRP, _I32, _P, _P],
     "spx_spmm_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
@@ -216,8 +219,9 @@ def spx_csr_validate(A: spx_csr, device) -> None:
            "spx_csr_validate")
 
 
-def spx_rowplan_build(A: spx_csr, threshold: int, device, medium_threshold: int = 0):
-    """Returns (row-list tensors, spx_rowplan); medium_threshold > 0 adds the medium bin."""
+def spx_rowplan_build(A: spx_csr, threshold: int, device, medium_threshold: int = 0, short_order: bool = True):
+    """Returns (row-list tensors, spx_rowplan); medium_threshold > 0 adds the medium bin;
+    short_order adds the length-grouped order of the short rows."""
     sz = _SZ(0)
     _check(lib().spx_rowplan_workspace_size(A.m, ctypes.byref(sz)), "spx_rowplan_workspace_size")
     ws = workspace(sz.value, device)
@@ -234,10 +238,21 @@ def spx_rowplan_build(A: spx_csr, threshold: int, device, medium_threshold: int 
                                               ctypes.byref(n_med), ptr(ws), ws.numel(), _stream()),
                "spx_rowplan_build_medium")
         med = med[: n_med.value].clone() if n_med.value > 0 else med[:0]
+    short = rows[:0]
+    n_short, n_groups = _I32(0), _I32(0)
+    if short_order and A.m > 0:
+        short = torch.empty(max(A.m, 1), dtype=torch.int32, device=device)
+        short_thr = int(medium_threshold) if n_med.value > 0 else int(threshold)
+        _check(lib().spx_rowplan_build_short(ctypes.byref(A), short_thr, ptr(short), ctypes.byref(n_short),
+                                             ctypes.byref(n_groups), ptr(ws), ws.numel(), _stream()),
+               "spx_rowplan_build_short")
+        short = short[: n_short.value].clone() if n_short.value > 0 else short[:1]
+    use_short = short_order and A.m > 0 and n_groups.value > 1       # one group: the natural order
     plan = spx_rowplan(rows.data_ptr() if n_long.value > 0 else None, n_long.value, int(threshold), 0, 0, 0,
                        med.data_ptr() if n_med.value > 0 else None, n_med.value,
-                       int(medium_threshold) if n_med.value > 0 else 0)
-    return (rows, med), plan
+                       int(medium_threshold) if n_med.value > 0 else 0, None, 0,
+                       short.data_ptr() if use_short else None, n_short.value if use_short else 0)
+    return (rows, med, short), plan
 
 
 def spx_rowplan_build_parts(A: spx_csr, n_parts: int, device):

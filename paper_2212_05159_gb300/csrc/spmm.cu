@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(SPMM_THREADS, SPMM_MIN_BLOCKS) spmm_kernel(
     const float* __restrict__ vals, const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t ldx,
     int32_t x_shift, int32_t col_begin, int32_t col_end, float* __restrict__ Y, int64_t ldy, float alpha, float beta,
     int32_t rows_per_group, int32_t threshold, const int32_t* __restrict__ long_rows, int32_t n_long,
-    int32_t long_blocks, const int32_t* __restrict__ med_rows, int32_t n_med, int32_t med_blocks) {
+    int32_t long_blocks, const int32_t* __restrict__ med_rows, int32_t n_med, int32_t med_blocks,
+    const int32_t* __restrict__ short_rows, int32_t n_short) {
     constexpr int G = 32 / LPR;                      // lane groups per warp
     constexpr int SLOTS = (BATCH + LPR - 1) / LPR;
     const int lane = threadIdx.x & 31;
@@ -230,12 +231,14 @@ __global__ void __launch_bounds__(SPMM_THREADS, SPMM_MIN_BLOCKS) spmm_kernel(
         return;
     }
 
-    // ---------------- short rows: one lane group per row
+    // ---------------- short rows: one lane group per row (in the plan's length order if given)
     const int64_t wglobal = ((int64_t)(blockIdx.x - long_blocks - med_blocks) * SPMM_THREADS + threadIdx.x) >> 5;
     const int64_t row0 = (wglobal * G + g) * rows_per_group;
+    const int64_t n_rows = short_rows ? (int64_t)n_short : (int64_t)m;
     for (int p = 0; p < rows_per_group; ++p) {
-        const int64_t row = row0 + p;
-        if (row >= m) break;
+        const int64_t idx = row0 + p;
+        if (idx >= n_rows) break;
+        const int64_t row = short_rows ? (int64_t)short_rows[idx] : idx;
         int a = indptr[row], b = indptr[row + 1];
         if (b - a > threshold) continue;            // a long-row block takes it
         if (split) {
@@ -457,13 +460,15 @@ spx_status launch_lpr(int lpr, unsigned grid, cudaStream_t st, const spx_csr* A,
                       const int32_t* seg_e, int32_t accumulate, const int32_t* perm,
                       const float* vals, const float* X, int64_t ldx, int32_t xs, int32_t c0, int32_t c1, float* Y,
                       int64_t ldy, float alpha, float beta, int32_t rpg, int32_t thr, const int32_t* lr,
-                      int32_t n_long, int32_t long_blocks, const int32_t* mr, int32_t n_med, int32_t med_blocks) {
+                      int32_t n_long, int32_t long_blocks, const int32_t* mr, int32_t n_med, int32_t med_blocks,
+                      const int32_t* sr, int32_t n_short) {
 #define SPX_SPMM_CASE(L)                                                                                        \
     case L:                                                                                                     \
         spmm_kernel<VEC, L, PERM><<<grid, SPMM_THREADS, 0, st>>>(A->m, A->indptr, seg_b, seg_e, accumulate,      \
                                                                  A->indices, vals, perm, X, ldx,                  \
                                                                  xs, c0, c1, Y, ldy, alpha, beta, rpg, thr, lr,  \
-                                                                 n_long, long_blocks, mr, n_med, med_blocks);    \
+                                                                 n_long, long_blocks, mr, n_med, med_blocks, sr, \
+                                                                 n_short);                                        \
         break;
     switch (lpr) {
         SPX_SPMM_CASE(1)
@@ -532,9 +537,16 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
         const int64_t want = ((int64_t)n_med + 2 * SPMM_WARPS - 1) / (2 * SPMM_WARPS);
         med_blocks = (int32_t)(want < 8 * num_sms() ? want : 8 * num_sms());
     }
+    // the short rows in the plan's order (grouped by length, so the groups of a warp walk
+    // rows of about the same length), or all rows in natural order
+    const int32_t* short_rows = plan && plan->short_rows ? plan->short_rows : nullptr;
+    const int32_t n_short = short_rows ? plan->n_short : 0;
+    if (short_rows && (n_short < 0 || n_short > A->m))
+        return set_error(SPX_INVALID_ARG, "%s: bad short-row order", who);
     const int G = 32 / sh.lpr;
     const int64_t rows_per_block = (int64_t)SPMM_WARPS * G * sh.rpg;
-    const int64_t short_blocks = ((int64_t)A->m + rows_per_block - 1) / rows_per_block;
+    const int64_t n_rows = short_rows ? (int64_t)n_short : (int64_t)A->m;
+    const int64_t short_blocks = (n_rows + rows_per_block - 1) / rows_per_block;
     const int64_t grid = short_blocks + long_blocks + med_blocks;
     if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
     if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, sh.cb, slab_ws, st));
@@ -574,7 +586,8 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
                 spx_status s = launch_lpr<4, false>(sh.lpr, (unsigned)(long_blocks + med_blocks), st, A,
                                                     A->indptr, A->indptr + 1, 0, perm, vals,
                                                     Xp, ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold,
-                                                    long_rows, n_long, long_blocks, med_rows, n_med, med_blocks);
+                                                    long_rows, n_long, long_blocks, med_rows, n_med, med_blocks,
+                                                    nullptr, 0);
                 if (s != SPX_OK) return s;
                 SPX_CHECK_LAUNCH(who);
             }
@@ -593,10 +606,12 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
             const int32_t accum = p > 0 ? 1 : 0;
             spx_status s = vec4 ? launch_lpr<4, PERM>(sh.lpr, (unsigned)grid, st, A, sb, se, accum, perm, vals, Xp,
                                                       ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold,
-                                                      long_rows, n_long, long_blocks, med_rows, n_med, med_blocks)
+                                                      long_rows, n_long, long_blocks, med_rows, n_med, med_blocks,
+                                                      short_rows, n_short)
                                 : launch_lpr<1, PERM>(sh.lpr, (unsigned)grid, st, A, sb, se, accum, perm, vals, Xp,
                                                       ldp, xs, c0, c1, Y, ldy, alpha, beta, sh.rpg, threshold,
-                                                      long_rows, n_long, long_blocks, med_rows, n_med, med_blocks);
+                                                      long_rows, n_long, long_blocks, med_rows, n_med, med_blocks,
+                                                      short_rows, n_short);
             if (s != SPX_OK) return s;
             SPX_CHECK_LAUNCH(who);
         }
@@ -618,6 +633,36 @@ __global__ void long_compact_kernel(int32_t m, const int32_t* __restrict__ flags
                                     int32_t* __restrict__ long_rows) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < m && flags[i]) long_rows[pos[i]] = (int32_t)i;
+}
+
+// Short-row order: rows of at most thr entries grouped by their count of 8-entry batches
+// (counts above SHORT_KEY_MAX share the last group), groups longest first, row ids
+// increasing within a group -- a stable counting sort, one flag / scan / compact pass per
+// group, the running count kept on the device.
+constexpr int SHORT_KEY_MAX = 8;
+
+__global__ void short_key_flag_kernel(int32_t m, const int32_t* __restrict__ indptr, int32_t thr, int32_t key,
+                                      int32_t* __restrict__ flags) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int len = indptr[i + 1] - indptr[i];
+    int k = (len + BATCH - 1) / BATCH;
+    if (k > SHORT_KEY_MAX) k = SHORT_KEY_MAX;
+    flags[i] = (len <= thr && k == key) ? 1 : 0;
+}
+
+__global__ void short_compact_kernel(int32_t m, const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
+                                     const int32_t* __restrict__ base, int32_t* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m && flags[i]) out[*base + pos[i]] = (int32_t)i;
+}
+
+// base[0]: rows placed so far; base[1]: non-empty groups so far
+__global__ void short_count_kernel(int32_t m, const int32_t* __restrict__ pos, int32_t* __restrict__ base) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        base[0] += pos[m];
+        base[1] += pos[m] > 0 ? 1 : 0;
+    }
 }
 
 // part_ptr[(p - 1) * m + i] = first entry of row i with column >= p * w (binary search in
@@ -643,7 +688,7 @@ __global__ void part_split_kernel(int32_t m, const int32_t* __restrict__ indptr,
 size_t rowplan_ws(int32_t m) {
     size_t a = ((size_t)m * 4 + 255) & ~size_t(255);
     size_t b = (((size_t)m + 1) * 4 + 255) & ~size_t(255);
-    return a + b + scan_workspace_bytes<int32_t>(m);
+    return a + b + scan_workspace_bytes<int32_t>(m) + 256;     // + the short order's running count
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -873,4 +918,42 @@ extern "C" spx_status spx_spmm_t_noalloc(const spx_csr* AT, const int32_t* perm,
     SPX_CHECK_LAUNCH("spx_spmm_t_noalloc gather");
     return launch_spmm<false>(AT, nullptr, tv, G, ldg, k, gX, ldgx, alpha, beta, plan, nullptr, 0, st,
                               "spx_spmm_t_noalloc");
+}
+
+extern "C" spx_status spx_rowplan_build_short(const spx_csr* A, int32_t threshold, int32_t* short_rows,
+                                              int32_t* n_short_host, int32_t* n_groups_host, void* ws,
+                                              size_t ws_bytes, void* stream) {
+    SPX_TRY(check_csr(A, false, "spx_rowplan_build_short"));
+    if (!n_short_host || (A->m > 0 && !short_rows) || threshold < 0)
+        return set_error(SPX_INVALID_ARG, "spx_rowplan_build_short: bad arguments");
+    const size_t need = rowplan_ws(A->m);
+    if (!ws || ws_bytes < need)
+        return set_error(SPX_OOM_WORKSPACE, "spx_rowplan_build_short: workspace %zu < %zu", ws_bytes, need);
+    *n_short_host = 0;
+    if (n_groups_host) *n_groups_host = 0;
+    if (A->m == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    char* w = static_cast<char*>(ws);
+    int32_t* flags = (int32_t*)w;
+    int32_t* pos = (int32_t*)(w + (((size_t)A->m * 4 + 255) & ~size_t(255)));
+    int32_t* sws = (int32_t*)((char*)pos + ((((size_t)A->m + 1) * 4 + 255) & ~size_t(255)));
+    int32_t* base = (int32_t*)(w + need - 256);
+    SPX_CUDA(cudaMemsetAsync(base, 0, 2 * sizeof(int32_t), st), "spx_rowplan_build_short memset");
+    const unsigned blocks = (unsigned)((A->m + 255) / 256);
+    for (int key = SHORT_KEY_MAX; key >= 0; --key) {
+        short_key_flag_kernel<<<blocks, 256, 0, st>>>(A->m, A->indptr, threshold, key, flags);
+        SPX_CHECK_LAUNCH("short_key_flag");
+        SPX_TRY((scan_counts<int32_t, int32_t>(flags, pos, A->m, sws, st)));
+        short_compact_kernel<<<blocks, 256, 0, st>>>(A->m, flags, pos, base, short_rows);
+        SPX_CHECK_LAUNCH("short_compact");
+        short_count_kernel<<<1, 32, 0, st>>>(A->m, pos, base);
+        SPX_CHECK_LAUNCH("short_count");
+    }
+    int32_t counts[2] = {0, 0};
+    SPX_CUDA(cudaMemcpyAsync(counts, base, sizeof(counts), cudaMemcpyDeviceToHost, st),
+             "spx_rowplan_build_short copy");
+    SPX_CUDA(cudaStreamSynchronize(st), "spx_rowplan_build_short sync");
+    *n_short_host = counts[0];
+    if (n_groups_host) *n_groups_host = counts[1];
+    return SPX_OK;
 }

@@ -331,3 +331,41 @@ def test_spmm_autotune_entry_point(mat):
     abi.spx_check_device()
     assert_close_normalised(host(Y), oracle.spmm(A, X), oracle.spmm(abs_csr(A), np.abs(X)),
                             what=f"spmm {name} autotuned rpg={plan.rows_per_group} engine={plan.engine}")
+
+
+@pytest.mark.parametrize("k", [8, 32, 128])
+def test_short_row_order_is_bitwise_neutral(mat, k):
+    """The plan's length-grouped short-row order only reschedules rows: SpMM, A^T G and
+    SDDMM give bit-identical results with and without it; the order is a permutation of
+    the short rows grouped by 8-entry batch count, longest group first."""
+    from paper_2212_05159_gb300 import abi
+    name, A, dA = mat
+    X, G = dev(synth.normal((A.n, k), seed=50)), dev(synth.normal((A.m, k), seed=51))
+    base, tb = dA.plan(), dA.t_plan()
+    _, _, perm = dA.transpose_pattern()
+    outs = []
+    for so in (True, False):
+        plan, tplan = base.with_params(k, 4, 0, short_order=so), tb.with_params(k, 4, 0, short_order=so)
+        Y = torch.empty(A.m, k, device="cuda")
+        abi.spx_spmm(dA.struct(), X, Y, 1.0, 0.0, plan)
+        gX = torch.empty(A.n, k, device="cuda")
+        abi.spx_spmm_t(dA.t_struct(), perm, G, gX, 1.0, 0.0, tplan,
+                       abi.workspace(abi.spx_spmm_t_workspace_size(dA.t_struct(), k, tplan), "cuda"))
+        gA = torch.empty(A.nnz, device="cuda")
+        abi.spx_sddmm(dA.struct(), G, X, gA, 1.0, k, abi.workspace(abi.spx_sddmm_workspace_size(dA.struct(), k, k),
+                                                                  "cuda"), plan=plan)
+        outs.append((host(Y), host(gX), host(gA)))
+    for u, w in zip(*outs):
+        np.testing.assert_array_equal(u, w)
+    if base.short_rows:
+        rows_t = dA._plan[0][2]
+        order = host(rows_t)[: base.n_short]
+        lens = np.diff(np.asarray(A.indptr, np.int64))
+        thr = base.medium_threshold if base.n_medium > 0 else base.threshold
+        short = np.nonzero(lens <= thr)[0]
+        assert sorted(order.tolist()) == short.tolist()
+        key = np.minimum((lens[order] + 7) // 8, 8)
+        assert np.all(np.diff(key) <= 0)
+        for kk in np.unique(key):
+            ids = order[key == kk]
+            assert np.all(np.diff(ids) > 0)
