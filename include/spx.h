@@ -145,7 +145,8 @@ spx_status spx_rowplan_build_parts(const spx_csr* A, int32_t n_parts, int32_t* p
 spx_status spx_spmm_workspace_size(const spx_csr* A, int32_t k, const spx_rowplan* plan,
                                    size_t* bytes);
 
-/* Builds a plan's short-row order: the ids of the rows with at most `threshold` entries,
+/* Scheduling of the row-wise products of Sections 3.1.1 / 3.1.3 (SpMM, A^T G) and of the
+ * SDDMM VJP.  Builds a plan's short-row order: the ids of the rows with at most `threshold` entries,
  * grouped by their number of 8-entry batches (more than 8 batches share one group),
  * groups in decreasing length, ids increasing within a group (stable), into short_rows
  * (device int32[m]); count to *n_short_host, number of non-empty groups to *n_groups_host
