@@ -440,11 +440,34 @@ __global__ void __launch_bounds__(BK_WARPS * 32) spmm_bulk_kernel(
     }
 }
 
+// out[e] = vals[perm[e]].  Each thread takes GV_UNROLL grid-strided entries at a time and
+// issues all their index loads, then all their value loads, before any store: the value
+// gathers depend on the index loads, so one entry per iteration would leave a single
+// dependent pair in flight per thread.
+constexpr int GV_UNROLL = 8;
+
 __global__ void gather_values_kernel(int64_t nnz, const int32_t* __restrict__ perm, const float* __restrict__ vals,
                                      float* __restrict__ out) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += stride)
-        __stcs(out + e, __ldg(vals + ld_stream(perm + e)));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < nnz; e0 += stride * GV_UNROLL) {
+        int32_t p[GV_UNROLL];
+#pragma unroll
+        for (int u = 0; u < GV_UNROLL; ++u) {
+            const int64_t e = e0 + u * stride;
+            p[u] = e < nnz ? ld_stream(perm + e) : 0;
+        }
+        float v[GV_UNROLL];
+#pragma unroll
+        for (int u = 0; u < GV_UNROLL; ++u) {
+            const int64_t e = e0 + u * stride;
+            v[u] = e < nnz ? __ldg(vals + p[u]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < GV_UNROLL; ++u) {
+            const int64_t e = e0 + u * stride;
+            if (e < nnz) __stcs(out + e, v[u]);
+        }
+    }
 }
 
 int ilog2_ceil(int64_t x) {
