@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or \
             os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC,
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC,
                                "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -68,6 +68,9 @@ def _declare(lib):
         "orc_sddmm": (None, [_I, _P, _P, _P, _P, _I, _P]),
         "orc_transpose": (None, [_I, _I, _P, _P, _P, _P, _P]),
         "orc_spmm_t": (None, [_I, _I, _P, _P, _P, _P, _I, _P]),
+        "orc_spmm_mt": (ctypes.c_int, [_I, _P, _P, _P, _P, _I, _P, ctypes.c_int]),
+        "orc_sddmm_mt": (ctypes.c_int, [_I, _P, _P, _P, _P, _I, _P, ctypes.c_int]),
+        "orc_spmm_t_mt": (ctypes.c_int, [_I, _P, _P, _P, _P, _P, _I, _P, ctypes.c_int]),
         "orc_spgemm_count": (_I, [_I, _I, _P, _P, _P, _P, _P, _P]),
         "orc_spgemm_fill": (None, [_I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
         "orc_spgemm_grad_a": (None, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -141,6 +144,41 @@ def spmm_t(A, G):
     ip, ix, v = _i32(A.indptr), _i32(A.indices), _f64(A.values)
     _L().orc_spmm_t(A.m, A.n, _p(ip), _p(ix), _p(v), _p(G2), k, _p(gX))
     return gX.reshape(-1) if vec else gX
+
+
+def spmm_mt(A, X, threads):
+    """spmm on `threads` host threads (row blocks of equal entry counts); equal bit for bit
+    to spmm.  Returns (Y, threads used)."""
+    X2 = _f64(X).reshape(A.n, -1)
+    k = X2.shape[1]
+    Y = np.empty((A.m, k), dtype=np.float64)
+    ip, ix, v = _i32(A.indptr), _i32(A.indices), _f64(A.values)
+    used = _L().orc_spmm_mt(A.m, _p(ip), _p(ix), _p(v), _p(X2), k, _p(Y), int(threads))
+    return Y, used
+
+
+def sddmm_mt(A, G, X, threads):
+    """sddmm on `threads` host threads; equal bit for bit to sddmm.  Returns (out, threads)."""
+    G = _f64(G).reshape(A.m, -1)
+    X = _f64(X).reshape(A.n, -1)
+    k = G.shape[1]
+    out = np.empty(A.nnz, dtype=np.float64)
+    ip, ix = _i32(A.indptr), _i32(A.indices)
+    used = _L().orc_sddmm_mt(A.m, _p(ip), _p(ix), _p(G), _p(X), k, _p(out), int(threads))
+    return out, used
+
+
+def spmm_t_mt(A, G, threads, t=None):
+    """spmm_t on `threads` host threads as rows of the transpose (t = transpose(A), computed
+    here if not given); equal bit for bit to spmm_t.  Returns (gX, threads used)."""
+    t_ip, t_ix, perm = t if t is not None else transpose(A)
+    G2 = _f64(G).reshape(A.m, -1)
+    k = G2.shape[1]
+    gX = np.empty((A.n, k), dtype=np.float64)
+    v = _f64(A.values)
+    used = _L().orc_spmm_t_mt(A.n, _p(_i32(t_ip)), _p(_i32(t_ix)), _p(_i32(perm)), _p(v), _p(G2), k, _p(gX),
+                              int(threads))
+    return gX, used
 
 
 def spgemm_count(A, B):

@@ -21,6 +21,22 @@ the GNN of Section 4.5); parity of the trained weights themselves is unpinned.
                       o_e = t_e . v + (bd if i == j else bo)
   factor              Lhat_e = softplus(o_e) if i == j else o_e;   L_e = d_i Lhat_e
 With v = 0, bo = 0 and softplus(bd) = 1 the factor is L = D^(-1/2): M = D^(-1) (Jacobi).
+
+Two options of `forward` serve the parity tests of the GPU network:
+  bf16=True      the operands of every dense product (the encoder, the three layers and
+                 the two heads P = h Ua, Q = h Ub) are rounded to BF16 where a
+                 tensor-core kernel rounds them: the activations in the forward product;
+                 in the reverse pass the incoming gradient G of the product output, for
+                 both dX = bf(G) W^T and dW = bf(X)^T bf(G).  Weights hold BF16 values
+                 already; biases, the aggregation E h, the edge head and every sum stay
+                 in float64.  A value is rounded as a float32 kernel value is: to float32
+                 first, then to BF16 (round to nearest even).  With bf16=False the network
+                 is unchanged (exact products).
+`error_scale` gives the elementwise normaliser of the parity tests: for L and for every
+parameter gradient, the last product that produces it evaluated on absolute values
+(|X||W| + |b| forward, |X|^T |G| for a weight gradient), from this oracle's own float64
+intermediates -- the |A||X| normaliser of a single sparse product, applied to the
+network's final steps.
 """
 from __future__ import annotations
 
@@ -59,6 +75,71 @@ def init_params(seed: int, dtype=np.float32):
     return p
 
 
+def bf16_round(x: torch.Tensor) -> torch.Tensor:
+    """x rounded as a kernel rounds a float32 value to BF16: to float32 (nearest), then
+    to BF16 (nearest, ties to even); returned in float64."""
+    return x.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+class _Bf16Product(torch.autograd.Function):
+    """X W with BF16 operands: the forward rounds the activations X (W is BF16 already);
+    the reverse rounds the incoming gradient G once and uses it in both products,
+    dX = bf(G) W^T and dW = bf(X)^T bf(G), summed in float64."""
+
+    @staticmethod
+    def forward(ctx, X, W):
+        Xr = bf16_round(X)
+        ctx.save_for_backward(Xr, W)
+        return Xr @ W
+
+    @staticmethod
+    def backward(ctx, G):
+        Xr, W = ctx.saved_tensors
+        Gr = bf16_round(G)
+        return Gr @ W.t(), Xr.t() @ Gr
+
+
+class _MagnitudeProduct(torch.autograd.Function):
+    """X W forward; the reverse pass takes both products on absolute values,
+    dX = |G| |W|^T and dW = S_X^T |G|, with S_X >= |X| the error scale of the forward
+    operand (the first-order bound of rounding errors carried backwards, used by
+    `error_scale`)."""
+
+    @staticmethod
+    def forward(ctx, X, W, S_X):
+        ctx.save_for_backward(W, S_X)
+        return X @ W
+
+    @staticmethod
+    def backward(ctx, G):
+        W, S_X = ctx.saved_tensors
+        Ga = G.abs()
+        return Ga @ W.abs().t(), S_X.t() @ Ga, None
+
+
+class _MagnitudeScale(torch.autograd.Function):
+    """s[:, None] * X (s a fixed weight per row, X differentiable); reverse |s| |G|."""
+
+    @staticmethod
+    def forward(ctx, s, X):
+        ctx.save_for_backward(s)
+        return s[:, None] * X
+
+    @staticmethod
+    def backward(ctx, G):
+        (s,) = ctx.saved_tensors
+        return None, s.abs()[:, None] * G.abs()
+
+
+def _product(bf16: bool, magnitude: bool = False):
+    """X W as the chosen mode computes it; S (magnitude mode only) is X's error scale."""
+    if magnitude:
+        return lambda X, W, S=None: _MagnitudeProduct.apply(X, W, X.detach().abs() if S is None else S)
+    if bf16:
+        return lambda X, W, S=None: _Bf16Product.apply(X, W)
+    return lambda X, W, S=None: X @ W
+
+
 def _rows(indptr):
     ip = np.asarray(indptr, np.int64)
     return np.repeat(np.arange(len(ip) - 1), np.diff(ip))
@@ -78,11 +159,25 @@ def square_pattern(A):
     return rows
 
 
-def forward(A, params: dict, want_graph=False, pattern: str = "A"):
+def forward(A, params: dict, want_graph=False, pattern: str = "A", bf16: bool = False,
+            record: dict | None = None, magnitude: bool = False):
     """L values (float64 torch tensor on the pattern of tril(A), or of tril(A + A^2) with
     pattern="A2") and that pattern as (rows, cols).
 
-    params: dict of torch float64 tensors (requires_grad as the caller wishes)."""
+    params: dict of torch float64 tensors (requires_grad as the caller wishes).
+    bf16: see the module docstring.  record: if given, filled with the intermediates
+    (features, layer inputs and pre-activations, heads, edge terms) for `error_scale`.
+    magnitude: the same forward values, with a reverse pass that takes every product on
+    absolute values (for `error_scale`); the forward operand of a weight gradient enters
+    with its error scale: the absolute form of the operation that produced it, carried
+    along the residual path (S_h + mask (|X||W| + |b|) for a layer output h + relu(X W + b),
+    |E| |h| for an aggregate, mask (|h_i| |Ua| + |h_j| |Ub| + |e| |u| + |c|) for the
+    edge activation)."""
+    mm = _product(bf16, magnitude)
+    mm_edge = _product(False, magnitude)          # the edge head is not a BF16 product
+    scale = _MagnitudeScale.apply if magnitude else (lambda w, X: w[:, None] * X)
+    act = torch.relu
+    rec = record if record is not None else {}
     n = A.m
     rows = torch.from_numpy(_rows(A.indptr))
     cols = torch.from_numpy(np.asarray(A.indices, np.int64))
@@ -102,10 +197,30 @@ def forward(A, params: dict, want_graph=False, pattern: str = "A"):
     mx = torch.where(has, mx, torch.zeros_like(mx))
     f = torch.stack([torch.ones(n, dtype=torch.float64), s, mn, mx], dim=1)
     # encoder and message passing
-    h = torch.relu(f @ params["W0"] + params["b0"])
+    def absf(name):
+        return params[name].detach().abs()
+
+    with torch.no_grad():
+        sf = torch.stack([torch.ones(n, dtype=torch.float64),
+                          torch.zeros(n, dtype=torch.float64).index_add(0, rows[off], e[off].abs()),
+                          mn.abs(), mx.abs()], dim=1)
+    u = mm(f, params["W0"], sf) + params["b0"]
+    rec["X"], rec["U"] = [f], [u]
+    h = act(u)
+    with torch.no_grad():
+        sh = (u > 0) * (sf @ absf("W0") + absf("b0"))
     for layer in range(1, N_LAYERS + 1):
-        g = torch.zeros(n, H, dtype=torch.float64).index_add(0, rows, e[:, None] * h[cols])
-        h = h + torch.relu(torch.cat([h, g], dim=1) @ params[f"W{layer}"] + params[f"b{layer}"])
+        g = torch.zeros(n, H, dtype=torch.float64).index_add(0, rows, scale(e, h[cols]))
+        x = torch.cat([h, g], dim=1)
+        with torch.no_grad():
+            sg = torch.zeros(n, H, dtype=torch.float64).index_add(0, rows, e.abs()[:, None] * h.detach().abs()[cols])
+            sx = torch.cat([sh, sg], dim=1)
+        u = mm(x, params[f"W{layer}"], sx) + params[f"b{layer}"]
+        rec["X"].append(x)
+        rec["U"].append(u)
+        with torch.no_grad():
+            sh = sh + (u > 0) * (x.detach().abs() @ absf(f"W{layer}") + absf(f"b{layer}"))
+        h = h + act(u)
     # edge head on tril(A) or tril(A + A^2)
     if pattern == "A":
         low = cols <= rows
@@ -124,13 +239,19 @@ def forward(A, params: dict, want_graph=False, pattern: str = "A"):
         el = torch.where(src >= 0, e[src.clamp(min=0)], torch.zeros((), dtype=torch.float64))
     else:
         raise ValueError(f"unknown pattern {pattern!r}")
-    P = h @ params["Ua"]
-    Q = h @ params["Ub"]
-    t = torch.relu(P[ri] + Q[ci] + el[:, None] * params["u"] + params["c"])
+    P = mm(h, params["Ua"], sh)
+    Q = mm(h, params["Ub"], sh)
+    s_pre = P[ri] + Q[ci] + scale(el, params["u"].expand(len(el), H)) + params["c"]
+    t = act(s_pre)
+    with torch.no_grad():
+        ha = h.detach().abs()
+        st = (s_pre > 0) * ((ha @ absf("Ua"))[ri] + (ha @ absf("Ub"))[ci] + el.abs()[:, None] * absf("u") + absf("c"))
     isd = ri == ci
-    o = t @ params["v"] + torch.where(isd, params["bd"], params["bo"])
+    o = mm_edge(t, params["v"][:, None], st)[:, 0] + torch.where(isd, params["bd"], params["bo"])
     lhat = torch.where(isd, torch.nn.functional.softplus(o), o)
     L = d[ri] * lhat
+    rec.update({"h": h, "P": P, "Q": Q, "s": s_pre, "t": t, "el": el, "o": o, "lhat": lhat,
+                "d": d, "ri": ri, "diag": isd})
     if want_graph:
         return L, (ri.numpy(), ci.numpy()), {"h": h, "e": e, "f": f}
     return L, (ri.numpy(), ci.numpy())
@@ -138,3 +259,27 @@ def forward(A, params: dict, want_graph=False, pattern: str = "A"):
 
 def params_to_torch(p: dict, requires_grad=True):
     return {k: torch.tensor(np.asarray(v, np.float64), requires_grad=requires_grad) for k, v in p.items()}
+
+
+def error_scale(A, params: dict, gL=None, pattern: str = "A", bf16: bool = False):
+    """Elementwise normaliser of the parity tests of the network, from float64 intermediates.
+
+    Returns (N_L, N_grad).  N_L = d_i (|t_e| . |v| + |bias_e| + |Lhat_e|): the absolute
+    form of the edge head's last product (plus the softplus value on the diagonal).  With
+    an upstream gradient gL on L's entries, N_grad[name] is the parameter gradient of the
+    reverse pass taken on absolute values from |gL| (`magnitude`): every product of the
+    reverse pass as |G| |W|^T and |X|^T |G|, every fixed weight (e, d) by its absolute
+    value, relu and softplus derivatives as they are.  It is the first-order bound of the
+    rounding errors a float32 reverse pass accumulates, carried from |gL| to each
+    parameter (the |A^T| |G| normaliser of a single transposed product, composed).
+    params: dict of numpy arrays."""
+    tp = params_to_torch(params, requires_grad=gL is not None)
+    rec = {}
+    L, _ = forward(A, tp, pattern=pattern, bf16=bf16, record=rec, magnitude=True)
+    with torch.no_grad():
+        bias = torch.where(rec["diag"], tp["bd"], tp["bo"]).abs()
+        N_L = (rec["d"][rec["ri"]] * (rec["t"].abs() @ tp["v"].abs() + bias + rec["lhat"].abs())).numpy()
+    if gL is None:
+        return N_L, None
+    (L * torch.from_numpy(np.abs(np.asarray(gL, np.float64)))).sum().backward()
+    return N_L, {k: v.grad.numpy().copy() for k, v in tp.items()}

@@ -431,3 +431,112 @@ done:
     free(r); free(z); free(p); free(q); free(t);
     return status;
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Row-parallel variants, for timing the oracle on every host core (the CPU baseline).
+ * Each thread takes a contiguous block of output rows holding about the same number of
+ * stored entries and runs the serial loops above on it, so every output is the same
+ * sum in the same order as in the serial routine: the results are equal bit for bit.
+ * A^T G runs as rows of the transpose (orc_transpose's pattern and permutation):
+ * gX[j,:] = sum over the entries of column j of A, in increasing row order, of
+ * A_e G[i,:] -- the terms and order of orc_spmm_t's scatter, started from zero. */
+#include <pthread.h>
+
+typedef struct {
+    int op;                         /* 0 spmm, 1 sddmm, 2 spmm on the transpose */
+    i64 r0, r1;
+    const i32 *indptr, *indices, *perm;
+    const double *vals, *A, *B;     /* spmm: X; sddmm: G, X; transpose: G */
+    i64 k;
+    double *out;
+} orc_job;
+
+static void *orc_run_job(void *arg)
+{
+    orc_job *j = (orc_job *)arg;
+    const i64 k = j->k;
+    for (i64 i = j->r0; i < j->r1; ++i) {
+        if (j->op == 0) {
+            for (i64 c = 0; c < k; ++c) {
+                double s = 0.0;
+                for (i64 e = j->indptr[i]; e < j->indptr[i + 1]; ++e)
+                    s += j->vals[e] * j->A[(i64)j->indices[e] * k + c];
+                j->out[i * k + c] = s;
+            }
+        } else if (j->op == 1) {
+            for (i64 e = j->indptr[i]; e < j->indptr[i + 1]; ++e) {
+                i64 col = j->indices[e];
+                double s = 0.0;
+                for (i64 c = 0; c < k; ++c)
+                    s += j->A[i * k + c] * j->B[col * k + c];
+                j->out[e] = s;
+            }
+        } else {
+            for (i64 c = 0; c < k; ++c) {
+                double s = 0.0;
+                for (i64 e = j->indptr[i]; e < j->indptr[i + 1]; ++e)
+                    s += j->vals[j->perm[e]] * j->A[(i64)j->indices[e] * k + c];
+                j->out[i * k + c] = s;
+            }
+        }
+    }
+    return NULL;
+}
+
+/* Splits rows [0, m) into `threads` blocks of about nnz / threads entries each and runs
+ * them in parallel; returns the number of threads that ran. */
+static int orc_parallel(orc_job base, i64 m, int threads)
+{
+    if (threads < 1)
+        threads = 1;
+    if (threads > 256)
+        threads = 256;
+    orc_job jobs[256];
+    pthread_t tid[256];
+    const i64 nnz = base.indptr[m];
+    i64 r = 0;
+    int used = 0;
+    for (int t = 0; t < threads && r < m; ++t) {
+        i64 target = (t == threads - 1) ? nnz : (nnz * (t + 1)) / threads;
+        i64 r1 = r;
+        while (r1 < m && (base.indptr[r1 + 1] <= target || r1 == r))
+            ++r1;
+        if (t == threads - 1)
+            r1 = m;
+        jobs[used] = base;
+        jobs[used].r0 = r;
+        jobs[used].r1 = r1;
+        r = r1;
+        ++used;
+    }
+    int started = 0;
+    for (int t = 0; t < used; ++t)
+        if (pthread_create(&tid[t], NULL, orc_run_job, &jobs[t]) == 0)
+            ++started;
+        else
+            orc_run_job(&jobs[t]);           /* no thread available: run it here */
+    for (int t = 0, s = 0; t < used && s < started; ++t, ++s)
+        pthread_join(tid[t], NULL);
+    return used;
+}
+
+int orc_spmm_mt(i64 m, const i32 *indptr, const i32 *indices, const double *vals,
+                const double *X, i64 k, double *Y, int threads)
+{
+    orc_job b = {0, 0, 0, indptr, indices, NULL, vals, X, NULL, k, Y};
+    return orc_parallel(b, m, threads);
+}
+
+int orc_sddmm_mt(i64 m, const i32 *indptr, const i32 *indices, const double *G,
+                 const double *X, i64 k, double *out, int threads)
+{
+    orc_job b = {1, 0, 0, indptr, indices, NULL, NULL, G, X, k, out};
+    return orc_parallel(b, m, threads);
+}
+
+int orc_spmm_t_mt(i64 n, const i32 *t_indptr, const i32 *t_indices, const i32 *perm,
+                  const double *vals, const double *G, i64 k, double *gX, int threads)
+{
+    orc_job b = {2, 0, 0, t_indptr, t_indices, perm, vals, G, NULL, k, gX};
+    return orc_parallel(b, n, threads);
+}

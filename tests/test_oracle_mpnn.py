@@ -137,3 +137,147 @@ def test_square_pattern_factor_extends_the_tril_factor():
     p0 = mpnn.params_to_torch(mpnn.init_params(3), requires_grad=False)
     L0, (r0, c0) = mpnn.forward(A, p0, pattern="A2")
     assert np.all(L0.numpy()[np.asarray(r0) != np.asarray(c0)] == 0)
+
+
+def _rand_params(seed, scale=0.3):
+    p = mpnn.init_params(seed)
+    rng = np.random.default_rng(seed + 1)
+    p["v"] = rng.normal(0, scale, p["v"].shape).astype(np.float32)
+    p["c"] = rng.normal(0, 0.1, p["c"].shape).astype(np.float32)
+    for k in ("b0", "b1", "b2", "b3"):
+        p[k] = rng.normal(0, 0.1, p[k].shape).astype(np.float32)
+    for k in ("W0", "W1", "W2", "W3", "Ua", "Ub"):        # BF16 weights, as the network stores them
+        p[k] = torch.from_numpy(p[k]).to(torch.bfloat16).to(torch.float32).numpy()
+    return p
+
+
+def _rne_bf16_bits(x32: np.ndarray) -> np.ndarray:
+    """BF16 rounding written on the float32 bit pattern: add 0x7FFF plus the lowest kept
+    bit (ties to even) and clear the 16 dropped bits (finite inputs)."""
+    b = x32.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(0, 1, 5000), rng.normal(0, 1e-30, 100), rng.normal(0, 1e30, 100)])
+    # exact ties between two BF16 neighbours: 1 + (2k + 1) 2^-8 ties to the even neighbour
+    ties = 1.0 + (2 * np.arange(20) + 1) * 2.0 ** -8
+    x = np.concatenate([x, ties, -ties, [0.0, -0.0, 1.0, 2.0 ** -126]])
+    got = mpnn.bf16_round(torch.from_numpy(x)).numpy()
+    want = _rne_bf16_bits(x.astype(np.float32)).astype(np.float64)
+    np.testing.assert_array_equal(got, want)
+    # a float64 value is rounded to float32 first, as a kernel's float32 value would be
+    y = np.float64(1.0 + 2.0 ** -8 + 2.0 ** -30)          # just above a tie; float32 rounds it onto it
+    assert float(mpnn.bf16_round(torch.tensor([y]))[0]) == 1.0
+
+
+def test_bf16_option_off_is_the_exact_network():
+    A = synth.diffusion2d(5, 1.3, seed=6)
+    p = _rand_params(8)
+    tp = mpnn.params_to_torch(p, requires_grad=False)
+    L0, pat0 = mpnn.forward(A, tp)
+    L1, pat1 = mpnn.forward(A, tp, bf16=False, record={})
+    assert torch.equal(L0, L1)
+    np.testing.assert_array_equal(pat0[0], pat1[0])
+
+
+def test_bf16_product_on_representable_operands_is_the_plain_product():
+    """With X and the incoming gradient already BF16 values, rounding changes nothing:
+    forward and both gradients equal float64 autograd of X W."""
+    rng = np.random.default_rng(3)
+    bf = lambda a: torch.from_numpy(a).to(torch.bfloat16).to(torch.float64)  # noqa: E731
+    X = bf(rng.normal(size=(7, 5)).astype(np.float32)).requires_grad_(True)
+    W = bf(rng.normal(size=(5, 4)).astype(np.float32)).requires_grad_(True)
+    G = bf(rng.normal(size=(7, 4)).astype(np.float32))
+    Y = mpnn._Bf16Product.apply(X, W)
+    Y.backward(G)
+    X2, W2 = X.detach().clone().requires_grad_(True), W.detach().clone().requires_grad_(True)
+    (X2 @ W2).backward(G)
+    assert torch.equal(Y.detach(), (X2 @ W2).detach())
+    assert torch.equal(X.grad, X2.grad) and torch.equal(W.grad, W2.grad)
+
+
+def test_bf16_network_within_the_bf16_error_bound():
+    """Rounding the dense operands to BF16 (unit roundoff u = 2^-8) moves L by more than
+    float64 rounding but within 2u of its normaliser elementwise; the parameter gradients
+    move by well under a third in relative Frobenius norm (relu derivatives of
+    pre-activations within a BF16 rounding of zero flip, so no elementwise bound holds
+    for them).  A dropped term, a wrong sign or a transposed operand in the rounded
+    reverse pass would move them by O(1)."""
+    A = synth.diffusion2d(6, 1.0, seed=2)
+    p = _rand_params(5)
+    tp = mpnn.params_to_torch(p)
+    tq = mpnn.params_to_torch(p)
+    L, _ = mpnn.forward(A, tp)
+    Lb, _ = mpnn.forward(A, tq, bf16=True)
+    gL = np.random.default_rng(4).normal(size=L.numel())
+    (L * torch.from_numpy(gL)).sum().backward()
+    (Lb * torch.from_numpy(gL)).sum().backward()
+    N_L, _ = mpnn.error_scale(A, p)
+    u = 2.0 ** -8
+    dl = np.abs(Lb.detach().numpy() - L.detach().numpy())
+    assert dl.max() > 1e-3 * u * N_L.max()                # the option does round something
+    assert np.all(dl <= 2 * u * N_L)
+    for name in tp:
+        a, b = tp[name].grad.numpy(), tq[name].grad.numpy()
+        assert np.linalg.norm(b - a) <= 0.3 * max(np.linalg.norm(a), 1e-300), name
+
+
+def test_bf16_network_on_representable_activations_is_exact():
+    """On 2 A_N (diagonal 4, so d = 1/2 and e = -1/2 exactly; features -1, -1/2) with
+    weights of a few dyadic values and zero biases, every activation that the option
+    rounds is a BF16 value already, so L is the exact network's bit for bit: the option
+    rounds nothing but those operands."""
+    A = synth.poisson1d(12)
+    A = synth.with_values(A, A.values * 2)
+    rng = np.random.default_rng(6)
+    p = mpnn.init_params(0)
+    for name in ("W0", "W1", "W2", "W3", "Ua", "Ub"):
+        shp = p[name].shape
+        w = rng.choice([-1.0, -0.5, 0.5, 1.0], size=shp) * (rng.random(shp) < 1.5 / shp[0])
+        p[name] = w.astype(np.float32)
+    for name in ("b0", "b1", "b2", "b3"):
+        p[name][:] = 0
+    p["v"] = rng.normal(0, 0.3, p["v"].shape).astype(np.float32)
+    p["c"] = rng.normal(0, 0.1, p["c"].shape).astype(np.float32)
+    tp = mpnn.params_to_torch(p, requires_grad=False)
+    rec = {}
+    L, _ = mpnn.forward(A, tp, record=rec)
+    for x in rec["X"] + [rec["h"]]:
+        assert torch.equal(mpnn.bf16_round(x), x)          # the construction holds
+    assert float(rec["h"].abs().max()) > 0
+    Lb, _ = mpnn.forward(A, tp, bf16=True)
+    assert torch.equal(L, Lb)
+
+
+def test_error_scale_bounds_the_values_and_is_exact_on_nonnegative_data():
+    """The normaliser is the absolute form of each output's last product, so it bounds the
+    output (triangle inequality); with non-negative parameters, e (positive off-diagonal
+    entries) and upstream gradient every relu passes its input, and the normaliser is
+    2 L off the diagonal (|t| . |v| + |bo| = L / d_i, plus |Lhat|) and exactly each
+    parameter gradient."""
+    A = synth.diffusion2d(5, 1.0, seed=7)
+    p = _rand_params(9)
+    tp = mpnn.params_to_torch(p)
+    L, _ = mpnn.forward(A, tp)
+    gL = np.random.default_rng(2).normal(size=L.numel())
+    (L * torch.from_numpy(gL)).sum().backward()
+    N_L, N_g = mpnn.error_scale(A, p, gL)
+    assert np.all(np.abs(L.detach().numpy()) <= N_L * (1 + 1e-12))
+    for name in tp:
+        assert np.all(np.abs(tp[name].grad.numpy()) <= N_g[name] * (1 + 1e-12) + 1e-300), name
+
+    A = synth.diffusion2d(4, 1.0, seed=3)
+    A = synth.with_values(A, np.abs(A.values))
+    p = {k: np.abs(v) for k, v in _rand_params(2).items()}
+    tp = mpnn.params_to_torch(p)
+    L, (ri, ci) = mpnn.forward(A, tp)
+    off = np.asarray(ri) != np.asarray(ci)
+    gL = np.where(off, np.random.default_rng(1).random(L.numel()), 0.0)
+    (L * torch.from_numpy(gL)).sum().backward()
+    N_L, N_g = mpnn.error_scale(A, p, gL)
+    np.testing.assert_allclose(N_L[off], 2 * L.detach().numpy()[off], rtol=1e-13)
+    for name in tp:
+        np.testing.assert_allclose(N_g[name], tp[name].grad.numpy(), rtol=1e-12, atol=1e-300, err_msg=name)

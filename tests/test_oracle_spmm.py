@@ -137,3 +137,21 @@ def test_empty_matrix(orc):
     assert orc.sddmm(A, np.ones((3, 2)), np.ones((4, 2))).size == 0
     t_ip, t_ix, perm = orc.transpose(A)
     assert np.all(t_ip == 0) and t_ix.size == 0
+
+
+def test_row_parallel_variants_equal_the_serial_routines(orc):
+    """The all-cores timing variants: the same sums in the same order, so bitwise equal
+    (power-law rows, empty rows and a hub row, a rectangular matrix, 1 to 7 threads)."""
+    A = synth.powerlaw_csr(3000, seed=4, max_len=400)
+    R = synth.random_k_per_row(500, 3, seed=2, ncols=800)
+    E = synth.empty_rows_csr(700, 900, seed=3)
+    for M in (A, R, E):
+        X = synth.normal((M.n, 5), seed=1)
+        G = synth.normal((M.m, 5), seed=2)
+        t = orc.transpose(M)
+        for threads in (1, 3, 7):
+            Y, used = orc.spmm_mt(M, X, threads)
+            assert 1 <= used <= threads
+            np.testing.assert_array_equal(Y, orc.spmm(M, X))
+            np.testing.assert_array_equal(orc.sddmm_mt(M, G, X, threads)[0], orc.sddmm(M, G, X))
+            np.testing.assert_array_equal(orc.spmm_t_mt(M, G, threads, t)[0], orc.spmm_t(M, G))
