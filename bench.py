@@ -2,9 +2,10 @@
 """Benchmark of the sparse forward + reverse-mode hot path on one GB300.
 
 One step = the forward and both VJPs of Y = A X (Table 1, SpDMM rows):
-  SpMM        Y  = A X                    (spx_spmm)
-  SDDMM       gA = (G X^T) masked to A    (spx_sddmm)
-  A^T-SpMM    gX = A^T G                  (spx_spmm_t)
+  SpMM        Y  = A X                    (spx_spmm: spmm_kernel)
+  SDDMM       gA = (G X^T) masked to A    (spx_sddmm: sddmm_rows_kernel)
+  A^T-SpMM    gX = A^T G                  (spx_spmm_t's two launches as two calls:
+                                           spx_gather_values, then spx_spmm on A^T)
 on the random power-law CSR workload: n = 2^20 rows/cols, row lengths
 min(4096, floor(5.62 U^(-1/1.5))) (mean 16), uniform unique columns, N(0,1) values,
 dense X and G of width k = 32 (N(0,1)).  Inputs stay resident in HBM and exceed L2.
@@ -12,9 +13,12 @@ The transpose pattern and row plans are per-pattern setup, outside the timed reg
 
 The headline value is compulsory bytes per step (each CSR array, X, G and the outputs
 moved once) divided by the step time: an effective GB/s that earns no credit for
-extra traffic.  The JSON line also carries a roofline object for the dominant kernel,
-a CPU baseline of the FP64 oracle on a bounded sample, an end-to-end number through
-host buffers, sampled SM clocks and extra sections: k = 128 and 3D Poisson 128^3,
+extra traffic.  The JSON line also carries a roofline object for the dominant CUDA kernel
+(spmm_kernel, two launches per step) with the gather bound measured by the probe kernel
+(spx_gather_probe: the same row gathers and nothing else), a CPU baseline of the FP64
+oracle on a bounded sample (all host cores, and one thread), an end-to-end number through
+host buffers, sampled SM clocks and extra sections: k = 128 and 3D Poisson 128^3 (each
+with its own roofline object and gather bound),
 SpGEMM forward and backward, sparse add, the batched triangular solve, SPAI descent, and
 "cg": the 256-system Jacobi batch replayed from a CUDA graph, training of the learned
 factor (tril(A) and tril(A + A^2)) on 10,016 generated systems, and PCG to a true
@@ -57,19 +61,31 @@ def measured_peaks():
 
 # ----------------------------------------------------------------------------- bytes
 def compulsory_bytes(m, n, nnz, k):
-    """Per-kernel compulsory bytes (int32 index / float32 value = 4 B)."""
+    """Compulsory bytes of the three products of a step (int32 index / float32 value = 4 B):
+    every CSR array, dense operand and output moved once.  A^T G reads A^T's pattern, the
+    permutation and A's values once (12 nnz)."""
     spmm = 4 * (m + 1) + 8 * nnz + 4 * n * k + 4 * m * k
     sddmm = 4 * (m + 1) + 4 * nnz + 4 * m * k + 4 * n * k + 4 * nnz
     spmm_t = 4 * (n + 1) + 12 * nnz + 4 * m * k + 4 * n * k
     return {"spmm": spmm, "sddmm": sddmm, "spmm_t": spmm_t}
 
 
+def launch_bytes(m, n, nnz, k):
+    """Algorithmic bytes of each launch of a step: spmm_kernel on A (Y = A X), the SDDMM,
+    gather_values_kernel (A^T's values through the permutation: read perm and A's values,
+    write the gathered copy) and spmm_kernel on A^T with the gathered values (gX = A^T G)."""
+    return {"spmm": 4 * (m + 1) + 8 * nnz + 4 * n * k + 4 * m * k,
+            "sddmm": 4 * (m + 1) + 8 * nnz + 4 * m * k + 4 * n * k,
+            "gather": 12 * nnz,
+            "spmm_t": 4 * (n + 1) + 8 * nnz + 4 * m * k + 4 * n * k}
+
+
 def gather_bytes(m, n, nnz, k):
-    """Bytes when every entry's dense row is fetched from DRAM (no cache reuse)."""
-    spmm = 4 * (m + 1) + 8 * nnz + 4 * nnz * k + 4 * m * k
-    sddmm = 4 * (m + 1) + 8 * nnz + 4 * m * k + 4 * nnz * k
-    spmm_t = 4 * (n + 1) + 12 * nnz + 4 * nnz * k + 4 * n * k
-    return {"spmm": spmm, "sddmm": sddmm, "spmm_t": spmm_t}
+    """Bytes of each launch when every entry's dense row is fetched from DRAM (no reuse)."""
+    return {"spmm": 4 * (m + 1) + 8 * nnz + 4 * nnz * k + 4 * m * k,
+            "sddmm": 4 * (m + 1) + 8 * nnz + 4 * m * k + 4 * nnz * k,
+            "gather": 12 * nnz,
+            "spmm_t": 4 * (n + 1) + 8 * nnz + 4 * nnz * k + 4 * n * k}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -300,10 +316,14 @@ class Workload:
             self.sddmm_cb, self.sddmm_plan = tune.tuned_sddmm_plan(self.dA, k)
         self.s_A = self.dA.struct()
         self.s_AT = self.dA.t_struct()
+        t_ip, t_ix, _ = self.dA.transpose_pattern()
+        self.t_vals = torch.empty(max(A.nnz, 1), device=device)[: A.nnz]
+        self.s_ATv = abi.csr_struct(A.n, A.m, t_ip, t_ix, self.t_vals)     # A^T with gathered values
         ws = lambda nb: abi.workspace(nb, device) if nb > 0 else None  # noqa: E731
         self.ws_spmm = ws(abi.spx_spmm_workspace_size(self.s_A, k, self.plan))
         self.ws_sddmm = ws(abi.spx_sddmm_workspace_size(self.s_A, k, self.sddmm_cb))
         self.ws_t = ws(abi.spx_spmm_t_workspace_size(self.s_AT, k, self.t_plan))
+        self.ws_tv = ws(abi.spx_spmm_workspace_size(self.s_ATv, k, self.t_plan))
         npass = lambda cb: -(-k // cb)  # noqa: E731
         rp = lambda cb: 1 if cb < k else 0  # noqa: E731  (slab repack launch)
         nparts = lambda pl: max(1, pl.n_parts) if pl is not None else 1  # noqa: E731
@@ -311,6 +331,8 @@ class Workload:
         self.launches = (npass(self.plan.col_block) * nparts(self.plan) + rp(self.plan.col_block)
                          + npass(self.sddmm_cb) * nparts(sp) + rp(self.sddmm_cb) + 1
                          + npass(self.t_plan.col_block) * nparts(self.t_plan) + rp(self.t_plan.col_block))
+        self.spmm_kernel_launches = npass(self.plan.col_block) * nparts(self.plan) + \
+            npass(self.t_plan.col_block) * nparts(self.t_plan)
         self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine,
                                 nparts(self.plan)],
                        "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group, self.t_plan.engine,
@@ -324,15 +346,23 @@ class Workload:
         return self.launches
 
     def run_kernel(self, which):
+        """One launch of the step.  gX = A^T G is spx_spmm_t's two launches made as two calls
+        (the values gathered into A^T's order, then the product on A^T), so that each is
+        timed on its own; the result is spx_spmm_t's bit for bit."""
         a = self.abi
         if which == "spmm":
             a.spx_spmm(self.s_A, self.X, self.Y, 1.0, 0.0, self.plan, self.ws_spmm)
         elif which == "sddmm":
             a.spx_sddmm(self.s_A, self.G, self.X, self.gA, 1.0, self.sddmm_cb, self.ws_sddmm, plan=self.sddmm_plan)
+        elif which == "gather":
+            a.spx_gather_values(self.perm, self.dA.values, self.t_vals)
         else:
-            a.spx_spmm_t(self.s_AT, self.perm, self.G, self.gX, 1.0, 0.0, self.t_plan, self.ws_t)
+            a.spx_spmm(self.s_ATv, self.G, self.gX, 1.0, 0.0, self.t_plan, self.ws_tv)
 
-    KERNELS = ("spmm", "sddmm", "spmm_t")
+    KERNELS = ("spmm", "sddmm", "gather", "spmm_t")
+    # the CUDA function each launch runs (spmm and spmm_t both run spmm_kernel)
+    CUDA_KERNEL = {"spmm": "spmm_kernel", "sddmm": "sddmm_rows_kernel", "gather": "gather_values_kernel",
+                   "spmm_t": "spmm_kernel"}
 
 
 def time_workload(W, steps, warmup, ws):
@@ -371,6 +401,65 @@ def time_workload(W, steps, warmup, ws):
     return total_ms / steps, per
 
 
+def gather_probe(W, reps=5):
+    """The gather bound of each column stream of the step: the best time of the probe kernel
+    (spx_gather_probe: the same 16-byte row gathers as spmm_kernel, nothing else) over a
+    small sweep of its launch shape, back to back so that the L2 holds what it can."""
+    import torch
+    t_ip, t_ix, _ = W.dA.transpose_pattern()
+    buf = torch.empty(16 * 256 * torch.cuda.get_device_properties(0).multi_processor_count, device="cuda")
+    out = {}
+    for name, idx, rows, D in (("A", W.dA.indices, W.n, W.X), ("AT", t_ix, W.m, W.G)):
+        best = None
+        for unroll, bps in ((1, 8), (2, 5), (2, 8), (4, 4)):
+            ms = _ev_time(lambda: W.abi.spx_gather_probe(idx, rows, D, unroll, bps, buf), reps)
+            if best is None or ms < best[0]:
+                best = (ms, unroll, bps)
+        gathered = 4 * W.nnz + 4 * W.nnz * W.k
+        out[name] = {"ms": best[0], "unroll": best[1], "blocks_per_sm": best[2],
+                     "gathered_bytes": gathered, "gathered_gbs": gathered / (best[0] * 1e-3) / 1e9}
+    return out
+
+
+def workload_report(W, ms, per, hbm, hbm_src, probe=None):
+    """Roofline object of the dominant CUDA kernel of the step (the one with the largest share
+    of the step time, summed over its launches) and per-launch figures."""
+    lb = launch_bytes(W.m, W.n, W.nnz, W.k)
+    gb = gather_bytes(W.m, W.n, W.nnz, W.k)
+    by_kernel = {}
+    for launch, t in per.items():
+        kern = W.CUDA_KERNEL[launch]
+        d = by_kernel.setdefault(kern, {"ms": 0.0, "bytes": 0, "gather_bytes": 0, "launches": []})
+        d["ms"] += t
+        d["bytes"] += lb[launch]
+        d["gather_bytes"] += gb[launch]
+        d["launches"].append(launch)
+    dom = max(by_kernel, key=lambda kk: by_kernel[kk]["ms"])
+    d = by_kernel[dom]
+    nl = len(d["launches"])
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+    tag = {"powerlaw": f"powerlaw_k{W.k}", "poisson3d": f"poisson3d_128_k{W.k}"}[W.kind]
+    roofline = {"bound": "hbm", "kernel": dom, "launches_per_step": nl, "launches": d["launches"],
+                "achieved": achieved, "peak": hbm, "peak_source": hbm_src, "unit": "GB/s",
+                "frac": achieved / hbm, "share_of_step": d["ms"] / ms,
+                "traffic": ncu_traffic(f"{dom}_{tag}", os.path.join(ROOT, "paper_2212_05159_gb300", "csrc",
+                                                                   KERNEL_SOURCE[dom])),
+                "algorithmic_bytes": d["bytes"] / nl, "bytes_model": "compulsory, per launch (mean of its launches)",
+                "gather_model_frac": d["gather_bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm}
+    if probe is not None and dom == "spmm_kernel":
+        t_floor = sum(probe["A" if ln == "spmm" else "AT"]["ms"] for ln in d["launches"])
+        roofline["gather_probe_ms"] = t_floor
+        roofline["vs_gather_probe"] = d["ms"] / t_floor
+    return {"roofline": roofline,
+            "per_launch_ms": per,
+            "per_launch_gbs_compulsory": {kk: lb[kk] / (per[kk] * 1e-3) / 1e9 for kk in per},
+            "per_kernel_share": {kk: v["ms"] / ms for kk, v in by_kernel.items()}}
+
+
+KERNEL_SOURCE = {"spmm_kernel": "spmm.cu", "sddmm_rows_kernel": "sddmm.cu", "sddmm_kernel": "sddmm.cu",
+                 "gather_values_kernel": "spmm.cu"}
+
+
 def time_e2e(W, steps, warmup):
     """The step end to end through host buffers: every step copies its inputs (A's values, X,
     G) from pinned host memory and its results (Y, gA, gX) back.  Streamed the way a user
@@ -383,14 +472,15 @@ def time_e2e(W, steps, warmup):
     hv = torch.from_numpy(W.host.values).pin_memory()
     hX = W.X.cpu().pin_memory()
     hG = W.G.cpu().pin_memory()
-    oY = torch.empty_like(W.Y, device="cpu").pin_memory()
-    oA = torch.empty_like(W.gA, device="cpu").pin_memory()
-    oX = torch.empty_like(W.gX, device="cpu").pin_memory()
     slots = [dict(v=W.dA.values, X=W.X, G=W.G, Y=W.Y, gA=W.gA, gX=W.gX)]
     slots.append({k: torch.empty_like(t) for k, t in slots[0].items()})
     for sl in slots:
         sl["sA"] = W.dA.struct(sl["v"])
         sl["sAT"] = W.dA.t_struct(sl["v"])
+        # each slot's results land in host buffers of their own: consecutive steps' copies
+        # back never share memory
+        for key in ("Y", "gA", "gX"):
+            sl["o" + key] = torch.empty_like(sl[key], device="cpu").pin_memory()
 
     def compute(sl):
         abi.spx_spmm(sl["sA"], sl["X"], sl["Y"], 1.0, 0.0, W.plan, W.ws_spmm)
@@ -403,9 +493,8 @@ def time_e2e(W, steps, warmup):
         sl["G"].copy_(hG, non_blocking=True)
 
     def d2h(sl):
-        oY.copy_(sl["Y"], non_blocking=True)
-        oA.copy_(sl["gA"], non_blocking=True)
-        oX.copy_(sl["gX"], non_blocking=True)
+        for key in ("Y", "gA", "gX"):
+            sl["o" + key].copy_(sl[key], non_blocking=True)
 
     # one stream, no overlap (reported beside the streamed figure)
     def serial_step():
@@ -422,6 +511,7 @@ def time_e2e(W, steps, warmup):
     b.record()
     torch.cuda.synchronize()
     serial_ms = a.elapsed_time(b) / steps
+    serial_out = {key: slots[0]["o" + key].clone() for key in ("Y", "gA", "gX")}
 
     s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     ev = lambda: torch.cuda.Event()  # noqa: E731
@@ -459,53 +549,76 @@ def time_e2e(W, steps, warmup):
     s_out.wait_stream(s_cmp)
     t1.record(s_out)
     torch.cuda.synchronize()
+    # the kernels are deterministic: every slot's streamed results equal the one-stream step's
+    same = all(torch.equal(sl["o" + key], serial_out[key]) for sl in slots for key in serial_out)
     h2d_b = hv.numel() * 4 + hX.numel() * 4 + hG.numel() * 4
-    d2h_b = oY.numel() * 4 + oA.numel() * 4 + oX.numel() * 4
-    return t0.elapsed_time(t1) / steps, h2d_b, d2h_b, serial_ms
+    d2h_b = sum(slots[0]["o" + key].numel() * 4 for key in ("Y", "gA", "gX"))
+    return t0.elapsed_time(t1) / steps, h2d_b, d2h_b, serial_ms, same
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_baseline(k=32, seed=0, budget_s=12.0):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(k=32, seed=0, budget_s=12.0, threads=1):
+    """The FP64 oracle's spmm + sddmm + spmm_t on a contiguous row block of the power-law
+    matrix, grown until one pass costs about budget_s / 3; on `threads` host threads (row
+    blocks of equal entry counts; A^T G as rows of the sample's transpose, whose pattern is
+    set-up outside the timed pass, as on the GPU).  Returns (GB/s, description, threads)."""
     import oracle
     import synth
     A = synth.powerlaw_csr(1 << 20, seed=seed)
     X = synth.normal((A.n, k), seed + 1)
     G = synth.normal((A.m, k), seed + 2)
     oracle.build()
-    # grow a contiguous row block until one pass of the three oracle routines costs ~budget/3
     rows = 4096
     while True:
-        sub, t = _oracle_pass(A, X, G, rows)
+        sub, t, used = _oracle_pass(A, X, G, rows, threads)
         if t > budget_s / 3 or rows >= A.m:
             break
         rows = min(A.m, int(rows * min(8.0, max(2.0, (budget_s / 3) / max(t, 1e-3)))))
     reps = max(1, int(budget_s // max(t, 1e-6)) - 1)
-    times = [t] + [_oracle_pass(A, X, G, rows)[1] for _ in range(min(reps, 2))]
+    times = [t] + [_oracle_pass(A, X, G, rows, threads)[1] for _ in range(min(reps, 4))]
     t_med = float(np.median(times))
-    b = compulsory_bytes(sub.m, A.n, sub.nnz, k)
-    # the dense operands are only touched where the sample reaches them; count the rows of
+    # the dense operands are only touched where the sample reaches them: count the rows of
     # X / gX the sample touches instead of all n
     touched = np.unique(sub.indices).size
     b_tot = (4 * (sub.m + 1) + 8 * sub.nnz + 4 * touched * k + 4 * sub.m * k) + \
             (4 * (sub.m + 1) + 8 * sub.nnz + 4 * sub.m * k + 4 * touched * k) + \
             (4 * (sub.m + 1) + 12 * sub.nnz + 4 * sub.m * k + 4 * touched * k)
-    del b
     desc = (f"rows [0,{sub.m}) of the n=2^20 power-law matrix ({sub.nnz} entries, k={k}): "
-            f"oracle spmm + sddmm + spmm_t, median of {len(times)} passes")
-    return b_tot / t_med / 1e9, desc, 1
+            f"oracle spmm + sddmm + spmm_t on {used} thread(s), median of {len(times)} passes")
+    return b_tot / t_med / 1e9, desc, used
 
 
-def _oracle_pass(A, X, G, rows):
+_T_CACHE = {}
+
+
+def _oracle_pass(A, X, G, rows, threads=1):
     import oracle
     import synth
     ip = A.indptr[: rows + 1]
     nnz = int(ip[-1])
     sub = synth.CSR(rows, A.n, ip, A.indices[:nnz], A.values[:nnz])
+    if threads == 1:
+        t0 = time.perf_counter()
+        oracle.spmm(sub, X)
+        oracle.sddmm(sub, G[:rows], X)
+        oracle.spmm_t(sub, G[:rows])
+        return sub, time.perf_counter() - t0, 1
+    if rows not in _T_CACHE:
+        _T_CACHE.clear()
+        _T_CACHE[rows] = oracle.transpose(sub)
+    t = _T_CACHE[rows]
     t0 = time.perf_counter()
-    oracle.spmm(sub, X)
-    oracle.sddmm(sub, G[:rows], X)
-    oracle.spmm_t(sub, G[:rows])
-    return sub, time.perf_counter() - t0
+    _, u1 = oracle.spmm_mt(sub, X, threads)
+    _, u2 = oracle.sddmm_mt(sub, G[:rows], X, threads)
+    _, u3 = oracle.spmm_t_mt(sub, G[:rows], threads, t)
+    return sub, time.perf_counter() - t0, max(u1, u2, u3)
 
 
 # ----------------------------------------------------------------------------- SpGEMM / CG
@@ -682,11 +795,12 @@ def run_reference(args, ws, rank):
     hbm, _ = measured_peaks()
     t0 = time.perf_counter()
     vals = []
+    threads = host_cores()
     for _ in range(args.warmup):
-        cpu_baseline(budget_s=1.0)
-    desc = ""
+        cpu_baseline(budget_s=1.0, threads=threads)
+    desc, cores = "", threads
     for _ in range(args.steps):
-        v, desc, cores = cpu_baseline(budget_s=3.0)
+        v, desc, cores = cpu_baseline(budget_s=3.0, threads=threads)
         vals.append(v)
     v = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
@@ -694,7 +808,7 @@ def run_reference(args, ws, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "powerlaw n=2^20 mean16 max4096 k=32 (bounded row sample)",
                        "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0, "hbm_peak_gbs": hbm}
     print(json.dumps(line))
@@ -751,20 +865,12 @@ def main():
     clk = clocks.stop(window=W.windows[1], load_from=W.windows[0])
     ms = max_over_ranks(ms, ws)
     cb = compulsory_bytes(W.m, W.n, W.nnz, W.k)
-    gb = gather_bytes(W.m, W.n, W.nnz, W.k)
     step_bytes = sum(cb.values())
     value = ws * step_bytes / (ms * 1e-3) / 1e9
     hbm, hbm_src = measured_peaks()
-    dom = max(per, key=per.get)
-    src = {"spmm": "spmm.cu", "sddmm": "sddmm.cu", "spmm_t": "spmm.cu"}[dom]
-    src_path = os.path.join(ROOT, "paper_2212_05159_gb300", "csrc", src)
-    achieved = cb[dom] / (per[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                "peak_source": hbm_src, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": ncu_traffic(f"{dom}_powerlaw_k{W.k}", src_path),
-                "algorithmic_bytes": cb[dom], "bytes_model": "compulsory",
-                "gather_model_frac": gb[dom] / (per[dom] * 1e-3) / 1e9 / hbm}
-    e2e_ms, h2d, d2h, e2e_serial_ms = time_e2e(W, max(3, args.steps // 2), 2)
+    probe = gather_probe(W)
+    rep = workload_report(W, ms, per, hbm, hbm_src, probe)
+    e2e_ms, h2d, d2h, e2e_serial_ms, e2e_same = time_e2e(W, max(3, args.steps // 2), 2)
     e2e_ms = max_over_ranks(e2e_ms, ws)
     e2e_serial_ms = max_over_ranks(e2e_serial_ms, ws)
     line = {
@@ -775,18 +881,23 @@ def main():
                    "m": W.m, "n": W.n, "nnz": W.nnz, "k": W.k,
                    "l2": "inputs larger than L2 (~0.9 GB touched per step), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "per_kernel_ms": per,
+        "per_launch_ms": rep["per_launch_ms"],
+        "per_kernel_share": rep["per_kernel_share"],
         "tuning": W.tuning,
-        "per_kernel_gbs_compulsory": {k: cb[k] / (per[k] * 1e-3) / 1e9 for k in per},
-        "roofline": roofline,
+        "per_launch_gbs_compulsory": rep["per_launch_gbs_compulsory"],
+        "step_frac_of_peak": value / ws / hbm,
+        "roofline": rep["roofline"],
+        "gather_probe": probe,
         "e2e": {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "mode": "streamed: inputs, products and results on three streams, two buffer sets",
-                "serial_ms_per_step": e2e_serial_ms},
+                "serial_ms_per_step": e2e_serial_ms, "streamed_results_equal_serial": e2e_same},
         "gpu_launches": W.launches_per_step() * args.steps,
         "clocks": clk,
     }
     if "extras" in secs and rank == 0:
+        # the other workloads of the same configuration: k = 128 (the largest power-law width)
+        # and the 3D Poisson stencil, each with the roofline object of its dominant kernel
         extras = {}
         for kind, k in (("powerlaw", 128), ("poisson3d", 32)):
             del W
@@ -794,9 +905,13 @@ def main():
             W = Workload(kind, k=k)
             ms2, per2 = time_workload(W, max(5, args.steps // 2), 3, 1)
             cb2 = compulsory_bytes(W.m, W.n, W.nnz, W.k)
+            probe2 = gather_probe(W)
+            rep2 = workload_report(W, ms2, per2, hbm, hbm_src, probe2)
             extras[W.name] = {"ms_per_step": ms2, "gbs_compulsory": sum(cb2.values()) / (ms2 * 1e-3) / 1e9,
                               "frac_of_peak": sum(cb2.values()) / (ms2 * 1e-3) / 1e9 / hbm,
-                              "per_kernel_ms": per2, "tuning": W.tuning}
+                              "m": W.m, "nnz": W.nnz, "k": W.k, "roofline": rep2["roofline"],
+                              "gather_probe": probe2, "per_launch_ms": per2,
+                              "per_kernel_share": rep2["per_kernel_share"], "tuning": W.tuning}
         line["extras"] = extras
     if ("spgemm" in secs or "cg" in secs) and rank == 0:
         del W
@@ -809,8 +924,10 @@ def main():
         if "cg" in secs:
             line["cg"] = cg_section(args)
     if rank == 0 and ws == 1 and "cpu" in secs:            # the CPU baseline: one process, N = 1 only
-        v, desc, cores = cpu_baseline(k=args.k)
-        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc}
+        v, desc, cores = cpu_baseline(k=args.k, threads=host_cores())
+        v1, desc1, _ = cpu_baseline(k=args.k, threads=1)
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc,
+                                "single_thread": {"value": v1, "unit": "GB/s", "cores": 1, "sample": desc1}}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

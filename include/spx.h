@@ -415,14 +415,80 @@ spx_status spx_spai_update(int64_t nnz, float* m, const float* g, const double* 
  *    message, before any device work;
  *  - it calls no cudaMalloc / cudaFree and allocates nothing;
  *  - the first call on a device looks the array's device address up once for that
- *    device (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture;
+ *    device (cudaGetSymbolAddress, with that device current), and looks it up again only
+ *    when that device's context is a new one (after cudaDeviceReset, say); make that
+ *    first call before any stream capture;
  *  - every call shares the one array and leaves its contents behind; each call writes
  *    all the entries it reads, so nothing needs clearing, but calls whose work overlaps
  *    on the GPU (other streams, other host threads) race on the array: serialise them. */
 spx_status spx_spmm_t_noalloc(const spx_csr* AT, const int32_t* perm, const float* G,
                               int64_t ldg, int32_t k, float* gX, int64_t ldgx, float alpha,
                               float beta, const spx_rowplan* plan, void* stream);
+
+/* ------------------------------------------- merge-path products (load balancing)
+ *
+ * The m row ends and the nnz entries of A merged into one sequence (entry e of row i
+ * before the end of row i) and cut into segments of `items` consecutive items, one per
+ * lane group: every group gets the same share of rows plus entries whatever the row
+ * lengths (power-law rows, empty rows, hub rows).  Row-plan products (spx_spmm,
+ * spx_sddmm) split the rows instead; both compute the same operations. */
+typedef struct spx_mergeplan {
+    const int32_t* seg_row;   /* device int32[n_segments + 1]: the row each segment starts in */
+    int32_t n_segments;       /* ceil((m + nnz) / items), at least 1 */
+    int64_t items;            /* merged items (row ends + entries) per segment */
+} spx_mergeplan;
+
+/* Number of segments of a merge plan with `items` per segment (host only). */
+spx_status spx_merge_plan_segments(const spx_csr* A, int64_t items, int32_t* n_segments);
+
+/* Fills seg_row (device int32[n_segments + 1]) for A's pattern: seg_row[s] = the number of
+ * row ends among the first s * items merged items (a binary search along each cut).  Once
+ * per pattern and segment size; asynchronous. */
+spx_status spx_merge_plan_build(const spx_csr* A, int64_t items, int32_t* seg_row,
+                                int32_t n_segments, void* stream);
+
+/* Workspace bytes of spx_spmm_merge: one carry row id and one k-wide partial sum per
+ * segment. */
+spx_status spx_spmm_merge_workspace_size(const spx_csr* A, int32_t k, const spx_mergeplan* plan,
+                                         size_t* bytes);
+
+/* Y = alpha * A X + beta * Y (Section 3.1.1 SpMV, 3.1.3 SpDMM) over the merge plan's
+ * segments; with perm non-NULL, entry e takes the value A->values[perm[e]] (the transpose
+ * product A^T G on spx_csr_transpose's pattern, Table 1).  X: n x k, Y: m x k row-major
+ * float32, 16-byte aligned, leading dimensions >= k and multiples of 4; k in {4, 8, 16,
+ * 32, 64, 128}.  A row cut by segment boundaries is finished by the segment holding its
+ * end; the earlier segments' partial sums go to the workspace and a second kernel adds
+ * them in segment order (deterministic).  variant: 0 = 8-entry batches with 4 resident
+ * blocks per SM, 1 = 8-entry batches with 5, 2 = 4-entry batches with 6 (launch shapes
+ * for the autotuner; same results).  m + nnz < 2^31.  Asynchronous. */
+spx_status spx_spmm_merge(const spx_csr* A, const int32_t* perm, const float* X, int64_t ldx,
+                          int32_t k, float* Y, int64_t ldy, float alpha, float beta,
+                          const spx_mergeplan* plan, int32_t variant, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* out[e] = scale * sum_c G[i,c] X[j,c] for every stored e = (i, j) (the SDDMM of Table 1:
+ * the SpDMM gradient w.r.t. A) over the merge plan's segments.  G: m x k, X: n x k with
+ * the same layout rules as spx_spmm_merge; variant 0 = 8 row gathers in flight per lane
+ * with 4 resident blocks per SM, 1 = 4 with 5, 2 = 8 with 3 (same results).  Every output
+ * written once; m + nnz < 2^31; asynchronous. */
+spx_status spx_sddmm_merge(const spx_csr* A, const float* G, int64_t ldg, const float* X,
+                           int64_t ldx, int32_t k, float scale, float* out,
+                           const spx_mergeplan* plan, int32_t variant, void* stream);
+
+/* Measurement instrument, not an operation of the paper: the gather bound of the products
+ * that read dense rows through a column stream (spx_spmm, spx_sddmm, spx_spmm_t).  For every
+ * e < nnz it reads row indices[e] of X (k float32 columns, row-major, leading dimension
+ * ldx) as the SpMM kernel gathers it -- k / 4 lanes per row with 16-byte loads, indices
+ * evict-first and X evict-last in L2 -- and adds it to a per-lane sum: no values, no row
+ * boundaries, no output rows.  Its time is the floor for any kernel that gathers the same
+ * rows in the same order.  unroll (1, 2 or 4): batches of 8 entries in flight per lane
+ * group; blocks_per_sm (1..16): resident 256-thread blocks per SM (the grid).  Entries with
+ * an index outside [0, n) are skipped.  out: device float32[out_len], out_len >=
+ * blocks_per_sm * SMs * 256 (per-thread sums).  k in {4, 8, 16, 32, 64, 128}; X 16-byte
+ * aligned, ldx % 4 == 0.  Device pointers; asynchronous. */
+spx_status spx_gather_probe(const int32_t* indices, int64_t nnz, int32_t n, const float* X,
+                            int64_t ldx, int32_t k, int32_t unroll, int32_t blocks_per_sm,
+                            float* out, int64_t out_len, void* stream);
 
 /* Diagonal of A (the paper's A.diagonal(), Section 4.1): for i < min(m, n),
  * diag[i] = a_ii, or 0 where row i stores no diagonal entry, and pos[i] = the index of
@@ -505,9 +571,12 @@ spx_status spx_masked_outer_f64(const spx_csr* A, const double* u, const double*
 
 /* ----------------------- learned preconditioner (Section 4.3) and its network */
 
-/* Workspace bytes of spx_pcg_train for an n-row batch and n_it iterations
- * (5 (n_it + 1) + 6 float vectors: the stored iterates and the adjoint vectors). */
-spx_status spx_pcg_train_workspace_size(int32_t n, int32_t n_it, size_t* bytes);
+/* Workspace bytes of spx_pcg_train for an n-row batch, n_it iterations and a checkpoint
+ * interval (0: keep every iterate).  With interval s < n_it: 5 (s + 1) + 6 + 2 ceil(n_it / s)
+ * float vectors (one segment of iterates, the adjoint vectors, r and p at every segment
+ * start); otherwise 5 (n_it + 1) + 6. */
+spx_status spx_pcg_train_workspace_size(int32_t n, int32_t n_it, int32_t ckpt_interval,
+                                        size_t* bytes);
 
 /* Loss of n_it unrolled PCG iterations with M = L L^T from x0 = 0 (Section 4.3):
  *   loss_s = sum_{i=1..n_it} weights[i-1] ||r_i|| / ||b_s||   for every system s,
@@ -516,12 +585,16 @@ spx_status spx_pcg_train_workspace_size(int32_t n, int32_t n_it, size_t* bytes);
  * A, sys_ptr: the block-diagonal batch as in spx_cg_batched; L: lower-triangular CSR
  * with values on the diagonal blocks; LT: its transpose with values.  weights: device
  * float32[n_it] (e.g. gamma^(n_it-i) normalised); b: device float32[n].
+ * ckpt_interval: 0 (or >= n_it) keeps every forward iterate for the reverse pass; s in
+ * 1..n_it-1 keeps r and p every s iterations and recomputes the iterates in between
+ * during the reverse pass (one more forward pass of work, workspace O(s + n_it / s)
+ * vectors instead of O(n_it)); the results are bitwise the same either way.
  * loss: device float32[nsys]; grad_L: device float32[nnz(L)] (overwritten).
  * 1 <= n_it <= 64.  One thread block per system; deterministic. */
 spx_status spx_pcg_train(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
                          const spx_csr* L, const spx_csr* LT, const float* b, int32_t n_it,
-                         const float* weights, float* loss, float* grad_L, void* workspace,
-                         size_t workspace_bytes, void* stream);
+                         int32_t ckpt_interval, const float* weights, float* loss,
+                         float* grad_L, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Scale-free inputs of the network: d[i] = a_ii^(-1/2), e_vals[k] = d_i a_ij d_j on A's
  * pattern, feats[i, 0..3] = [1, sum_{j != i} e_ij, min_{j != i} e_ij, max_{j != i} e_ij]

@@ -59,6 +59,10 @@ class spx_rowplan(ctypes.Structure):
                            self.medium_rows, self.n_medium, self.medium_threshold, pp, np_, sr, ns)
 
 
+class spx_mergeplan(ctypes.Structure):
+    _fields_ = [("seg_row", ctypes.c_void_p), ("n_segments", ctypes.c_int32), ("items", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
 _I64 = ctypes.c_int64
@@ -94,6 +98,13 @@ SIGNATURES = {
     "spx_spgemm_numeric": [_CSRP, _CSRP, _CSRP, _P, _P, _SZ, _P],
     "spx_spgemm_backward": [_CSRP, _CSRP, _CSRP, _P, _P, _P, _P, _P, _P, _P],
     "spx_gather_values": [_I64, _P, _P, _P, _P],
+    "spx_merge_plan_segments": [_CSRP, _I64, ctypes.POINTER(_I32)],
+    "spx_merge_plan_build": [_CSRP, _I64, _P, _I32, _P],
+    "spx_spmm_merge_workspace_size": [_CSRP, _I32, ctypes.POINTER(spx_mergeplan), ctypes.POINTER(_SZ)],
+    "spx_spmm_merge": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, ctypes.POINTER(spx_mergeplan), _I32, _P, _SZ,
+                       _P],
+    "spx_sddmm_merge": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, ctypes.POINTER(spx_mergeplan), _I32, _P],
+    "spx_gather_probe": [_P, _I64, _I32, _P, _I64, _I32, _I32, _I32, _P, _I64, _P],
     "spx_csr_diagonal": [_CSRP, _P, _P, _P],
     "spx_diagonal_backward": [_I32, _P, _P, _P, _P],
     "spx_cg_workspace_size": [_I32, ctypes.POINTER(_SZ)],
@@ -106,8 +117,8 @@ SIGNATURES = {
     "spx_cg_set_launch": [_I32, _I32, _I32],
     "spx_cg_set_vector_residency": [_I32],
     "spx_masked_outer_f64": [_CSRP, _P, _P, _D, _P, _P],
-    "spx_pcg_train_workspace_size": [_I32, _I32, ctypes.POINTER(_SZ)],
-    "spx_pcg_train": [_CSRP, _P, _I32, _CSRP, _CSRP, _P, _I32, _P, _P, _P, _P, _SZ, _P],
+    "spx_pcg_train_workspace_size": [_I32, _I32, _I32, ctypes.POINTER(_SZ)],
+    "spx_pcg_train": [_CSRP, _P, _I32, _CSRP, _CSRP, _P, _I32, _I32, _P, _P, _P, _P, _SZ, _P],
     "spx_mpnn_features": [_CSRP, _P, _P, _P, _P],
     "spx_dense_forward": [_I64, _P, _I32, _P, _I32, _P, _P, _I32, _I32, _P, _P, _P, _P],
     "spx_dense_forward_tc": [_I64, _P, _I32, _P, _I32, _P, _P, _I32, _I32, _P, _P, _P, _P],
@@ -286,6 +297,41 @@ def spx_spmm(A: spx_csr, X, Y, alpha=1.0, beta=0.0, plan: spx_rowplan | None = N
     return Y
 
 
+def spx_merge_plan_build(A: spx_csr, items: int, device):
+    """Merge-path partition of A's rows + entries into segments of `items` items: returns
+    (seg_row tensor, spx_mergeplan)."""
+    ns = _I32(0)
+    _check(lib().spx_merge_plan_segments(ctypes.byref(A), int(items), ctypes.byref(ns)), "spx_merge_plan_segments")
+    seg = torch.empty(ns.value + 1, dtype=torch.int32, device=device)
+    _check(lib().spx_merge_plan_build(ctypes.byref(A), int(items), seg.data_ptr(), ns.value, _stream()),
+           "spx_merge_plan_build")
+    return seg, spx_mergeplan(seg.data_ptr(), ns.value, int(items))
+
+
+def spx_spmm_merge_workspace_size(A: spx_csr, k: int, plan: spx_mergeplan) -> int:
+    sz = _SZ(0)
+    _check(lib().spx_spmm_merge_workspace_size(ctypes.byref(A), int(k), ctypes.byref(plan), ctypes.byref(sz)),
+           "spx_spmm_merge_workspace_size")
+    return sz.value
+
+
+def spx_spmm_merge(A: spx_csr, X, Y, plan: spx_mergeplan, ws, alpha=1.0, beta=0.0, perm=None, variant=0):
+    px, ldx = _dense(X, "X")
+    py, ldy = _dense(Y, "Y")
+    _check(lib().spx_spmm_merge(ctypes.byref(A), ptr(perm) if perm is not None else None, px, ldx, X.shape[1], py,
+                                ldy, float(alpha), float(beta), ctypes.byref(plan), int(variant), *_wsargs(ws),
+                                _stream()), "spx_spmm_merge")
+    return Y
+
+
+def spx_sddmm_merge(A: spx_csr, G, X, out, plan: spx_mergeplan, scale=1.0, variant=0):
+    pg, ldg = _dense(G, "G")
+    px, ldx = _dense(X, "X")
+    _check(lib().spx_sddmm_merge(ctypes.byref(A), pg, ldg, px, ldx, G.shape[1], float(scale), ptr(out),
+                                 ctypes.byref(plan), int(variant), _stream()), "spx_sddmm_merge")
+    return out
+
+
 def spx_sddmm_workspace_size(A: spx_csr, k: int, col_block: int = 0) -> int:
     sz = _SZ(0)
     _check(lib().spx_sddmm_workspace_size(ctypes.byref(A), int(k), int(col_block), ctypes.byref(sz)),
@@ -395,6 +441,18 @@ def spx_diagonal_backward(pos, g_diag, g_values):
            "spx_diagonal_backward")
 
 
+def spx_gather_probe(indices, n, X, unroll=2, blocks_per_sm=8, out=None):
+    """Reads X's rows in the order of the column stream `indices` (a measurement of the
+    gather bound); returns the per-thread sums buffer."""
+    if out is None:
+        out = torch.zeros(16 * 256 * torch.cuda.get_device_properties(X.device).multi_processor_count,
+                          device=X.device)
+    _check(lib().spx_gather_probe(ptr(indices), int(indices.numel()), int(n), ptr(X), int(X.stride(0)),
+                                  int(X.shape[1]), int(unroll), int(blocks_per_sm), ptr(out), int(out.numel()),
+                                  _stream()), "spx_gather_probe")
+    return out
+
+
 def spx_gather_values(perm, src, dst):
     _check(lib().spx_gather_values(int(perm.numel()), ptr(perm), ptr(src), ptr(dst), _stream()),
            "spx_gather_values")
@@ -457,10 +515,11 @@ def _size(fn, *args):
     return sz.value
 
 
-def spx_pcg_train(A: spx_csr, sys_ptr, nsys, L: spx_csr, LT: spx_csr, b, n_it, weights, loss, grad_L, ws):
+def spx_pcg_train(A: spx_csr, sys_ptr, nsys, L: spx_csr, LT: spx_csr, b, n_it, weights, loss, grad_L, ws,
+                  ckpt_interval=0):
     _check(lib().spx_pcg_train(ctypes.byref(A), ptr(sys_ptr), int(nsys), ctypes.byref(L), ctypes.byref(LT),
-                               ptr(b), int(n_it), ptr(weights), ptr(loss), ptr(grad_L), ptr(ws), ws.numel(),
-                               _stream()), "spx_pcg_train")
+                               ptr(b), int(n_it), int(ckpt_interval), ptr(weights), ptr(loss), ptr(grad_L), ptr(ws),
+                               ws.numel(), _stream()), "spx_pcg_train")
 
 
 def spx_mpnn_features(A: spx_csr, d, e_vals, feats):

@@ -31,6 +31,8 @@ class CSR:
         self._t_plan = None
         self._parts = {}
         self._t_parts = {}
+        self._merge = {}
+        self._t_merge = {}
 
     # ------------------------------------------------------------------ construction
     @classmethod
@@ -113,6 +115,21 @@ class CSR:
             st = abi.csr_struct(self.n, self.m, t_ip, t_ix, None)
             self._t_plan = abi.spx_rowplan_build(st, LONG_ROW_THRESHOLD, self.device, MEDIUM_ROW_THRESHOLD)
         return self._t_plan[1]
+
+    def merge_plan(self, items: int):
+        """Merge-path segments of `items` rows + entries (cached per size)."""
+        if items not in self._merge:
+            self._merge[items] = abi.spx_merge_plan_build(
+                abi.csr_struct(self.m, self.n, self.indptr, self.indices, None), items, self.device)
+        return self._merge[items][1]
+
+    def t_merge_plan(self, items: int):
+        """The same for A^T's pattern."""
+        if items not in self._t_merge:
+            t_ip, t_ix, _ = self.transpose_pattern()
+            self._t_merge[items] = abi.spx_merge_plan_build(abi.csr_struct(self.n, self.m, t_ip, t_ix, None), items,
+                                                            self.device)
+        return self._t_merge[items][1]
 
     def diagonal_positions(self) -> torch.Tensor:
         """int32[min(m, n)]: index of entry (i, i) in indices / values, -1 if absent (cached)."""

@@ -38,6 +38,9 @@
 #include <limits.h>
 
 #include <atomic>
+#include <mutex>
+
+#include <cuda.h>
 
 #include "common.cuh"
 #include "scan.cuh"
@@ -895,22 +898,65 @@ constexpr int64_t NOALLOC_MAX_NNZ = int64_t(1) << 22;          // 4,194,304 entr
 static __device__ __align__(256) float g_noalloc_values[NOALLOC_MAX_NNZ];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-std::atomic<float*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 
-// Device address of the scratch array for the current device, looked up once per device.
+// The array's device address belongs to the module image loaded into one CUDA context: it
+// is looked up with cudaGetSymbolAddress the first time a device is used, and again only
+// when the current context of that device is a different one (after cudaDeviceReset or
+// any re-creation of the primary context the module is loaded anew and may move).  A
+// context is identified by its unique id (cuCtxGetId), which is never reused.
+struct NoallocSlot {
+    unsigned long long ctx_id = 0;
+    float* ptr = nullptr;
+};
+NoallocSlot g_noalloc_slot[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context, 0 when there is none yet.
+spx_status current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        SPX_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1),
+                 "spx_spmm_t_noalloc: driver entry point cuCtxGetCurrent");
+        SPX_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2),
+                 "spx_spmm_t_noalloc: driver entry point cuCtxGetId");
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return set_error(SPX_NOT_SUPPORTED, "spx_spmm_t_noalloc: the driver lacks cuCtxGetCurrent / cuCtxGetId");
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return set_error(SPX_CUDA_ERROR, "spx_spmm_t_noalloc: cuCtxGetCurrent failed");
+    *id = 0;
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return set_error(SPX_CUDA_ERROR, "spx_spmm_t_noalloc: cuCtxGetId failed");
+    return SPX_OK;
+}
+
+// Device address of the scratch array in the current device's current context.
 spx_status noalloc_scratch(float** out) {
     int dev = 0;
     SPX_CUDA(cudaGetDevice(&dev), "spx_spmm_t_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
         return set_error(SPX_NOT_SUPPORTED, "spx_spmm_t_noalloc: device %d beyond %d", dev, NOALLOC_MAX_DEVICES);
-    float* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
-    if (!p) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    unsigned long long id = 0;
+    SPX_TRY(current_context_id(&id));
+    NoallocSlot& slot = g_noalloc_slot[dev];
+    if (id == 0 || slot.ctx_id != id || !slot.ptr) {
         void* addr = nullptr;
+        // also makes the device's primary context current when no runtime call did yet
         SPX_CUDA(cudaGetSymbolAddress(&addr, g_noalloc_values), "spx_spmm_t_noalloc: cudaGetSymbolAddress");
-        p = static_cast<float*>(addr);
-        g_noalloc_ptr[dev].store(p, std::memory_order_release);
+        SPX_TRY(current_context_id(&id));
+        slot.ctx_id = id;
+        slot.ptr = static_cast<float*>(addr);
     }
-    *out = p;
+    *out = slot.ptr;
     return SPX_OK;
 }
 }  // namespace

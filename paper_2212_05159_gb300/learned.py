@@ -252,11 +252,30 @@ class Trainer:
     """Unrolled-PCG training of the network on block-diagonal batches of systems."""
 
     def __init__(self, net: MPNN, n_it: int = 4, gamma: float = 0.6, lr: float = 1e-3, tensor_cores: bool = False,
-                 pattern: str = "A"):
+                 pattern: str = "A", checkpoint=0, max_workspace_bytes: int | None = None):
+        """checkpoint: 0 keeps every unrolled iterate for the reverse pass; s (1..n_it-1) keeps
+        every s-th state and recomputes the rest; "auto" keeps everything while the workspace
+        fits max_workspace_bytes (default: half the free device memory) and otherwise takes
+        the largest interval that fits (the least recomputation)."""
         self.net, self.n_it, self.gamma, self.lr = net, n_it, gamma, lr
         self.tensor_cores = tensor_cores
         self.pattern = pattern
+        self.checkpoint = checkpoint
+        self.max_workspace_bytes = max_workspace_bytes
         self.wts = torch.from_numpy(loss_weights(n_it, gamma)).to(net.device)
+
+    def interval(self, n: int) -> int:
+        """The checkpoint interval for an n-row batch (0: keep every iterate)."""
+        if self.checkpoint != "auto":
+            return int(self.checkpoint)
+        size = lambda s: abi._size("spx_pcg_train_workspace_size", int(n), int(self.n_it), int(s))  # noqa: E731
+        budget = self.max_workspace_bytes
+        if budget is None:
+            budget = torch.cuda.mem_get_info()[0] // 2
+        if size(0) <= budget:
+            return 0
+        fits = [s for s in range(self.n_it - 1, 0, -1) if size(s) <= budget]
+        return fits[0] if fits else min(range(1, self.n_it), key=size)
 
     def loss_and_grad(self, A: CSR, sys_ptr: torch.Tensor, nsys: int, b: torch.Tensor, G: Graph | None = None):
         """Mean loss over the systems and the L gradient (the network is not updated)."""
@@ -265,10 +284,11 @@ class Trainer:
         lt_vals = torch.empty_like(L)
         LT = G.LT_struct(L, lt_vals)
         Ls = abi.csr_struct(G.n, G.n, G.Lpat.indptr, G.Lpat.indices, L)
-        ws = abi.workspace(abi._size("spx_pcg_train_workspace_size", int(G.n), int(self.n_it)), A.device)
+        s = self.interval(G.n)
+        ws = abi.workspace(abi._size("spx_pcg_train_workspace_size", int(G.n), int(self.n_it), s), A.device)
         loss = torch.empty(nsys, dtype=torch.float32, device=A.device)
         gL = torch.empty_like(L)
-        abi.spx_pcg_train(A.struct(), sys_ptr, nsys, Ls, LT, b, self.n_it, self.wts, loss, gL, ws)
+        abi.spx_pcg_train(A.struct(), sys_ptr, nsys, Ls, LT, b, self.n_it, self.wts, loss, gL, ws, ckpt_interval=s)
         return loss, gL, L, G, saved
 
     def step(self, A: CSR, sys_ptr: torch.Tensor, nsys: int, b: torch.Tensor):

@@ -236,22 +236,3 @@ def batch256_jacobi(graph_replay: bool = True, seed: int = 0, reps: int = 3):
             "converged": int((st == 0).sum()), "max_true_relres": float(rr.max()),
             "row_iterations_per_s": float((np.diff(ptr) * it).sum() / (np.median(times) * 1e-3))}
 
-
-if __name__ == "__main__":
-    # A small case for profiling: 16 diffusion systems of 256^2 (1,048,576 rows), the network
-    # (untrained) forward and reverse on the tensor cores, then Jacobi PCG to 1e-8 in one launch.
-    import synth
-    A, ptr, _, _ = synth.diffusion_batch(16, seed=5, side_lo=256, side_hi=256, sigma=1.0)
-    dA = CSR.from_host(A)
-    batch = solve.SystemBatch(dA, ptr)
-    b = torch.from_numpy(synth.normal(A.m, seed=6)).cuda()
-    net = learned.MPNN(seed=0)
-    G = learned.Graph(dA)
-    G.features(dA.values)
-    L, saved = net.forward(G, tensor_cores=True)
-    gL = torch.from_numpy(synth.normal(L.numel(), seed=7)).cuda()
-    grad = net.backward(G, saved, gL, tensor_cores=True)
-    _, it, st, rr = solve.cg(batch, b, pc="jacobi")
-    torch.cuda.synchronize()
-    print("profile case:", int(it.sum()), "iterations,", int((st == 0).sum()), "of 16 converged,",
-          "L finite:", bool(torch.isfinite(L).all()), "gradient finite:", bool(torch.isfinite(grad).all()))

@@ -369,3 +369,22 @@ def test_short_row_order_is_bitwise_neutral(mat, k):
         for kk in np.unique(key):
             ids = order[key == kk]
             assert np.all(np.diff(ids) > 0)
+
+
+@pytest.mark.parametrize("k", [4, 32, 128])
+@pytest.mark.parametrize("unroll,bps", [(1, 8), (2, 5), (4, 4)])
+def test_gather_probe_reads_every_row_once(k, unroll, bps):
+    """The gather-bound probe reads row indices[e] of X for every entry (and nothing else):
+    the sum of its per-thread sums is the sum of those rows, in float64 within float32
+    accumulation error; indices outside [0, n) are skipped."""
+    A = synth.powerlaw_csr(20000, seed=3, max_len=500)
+    idx = A.indices.astype(np.int32).copy()
+    idx[::97] = -5                                  # out of range: skipped
+    idx[1::89] = A.n + 3
+    X = synth.normal((A.n, k), seed=4)
+    out = spx.abi.spx_gather_probe(torch.from_numpy(idx).cuda(), A.n, torch.from_numpy(X).cuda(), unroll, bps)
+    got = float(out.double().sum())
+    ok = (idx >= 0) & (idx < A.n)
+    rows = X.astype(np.float64)[idx[ok]]
+    want = float(rows.sum())
+    assert abs(got - want) <= 1e-5 * float(np.abs(rows).sum())

@@ -1,9 +1,10 @@
 """spx_spmm_t_noalloc: the transpose product for callers that cannot allocate device
 memory when they call it (the library stages A^T's values in a built-in scratch array).
 
-Checked against the workspace entry point spx_spmm_t on two calls in a row (the shared
-scratch keeps the previous call's contents, which must not leak into the next result),
-and the size limit is checked to fail cleanly before any device work.  This file is
+Checked against the FP64 oracle (A^T G) and against the workspace entry point spx_spmm_t
+on two calls in a row (the shared scratch keeps the previous call's contents, which must
+not leak into the next result), and the size limit is checked to fail cleanly before any
+device work.  This file is
 collected last so that a failure here never hides another test's result."""
 import ctypes
 
@@ -38,7 +39,9 @@ def test_noalloc_matches_workspace_entry_point_twice():
         abi.spx_spmm_t_noalloc(st, perm, G, got, 1.0, 0.0, plan)
         torch.cuda.synchronize()
         g, r = got.cpu().numpy(), ref.cpu().numpy()
-        norm = oracle.spmm_t(abs_csr(A), np.abs(G.cpu().numpy()))
+        Gh = G.cpu().numpy()
+        norm = oracle.spmm_t(abs_csr(A), np.abs(Gh))
+        assert_close_normalised(g, oracle.spmm_t(A, Gh), norm, rel=REL_TOL, what=f"noalloc vs oracle, call {call}")
         assert_close_normalised(g, r, norm, rel=REL_TOL, what=f"noalloc vs workspace, call {call}")
         assert np.all(np.isfinite(g))
 
