@@ -324,16 +324,32 @@ class Workload:
         self.ws_sddmm = ws(abi.spx_sddmm_workspace_size(self.s_A, k, self.sddmm_cb))
         self.ws_t = ws(abi.spx_spmm_t_workspace_size(self.s_AT, k, self.t_plan))
         self.ws_tv = ws(abi.spx_spmm_workspace_size(self.s_ATv, k, self.t_plan))
+        # row plan or merge path, per product (device-timed on this pattern and width)
+        self.engine = {}
+        for kind in ("spmm", "sddmm", "spmm_t"):
+            ch = ("rows",) if NO_TUNE else tune.tune_engine(self.dA, k, kind)
+            if ch[0] == "merge":
+                mp = self.dA.t_merge_plan(ch[1]) if kind == "spmm_t" else self.dA.merge_plan(ch[1])
+                st = self.s_ATv if kind == "spmm_t" else self.s_A
+                mws = ws(abi.spx_spmm_merge_workspace_size(st, k, mp)) if kind != "sddmm" else None
+                self.engine[kind] = ("merge", mp, ch[2], mws, ch[1])
+            else:
+                self.engine[kind] = ("rows",)
         npass = lambda cb: -(-k // cb)  # noqa: E731
         rp = lambda cb: 1 if cb < k else 0  # noqa: E731  (slab repack launch)
         nparts = lambda pl: max(1, pl.n_parts) if pl is not None else 1  # noqa: E731
         sp = self.sddmm_plan
-        self.launches = (npass(self.plan.col_block) * nparts(self.plan) + rp(self.plan.col_block)
-                         + npass(self.sddmm_cb) * nparts(sp) + rp(self.sddmm_cb) + 1
-                         + npass(self.t_plan.col_block) * nparts(self.t_plan) + rp(self.t_plan.col_block))
-        self.spmm_kernel_launches = npass(self.plan.col_block) * nparts(self.plan) + \
-            npass(self.t_plan.col_block) * nparts(self.t_plan)
-        self.tuning = {"spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine,
+        row_launches = {"spmm": npass(self.plan.col_block) * nparts(self.plan) + rp(self.plan.col_block),
+                        "sddmm": npass(self.sddmm_cb) * nparts(sp) + rp(self.sddmm_cb),
+                        "spmm_t": npass(self.t_plan.col_block) * nparts(self.t_plan) + rp(self.t_plan.col_block)}
+        # a merge-path product is its kernel plus, for SpMM, the carry fix-up
+        per = {kk: ((2 if kk != "sddmm" else 1) if self.engine[kk][0] == "merge" else row_launches[kk])
+               for kk in row_launches}
+        self.launches = per["spmm"] + per["sddmm"] + 1 + per["spmm_t"]
+        merge_desc = {kk: (f"merge: {v[4]} items per segment, variant {v[2]}" if v[0] == "merge" else "rows")
+                      for kk, v in self.engine.items()}
+        self.tuning = {"engine": merge_desc,
+                       "spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine,
                                 nparts(self.plan)],
                        "spmm_t": [self.t_plan.col_block, self.t_plan.rows_per_group, self.t_plan.engine,
                                   nparts(self.t_plan)],
@@ -345,24 +361,56 @@ class Workload:
     def launches_per_step(self):
         return self.launches
 
-    def run_kernel(self, which):
-        """One launch of the step.  gX = A^T G is spx_spmm_t's two launches made as two calls
-        (the values gathered into A^T's order, then the product on A^T), so that each is
-        timed on its own; the result is spx_spmm_t's bit for bit."""
+    def buffers(self):
+        """The operands of a step: A's values, X, G, the outputs, A^T's gathered values and the
+        structs that point at them."""
+        return dict(v=self.dA.values, X=self.X, G=self.G, Y=self.Y, gA=self.gA, gX=self.gX, tv=self.t_vals,
+                    sA=self.s_A, sATv=self.s_ATv)
+
+    def slot_like(self, b):
+        """A second set of step buffers with the same shapes (for double buffering)."""
+        import torch
+        nb = {kk: torch.empty_like(b[kk]) for kk in ("v", "X", "G", "Y", "gA", "gX", "tv")}
+        t_ip, t_ix, _ = self.dA.transpose_pattern()
+        nb["sA"] = self.dA.struct(nb["v"])
+        nb["sATv"] = self.abi.csr_struct(self.n, self.m, t_ip, t_ix, nb["tv"])
+        return nb
+
+    def run_kernel(self, which, b=None):
+        """One launch of the step on the buffers b (default: the workload's own).  gX = A^T G is
+        spx_spmm_t's two launches made as two calls (the values gathered into A^T's order,
+        then the product on A^T), so that each is timed on its own; with the row engine the
+        result is spx_spmm_t's bit for bit."""
         a = self.abi
+        b = b or self.buffers()
+        eng = self.engine.get(which, ("rows",))
         if which == "spmm":
-            a.spx_spmm(self.s_A, self.X, self.Y, 1.0, 0.0, self.plan, self.ws_spmm)
+            if eng[0] == "merge":
+                a.spx_spmm_merge(b["sA"], b["X"], b["Y"], eng[1], eng[3], variant=eng[2])
+            else:
+                a.spx_spmm(b["sA"], b["X"], b["Y"], 1.0, 0.0, self.plan, self.ws_spmm)
         elif which == "sddmm":
-            a.spx_sddmm(self.s_A, self.G, self.X, self.gA, 1.0, self.sddmm_cb, self.ws_sddmm, plan=self.sddmm_plan)
+            if eng[0] == "merge":
+                a.spx_sddmm_merge(b["sA"], b["G"], b["X"], b["gA"], eng[1], variant=eng[2])
+            else:
+                a.spx_sddmm(b["sA"], b["G"], b["X"], b["gA"], 1.0, self.sddmm_cb, self.ws_sddmm,
+                            plan=self.sddmm_plan)
         elif which == "gather":
-            a.spx_gather_values(self.perm, self.dA.values, self.t_vals)
+            a.spx_gather_values(self.perm, b["v"], b["tv"])
         else:
-            a.spx_spmm(self.s_ATv, self.G, self.gX, 1.0, 0.0, self.t_plan, self.ws_tv)
+            if eng[0] == "merge":
+                a.spx_spmm_merge(b["sATv"], b["G"], b["gX"], eng[1], eng[3], variant=eng[2])
+            else:
+                a.spx_spmm(b["sATv"], b["G"], b["gX"], 1.0, 0.0, self.t_plan, self.ws_tv)
 
     KERNELS = ("spmm", "sddmm", "gather", "spmm_t")
-    # the CUDA function each launch runs (spmm and spmm_t both run spmm_kernel)
-    CUDA_KERNEL = {"spmm": "spmm_kernel", "sddmm": "sddmm_rows_kernel", "gather": "gather_values_kernel",
-                   "spmm_t": "spmm_kernel"}
+    def cuda_kernel(self, launch):
+        """The CUDA function a launch runs (spmm and spmm_t share one per engine)."""
+        merge = self.engine.get(launch, ("rows",))[0] == "merge"
+        return {"spmm": "spmm_merge_kernel" if merge else "spmm_kernel",
+                "sddmm": "sddmm_merge_kernel" if merge else "sddmm_rows_kernel",
+                "gather": "gather_values_kernel",
+                "spmm_t": "spmm_merge_kernel" if merge else "spmm_kernel"}[launch]
 
 
 def time_workload(W, steps, warmup, ws):
@@ -428,7 +476,7 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
     gb = gather_bytes(W.m, W.n, W.nnz, W.k)
     by_kernel = {}
     for launch, t in per.items():
-        kern = W.CUDA_KERNEL[launch]
+        kern = W.cuda_kernel(launch)
         d = by_kernel.setdefault(kern, {"ms": 0.0, "bytes": 0, "gather_bytes": 0, "launches": []})
         d["ms"] += t
         d["bytes"] += lb[launch]
@@ -446,7 +494,7 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
                                                                    KERNEL_SOURCE[dom])),
                 "algorithmic_bytes": d["bytes"] / nl, "bytes_model": "compulsory, per launch (mean of its launches)",
                 "gather_model_frac": d["gather_bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm}
-    if probe is not None and dom == "spmm_kernel":
+    if probe is not None and dom in ("spmm_kernel", "spmm_merge_kernel"):
         t_floor = sum(probe["A" if ln == "spmm" else "AT"]["ms"] for ln in d["launches"])
         roofline["gather_probe_ms"] = t_floor
         roofline["vs_gather_probe"] = d["ms"] / t_floor
@@ -457,7 +505,8 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
 
 
 KERNEL_SOURCE = {"spmm_kernel": "spmm.cu", "sddmm_rows_kernel": "sddmm.cu", "sddmm_kernel": "sddmm.cu",
-                 "gather_values_kernel": "spmm.cu"}
+                 "gather_values_kernel": "spmm.cu", "spmm_merge_kernel": "merge.cu",
+                 "sddmm_merge_kernel": "merge.cu"}
 
 
 def time_e2e(W, steps, warmup):
@@ -468,24 +517,20 @@ def time_e2e(W, steps, warmup):
     step s - 1's results travel back (the link is full duplex).  Returns (ms per step,
     H2D bytes per step, D2H bytes per step, ms per step with everything on one stream)."""
     import torch
-    from paper_2212_05159_gb300 import abi
     hv = torch.from_numpy(W.host.values).pin_memory()
     hX = W.X.cpu().pin_memory()
     hG = W.G.cpu().pin_memory()
-    slots = [dict(v=W.dA.values, X=W.X, G=W.G, Y=W.Y, gA=W.gA, gX=W.gX)]
-    slots.append({k: torch.empty_like(t) for k, t in slots[0].items()})
+    slots = [W.buffers()]
+    slots.append(W.slot_like(slots[0]))
     for sl in slots:
-        sl["sA"] = W.dA.struct(sl["v"])
-        sl["sAT"] = W.dA.t_struct(sl["v"])
         # each slot's results land in host buffers of their own: consecutive steps' copies
         # back never share memory
         for key in ("Y", "gA", "gX"):
             sl["o" + key] = torch.empty_like(sl[key], device="cpu").pin_memory()
 
     def compute(sl):
-        abi.spx_spmm(sl["sA"], sl["X"], sl["Y"], 1.0, 0.0, W.plan, W.ws_spmm)
-        abi.spx_sddmm(sl["sA"], sl["G"], sl["X"], sl["gA"], 1.0, W.sddmm_cb, W.ws_sddmm, plan=W.sddmm_plan)
-        abi.spx_spmm_t(sl["sAT"], W.perm, sl["G"], sl["gX"], 1.0, 0.0, W.t_plan, W.ws_t)
+        for kname in W.KERNELS:
+            W.run_kernel(kname, sl)
 
     def h2d(sl):
         sl["v"].copy_(hv, non_blocking=True)

@@ -113,20 +113,32 @@ __global__ void __launch_bounds__(MG_THREADS, MINB) spmm_merge_kernel(
         row_end = next_end;
         next_end = row + 1 < m ? indptr[row + 2] : INT_MAX;
     };
+    // batch loads: lane c holds entries c*SLOTS .. of the batch starting at e0 (column -1: none)
+    auto load_batch = [&](int e0, int (&jl)[SLOTS], float (&vl)[SLOTS]) {
+        const int nb = e_end - e0 < B ? e_end - e0 : B;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            const int q = c * SLOTS + s;
+            if (q < nb) {
+                jl[s] = ld_hint(indices + e0 + q, pol_stream);
+                vl[s] = PERM ? __ldg(vals + ld_hint(perm + e0 + q, pol_stream)) : ld_hint(vals + e0 + q, pol_stream);
+            } else {
+                jl[s] = 0;
+                vl[s] = 0.f;
+            }
+        }
+    };
+    int jn[SLOTS];
+    float vn[SLOTS];
+    if (e < e_end) load_batch(e, jn, vn);
     while (e < e_end) {
         const int nb = e_end - e < B ? e_end - e : B;
         int jl[SLOTS];
         float vl[SLOTS];
 #pragma unroll
         for (int s = 0; s < SLOTS; ++s) {
-            const int q = c * SLOTS + s;
-            if (q < nb) {
-                jl[s] = ld_hint(indices + e + q, pol_stream);
-                vl[s] = PERM ? __ldg(vals + ld_hint(perm + e + q, pol_stream)) : ld_hint(vals + e + q, pol_stream);
-            } else {
-                jl[s] = 0;
-                vl[s] = 0.f;
-            }
+            jl[s] = jn[s];
+            vl[s] = vn[s];
         }
         float4 xv[B];
 #pragma unroll
@@ -134,6 +146,8 @@ __global__ void __launch_bounds__(MG_THREADS, MINB) spmm_merge_kernel(
             const int jq = __shfl_sync(gmask, jl[q % SLOTS], q / SLOTS, LPR);
             xv[q] = q < nb ? ld_hint4(xc + (int64_t)jq * ldx, pol_keep) : f4_zero();
         }
+        // the next batch's indices and values travel while this batch's rows are gathered
+        if (e + nb < e_end) load_batch(e + nb, jn, vn);
         // the batch as runs of entries of one row: [q, cut) belongs to the current row
         int q = 0;
         for (;;) {
@@ -224,9 +238,10 @@ __global__ void __launch_bounds__(MG_THREADS, MINB) sddmm_merge_kernel(
     float4 gcur = grow(row);
     int32_t gnext_row = row + 1;
     float4 gnext = grow(gnext_row);
+    int jnext = c < e_end - e ? ld_hint(indices + e + c, pol_stream) : -1;
     while (e < e_end) {
         const int nb = e_end - e < LPR ? e_end - e : LPR;
-        const int jmine = c < nb ? ld_hint(indices + e + c, pol_stream) : -1;
+        const int jmine = jnext;
         float P[LPR];
 #pragma unroll
         for (int q0 = 0; q0 < LPR; q0 += SB) {
@@ -235,6 +250,10 @@ __global__ void __launch_bounds__(MG_THREADS, MINB) sddmm_merge_kernel(
             for (int u = 0; u < SB; ++u) {
                 const int jq = __shfl_sync(gmask, jmine, q0 + u, LPR);
                 xv[u] = jq >= 0 ? ld_hint4(xc + (int64_t)jq * ldx, pol_keep) : f4_zero();
+            }
+            if (q0 == 0) {                       // the next batch's columns travel with these gathers
+                const int en = e + nb;
+                jnext = c < e_end - en ? ld_hint(indices + en + c, pol_stream) : -1;
             }
             // runs of entries of one row: [q, cut) of this part of the batch use G's row `row`
             const int hi = nb < q0 + SB ? nb : q0 + SB;

@@ -162,3 +162,72 @@ def tuned_sddmm_plan(A: CSR, k: int):
     """(column block, plan or None) for spx_sddmm: plan None selects the entry-chunk kernel."""
     cb, mode, np_ = tune_sddmm(A, k)
     return cb, (A.plan().with_params(cb, 2, 0, A.parts(np_)) if mode == "rows" else None)
+
+
+MERGE_KS = (4, 8, 16, 32, 64, 128)
+
+
+def merge_items(A: CSR, k: int, blocks_per_sm: int, waves: int, transposed: bool = False) -> int:
+    """Merged items (row ends + entries) per segment so that the segments fill `waves` rounds
+    of the lane groups that `blocks_per_sm` resident 256-thread blocks per SM hold."""
+    sms = torch.cuda.get_device_properties(A.device).multi_processor_count
+    groups = sms * blocks_per_sm * 256 // (k // 4)
+    rows = A.n if transposed else A.m
+    return max(8, -(-(rows + A.nnz) // (groups * waves)))
+
+
+def tune_engine(A: CSR, k: int, kind: str, force: bool = False):
+    """Row plan or merge path for one product, by device timing on this pattern and width.
+
+    kind: "spmm" (Y = A X), "spmm_t" (A^T G with A^T's values already gathered) or "sddmm".
+    Returns ("rows",) or ("merge", items, variant)."""
+    if k not in MERGE_KS:
+        return ("rows",)
+    key = _key(A, k, "engine:" + kind)
+    with _lock:
+        c = _load()
+        if key in c and not force:
+            return tuple(c[key]["best"])
+    dev = A.device
+    transposed = kind == "spmm_t"
+    rows_in, rows_out = (A.m, A.n) if transposed else (A.n, A.m)
+    if transposed:
+        t_ip, t_ix, perm = A.transpose_pattern()
+        tv = torch.empty(max(A.nnz, 1), device=dev)[: A.nnz]
+        abi.spx_gather_values(perm, A.values, tv)
+        s = abi.csr_struct(A.n, A.m, t_ip, t_ix, tv)
+    else:
+        s = A.struct()
+    table = {}
+    if kind == "sddmm":
+        G = torch.randn(A.m, k, device=dev)
+        X = torch.randn(A.n, k, device=dev)
+        out = torch.empty(A.nnz, device=dev)
+        cb, plan = tuned_sddmm_plan(A, k)
+        ws = abi.workspace(abi.spx_sddmm_workspace_size(s, k, cb), dev)
+        table["rows"] = _time(lambda: abi.spx_sddmm(s, G, X, out, 1.0, cb, ws, plan=plan))
+    else:
+        X = torch.randn(rows_in, k, device=dev)
+        Y = torch.empty(rows_out, k, device=dev)
+        plan = tuned_plan(A, k, transposed)
+        ws = abi.workspace(abi.spx_spmm_workspace_size(s, k, plan), dev)
+        table["rows"] = _time(lambda: abi.spx_spmm(s, X, Y, 1.0, 0.0, plan, ws))
+    best, best_ms = ("rows",), table["rows"]
+    for bps in (4, 6):
+        for waves in (1, 2, 4, 8):
+            items = merge_items(A, k, bps, waves, transposed)
+            mp = A.t_merge_plan(items) if transposed else A.merge_plan(items)
+            if kind == "sddmm":
+                fns = {v: (lambda v=v: abi.spx_sddmm_merge(s, G, X, out, mp, variant=v)) for v in (0, 1, 2)}
+            else:
+                mws = abi.workspace(abi.spx_spmm_merge_workspace_size(s, k, mp), dev)
+                fns = {v: (lambda v=v, mws=mws: abi.spx_spmm_merge(s, X, Y, mp, mws, variant=v)) for v in (0, 1, 2)}
+            for v, fn in fns.items():
+                ms = _time(fn)
+                table[f"merge:{items},{v}"] = ms
+                if ms < best_ms:
+                    best, best_ms = ("merge", items, v), ms
+    with _lock:
+        _load()[key] = {"best": list(best), "ms": best_ms, "table": table}
+        _save()
+    return best
