@@ -21,9 +21,10 @@ host buffers, sampled SM clocks and extra sections: k = 128 and 3D Poisson 128^3
 with its own roofline object and gather bound),
 SpGEMM forward and backward, sparse add, the batched triangular solve, SPAI descent, and
 "cg": the 256-system Jacobi batch replayed from a CUDA graph, training of the learned
-factor (tril(A) and tril(A + A^2)) on 10,016 generated systems, and PCG to a true
-relative residual of 1e-8 on 1000 held-out 256^2 systems with Jacobi, each learned
-factor and IC(0) (the first 128).
+factor (tril(A) and tril(A + A^2); and tril(A) with the paper's N_it = 4, gamma = 0.6) on
+10,016 generated systems each, and PCG to a true relative residual of 1e-8 on 1000
+held-out 256^2 systems with Jacobi, each learned factor and IC(0), every method's time
+including its set-up and its per-pattern analysis.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -819,14 +820,23 @@ def cg_section(args):
     from paper_2212_05159_gb300 import learned, pcg_study
     out = {"batch256_jacobi": pcg_study.batch256_jacobi(graph_replay=True)}
     nets = {}
-    for pattern in args.learned_patterns.split(","):
+    # the training loss of Section 4.3 with this build's horizon and weighting (N_it = 8,
+    # gamma = 0.8) on each factor pattern, and with the paper's (N_it = 4, gamma = 0.6)
+    runs = [(pattern, 8, 0.8) for pattern in args.learned_patterns.split(",")]
+    if args.paper_loss:
+        runs.append(("A", 4, 0.6))
+    for pattern, n_it, gamma in runs:
         net = learned.MPNN(seed=0)
-        tr = pcg_study.train(net, steps=args.train_steps, batch=32, n_it=8, gamma=0.8, lr=2e-3, workers=4,
+        tr = pcg_study.train(net, steps=args.train_steps, batch=32, n_it=n_it, gamma=gamma, lr=2e-3, workers=4,
                              pattern=pattern)
         tr.pop("loss_history", None)
         name = "learned" if pattern == "A" else f"learned_{pattern}"
-        out["training" if pattern == "A" else f"training_{pattern}"] = tr
+        if (n_it, gamma) != (8, 0.8):
+            name += f"_nit{n_it}_gamma{gamma}"
+        out["training" + name[len("learned"):]] = tr
         nets[name] = (net, pattern)
+        if name == "learned":                  # the same network applied as the explicit M = L L^T
+            nets["learned_explicit_M"] = (net, pattern, "M")
     out["eval_256x256"] = pcg_study.evaluate(None, nsys=args.eval_systems, per_batch=args.eval_batch,
                                              methods=("jacobi", *nets, "ic0"), learned_nets=nets,
                                              ic0_systems=min(args.ic0_systems, args.eval_systems))
@@ -879,8 +889,10 @@ def main():
                     help="factor patterns to train and evaluate: A = tril(A), A2 = tril(A + A^2)")
     ap.add_argument("--eval-systems", type=int, default=1000, help="held-out 256^2 systems")
     ap.add_argument("--eval-batch", type=int, default=256, help="held-out systems per PCG launch")
-    ap.add_argument("--ic0-systems", type=int, default=128,
-                    help="the first this many held-out systems are also solved with IC(0) (~50 ms each)")
+    ap.add_argument("--ic0-systems", type=int, default=1000,
+                    help="the first this many held-out systems are also solved with IC(0)")
+    ap.add_argument("--paper-loss", type=int, default=1,
+                    help="also train (and evaluate) a network with the paper's N_it = 4, gamma = 0.6")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

@@ -545,6 +545,41 @@ spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys
                           double delta, int32_t* iters, int32_t* status, double* relres,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* The factored approximate inverse M = L L^T of Section 4.3 with L lower-triangular in
+ * diagonal form, per system: L_{i, i + off_d} for at most 3 offsets off_d <= 0 (e.g. the
+ * 0, -1, -N of tril(A) for a 5-point grid of side N).  spx_dia_analyse finds each system's
+ * offsets from L's pattern (offsets: device int32[nsys * 3], ascending |off|; nd: device
+ * int32[nsys], -1 for a system with more than 3 offsets or an entry above the diagonal)
+ * and writes 1 to *supported_host when every system has at most 3 (synchronizes: reads nd
+ * back).  Once per pattern. */
+spx_status spx_dia_analyse(const spx_csr* L, const int32_t* sys_ptr, int32_t nsys,
+                           int32_t* offsets, int32_t* nd, int32_t* supported_host, void* stream);
+
+/* values_bf16 (device BF16[3 * n], n = L->m): values[d * n + i] = L_{i, i + off_d} rounded
+ * to BF16 (round to nearest even), 0 where row i has no such entry.  Per value set of L;
+ * asynchronous. */
+spx_status spx_dia_fill(const spx_csr* L, const int32_t* sys_ptr, int32_t nsys,
+                        const int32_t* offsets, const int32_t* nd, void* values_bf16, void* stream);
+
+/* spx_cg_batched with M = L L^T, L in the diagonal form above.  Each block keeps its rows of
+ * L (BF16) and of q = A p, z, r, p and w = L^T q in shared memory for the whole solve
+ * (209 KB per 1024-thread block: 8 rows per thread, every system's rows must fit 8 per
+ * thread per block of the cluster) and carries z = M r by z <- z - alpha M q: q is complete
+ * over the cluster after the reduction that gives alpha, so M q needs no cluster barrier.
+ * Rows of q beyond the block are read from the neighbouring blocks' shared memory (the
+ * cluster's distributed shared memory), and the rows of L^T q that L reaches in the
+ * previous block are recomputed locally; at the start and after every reliable update
+ * z = M r is formed directly from the recomputed r.  The sums use L's BF16 values in
+ * FP32.  A system whose offsets are unsupported, or whose halo max|off| exceeds a block's
+ * rows, gets status SPX_NOT_SUPPORTED and relres -1.  Other arguments and results as in
+ * spx_cg_batched (threads per block and cluster from spx_cg_set_launch). */
+spx_status spx_cg_batched_dia(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
+                              const int32_t* order, const float* b, double* x,
+                              const int32_t* dia_offsets, const int32_t* dia_nd,
+                              const void* dia_values_bf16, double tol, int32_t maxit,
+                              double delta, int32_t* iters, int32_t* status, double* relres,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
 /* Launch shape of spx_cg_batched for this process: threads per block (256, 512 or 1024),
  * blocks per cluster (1, 2, 4, 8, or 16 -- a non-portable cluster size the call opts into)
  * and the most clusters resident at once (fewer systems in flight keep their vectors in
@@ -613,8 +648,12 @@ spx_status spx_dense_forward(int64_t n, const float* X1, int32_t K1, const float
 /* spx_dense_forward on the tensor cores (tcgen05, accumulator in tensor memory): the
  * activations are rounded to BF16 (round to nearest even) while they are staged, so the
  * result equals spx_dense_forward applied to BF16-rounded X1, X2 up to the order of the
- * FP32 accumulation.  N must be a multiple of 16 (16..128), K1 + K2 <= 128.  One
- * 128-row tile per block.  Device pointers; asynchronous on `stream`. */
+ * FP32 accumulation.  N must be a multiple of 16 (16..128), K1 + K2 <= 128.  Besides modes
+ * 0-2, two epilogues for inference: mode 3 = the residual layer without U (Y = Hin +
+ * relu(pre), the pre-activation kept nowhere), mode 4 = the product's column halves to two
+ * outputs, Y = pre[:, :N/2] and U = pre[:, N/2:] (each n x N/2), e.g. both heads of the
+ * network from one pass over the activations.  One 128-row tile per block.  Device
+ * pointers; asynchronous on `stream`. */
 spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K1, const float* X2,
                                 int32_t K2, const void* W_bf16, const float* bias, int32_t N,
                                 int32_t mode, const float* Hin, float* Y, float* U, void* stream);

@@ -104,6 +104,9 @@ SIGNATURES = {
     "spx_spmm_merge": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, ctypes.POINTER(spx_mergeplan), _I32, _P, _SZ,
                        _P],
     "spx_sddmm_merge": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, ctypes.POINTER(spx_mergeplan), _I32, _P],
+    "spx_dia_analyse": [_CSRP, _P, _I32, _P, _P, ctypes.POINTER(_I32), _P],
+    "spx_dia_fill": [_CSRP, _P, _I32, _P, _P, _P, _P],
+    "spx_cg_batched_dia": [_CSRP, _P, _I32, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _P, _P, _P, _P, _SZ, _P],
     "spx_gather_probe": [_P, _I64, _I32, _P, _I64, _I32, _I32, _I32, _P, _I64, _P],
     "spx_csr_diagonal": [_CSRP, _P, _P, _P],
     "spx_diagonal_backward": [_I32, _P, _P, _P, _P],
@@ -476,6 +479,33 @@ def spx_cg_batched(A: spx_csr, sys_ptr, nsys: int, order, b, x, pc_kind: int, di
                                 ctypes.byref(LT) if LT is not None else None, lev, float(tol), int(maxit),
                                 float(delta), ptr(iters), ptr(status), ptr(relres), ptr(ws), ws.numel(),
                                 _stream()), "spx_cg_batched")
+
+
+DIA_MAX = 3
+
+
+def spx_dia_analyse(L: spx_csr, sys_ptr, nsys: int, device):
+    """Diagonal form of a lower-triangular pattern per system: (offsets int32[nsys * 3],
+    counts int32[nsys], every system supported)."""
+    offs = torch.zeros(max(nsys, 1) * DIA_MAX, dtype=torch.int32, device=device)
+    nd = torch.zeros(max(nsys, 1), dtype=torch.int32, device=device)
+    ok = _I32(0)
+    _check(lib().spx_dia_analyse(ctypes.byref(L), ptr(sys_ptr), int(nsys), ptr(offs), ptr(nd), ctypes.byref(ok),
+                                 _stream()), "spx_dia_analyse")
+    return offs, nd, bool(ok.value)
+
+
+def spx_dia_fill(L: spx_csr, sys_ptr, nsys: int, offs, nd, out_bf16):
+    _check(lib().spx_dia_fill(ctypes.byref(L), ptr(sys_ptr), int(nsys), ptr(offs), ptr(nd), ptr(out_bf16),
+                              _stream()), "spx_dia_fill")
+    return out_bf16
+
+
+def spx_cg_batched_dia(A: spx_csr, sys_ptr, nsys: int, order, b, x, offs, nd, vals_bf16, tol: float, maxit: int,
+                       delta: float, iters, status, relres, ws):
+    _check(lib().spx_cg_batched_dia(ctypes.byref(A), ptr(sys_ptr), int(nsys), ptr(order), ptr(b), ptr(x), ptr(offs),
+                                    ptr(nd), ptr(vals_bf16), float(tol), int(maxit), float(delta), ptr(iters),
+                                    ptr(status), ptr(relres), ptr(ws), ws.numel(), _stream()), "spx_cg_batched_dia")
 
 
 def spx_ic0_analyse(Lpat: spx_csr, sys_ptr, nsys: int, device):

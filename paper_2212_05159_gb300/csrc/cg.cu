@@ -31,9 +31,13 @@
 // Status per system: SPX_OK, SPX_MAXITER, SPX_BREAKDOWN (p^T A p <= 0 or r^T z <= 0),
 // SPX_NONFINITE.  No spin waits: only cluster / block barriers.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <math.h>
 
+#include <limits.h>
+
 #include <atomic>
+#include <vector>
 
 #include "common.cuh"
 #include "trisolve.cuh"
@@ -54,6 +58,11 @@ constexpr int CG_ROW2_W = 5;
 // threads the blocks that share an SM split the same budget).
 constexpr int CG_SMEM_ROWS_PER_THREAD = 8;
 constexpr int CG_SMEM_VECTORS = 6;
+// Kind 5 keeps q, z, r, p's own entries and w = L^T q in shared memory (5 vectors), a halo of
+// NT rows of w, and the block's rows of at most CG_DIA_MAX diagonals of L in BF16; x's FP32
+// partial stays in the workspace.  160 + 4 + 48 KB at 1024 threads.
+constexpr int CG_DIA_MAX = 3;
+constexpr int CG_DIA_VECTORS = 5;
 
 struct CgArgs {
     int32_t nsys;
@@ -89,6 +98,11 @@ struct CgArgs {
     const int32_t* lev_ptr;   // IC(0): level l of a system = lev_rows[lev_ptr[l] .. lev_ptr[l+1])
     const int32_t* lev_rows;
     int32_t smem_rows;        // rows of a block's private vectors that fit in shared memory (0: none)
+    // diagonal-form factor (kind 5): L_{i, i + off[d]} = dia_val[d * n + i], per system
+    const int32_t* dia_off;   // [nsys * CG_DIA_MAX] offsets (<= 0), ascending |offset|
+    const int32_t* dia_nd;    // [nsys] diagonals per system
+    const __nv_bfloat16* dia_val;
+    int32_t n;                // rows of the batch
 };
 
 // The vectors a thread reads only on its own rows, as seen by one system: in shared memory
@@ -104,6 +118,22 @@ struct Vecs {
     float* po;        // the thread's own entries of p
     int off;
     bool sm;
+    // kind 5 only (shared memory): w = L^T x on the block's rows, w on the halo rows
+    // [lo - H, lo) of the previous block, and the block's rows of L's diagonals
+    float* w = nullptr;
+    float* halo = nullptr;
+    const __nv_bfloat16* ld = nullptr;
+    int cap = 0;
+};
+
+// A system's diagonal-form factor as a block sees it: L_{i, i + off[d]} for d < nd, halo
+// depth H = max |off[d]|, the system's rows [R0, R1), the block's rows [lo, hi) and the
+// row count of a block (chunk; the next block's rows start at hi, the previous block's at
+// lo - chunk).
+struct DiaSys {
+    int nd, H, R0, R1, lo, hi, chunk;
+    int off[CG_DIA_MAX];
+    bool ok;
 };
 
 // ---------------------------------------------------------------- double-float sums
@@ -328,6 +358,136 @@ __device__ __noinline__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) 
     }
 }
 
+// Kind 5: the system's diagonals of L for the block's rows into shared memory (BF16).
+template <int NT>
+__device__ __forceinline__ void dia_load(const CgArgs& a, const Vecs& v, const DiaSys& ds) {
+    __nv_bfloat16* ld = const_cast<__nv_bfloat16*>(v.ld);
+    for (int d = 0; d < ds.nd; ++d)
+        for (int i = ds.lo + threadIdx.x; i < ds.hi; i += NT)
+            ld[d * v.cap + (i - ds.lo)] = a.dia_val[(size_t)d * a.n + i];
+}
+
+// Kind 5: zs = scale * L (L^T xs) on the block's rows (accumulate: zs += ...), with xs
+// complete over the whole cluster (a cluster barrier since it was written).  xs and zs are
+// this block's shared-memory vectors (row i at [i - lo]).  With s_d = -off_d >= 0:
+//   w_i = (L^T x)_i = sum_d L_{i + s_d, i} x_{i + s_d},   (L w)_i = sum_d L_{i, i - s_d} w_{i - s_d}.
+// A row whose terms all lie in the block (i + H < hi for w, i - H >= lo for L w) reads only
+// shared memory; the block's last H rows read x from the next block's shared memory (the
+// same offset, through the cluster's distributed shared memory) and L from the global
+// diagonals, and w is formed again on the previous block's last H rows (the only rows
+// outside the block that L w reaches), so the block never waits for another block's w.
+// Every sum runs over the diagonals in a fixed order.
+// FUSED (the iteration's step, xs = q, scale = -alpha): the first pass also takes
+// x_p += alpha p (xp, po) and r -= alpha q on the row, the second adds <r, z> and <r, r> of
+// the updated row to dots -- the same operations as separate passes, one pass fewer each.
+template <int NT, int ND, bool FUSED>
+__device__ __forceinline__ void dia_apply_nd(cg::cluster_group& cl, unsigned rank, const __nv_bfloat16* __restrict__ gval,
+                                             int n, const float* xs, float* zs, float* w, float* halo,
+                                             const __nv_bfloat16* ld, int cap, int s0, int s1, int s2, int H, int R0,
+                                             int R1, int lo, int hi, int chunk, float scale, bool accumulate,
+                                             float* xp, const float* po, float* rs, DF (&dots)[2]) {
+    const int sd[3] = {s0, s1, s2};
+    const float* xnext = hi < R1 ? cl.map_shared_rank(xs, rank + 1) : nullptr;
+    const float* xprev = lo > R0 ? cl.map_shared_rank(xs, rank - 1) : nullptr;
+    const int lo_prev = lo - chunk;
+    // w_i on any row of the system within reach (general form: x and L anywhere)
+    auto wgeneral = [&](int i) -> float {
+        float t = 0.f;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const int j = i + sd[d];
+            if (j < R1) {
+                const bool own = j >= lo && j < hi;
+                const float lv = own ? __bfloat162float(ld[d * cap + (j - lo)])
+                                     : __bfloat162float(gval[(size_t)d * n + j]);
+                const float xv = own ? xs[j - lo] : (j >= hi ? xnext[j - hi] : xprev[j - lo_prev]);
+                t = fmaf(lv, xv, t);
+            }
+        }
+        return t;
+    };
+    // the halo row of this thread (if any; H <= NT): its terms are loaded first, so that the
+    // remote loads travel while the thread works on its own rows
+    const int hrow = (lo - H > R0 ? lo - H : R0) + (int)threadIdx.x;
+    float hl[ND], hx[ND];
+    const bool has_h = hrow < lo;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        const int j = hrow + sd[d];
+        const bool ok = has_h && j < R1;
+        const bool own = j >= lo && j < hi;
+        hl[d] = !ok ? 0.f : own ? __bfloat162float(ld[d * cap + (j - lo)]) : __bfloat162float(gval[(size_t)d * n + j]);
+        hx[d] = !ok ? 0.f : own ? xs[j - lo] : (j >= hi ? xnext[j - hi] : xprev[j - lo_prev]);
+    }
+    if constexpr (FUSED) {
+        // x_p += alpha p on the thread's rows: x_p lives in global memory, so its loads are all
+        // issued at once (scale = -alpha)
+#pragma unroll
+        for (int k = 0; k < CG_SMEM_ROWS_PER_THREAD; ++k) {
+            const int r = (int)threadIdx.x + k * NT;
+            if (lo + r < hi) xp[r] = fmaf(-scale, po[r], xp[r]);
+        }
+    }
+    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+        const int r = i - lo;
+        if constexpr (FUSED) rs[r] = fmaf(scale, xs[r], rs[r]);  // r -= alpha q
+        float t = 0.f;
+        if (i + H < hi) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) t = fmaf(__bfloat162float(ld[d * cap + r + sd[d]]), xs[r + sd[d]], t);
+        } else {
+            t = wgeneral(i);
+        }
+        w[r] = t;
+    }
+    if (has_h) {
+        float t = 0.f;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) t = fmaf(hl[d], hx[d], t);
+        halo[hrow - (lo - H)] = t;
+    }
+    __syncthreads();
+    for (int i = lo + threadIdx.x; i < hi; i += NT) {
+        const int r = i - lo;
+        float t = 0.f;
+        if (i - H >= lo) {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) t = fmaf(__bfloat162float(ld[d * cap + r]), w[r - sd[d]], t);
+        } else {
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                const int j = i - sd[d];
+                if (j >= R0) t = fmaf(__bfloat162float(ld[d * cap + r]), j >= lo ? w[j - lo] : halo[j - (lo - H)], t);
+            }
+        }
+        const float zr = accumulate ? fmaf(scale, t, zs[r]) : scale * t;
+        zs[r] = zr;
+        if constexpr (FUSED) {
+            const float rr = rs[r];
+            df_add_prod(dots[0], rr, zr);
+            df_add_prod(dots[1], rr, rr);
+        }
+    }
+}
+
+template <int NT, bool FUSED>
+__device__ __forceinline__ void dia_apply(const __nv_bfloat16* gval, int n, cg::cluster_group& cl, unsigned rank,
+                                          const DiaSys& ds, const float* xs, float* zs, float* w, float* halo,
+                                          const __nv_bfloat16* ld, int cap, float scale, bool accumulate, float* xp,
+                                          const float* po, float* rs, DF (&dots)[2]) {
+    const int nd = ds.nd, s0 = -ds.off[0], s1 = -ds.off[1], s2 = -ds.off[2];
+    const int H = ds.H, R0 = ds.R0, R1 = ds.R1, lo = ds.lo, hi = ds.hi, chunk = ds.chunk;
+    if (nd == 3)
+        dia_apply_nd<NT, 3, FUSED>(cl, rank, gval, n, xs, zs, w, halo, ld, cap, s0, s1, s2, H, R0, R1, lo, hi, chunk,
+                                   scale, accumulate, xp, po, rs, dots);
+    else if (nd == 2)
+        dia_apply_nd<NT, 2, FUSED>(cl, rank, gval, n, xs, zs, w, halo, ld, cap, s0, s1, s2, H, R0, R1, lo, hi, chunk,
+                                   scale, accumulate, xp, po, rs, dots);
+    else
+        dia_apply_nd<NT, 1, FUSED>(cl, rank, gval, n, xs, zs, w, halo, ld, cap, s0, s1, s2, H, R0, R1, lo, hi, chunk,
+                                   scale, accumulate, xp, po, rs, dots);
+}
+
 template <int NT, int PC>
 __device__ void apply_pc(const CgArgs& a, const Vecs& v, cg::cluster_group& cl, int lo, int hi, unsigned rank,
                          int sid) {
@@ -371,7 +531,16 @@ __device__ __forceinline__ double true_residual(const CgArgs& a, const Vecs& v, 
 template <int NT, int PC, bool SM>
 __device__ __forceinline__ Vecs make_vecs(const CgArgs& a, float* sv, int lo, int hi) {
     constexpr int cap = CG_SMEM_ROWS_PER_THREAD * NT;
-    if constexpr (SM) {
+    if constexpr (PC == 5) {
+        // [q | z | r | po | w] (cap floats each), halo (NT floats), then the BF16 diagonals
+        __nv_bfloat16* ld = reinterpret_cast<__nv_bfloat16*>(sv + CG_DIA_VECTORS * cap + NT);
+        Vecs v{a.xp + lo, sv, sv + cap, sv + 2 * cap, nullptr, sv + 3 * cap, lo, true};
+        v.w = sv + 4 * cap;
+        v.halo = sv + CG_DIA_VECTORS * cap;
+        v.ld = ld;
+        v.cap = cap;
+        return v;
+    } else if constexpr (SM) {
         if constexpr (PC == 1)
             for (int i = lo + threadIdx.x; i < hi; i += NT) sv[4 * cap + i - lo] = a.dinv[i];
         // element i of every view is at [i - lo]: the global r (gathered by M r) is shifted to match
@@ -386,9 +555,21 @@ __device__ __forceinline__ Vecs make_vecs(const CgArgs& a, float* sv, int lo, in
 template <int NT, int PC, bool SM>
 __device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& cl, unsigned rank, int sid, int lo,
                                            int hi, float* sv, float2 (&red)[CG_MAX_WARPS][4], float2 (&part)[2][4],
-                                           CgBcast& bc, CgScal& sc, int& slot) {
+                                           CgBcast& bc, CgScal& sc, int& slot, const DiaSys& ds) {
     const bool t0 = threadIdx.x == 0;
     const Vecs v = make_vecs<NT, PC, SM>(a, sv, lo, hi);
+    if constexpr (PC == 5) dia_load<NT>(a, v, ds);
+    // z = M r applied directly (at the start and after a reliable update)
+    auto precondition = [&]() {
+        if constexpr (PC == 5) {
+            cl.sync();                                           // r (and L's rows) complete
+            DF unused[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            dia_apply<NT, false>(a.dia_val, a.n, cl, rank, ds, v.r, v.z, v.w, v.halo, v.ld, v.cap, 1.f, false,
+                                 nullptr, nullptr, nullptr, unused);
+        } else {
+            apply_pc<NT, PC>(a, v, cl, lo, hi, rank, sid);
+        }
+    };
     // thread 0 of each block keeps the FP64 scalars; every block computes the same ones
     double& bnorm = sc.bnorm;
     double& rz = sc.rz;
@@ -412,7 +593,7 @@ __device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& c
         v.r[i - v.off] = bi;
         df_add_prod(v2[0], bi, bi);
     }
-    apply_pc<NT, PC>(a, v, cl, lo, hi, rank, sid);
+    precondition();
     for (int i = lo + threadIdx.x; i < hi; i += NT) {
         const float zi = v.z[i - v.off];
         a.p[i] = zi;
@@ -525,6 +706,11 @@ __device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& c
                     df_add_prod(v2n[0], ri, zi);
                     df_add_prod(v2n[1], ri, ri);
                 }
+            } else if constexpr (PC == 5) {
+                // x_p += alpha p; r -= alpha q; z -= alpha M q, with <r, z> and <r, r>: q = A p is
+                // complete over the cluster since the reduction above, so M q needs no barrier
+                dia_apply<NT, true>(a.dia_val, a.n, cl, rank, ds, v.q, v.z, v.w, v.halo, v.ld, v.cap, -alpha, true,
+                                    v.xp, v.po, v.r, v2n);
             } else {
                 float* __restrict__ XP = v.xp - v.off;
                 float* __restrict__ R = v.r - v.off;
@@ -599,7 +785,7 @@ __device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& c
                     __syncthreads();
                 }
                 if (bc.action == ACT_STOP) break;
-                apply_pc<NT, PC>(a, v, cl, lo, hi, rank, sid);
+                precondition();
                 DF vz[1] = {{0.f, 0.f}};
                 for (int i = lo + threadIdx.x; i < hi; i += NT) df_add_prod(vz[0], v.r[i - v.off], v.z[i - v.off]);
                 double o1[1];
@@ -685,12 +871,41 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
         const int chunk = (R1 - R0 + (int)ncl - 1) / (int)ncl;
         const int lo = min(R1, R0 + (int)rank * chunk), hi = min(R1, lo + chunk);
         bool in_smem = false;
-        if constexpr (PC == 0 || PC == 1 || PC == 3)
+        if constexpr (PC == 0 || PC == 1 || PC == 3 || PC == 5)
             in_smem = a.smem_rows >= CG_SMEM_ROWS_PER_THREAD * NT && chunk <= CG_SMEM_ROWS_PER_THREAD * NT;
+        __shared__ DiaSys ds;                                   // block-uniform: kept out of registers
+        if constexpr (PC == 5) {
+            if (t0) {
+                ds.nd = a.dia_nd[sid];
+                ds.H = 0;
+                for (int d = 0; d < CG_DIA_MAX; ++d) {
+                    ds.off[d] = d < ds.nd ? a.dia_off[sid * CG_DIA_MAX + d] : 0;
+                    if (d < ds.nd && -ds.off[d] > ds.H) ds.H = -ds.off[d];
+                }
+                ds.R0 = R0;
+                ds.R1 = R1;
+                ds.lo = lo;
+                ds.hi = hi;
+                ds.chunk = chunk;
+                // the block holds its rows in shared memory and reaches only the adjacent blocks
+                ds.ok = in_smem && ds.nd >= 1 && ds.nd <= CG_DIA_MAX && ds.H <= NT &&
+                        (ds.H <= chunk || (int)ncl == 1);
+            }
+            __syncthreads();
+            if (!ds.ok) {                                       // uniform across the cluster
+                if (rank == 0 && t0) {
+                    a.iters[sid] = 0;
+                    a.status[sid] = SPX_NOT_SUPPORTED;
+                    a.relres[sid] = -1.0;
+                }
+                cl.sync();
+                continue;
+            }
+        }
         if (in_smem)                                            // uniform across the cluster
-            pcg_system<NT, PC, true>(a, cl, rank, sid, lo, hi, sv, red, part, bc, sc, slot);
+            pcg_system<NT, PC, true>(a, cl, rank, sid, lo, hi, sv, red, part, bc, sc, slot, ds);
         else
-            pcg_system<NT, PC, false>(a, cl, rank, sid, lo, hi, sv, red, part, bc, sc, slot);
+            pcg_system<NT, PC, false>(a, cl, rank, sid, lo, hi, sv, red, part, bc, sc, slot, ds);
         cl.sync();                                              // finish before the next system
     }
 }
@@ -716,6 +931,75 @@ __global__ void masked_outer_f64_kernel(int32_t m, const int32_t* __restrict__ p
     for (int e = ptr[row] + lane; e < ptr[row + 1]; e += 32) out[e] = (float)(ui * v[idx[e]]);
 }
 
+// Diagonal form of a lower-triangular factor, per system: the distinct offsets j - i of its
+// stored entries (at most CG_DIA_MAX, all <= 0), ascending in |offset|; nd = -1 when a system
+// has more, or an entry above the diagonal.  One block per system; the set is the same
+// whatever order the threads insert it in, and it is sorted at the end (deterministic).
+__global__ void dia_analyse_kernel(int32_t nsys, const int32_t* __restrict__ sys_ptr,
+                                   const int32_t* __restrict__ l_ptr, const int32_t* __restrict__ l_idx,
+                                   int32_t* __restrict__ offs, int32_t* __restrict__ nd) {
+    constexpr int SLOTS = CG_DIA_MAX + 1;
+    __shared__ int tab[SLOTS];
+    __shared__ int bad;
+    const int sid = blockIdx.x;
+    if (sid >= nsys) return;
+    if (threadIdx.x < SLOTS) tab[threadIdx.x] = INT_MIN;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int i = sys_ptr[sid] + threadIdx.x; i < sys_ptr[sid + 1]; i += blockDim.x) {
+        for (int e = l_ptr[i]; e < l_ptr[i + 1]; ++e) {
+            const int off = l_idx[e] - i;
+            if (off > 0) {
+                bad = 1;
+                continue;
+            }
+            int k = 0;
+            for (; k < SLOTS; ++k) {
+                const int cur = atomicCAS(&tab[k], INT_MIN, off);
+                if (cur == INT_MIN || cur == off) break;
+            }
+            if (k == SLOTS) bad = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int o[SLOTS], c = 0;
+        for (int k = 0; k < SLOTS; ++k)
+            if (tab[k] != INT_MIN) o[c++] = tab[k];
+        for (int x = 1; x < c; ++x)              // insertion sort, descending offset (ascending |offset|)
+            for (int y = x; y > 0 && o[y] > o[y - 1]; --y) {
+                const int t = o[y];
+                o[y] = o[y - 1];
+                o[y - 1] = t;
+            }
+        const bool ok = !bad && c <= CG_DIA_MAX;
+        nd[sid] = ok ? c : -1;
+        for (int d = 0; d < CG_DIA_MAX; ++d) offs[sid * CG_DIA_MAX + d] = ok && d < c ? o[d] : 0;
+    }
+}
+
+// values[d * n + i] = L_{i, i + off_d} rounded to BF16 (zeros, written beforehand, elsewhere);
+// one thread per row, its system by binary search in sys_ptr.
+__global__ void dia_fill_kernel(int32_t n, int32_t nsys, const int32_t* __restrict__ sys_ptr,
+                                const int32_t* __restrict__ l_ptr, const int32_t* __restrict__ l_idx,
+                                const float* __restrict__ l_val, const int32_t* __restrict__ offs,
+                                const int32_t* __restrict__ nd, __nv_bfloat16* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nsys;                       // the system s with sys_ptr[s] <= i < sys_ptr[s + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sys_ptr[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    const int c = nd[lo];
+    for (int e = l_ptr[i]; e < l_ptr[i + 1]; ++e) {
+        const int off = l_idx[e] - (int)i;
+        for (int d = 0; d < c; ++d)
+            if (offs[lo * CG_DIA_MAX + d] == off) out[(int64_t)d * n + i] = __float2bfloat16(l_val[e]);
+    }
+}
+
 // Launch shape of the batched PCG (threads per block, blocks per cluster); 0 = default.
 std::atomic<int> g_cg_threads{0};
 std::atomic<int> g_cg_cluster{0};
@@ -727,6 +1011,67 @@ std::atomic<int> g_cg_smem_vectors{1};
 }  // namespace spx
 
 using namespace spx;
+
+// The persistent launch of the batched PCG for preconditioner kind pc_kind (CgArgs filled).
+static spx_status launch_pcg(CgArgs& a, int pc_kind, cudaStream_t st) {
+    SPX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "spx_cg_batched memset");
+
+    const int nt = g_cg_threads.load() > 0 ? g_cg_threads.load() : 512;
+    const int cl = g_cg_cluster.load() > 0 ? g_cg_cluster.load() : 8;
+    const int blocks_per_sm = nt >= 1024 ? 1 : 1024 / nt;      // 64 registers per thread
+    int clusters = blocks_per_sm * num_sms() / cl;
+    const int maxc = g_cg_max_clusters.load();
+    if (maxc > 0 && clusters > maxc) clusters = maxc;
+    if (clusters < 1) clusters = 1;
+    if (clusters > a.nsys) clusters = a.nsys;
+    const bool smem_vecs = pc_kind == 5 ||
+                           (g_cg_smem_vectors.load() != 0 && (pc_kind == 0 || pc_kind == 1 || pc_kind == 3));
+    a.smem_rows = smem_vecs ? CG_SMEM_ROWS_PER_THREAD * nt : 0;
+    const size_t smem = pc_kind == 5
+        ? (size_t)a.smem_rows * (CG_DIA_VECTORS * sizeof(float) + CG_DIA_MAX * sizeof(__nv_bfloat16)) +
+              (size_t)nt * sizeof(float)
+        : (size_t)a.smem_rows * CG_SMEM_VECTORS * sizeof(float);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(clusters * cl));
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    auto launch = [&](auto kern) -> spx_status {
+        if (cl > 8)   // 16 blocks per cluster is beyond the portable size: opt in
+            SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+                     "spx_cg_batched cluster attribute");
+        if (smem > 0)
+            SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                     "spx_cg_batched shared memory attribute");
+        SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, a), "spx_cg_batched launch");
+        return SPX_OK;
+    };
+    auto by_pc = [&](auto k0, auto k1, auto k2, auto k3, auto k4, auto k5) -> spx_status {
+        switch (pc_kind) {
+            case 0: return launch(k0);
+            case 1: return launch(k1);
+            case 2: return launch(k2);
+            case 3: return launch(k3);
+            case 4: return launch(k4);
+            default: return launch(k5);
+        }
+    };
+    if (nt == 256)
+        return by_pc(pcg_kernel<256, 0>, pcg_kernel<256, 1>, pcg_kernel<256, 2>, pcg_kernel<256, 3>, pcg_kernel<256, 4>,
+                     pcg_kernel<256, 5>);
+    if (nt == 1024)
+        return by_pc(pcg_kernel<1024, 0>, pcg_kernel<1024, 1>, pcg_kernel<1024, 2>, pcg_kernel<1024, 3>,
+                     pcg_kernel<1024, 4>, pcg_kernel<1024, 5>);
+    return by_pc(pcg_kernel<512, 0>, pcg_kernel<512, 1>, pcg_kernel<512, 2>, pcg_kernel<512, 3>, pcg_kernel<512, 4>,
+                 pcg_kernel<512, 5>);
+}
 
 extern "C" spx_status spx_cg_workspace_size(int32_t n, size_t* bytes) {
     if (!bytes || n < 0) return set_error(SPX_INVALID_ARG, "spx_cg_workspace_size: bad arguments");
@@ -802,56 +1147,7 @@ extern "C" spx_status spx_cg_batched(const spx_csr* A, const int32_t* sys_ptr, i
         a.lev_ptr = ic0_levels[1];
         a.lev_rows = ic0_levels[2];
     }
-    SPX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(int32_t), st), "spx_cg_batched memset");
-
-    const int nt = g_cg_threads.load() > 0 ? g_cg_threads.load() : 512;
-    const int cl = g_cg_cluster.load() > 0 ? g_cg_cluster.load() : 8;
-    const int blocks_per_sm = nt >= 1024 ? 1 : 1024 / nt;      // 64 registers per thread
-    int clusters = blocks_per_sm * num_sms() / cl;
-    const int maxc = g_cg_max_clusters.load();
-    if (maxc > 0 && clusters > maxc) clusters = maxc;
-    if (clusters < 1) clusters = 1;
-    if (clusters > nsys) clusters = nsys;
-    const bool smem_vecs = g_cg_smem_vectors.load() != 0 && (pc_kind == 0 || pc_kind == 1 || pc_kind == 3);
-    a.smem_rows = smem_vecs ? CG_SMEM_ROWS_PER_THREAD * nt : 0;
-    const size_t smem = (size_t)a.smem_rows * CG_SMEM_VECTORS * sizeof(float);
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)(clusters * cl));
-    cfg.blockDim = dim3(nt);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    auto launch = [&](auto kern) -> spx_status {
-        if (cl > 8)   // 16 blocks per cluster is beyond the portable size: opt in
-            SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
-                     "spx_cg_batched cluster attribute");
-        if (smem > 0)
-            SPX_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                     "spx_cg_batched shared memory attribute");
-        SPX_CUDA(cudaLaunchKernelEx(&cfg, kern, a), "spx_cg_batched launch");
-        return SPX_OK;
-    };
-    auto by_pc = [&](auto k0, auto k1, auto k2, auto k3, auto k4) -> spx_status {
-        switch (pc_kind) {
-            case 0: return launch(k0);
-            case 1: return launch(k1);
-            case 2: return launch(k2);
-            case 3: return launch(k3);
-            default: return launch(k4);
-        }
-    };
-    if (nt == 256)
-        return by_pc(pcg_kernel<256, 0>, pcg_kernel<256, 1>, pcg_kernel<256, 2>, pcg_kernel<256, 3>, pcg_kernel<256, 4>);
-    if (nt == 1024)
-        return by_pc(pcg_kernel<1024, 0>, pcg_kernel<1024, 1>, pcg_kernel<1024, 2>, pcg_kernel<1024, 3>,
-                     pcg_kernel<1024, 4>);
-    return by_pc(pcg_kernel<512, 0>, pcg_kernel<512, 1>, pcg_kernel<512, 2>, pcg_kernel<512, 3>, pcg_kernel<512, 4>);
+    return launch_pcg(a, pc_kind, st);
 }
 
 extern "C" spx_status spx_diag_inverse(const spx_csr* A, float* dinv, void* stream) {
@@ -896,4 +1192,89 @@ extern "C" spx_status spx_cg_set_vector_residency(int32_t shared_memory) {
         return set_error(SPX_INVALID_ARG, "spx_cg_set_vector_residency: 0 or 1");
     g_cg_smem_vectors.store(shared_memory);
     return SPX_OK;
+}
+
+extern "C" spx_status spx_dia_analyse(const spx_csr* L, const int32_t* sys_ptr, int32_t nsys, int32_t* offsets,
+                                      int32_t* nd, int32_t* supported_host, void* stream) {
+    SPX_TRY(check_csr(L, false, "spx_dia_analyse"));
+    if (nsys < 0 || (nsys > 0 && (!sys_ptr || !offsets || !nd)) || !supported_host)
+        return set_error(SPX_INVALID_ARG, "spx_dia_analyse: bad arguments");
+    *supported_host = 1;
+    if (nsys == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    dia_analyse_kernel<<<(unsigned)nsys, 256, 0, st>>>(nsys, sys_ptr, L->indptr, L->indices, offsets, nd);
+    SPX_CHECK_LAUNCH("spx_dia_analyse");
+    // a system is unsupported when nd < 0: the minimum over the systems, read back once
+    std::vector<int32_t> host((size_t)nsys);
+    SPX_CUDA(cudaMemcpyAsync(host.data(), nd, (size_t)nsys * sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+             "spx_dia_analyse copy");
+    SPX_CUDA(cudaStreamSynchronize(st), "spx_dia_analyse sync");
+    for (int32_t k = 0; k < nsys; ++k)
+        if (host[(size_t)k] < 1) *supported_host = 0;
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_dia_fill(const spx_csr* L, const int32_t* sys_ptr, int32_t nsys, const int32_t* offsets,
+                                   const int32_t* nd, void* values_bf16, void* stream) {
+    SPX_TRY(check_csr(L, true, "spx_dia_fill"));
+    if (nsys < 0 || (nsys > 0 && (!sys_ptr || !offsets || !nd || !values_bf16)))
+        return set_error(SPX_INVALID_ARG, "spx_dia_fill: bad arguments");
+    if (L->m == 0 || nsys == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    SPX_CUDA(cudaMemsetAsync(values_bf16, 0, (size_t)CG_DIA_MAX * L->m * sizeof(__nv_bfloat16), st),
+             "spx_dia_fill memset");
+    dia_fill_kernel<<<(unsigned)((L->m + 255) / 256), 256, 0, st>>>(L->m, nsys, sys_ptr, L->indptr, L->indices,
+                                                                   L->values, offsets, nd,
+                                                                   static_cast<__nv_bfloat16*>(values_bf16));
+    SPX_CHECK_LAUNCH("spx_dia_fill");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_cg_batched_dia(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys, const int32_t* order,
+                                         const float* b, double* x, const int32_t* dia_offsets, const int32_t* dia_nd,
+                                         const void* dia_values_bf16, double tol, int32_t maxit, double delta,
+                                         int32_t* iters, int32_t* status, double* relres, void* ws, size_t ws_bytes,
+                                         void* stream) {
+    SPX_TRY(check_csr(A, true, "spx_cg_batched_dia"));
+    if (A->m != A->n) return set_error(SPX_INVALID_ARG, "spx_cg_batched_dia: A must be square");
+    if (nsys < 0 || (nsys > 0 && (!sys_ptr || !b || !x || !iters || !status || !relres || !dia_offsets || !dia_nd ||
+                                  !dia_values_bf16)))
+        return set_error(SPX_INVALID_ARG, "spx_cg_batched_dia: NULL argument");
+    if (!(tol > 0.0) || maxit < 0 || !(delta > 0.0 && delta < 1.0))
+        return set_error(SPX_INVALID_ARG, "spx_cg_batched_dia: tol > 0, maxit >= 0, 0 < delta < 1 required");
+    size_t need = 0;
+    spx_cg_workspace_size(A->m, &need);
+    if (!ws || ws_bytes < need)
+        return set_error(SPX_OOM_WORKSPACE, "spx_cg_batched_dia: workspace %zu < %zu", ws_bytes, need);
+    if (nsys == 0) return SPX_OK;
+    const size_t v = ((size_t)A->m * 4 + 255) & ~size_t(255);
+    char* w = static_cast<char*>(ws);
+    CgArgs a{};
+    a.nsys = nsys;
+    a.sys_ptr = sys_ptr;
+    a.order = order;
+    a.a_ptr = A->indptr;
+    a.a_idx = A->indices;
+    a.a_val = A->values;
+    a.b = b;
+    a.x = x;
+    a.pc = 5;
+    a.dia_off = dia_offsets;
+    a.dia_nd = dia_nd;
+    a.dia_val = static_cast<const __nv_bfloat16*>(dia_values_bf16);
+    a.n = A->m;
+    a.r = (float*)(w + 0 * v);
+    a.p = (float*)(w + 1 * v);
+    a.q = (float*)(w + 2 * v);
+    a.z = (float*)(w + 3 * v);
+    a.w = (float*)(w + 4 * v);
+    a.xp = (float*)(w + 5 * v);
+    a.queue = (int32_t*)(w + 6 * v);
+    a.tol = tol;
+    a.delta = delta;
+    a.maxit = maxit;
+    a.iters = iters;
+    a.status = status;
+    a.relres = relres;
+    return launch_pcg(a, 5, as_stream(stream));
 }

@@ -3,7 +3,9 @@
 // BF16 operands (activations rounded to BF16 while staged, BF16 weights), FP32
 // accumulation in tensor memory.
 //
-// One CTA of 128 threads per 128-row tile (the layer is memory-bound: K, N <= 128):
+// Persistent CTAs of 128 threads, as many per SM as shared memory allows, each walking
+// 128-row tiles (the layer is memory-bound: K, N <= 128); W^T, the mbarrier and the
+// accumulator columns are set up once per CTA:
 //   * the threads stage the tile's activations with coalesced float4 loads (consecutive
 //     threads read consecutive 16-byte pieces of a row), convert them to BF16 and store
 //     them in the canonical no-swizzle K-major layout: 8-row x 16-byte core matrices, the
@@ -50,6 +52,15 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
 // byte offset of element (row, k) in the core-matrix layout of a rows x Kpad operand
 __device__ __forceinline__ uint32_t core_off(int row, int k, int kpad) {
     return (uint32_t)((row >> 3) * (kpad >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Byte offset of W^T in the forward kernel's shared memory: after the larger of the A tile
+// and the epilogue rows, rounded up to 1 KB.
+__host__ __device__ inline size_t tc_b_offset(int K, int N) {
+    const size_t kpad = (size_t)((K + 15) & ~15);
+    const size_t a = (size_t)TC_M * kpad * 2;
+    const size_t stage = (size_t)TC_M * (N + 4) * 4;
+    return ((a > stage ? a : stage) + 1023) & ~size_t(1023);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -101,23 +112,14 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
     __shared__ uint32_t tmem_slot;
     const int K = K1 + K2;
     const int kpad = (K + 15) & ~15;
+    // [A tile | epilogue rows] (reused every tile), then W^T (staged once per CTA)
     unsigned char* sA = smem;                                   // 128 x kpad bf16
-    unsigned char* sB = smem + TC_M * kpad * 2;                 // N x kpad bf16, after A
+    unsigned char* sB = smem + tc_b_offset(K, N);               // N x kpad bf16
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * TC_M;
     const int ncols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+    const int64_t ntiles = (n + TC_M - 1) / TC_M;
 
-    // ---- stage A = [X1 X2] (FP32 -> BF16) and its zero padding up to kpad
-    stage_rows(sA, X1, K1, 0, kpad, row0, n);
-    if (K2 > 0) stage_rows(sA, X2, K2, K1, kpad, row0, n);
-    if (kpad > K) {
-        const int pq = (kpad - K) >> 2;                        // K % 4 == 0: padding in 4-column pieces
-        for (int t = threadIdx.x; t < TC_M * pq; t += TC_THREADS) {
-            const int r = t / pq, kq = t - r * pq;
-            *reinterpret_cast<uint2*>(sA + core_off(r, K + kq * 4, kpad)) = make_uint2(0u, 0u);
-        }
-    }
-    // ---- stage B = W^T (N rows, K-major); consecutive threads read consecutive columns of W
+    // ---- once per CTA: B = W^T (N rows, K-major), the mbarrier, the accumulator columns
     for (int t = threadIdx.x; t < N * kpad; t += TC_THREADS) {
         const int k = t / N, nn = t - k * N;
         const __nv_bfloat16 w = k < K ? W[k * N + nn] : __float2bfloat16(0.f);
@@ -133,38 +135,62 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    fence_proxy_async();                   // generic smem writes -> visible to the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    if (threadIdx.x == 0) {
-        const uint32_t idesc = instr_desc(TC_M, N);
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-        const uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
-        for (int s = 0; s < kpad / 16; ++s) {
-            const uint64_t ad = smem_desc(a0 + s * 256u, 128u, sbo);
-            const uint64_t bd = smem_desc(b0 + s * 256u, 128u, sbo);
-            const uint32_t acc = s > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
+        const int64_t row0 = tile * TC_M;
+        // ---- stage A = [X1 X2] (FP32 -> BF16) and its zero padding up to kpad
+        stage_rows(sA, X1, K1, 0, kpad, row0, n);
+        if (K2 > 0) stage_rows(sA, X2, K2, K1, kpad, row0, n);
+        if (kpad > K) {
+            const int pq = (kpad - K) >> 2;                    // K % 4 == 0: padding in 4-column pieces
+            for (int t = threadIdx.x; t < TC_M * pq; t += TC_THREADS) {
+                const int r = t / pq, kq = t - r * pq;
+                *reinterpret_cast<uint2*>(sA + core_off(r, K + kq * 4, kpad)) = make_uint2(0u, 0u);
+            }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&mbar))
-                     : "memory");
-    }
-    const bool ok = __all_sync(FULL, mbar_wait(smem_u32(&mbar), 0, 2000000000ull));   // warp-uniform
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) {
-        if (threadIdx.x == 0 && err) atomicOr(err, 2);
-    } else {
+        fence_proxy_async();               // generic smem writes -> visible to the tensor cores
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+        if (threadIdx.x == 0) {
+            const uint32_t idesc = instr_desc(TC_M, N);
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            const uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
+            for (int s = 0; s < kpad / 16; ++s) {
+                const uint64_t ad = smem_desc(a0 + s * 256u, 128u, sbo);
+                const uint64_t bd = smem_desc(b0 + s * 256u, 128u, sbo);
+                const uint32_t acc = s > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        const bool ok = __all_sync(FULL, mbar_wait(smem_u32(&mbar), phase, 2000000000ull));   // warp-uniform
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // a wait that ran out in one warp ends the CTA's work after this tile for all warps
+        __shared__ int stop;
+        if (threadIdx.x == 0) stop = 0;
+        __syncthreads();
+        if (!ok && lane == 0) stop = 1;
+        __syncthreads();
+        if (stop) {
+            if (threadIdx.x == 0 && err) atomicOr(err, 2);
+            break;
+        }
         // ---- epilogue 1: accumulator lanes of this warp (rows 32w .. 32w + 31) -> shared
-        // memory, bias added.  The MMAs have completed (mbarrier), so the operand tiles are
-        // free; each warp reuses its own slice: 32 rows x (N + 4) floats.
+        // memory, bias added.  The MMAs have completed (mbarrier), so the A tile is free;
+        // each warp reuses its own slice of it: 32 rows x (N + 4) floats.
         const int ldst = N + 4;                                      // padded row stride (floats)
         float* stage = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * ldst;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -194,9 +220,10 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
         const int64_t wrow0 = row0 + warp * 32;
         const int nv = n - wrow0 >= 32 ? 32 : (n > wrow0 ? (int)(n - wrow0) : 0);
         const int total = nv * n4;
+        const bool residual = mode == 2 || mode == 3;
         for (int t0 = lane; t0 < total; t0 += EPI_BATCH * 32) {
             float4 h[EPI_BATCH];
-            if (mode == 2) {
+            if (residual) {
 #pragma unroll
                 for (int u = 0; u < EPI_BATCH; ++u) {
                     const int t = t0 + u * 32;
@@ -218,14 +245,24 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_kernel(int64_t n, const f
                 } else if (mode == 1) {
                     __stcs(reinterpret_cast<float4*>(Y + o),
                            make_float4(fmaxf(pre.x, 0.f), fmaxf(pre.y, 0.f), fmaxf(pre.z, 0.f), fmaxf(pre.w, 0.f)));
+                } else if (mode == 4) {
+                    // two outputs of N / 2 columns each: the column halves of the product
+                    const int h2 = N >> 1;
+                    const int c = cq * 4;
+                    float* dst = c < h2 ? Y + (wrow0 + r) * h2 + c : U + (wrow0 + r) * h2 + (c - h2);
+                    __stcs(reinterpret_cast<float4*>(dst), pre);
                 } else {
-                    __stcs(reinterpret_cast<float4*>(U + o), pre);
+                    if (mode == 2) __stcs(reinterpret_cast<float4*>(U + o), pre);
                     __stcs(reinterpret_cast<float4*>(Y + o),
                            make_float4(h[u].x + fmaxf(pre.x, 0.f), h[u].y + fmaxf(pre.y, 0.f),
                                        h[u].z + fmaxf(pre.z, 0.f), h[u].w + fmaxf(pre.w, 0.f)));
                 }
             }
         }
+        // the A / epilogue region and the accumulator are free for the next tile
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -619,9 +656,7 @@ __global__ void __launch_bounds__(256) tc_wgrad_reduce_kernel(int nparts, int K,
 // N, whichever is larger (smaller layers fit more blocks per SM).
 size_t tc_smem_bytes(int K, int N) {
     const size_t kpad = (size_t)((K + 15) & ~15);
-    const size_t tiles = (size_t)TC_M * kpad * 2 + (size_t)N * kpad * 2;
-    const size_t stage = (size_t)TC_M * (N + 4) * 4;
-    return tiles > stage ? tiles : stage;
+    return tc_b_offset(K, N) + (size_t)N * kpad * 2;
 }
 
 // Shared memory of the data-gradient kernel: G's and W's tiles over N, or the epilogue rows
@@ -643,21 +678,31 @@ using namespace spx;
 extern "C" spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K1, const float* X2, int32_t K2,
                                            const void* W_bf16, const float* bias, int32_t N, int32_t mode,
                                            const float* Hin, float* Y, float* U, void* stream) {
-    if (n < 0 || K1 < 1 || K2 < 0 || K1 + K2 > TC_KMAX || N < 16 || N > TC_NMAX || N % 16 != 0 || mode < 0 ||
-        mode > 2)
+    if (n < 0 || K1 < 1 || K2 < 0 || K1 + K2 > TC_KMAX || N < 16 || N > TC_NMAX || N % 16 != 0)
         return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: sizes (K <= 128, N in 16..128, N %% 16 == 0)");
-    if (n > 0 && (!X1 || (K2 > 0 && !X2) || !W_bf16 || !Y || (mode == 2 && (!Hin || !U))))
+    if (mode < 0 || mode > 4) return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: mode %d (0..4)", mode);
+    if (n > 0 && (!X1 || (K2 > 0 && !X2) || !W_bf16 || !Y || ((mode == 2 || mode == 4) && !U) ||
+                  ((mode == 2 || mode == 3) && !Hin)))
         return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: NULL operand");
     if (K1 % 4 != 0 || K2 % 4 != 0 || !al16(X1) || (K2 > 0 && !al16(X2)) || !al16(Y) ||
-        (mode == 2 && (!al16(Hin) || !al16(U))))
+        ((mode == 2 || mode == 3) && !al16(Hin)) || ((mode == 2 || mode == 4) && !al16(U)))
         return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: K1, K2 multiples of 4 and 16-byte aligned rows needed");
     if (n == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
     const size_t smem = tc_smem_bytes(K1 + K2, N);
     static std::atomic<unsigned long long> attr_done{0};
-    SPX_TRY(ensure_smem_attr(dense_tc_kernel, TC_SMEM, attr_done, "spx_dense_forward_tc attribute"));
+    SPX_TRY(ensure_smem_attr(dense_tc_kernel, (int)tc_smem_bytes(TC_KMAX, TC_NMAX), attr_done,
+                             "spx_dense_forward_tc attribute"));
+    // persistent CTAs: as many as fit an SM by shared memory (and by tensor-memory columns,
+    // 512 per SM), each walking its 128-row tiles
     const int64_t tiles = (n + TC_M - 1) / TC_M;
-    dense_tc_kernel<<<(unsigned)tiles, TC_THREADS, smem, st>>>(n, X1, K1, X2, K2,
+    const int ncols = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+    int per_sm = (int)((227 * 1024) / (smem + 1024));
+    if (per_sm > 512 / ncols) per_sm = 512 / ncols;
+    if (per_sm > 8) per_sm = 8;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t grid = tiles < (int64_t)per_sm * num_sms() ? tiles : (int64_t)per_sm * num_sms();
+    dense_tc_kernel<<<(unsigned)grid, TC_THREADS, smem, st>>>(n, X1, K1, X2, K2,
                                                               static_cast<const __nv_bfloat16*>(W_bf16), bias, N, mode,
                                                               Hin, Y, U, device_error_word());
     SPX_CHECK_LAUNCH("spx_dense_forward_tc");

@@ -93,6 +93,14 @@ class Graph:
         self.E.plan()
         self.features()
 
+    def rebind(self, A: CSR):
+        """Use this graph (patterns, transposes, plans) for another matrix of the same pattern
+        (other values); call features() next."""
+        if A.m != self.A.m or A.nnz != self.A.nnz:
+            raise ValueError("Graph.rebind: a matrix of another pattern")
+        self.A = A
+        return self
+
     def features(self, values: torch.Tensor | None = None):
         """(Re)computes d, e and the node features for A's values (same pattern)."""
         abi.spx_mpnn_features(self.A.struct(values), self.d, self.e, self.f)
@@ -159,11 +167,16 @@ class MPNN:
         return self.view(self.grad, name)
 
     # ------------------------------------------------------------------ forward
-    def forward(self, G: Graph, tensor_cores: bool = False):
+    def forward(self, G: Graph, tensor_cores: bool = False, inference: bool = False):
         """L values on G.Lpat; returns (L, saved activations).
 
         tensor_cores: run the dense layers on tcgen05 (activations rounded to BF16); the
-        default keeps FP32 activations (CUDA-core kernels)."""
+        default keeps FP32 activations (CUDA-core kernels).  inference (tensor cores only):
+        the same L without what the reverse pass needs -- the residual layers keep no
+        pre-activation and both heads come from one product (P | Q = h [Ua Ub]); returns
+        (L, None)."""
+        if inference and tensor_cores:
+            return self._infer(G), None
         n, dev = G.n, self.device
         emp = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
         dense = abi.spx_dense_forward_tc if tensor_cores else abi.spx_dense_forward
@@ -190,6 +203,28 @@ class MPNN:
         abi.spx_edge_forward(G.Lpat.struct(), G.e_low, G.d, P, Q, self.p("u"), self.p("c"), self.p("v"),
                              self.p("bd"), self.p("bo"), L)
         return L, {"hs": hs, "gs": gs, "us": us, "P": P, "Q": Q}
+
+    def _infer(self, G: Graph):
+        """forward(tensor_cores=True) without the saved activations (same arithmetic)."""
+        n, dev = G.n, self.device
+        emp = lambda *s: torch.empty(*s, dtype=torch.float32, device=dev)  # noqa: E731
+        h = emp(n, H)
+        abi.spx_dense_forward_tc(n, G.f, F_IN, None, 0, self.p16("W0"), self.p("b0"), H, 1, None, h)
+        Es = G.E.struct()
+        plan = G.E.plan()
+        g = emp(n, H)
+        hn = emp(n, H)
+        for layer in range(1, LAYERS + 1):
+            abi.spx_spmm(Es, h, g, 1.0, 0.0, plan)
+            abi.spx_dense_forward_tc(n, h, H, g, H, self.p16(f"W{layer}"), self.p(f"b{layer}"), H, 3, h, hn)
+            h, hn = hn, h
+        heads = torch.cat((self.p16("Ua"), self.p16("Ub")), dim=1).contiguous()     # [Ua Ub]: 64 x 128
+        P, Q = emp(n, H), emp(n, H)
+        abi.spx_dense_forward_tc(n, h, H, None, 0, heads, None, 2 * H, 4, None, P, Q)
+        L = emp(G.Lpat.nnz)
+        abi.spx_edge_forward(G.Lpat.struct(), G.e_low, G.d, P, Q, self.p("u"), self.p("c"), self.p("v"),
+                             self.p("bd"), self.p("bo"), L)
+        return L
 
     # ------------------------------------------------------------------ reverse
     def backward(self, G: Graph, saved, gL: torch.Tensor, tensor_cores: bool = False):

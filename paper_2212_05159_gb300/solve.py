@@ -14,7 +14,7 @@ import torch
 from . import abi
 from .csr import CSR
 
-PC = {"none": 0, "jacobi": 1, "llt": 2, "M": 3, "ic0": 4}
+PC = {"none": 0, "jacobi": 1, "llt": 2, "M": 3, "ic0": 4, "dia": 5}
 
 
 class SystemBatch:
@@ -51,7 +51,7 @@ class SystemBatch:
         system per thread."""
         if self.launch is not None:
             return self.launch
-        if kind in (0, 1, 3):
+        if kind in (0, 1, 3, 5):
             want = self.max_rows / (8.0 * 1024.0)
             cl = 2 ** int(np.ceil(np.log2(max(want, 1.0))))
         elif kind == 4:
@@ -109,6 +109,15 @@ class IC0:
         self.batch = batch
         self.factor(values)
 
+    def rebind(self, batch: SystemBatch):
+        """Use this analysis (pattern, level schedule) for another batch of the same pattern
+        and system partition (other values); call factor() next."""
+        if batch.A.m != self.batch.A.m or batch.A.nnz != self.batch.A.nnz or \
+                not np.array_equal(batch.sys_ptr_host, self.batch.sys_ptr_host):
+            raise ValueError("IC0.rebind: a batch of another pattern")
+        self.batch = batch
+        return self
+
     def factor(self, values: torch.Tensor | None = None):
         A = self.batch.A
         v = A.values if values is None else values
@@ -123,18 +132,54 @@ class IC0:
                 abi.csr_struct(n, n, self.t_ip, self.t_ix, self.lt_vals))
 
 
+class DiagonalFactor:
+    """M = L L^T (Section 4.3) with L lower-triangular in diagonal form: per system at most
+    three diagonals L_{i, i + off} (off <= 0), the values in BF16.  The PCG keeps each
+    block's rows of L in shared memory for the whole solve and applies M with block
+    barriers only (spx_cg_batched_dia).  The analysis (offsets per system) depends on the
+    pattern; fill() takes new values of L on the same pattern."""
+
+    def __init__(self, batch: SystemBatch, Lpat: CSR):
+        self.batch = batch
+        self.Lpat = Lpat
+        self.offsets, self.nd, self.supported = abi.spx_dia_analyse(Lpat.struct(), batch.sys_ptr, batch.nsys,
+                                                                    Lpat.device)
+        self.values = torch.zeros(abi.DIA_MAX * max(Lpat.m, 1), dtype=torch.bfloat16, device=Lpat.device)
+
+    def rebind(self, batch: SystemBatch):
+        if batch.A.m != self.batch.A.m or not np.array_equal(batch.sys_ptr_host, self.batch.sys_ptr_host):
+            raise ValueError("DiagonalFactor.rebind: a batch of another partition")
+        self.batch = batch
+        return self
+
+    def fill(self, L_values: torch.Tensor):
+        abi.spx_dia_fill(self.Lpat.struct(L_values), self.batch.sys_ptr, self.batch.nsys, self.offsets, self.nd,
+                         self.values)
+        return self
+
+
 def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor | None = None,
        tol: float = 1e-8, maxit: int | None = None, delta: float = 0.1, values: torch.Tensor | None = None,
-       x: torch.Tensor | None = None, M: CSR | None = None, ic0: IC0 | None = None):
+       x: torch.Tensor | None = None, M: CSR | None = None, ic0: IC0 | None = None,
+       dia: DiagonalFactor | None = None):
     """Solve every system of the batch; returns (x float64, iters, status, relres) tensors.
 
-    pc: "none", "jacobi", "llt" (factor: M = L L^T as two products) or "M" (an explicit
-    sparse SPD M, one product per iteration)."""
+    pc: "none", "jacobi", "llt" (factor: M = L L^T as two products), "M" (an explicit
+    sparse SPD M, one product per iteration), "ic0" or "dia" (M = L L^T with L in diagonal
+    form in shared memory: dia)."""
     A = batch.A
     if maxit is None:
         maxit = int(10 * np.diff(batch.sys_ptr_host).max(initial=1))
     x = x if x is not None else torch.empty(A.m, dtype=torch.float64, device=A.device)
     kind = PC[pc]
+    if kind == 5:
+        if dia is None:
+            raise ValueError("pc='dia' needs a DiagonalFactor")
+        abi.spx_cg_set_launch(*batch.launch_for(kind))
+        abi.spx_cg_batched_dia(A.struct(values), batch.sys_ptr, batch.nsys, batch.order, b.contiguous(), x,
+                               dia.offsets, dia.nd, dia.values, tol, maxit, delta, batch.iters, batch.status,
+                               batch.relres, batch.ws)
+        return x, batch.iters, batch.status, batch.relres
     dinv = batch.dinv(values) if kind == 1 else None
     L = LT = None
     if kind == 2:

@@ -176,6 +176,20 @@ def test_tensor_core_network_matches_bf16_oracle(pattern):
             assert nb <= 0.1 * ne, name
 
 
+@pytest.mark.parametrize("pattern", ["A", "A2"])
+def test_inference_path_gives_the_forward_L(pattern):
+    """forward(inference=True) -- residual layers without their pre-activations, both heads
+    from one product -- computes the training forward's L on the tensor cores."""
+    A, ptr = _batch([6, 11, 30], seed=9, sigma=1.5)
+    net = learned.MPNN(params=_rand_params(4))
+    G = learned.Graph(spx.CSR.from_host(A), pattern)
+    L, _ = net.forward(G, tensor_cores=True)
+    Li, none = net.forward(G, tensor_cores=True, inference=True)
+    assert none is None
+    N_L, _ = ompnn.error_scale(A, net.get_params(), pattern=pattern, bf16=True)
+    assert_close_normalised(host(Li), host(L), N_L, what=f"inference L ({pattern})")
+
+
 def test_initial_network_is_jacobi():
     A, ptr = _batch([7, 9], seed=1)
     net = learned.MPNN(seed=0)

@@ -23,19 +23,21 @@ def _cpu(t):
 
 @pytest.mark.parametrize("n", [1, 127, 300, 4096])
 @pytest.mark.parametrize("K1,K2,N,mode", [(4, 0, 64, 1), (64, 64, 64, 2), (64, 0, 64, 0), (64, 0, 128, 0),
-                                           (32, 16, 32, 1), (12, 8, 16, 1), (60, 68, 128, 0)])
+                                           (32, 16, 32, 1), (12, 8, 16, 1), (60, 68, 128, 0), (64, 64, 64, 3),
+                                           (64, 0, 128, 4), (32, 0, 32, 4)])
 def test_tc_dense_matches_fp64_product(n, K1, K2, N, mode):
-    """Y = [X1 X2] W + b (mode 0), relu of it (1), or U = pre-activation and
-    Y = Hin + relu(U) (2), with X rounded to BF16, against the FP64 product of the rounded
-    X and the BF16 W; normaliser |X||W| + |b| (+ |Hin|)."""
+    """Y = [X1 X2] W + b (mode 0), relu of it (1), U = pre-activation and Y = Hin + relu(U)
+    (2), the same Y without U (3), or the column halves of the pre-activation to Y and U (4),
+    with X rounded to BF16, against the FP64 product of the rounded X and the BF16 W;
+    normaliser |X||W| + |b| (+ |Hin|)."""
     g = torch.Generator().manual_seed(n * 1000 + K1 + K2 + N + mode)
     X1 = torch.randn(n, K1, generator=g).cuda()
     X2 = torch.randn(n, K2, generator=g).cuda() if K2 else None
     W = (torch.randn(K1 + K2, N, generator=g) * 0.2).to(torch.bfloat16).cuda()
     b = torch.randn(N, generator=g).cuda()
-    Hin = torch.randn(n, N, generator=g).cuda() if mode == 2 else None
-    Y = torch.full((n, N), float("nan"), device="cuda")
-    U = torch.full((n, N), float("nan"), device="cuda") if mode == 2 else None
+    Hin = torch.randn(n, N, generator=g).cuda() if mode in (2, 3) else None
+    Y = torch.full((n, N // 2 if mode == 4 else N), float("nan"), device="cuda")
+    U = torch.full((n, N // 2 if mode == 4 else N), float("nan"), device="cuda") if mode in (2, 4) else None
     abi.spx_dense_forward_tc(n, X1, K1, X2, K2, W, b, N, mode, Hin, Y, U)
     abi.spx_check_device()
     Xr = torch.cat([_cpu(_bf16(X1)), _cpu(_bf16(X2))], 1) if K2 else _cpu(_bf16(X1))
@@ -46,8 +48,13 @@ def test_tc_dense_matches_fp64_product(n, K1, K2, N, mode):
         ref = pre
     elif mode == 1:
         ref = torch.relu(pre)
+    elif mode == 4:
+        h2 = N // 2
+        assert_close_normalised(U.cpu().numpy(), pre[:, h2:].numpy(), norm[:, h2:], what="tc second half")
+        ref, norm = pre[:, :h2], norm[:, :h2]
     else:
-        assert_close_normalised(U.cpu().numpy(), pre.numpy(), norm, what="tc pre-activation")
+        if mode == 2:
+            assert_close_normalised(U.cpu().numpy(), pre.numpy(), norm, what="tc pre-activation")
         ref = _cpu(Hin) + torch.relu(pre)
         norm = norm + _cpu(Hin).abs().numpy()
     assert_close_normalised(Y.cpu().numpy(), ref.numpy(), norm, what=f"tc dense n={n} K={K1}+{K2} mode={mode}")
