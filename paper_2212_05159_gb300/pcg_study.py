@@ -29,7 +29,7 @@ def _gen(nsys, seed, lo, hi, sigma):
     return synth.diffusion_system_batch(nsys, seed, lo, hi, sigma)
 
 
-def train(net: learned.MPNN, steps: int, batch: int = 32, n_it: int = 8, gamma: float = 0.8,
+def train(net: learned.MPNN, steps: int, batch: int = 32, n_it: int = 64, gamma: float = 0.9,
           lr: float = 2e-3, seed: int = 1, time_budget_s: float | None = None, log=None,
           tensor_cores: bool = True, workers: int = 0, depth: int = 8, pattern: str = "A", epochs: int = 1):
     """Trains on `steps` fresh batches (steps * batch generated systems).  tensor_cores: the
