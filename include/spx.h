@@ -251,18 +251,25 @@ spx_status spx_spgemm_workspace_size(int32_t m, size_t* bytes);
 
 /* C = A B, step 1 (expand): per-row product counts P_i = sum_{k in A_i} |B_k| and their
  * prefix sums.  Writes the total number of products to *products_host; the symbolic
- * step needs 4 * products bytes of scratch.  A, B patterns only.  Synchronizes. */
+ * step needs 4 * products bytes of scratch.  A, B patterns only.  Synchronizes to return
+ * the count; with products_host NULL (a caller that knows the count, e.g. from an earlier
+ * analysis of the same patterns) it is asynchronous. */
 spx_status spx_spgemm_analyse(const spx_csr* A, const spx_csr* B, int64_t* products_host,
                               void* workspace, size_t workspace_bytes, void* stream);
 
 /* Step 2 (sort / compress): the pattern of C is the structural product -- every (i, j)
  * reached by some A_ik B_kj, with no dropping of numerical zeros.  Writes C_indptr
  * (device int32[m+1]) and nnz(C) to *nnz_c_host, and keeps each row's sorted unique
- * columns in `scratch` (device, >= 4 * products bytes) for spx_spgemm_fill.
- * Synchronizes. */
-spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, int32_t* c_indptr,
-                               int64_t* nnz_c_host, void* workspace, size_t workspace_bytes,
-                               void* scratch, size_t scratch_bytes, void* stream);
+ * columns in `scratch` (device, >= 4 * products bytes) for spx_spgemm_fill.  products: the
+ * count spx_spgemm_analyse returned (sizes the scratch check without a read-back).
+ * Rows of at most 64 products are sorted in registers (bitonic network over shuffles),
+ * longer ones in shared memory or, above 512, with a block bitmap.  Synchronizes once to
+ * return nnz(C); with nnz_c_host NULL it is asynchronous (nnz(C) = C_indptr[m] on the
+ * device). */
+spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, int64_t products,
+                               int32_t* c_indptr, int64_t* nnz_c_host, void* workspace,
+                               size_t workspace_bytes, void* scratch, size_t scratch_bytes,
+                               void* stream);
 
 /* Step 3: C_indices (device int32[nnz(C)], sorted within rows) from the scratch. */
 spx_status spx_spgemm_fill(const spx_csr* A, const int32_t* c_indptr, int32_t* c_indices,

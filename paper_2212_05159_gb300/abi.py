@@ -93,7 +93,7 @@ SIGNATURES = {
     "spx_spmm_t_noalloc": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P],
     "spx_spgemm_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_spgemm_analyse": [_CSRP, _CSRP, ctypes.POINTER(_I64), _P, _SZ, _P],
-    "spx_spgemm_symbolic": [_CSRP, _CSRP, _P, ctypes.POINTER(_I64), _P, _SZ, _P, _SZ, _P],
+    "spx_spgemm_symbolic": [_CSRP, _CSRP, _I64, _P, ctypes.POINTER(_I64), _P, _SZ, _P, _SZ, _P],
     "spx_spgemm_fill": [_CSRP, _P, _P, _P, _SZ, _P, _P],
     "spx_spgemm_numeric": [_CSRP, _CSRP, _CSRP, _P, _P, _SZ, _P],
     "spx_spgemm_backward": [_CSRP, _CSRP, _CSRP, _P, _P, _P, _P, _P, _P, _P],
@@ -402,19 +402,21 @@ def spx_spgemm_workspace_size(m: int) -> int:
     return sz.value
 
 
-def spx_spgemm_analyse(A: spx_csr, B: spx_csr, ws) -> int:
+def spx_spgemm_analyse(A: spx_csr, B: spx_csr, ws, read_back: bool = True):
+    """The number of products (synchronises), or None without the read-back (asynchronous)."""
     prods = _I64(0)
-    _check(lib().spx_spgemm_analyse(ctypes.byref(A), ctypes.byref(B), ctypes.byref(prods), ptr(ws),
-                                    ws.numel(), _stream()), "spx_spgemm_analyse")
-    return prods.value
+    _check(lib().spx_spgemm_analyse(ctypes.byref(A), ctypes.byref(B), ctypes.byref(prods) if read_back else None,
+                                    ptr(ws), ws.numel(), _stream()), "spx_spgemm_analyse")
+    return prods.value if read_back else None
 
 
-def spx_spgemm_symbolic(A: spx_csr, B: spx_csr, c_indptr, ws, scratch) -> int:
+def spx_spgemm_symbolic(A: spx_csr, B: spx_csr, c_indptr, ws, scratch, products: int, read_back: bool = True):
+    """nnz(C) (synchronises), or None without the read-back (asynchronous)."""
     nnz = _I64(0)
-    _check(lib().spx_spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), ptr(c_indptr), ctypes.byref(nnz),
-                                     ptr(ws), ws.numel(), ptr(scratch), scratch.numel(), _stream()),
-           "spx_spgemm_symbolic")
-    return nnz.value
+    _check(lib().spx_spgemm_symbolic(ctypes.byref(A), ctypes.byref(B), int(products), ptr(c_indptr),
+                                     ctypes.byref(nnz) if read_back else None, ptr(ws), ws.numel(), ptr(scratch),
+                                     scratch.numel(), _stream()), "spx_spgemm_symbolic")
+    return nnz.value if read_back else None
 
 
 def spx_spgemm_fill(A: spx_csr, c_indptr, c_indices, ws, scratch):

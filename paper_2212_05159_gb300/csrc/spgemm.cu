@@ -41,6 +41,7 @@ constexpr int NUM_WARPS = 4;           // warps per block, numeric
 constexpr int GRP = 8;                 // lanes per group in the value kernels
 constexpr int NGRP = 32 / GRP;         // groups per warp
 constexpr int BIG_THREADS = 512;
+constexpr int FILL_LANES = 8;         // lanes per row, fill
 constexpr int BITMAP_WORDS = 8192;     // 32 KB shared bitmap: 262144 columns per chunk
 
 inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
@@ -113,6 +114,40 @@ __device__ __forceinline__ void warp_bitonic_sort(int* keys, int Q, int lane) {
     }
 }
 
+// Bitonic sort of a warp's 32 * NS keys held in registers, key e = lane + 32 s in v[s]:
+// compare-exchanges with a partner in another lane go through shuffles, those between the
+// two slots of a lane (stride 32) stay local.  Ascending.  Levels below `start` are
+// skipped: the caller guarantees that every aligned block of start / 2 keys is already
+// sorted, ascending where its block index is even and descending where it is odd (the
+// state the network itself leaves after those levels).
+template <int NS>
+__device__ __forceinline__ void warp_bitonic_sort_regs(int (&v)[NS], int lane, int start) {
+    constexpr int Q = 32 * NS;
+#pragma unroll
+    for (int size = 2; size <= Q; size <<= 1) {
+        if (size < start) continue;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {                              // NS == 2: slots 0 and 1 of the lane
+                const int e = lane;                          // the lower element of the pair
+                const bool up = (e & size) == 0;
+                const int a = v[0], b = v[1];
+                v[0] = up ? min(a, b) : max(a, b);
+                v[1] = up ? max(a, b) : min(a, b);
+            } else {
+#pragma unroll
+                for (int s2 = 0; s2 < NS; ++s2) {
+                    const int e = lane + 32 * s2;
+                    const int p = __shfl_xor_sync(FULL, v[s2], stride);
+                    const bool lower = (e & stride) == 0;
+                    const bool up = (e & size) == 0;
+                    v[s2] = (lower == up) ? min(v[s2], p) : max(v[s2], p);
+                }
+            }
+        }
+    }
+}
+
 // Sorted unique product columns of row i -> tmp + pptr[i]; count -> row_nnz[i].
 __global__ void __launch_bounds__(SYM_WARPS * 32) symbolic_warp_kernel(
     int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
@@ -124,22 +159,112 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) symbolic_warp_kernel(
     if (row >= m) return;
     const int P = prod[row];
     if (P > WARP_CAP) return;                       // a big-row block takes it
+    const int a0 = a_ptr[row], nA = a_ptr[row + 1] - a0;
+    int32_t* out = tmp + pptr[row];
+    if (P <= 64 && nA <= 32) {
+        // at most 64 products from at most 32 entries of A, every product column fetched
+        // straight into a register (two per lane, INT_MAX pads).  Lane e holds B_k's range
+        // for entry e.  When R (the smallest power of two >= every |B_k|) times |A_i| fits
+        // the 64 slots, entry e's sorted columns go to the aligned slots [e R, e R + R),
+        // ascending for even e and reversed for odd e, which is the state of the bitonic
+        // network after its levels up to R, so those levels are skipped.  Otherwise the
+        // products are packed: product t lies in the entry whose inclusive scan of the
+        // lengths first exceeds t (a binary search over the lanes).
+        int b0 = 0, len = 0;
+        if (lane < nA) {
+            const int k = a_idx[a0 + lane];
+            b0 = b_ptr[k];
+            len = b_ptr[k + 1] - b0;
+        }
+        const int lmax = __reduce_max_sync(FULL, (unsigned)len);
+        int R = 1;
+        while (R < lmax) R <<= 1;
+        int v[2];
+        int start, used;
+        if (nA * R <= 64) {
+            const int lg = __ffs(R) - 1;
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int sl = lane + 32 * s2;
+                const int e = sl >> lg, pos = sl & (R - 1);
+                const int bb = __shfl_sync(FULL, b0, e & 31);
+                const int ll = __shfl_sync(FULL, len, e & 31);
+                int key = INT_MAX;
+                if (e < nA) {
+                    if ((e & 1) == 0) {
+                        if (pos < ll) key = b_idx[bb + pos];
+                    } else {
+                        const int q = pos - (R - ll);          // descending: pads first
+                        if (q >= 0) key = b_idx[bb + ll - 1 - q];
+                    }
+                }
+                v[s2] = key;
+            }
+            start = 2 * R;
+            used = nA * R;
+        } else {
+            int incl = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int excl = incl - len;
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int t = lane + 32 * s2;
+                int e = 0;                                   // lanes with incl <= t
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int c = __shfl_sync(FULL, incl, e + step - 1);
+                    if (c <= t) e += step;
+                }
+                e = min(e, 31);
+                const int src = __shfl_sync(FULL, b0, e) + t - __shfl_sync(FULL, excl, e);
+                v[s2] = t < P ? b_idx[src] : INT_MAX;
+            }
+            start = 2;
+            used = P;
+        }
+        // sorted in registers, then the first of each run kept in order with ballots
+        if (used <= 32) {                                // slots 32..63 hold pads only
+            int w1[1] = {v[0]};
+            warp_bitonic_sort_regs<1>(w1, lane, start);
+            v[0] = w1[0];
+        } else {
+            warp_bitonic_sort_regs<2>(v, lane, start);
+        }
+        int base = 0;
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int t = lane + 32 * s2;
+            int prev = __shfl_up_sync(FULL, v[s2], 1);
+            const int last_lo = __shfl_sync(FULL, v[0], 31);    // key 31, before key 32
+            if (lane == 0) prev = s2 == 0 ? INT_MIN : last_lo;
+            const bool keep = t < P && (t == 0 || v[s2] != prev);
+            const unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) out[base + __popc(bal & lanemask_lt())] = v[s2];
+            base += __popc(bal);
+        }
+        if (lane == 0) row_nnz[row] = base;
+        return;
+    }
     int* keys = keys_all[warp];
     // expand
     int pos = 0;
-    for (int e = a_ptr[row]; e < a_ptr[row + 1]; ++e) {
+    for (int e = a0; e < a0 + nA; ++e) {
         const int k = a_idx[e];
         const int b0 = b_ptr[k], len = b_ptr[k + 1] - b0;
         for (int t = lane; t < len; t += 32) keys[pos + t] = b_idx[b0 + t];
         pos += len;
     }
+    __syncwarp();
     int Q = 1;
     while (Q < P) Q <<= 1;
     for (int t = P + lane; t < Q; t += 32) keys[t] = INT_MAX;
     __syncwarp();
     warp_bitonic_sort(keys, Q, lane);
     // compress: keep the first of each run, in order
-    int32_t* out = tmp + pptr[row];
     int base = 0;
     for (int t0 = 0; t0 < P; t0 += 32) {
         const int t = t0 + lane;
@@ -220,13 +345,22 @@ __global__ void __launch_bounds__(BIG_THREADS) symbolic_big_kernel(
 
 __global__ void fill_kernel(int32_t m, const int64_t* __restrict__ pptr, const int32_t* __restrict__ tmp,
                             const int32_t* __restrict__ c_ptr, int32_t* __restrict__ c_idx) {
-    // one warp per row
-    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    // FILL_LANES lanes per row, four loads in flight per lane
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / FILL_LANES;
+    const int sub = threadIdx.x % FILL_LANES;
     if (row >= m) return;
     const int32_t* src = tmp + pptr[row];
     const int a = c_ptr[row], n = c_ptr[row + 1] - a;
-    for (int t = lane; t < n; t += 32) c_idx[a + t] = src[t];
+    int32_t* dst = c_idx + a;
+    int t = sub;
+    for (; t + 3 * FILL_LANES < n; t += 4 * FILL_LANES) {
+        const int v0 = src[t], v1 = src[t + FILL_LANES], v2 = src[t + 2 * FILL_LANES], v3 = src[t + 3 * FILL_LANES];
+        dst[t] = v0;
+        dst[t + FILL_LANES] = v1;
+        dst[t + 2 * FILL_LANES] = v2;
+        dst[t + 3 * FILL_LANES] = v3;
+    }
+    for (; t < n; t += FILL_LANES) dst[t] = src[t];
 }
 
 // ------------------------------------------------------------------ numeric
@@ -425,7 +559,6 @@ extern "C" spx_status spx_spgemm_workspace_size(int32_t m, size_t* bytes) {
 extern "C" spx_status spx_spgemm_analyse(const spx_csr* A, const spx_csr* B, int64_t* products_host, void* ws,
                                          size_t ws_bytes, void* stream) {
     SPX_TRY(check_pair(A, B, false, "spx_spgemm_analyse"));
-    if (!products_host) return set_error(SPX_INVALID_ARG, "spx_spgemm_analyse: NULL output");
     const GemmLayout L = gemm_layout(A->m);
     if (!ws || ws_bytes < L.total)
         return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_analyse: workspace %zu < %zu", ws_bytes, L.total);
@@ -448,26 +581,25 @@ extern "C" spx_status spx_spgemm_analyse(const spx_csr* A, const spx_csr* B, int
         compact_kernel<<<(unsigned)((A->m + 255) / 256), 256, 0, st>>>(A->m, flags, bpos, brows);
         SPX_CHECK_LAUNCH("spgemm compact");
     }
-    SPX_CUDA(cudaMemcpyAsync(products_host, pptr + A->m, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
-             "spx_spgemm_analyse copy");
-    SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_analyse sync");
+    if (products_host) {
+        SPX_CUDA(cudaMemcpyAsync(products_host, pptr + A->m, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
+                 "spx_spgemm_analyse copy");
+        SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_analyse sync");
+    }
     return SPX_OK;
 }
 
-extern "C" spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, int32_t* c_indptr, int64_t* nnz_c_host,
-                                          void* ws, size_t ws_bytes, void* tmp, size_t tmp_bytes, void* stream) {
+extern "C" spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, int64_t products, int32_t* c_indptr,
+                                          int64_t* nnz_c_host, void* ws, size_t ws_bytes, void* tmp, size_t tmp_bytes,
+                                          void* stream) {
     SPX_TRY(check_pair(A, B, false, "spx_spgemm_symbolic"));
-    if (!c_indptr || !nnz_c_host) return set_error(SPX_INVALID_ARG, "spx_spgemm_symbolic: NULL output");
+    if (!c_indptr || products < 0) return set_error(SPX_INVALID_ARG, "spx_spgemm_symbolic: bad arguments");
     const GemmLayout L = gemm_layout(A->m);
     if (!ws || ws_bytes < L.total)
         return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_symbolic: workspace %zu < %zu", ws_bytes, L.total);
     cudaStream_t st = as_stream(stream);
     char* w = static_cast<char*>(ws);
     const int64_t* pptr = (const int64_t*)(w + L.pptr);
-    int64_t products = 0;
-    SPX_CUDA(cudaMemcpyAsync(&products, pptr + A->m, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
-             "spx_spgemm_symbolic copy");
-    SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_symbolic sync");
     if (tmp_bytes < (size_t)products * 4 || (products > 0 && !tmp))
         return set_error(SPX_OOM_WORKSPACE, "spx_spgemm_symbolic: scratch %zu < %lld", tmp_bytes,
                          (long long)products * 4);
@@ -483,11 +615,13 @@ extern "C" spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, in
         SPX_CHECK_LAUNCH("spgemm symbolic big");
     }
     SPX_TRY((scan_counts<int32_t, int32_t>(row_nnz, c_indptr, A->m, (int32_t*)(w + L.scan32), st)));
-    int32_t nnz = 0;
-    SPX_CUDA(cudaMemcpyAsync(&nnz, c_indptr + A->m, sizeof(int32_t), cudaMemcpyDeviceToHost, st),
-             "spx_spgemm_symbolic copy");
-    SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_symbolic sync");
-    *nnz_c_host = nnz;
+    if (nnz_c_host) {
+        int32_t nnz = 0;
+        SPX_CUDA(cudaMemcpyAsync(&nnz, c_indptr + A->m, sizeof(int32_t), cudaMemcpyDeviceToHost, st),
+                 "spx_spgemm_symbolic copy");
+        SPX_CUDA(cudaStreamSynchronize(st), "spx_spgemm_symbolic sync");
+        *nnz_c_host = nnz;
+    }
     return SPX_OK;
 }
 
@@ -500,7 +634,7 @@ extern "C" spx_status spx_spgemm_fill(const spx_csr* A, const int32_t* c_indptr,
     if (A->m == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
     const char* w = static_cast<const char*>(ws);
-    int64_t threads = (int64_t)A->m * 32;
+    int64_t threads = (int64_t)A->m * FILL_LANES;
     fill_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A->m, (const int64_t*)(w + L.pptr),
                                                                      (const int32_t*)tmp, c_indptr, c_indices);
     SPX_CHECK_LAUNCH("spgemm fill");

@@ -80,7 +80,7 @@ class SpGEMMPlan:
         self.products = abi.spx_spgemm_analyse(sA, sB, self.ws)
         scratch = abi.workspace(4 * self.products, dev)
         c_ip = torch.empty(A.m + 1, dtype=torch.int32, device=dev)
-        nnz = abi.spx_spgemm_symbolic(sA, sB, c_ip, self.ws, scratch)
+        nnz = abi.spx_spgemm_symbolic(sA, sB, c_ip, self.ws, scratch, self.products)
         c_ix = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
         abi.spx_spgemm_fill(sA, c_ip, c_ix, self.ws, scratch)
         del scratch

@@ -39,6 +39,9 @@ PAIRS = {
     "big_rows_wide": lambda: (synth.powerlaw_csr(3000, seed=5, max_len=400),
                               synth.random_k_per_row(3000, 6, seed=6, ncols=600000)),
     "poisson1d_sq": lambda: (synth.poisson1d(1000),) * 2,
+    # rows of A with more than 32 entries whose B rows are mostly empty (few products)
+    "long_a_rows_empty_b": lambda: (synth.empty_rows_csr(600, 800, seed=7, p_empty=0.1, max_len=60),
+                                    synth.empty_rows_csr(800, 300, seed=8, p_empty=0.93, max_len=3)),
 }
 
 
@@ -60,6 +63,17 @@ def test_pattern_bit_exact(pair):
     np.testing.assert_array_equal(host(plan.C.indices), r_ix)
     _, row_prod, _ = oracle.spgemm_count(A, B)
     assert plan.products == int(row_prod.sum())
+    # the same steps without the host read-backs (sizes known): the same pattern
+    from paper_2212_05159_gb300 import abi
+    sA, sB = dA.struct(), dB.struct()
+    scratch = abi.workspace(4 * plan.products, "cuda")
+    c_ip = torch.full_like(plan.C.indptr, -1)
+    c_ix = torch.full((max(r_ix.size, 1),), -1, dtype=torch.int32, device="cuda")
+    assert abi.spx_spgemm_analyse(sA, sB, plan.ws, read_back=False) is None
+    assert abi.spx_spgemm_symbolic(sA, sB, c_ip, plan.ws, scratch, plan.products, read_back=False) is None
+    abi.spx_spgemm_fill(sA, c_ip, c_ix, plan.ws, scratch)
+    np.testing.assert_array_equal(host(c_ip), r_ip)
+    np.testing.assert_array_equal(host(c_ix)[: r_ix.size], r_ix)
 
 
 def test_values(pair):
