@@ -659,8 +659,12 @@ spx_status spx_dense_forward(int64_t n, const float* X1, int32_t K1, const float
  * 0-2, two epilogues for inference: mode 3 = the residual layer without U (Y = Hin +
  * relu(pre), the pre-activation kept nowhere), mode 4 = the product's column halves to two
  * outputs, Y = pre[:, :N/2] and U = pre[:, N/2:] (each n x N/2), e.g. both heads of the
- * network from one pass over the activations.  One 128-row tile per block.  Device
- * pointers; asynchronous on `stream`. */
+ * network from one pass over the activations.  Shapes with K1 (and K2) multiples of 32,
+ * N a multiple of 32 (mode 4: N / 2) run on the pipelined kernel (one persistent CTA per
+ * SM: TMA tensor loads into a ring of stages, converter warps, one MMA-issuing thread, two
+ * accumulators in tensor memory, epilogue warps storing through TMA); other shapes on
+ * persistent CTAs that stage, multiply and store in turn.  Both give bitwise the same
+ * result.  Device pointers; asynchronous on `stream`. */
 spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K1, const float* X2,
                                 int32_t K2, const void* W_bf16, const float* bias, int32_t N,
                                 int32_t mode, const float* Hin, float* Y, float* U, void* stream);
@@ -668,10 +672,18 @@ spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K1, const fl
 /* spx_dense_backward_data on the tensor cores (tcgen05, accumulator in tensor memory): G is
  * rounded to BF16 while staged, so the result equals spx_dense_backward_data applied to a
  * BF16-rounded G up to the order of the FP32 accumulation.  N, K1, K2 multiples of 4,
- * N <= 128, K1 + K2 <= 128; G, dX1, dX2 16-byte aligned.  Asynchronous. */
+ * N <= 128, K1 + K2 <= 128; G, dX1, dX2 16-byte aligned.  With N, K1 (and K2) multiples
+ * of 32 it runs on the pipelined kernel of spx_dense_forward_tc, accumulating by TMA
+ * reduce-add stores (old + new, the same single rounding as a load-add-store).
+ * Asynchronous. */
 spx_status spx_dense_backward_data_tc(int64_t n, const float* G, int32_t N, const void* W_bf16,
                                       int32_t K1, int32_t K2, float* dX1, float* dX2,
                                       int32_t accumulate, void* stream);
+
+/* Enables (1, the default) or disables (0) the pipelined kernel of spx_dense_forward_tc and
+ * spx_dense_backward_data_tc for the calls that follow (process-wide), e.g. to time or
+ * compare the two kernels; results are bitwise equal either way.  Never fails. */
+spx_status spx_tc_set_pipeline(int32_t enabled);
 
 /* Data gradient [dX1 dX2] = G W^T (or += with accumulate != 0); dX2 may be NULL. */
 spx_status spx_dense_backward_data(int64_t n, const float* G, int32_t N, const void* W_bf16,

@@ -139,6 +139,7 @@ SIGNATURES = {
     "spx_to_bf16": [_I64, _P, _P, _P],
     "spx_spai_residual": [_CSRP, _F, _P, _P, _P],
     "spx_dense_backward_data_tc": [_I64, _P, _I32, _P, _I32, _I32, _P, _P, _I32, _P],
+    "spx_tc_set_pipeline": [_I32],
     "spx_dense_backward_weight_tc_workspace_size": [_I64, _I32, _I32, ctypes.POINTER(_SZ)],
     "spx_dense_backward_weight_tc": [_I64, _P, _I32, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P],
     "spx_precond_apply": [_I32, _I64, _P, _P, _P, _CSRP, _CSRP, _I32, _P, _P, _P],
@@ -577,6 +578,10 @@ def spx_dense_backward_data(n, G, N, W16, K1, K2, dX1, dX2, accumulate):
 def spx_dense_backward_data_tc(n, G, N, W16, K1, K2, dX1, dX2, accumulate):
     _check(lib().spx_dense_backward_data_tc(int(n), ptr(G), int(N), ptr(W16), int(K1), int(K2), ptr(dX1),
                                             ptr(dX2), int(accumulate), _stream()), "spx_dense_backward_data_tc")
+
+
+def spx_tc_set_pipeline(enabled: bool):
+    _check(lib().spx_tc_set_pipeline(1 if enabled else 0), "spx_tc_set_pipeline")
 
 
 def spx_dense_backward_weight_tc(n, X1, K1, X2, K2, G, N, dW, db, ws):

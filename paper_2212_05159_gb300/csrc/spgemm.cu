@@ -7,11 +7,14 @@
 //             "big" rows (P_i > WARP_CAP);
 //   symbolic  per row: expand the P_i product columns, sort, keep the unique ones; the
 //             sorted unique columns go to a products-sized scratch at offset Pptr[i] and
-//             their count to row_nnz[i]; C_indptr = scan(row_nnz).  One warp per row
-//             (shared-memory bitonic sort); a big row takes a whole block and a shared
-//             bitmap of the column space (chunked), which yields the columns already
+//             their count to row_nnz[i]; C_indptr = scan(row_nnz).  One warp per row:
+//             rows of at most 64 products fetch them straight into registers (two per
+//             lane) and sort them there with a bitonic network over shuffles, skipping its
+//             first levels when B's rows can be laid out as aligned sorted runs; rows of
+//             65..512 products sort in shared memory; a big row takes a whole block and a
+//             shared bitmap of the column space (chunked), which yields the columns already
 //             sorted.  mask(C) is structural: no numerical-zero dropping.
-//   fill      copies the unique columns into C_indices.
+//   fill      copies the unique columns into C_indices (8 lanes per row).
 //   numeric   per row, C_ij = sum over k in A_i of A_ik B_kj.  Rows with at most 128
 //             columns: four 8-lane groups, group g takes the entries k = g, g+4, ... of A_i
 //             (in A's order) into a private slice of the row's accumulator (the four slices

@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tc_pipe.h"
 
 namespace spx {
 namespace {
@@ -689,6 +690,10 @@ extern "C" spx_status spx_dense_forward_tc(int64_t n, const float* X1, int32_t K
         return set_error(SPX_INVALID_ARG, "spx_dense_forward_tc: K1, K2 multiples of 4 and 16-byte aligned rows needed");
     if (n == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
+    bool launched = false;
+    SPX_TRY(tc_pipe_forward(n, X1, K1, X2, K2, static_cast<const __nv_bfloat16*>(W_bf16), bias, N, mode, Hin, Y, U, st,
+                            &launched));
+    if (launched) return SPX_OK;
     const size_t smem = tc_smem_bytes(K1 + K2, N);
     static std::atomic<unsigned long long> attr_done{0};
     SPX_TRY(ensure_smem_attr(dense_tc_kernel, (int)tc_smem_bytes(TC_KMAX, TC_NMAX), attr_done,
@@ -721,6 +726,10 @@ extern "C" spx_status spx_dense_backward_data_tc(int64_t n, const float* G, int3
         return set_error(SPX_INVALID_ARG, "spx_dense_backward_data_tc: 16-byte aligned rows needed");
     if (n == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
+    bool launched = false;
+    SPX_TRY(tc_pipe_bwd_data(n, G, N, static_cast<const __nv_bfloat16*>(W_bf16), K1, K2, dX1, dX2, accumulate, st,
+                             &launched));
+    if (launched) return SPX_OK;
     const int kout = ((K1 + K2) + 15) & ~15;
     const size_t smem = td_smem_bytes(N, kout);
     static std::atomic<unsigned long long> attr_done{0};

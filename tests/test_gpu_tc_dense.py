@@ -21,21 +21,28 @@ def _cpu(t):
     return t.detach().cpu().double()
 
 
-@pytest.mark.parametrize("n", [1, 127, 300, 4096])
-@pytest.mark.parametrize("K1,K2,N,mode", [(4, 0, 64, 1), (64, 64, 64, 2), (64, 0, 64, 0), (64, 0, 128, 0),
-                                           (32, 16, 32, 1), (12, 8, 16, 1), (60, 68, 128, 0), (64, 64, 64, 3),
-                                           (64, 0, 128, 4), (32, 0, 32, 4)])
-def test_tc_dense_matches_fp64_product(n, K1, K2, N, mode):
+@pytest.mark.parametrize("n", [1, 127, 300, 4096, 50003])
+@pytest.mark.parametrize("K1,K2,N,mode,hin_is_x1", [
+    (4, 0, 64, 1, False), (64, 64, 64, 2, False), (64, 0, 64, 0, False), (64, 0, 128, 0, False),
+    (32, 16, 32, 1, False), (12, 8, 16, 1, False), (60, 68, 128, 0, False), (64, 64, 64, 3, False),
+    (64, 0, 128, 4, False), (32, 0, 32, 4, False),
+    # the network's residual layer (Hin is X1), on the pipelined kernel, and other pipelined shapes
+    (64, 64, 64, 3, True), (64, 64, 64, 2, True), (32, 32, 32, 3, True), (96, 32, 96, 1, False),
+    (32, 0, 64, 4, False), (128, 0, 128, 2, True)])
+def test_tc_dense_matches_fp64_product(n, K1, K2, N, mode, hin_is_x1):
     """Y = [X1 X2] W + b (mode 0), relu of it (1), U = pre-activation and Y = Hin + relu(U)
     (2), the same Y without U (3), or the column halves of the pre-activation to Y and U (4),
     with X rounded to BF16, against the FP64 product of the rounded X and the BF16 W;
-    normaliser |X||W| + |b| (+ |Hin|)."""
+    normaliser |X||W| + |b| (+ |Hin|).  n = 50003 gives every CTA of the pipelined kernel
+    several tiles (each stage, operand buffer and accumulator reused, a ragged last tile)."""
+    if n == 50003 and (K1 % 32 or K2 % 32 or N % 32):
+        pytest.skip("the large case is for the pipelined shapes")
     g = torch.Generator().manual_seed(n * 1000 + K1 + K2 + N + mode)
     X1 = torch.randn(n, K1, generator=g).cuda()
     X2 = torch.randn(n, K2, generator=g).cuda() if K2 else None
     W = (torch.randn(K1 + K2, N, generator=g) * 0.2).to(torch.bfloat16).cuda()
     b = torch.randn(N, generator=g).cuda()
-    Hin = torch.randn(n, N, generator=g).cuda() if mode in (2, 3) else None
+    Hin = (X1 if hin_is_x1 else torch.randn(n, N, generator=g).cuda()) if mode in (2, 3) else None
     Y = torch.full((n, N // 2 if mode == 4 else N), float("nan"), device="cuda")
     U = torch.full((n, N // 2 if mode == 4 else N), float("nan"), device="cuda") if mode in (2, 4) else None
     abi.spx_dense_forward_tc(n, X1, K1, X2, K2, W, b, N, mode, Hin, Y, U)
@@ -60,13 +67,15 @@ def test_tc_dense_matches_fp64_product(n, K1, K2, N, mode):
     assert_close_normalised(Y.cpu().numpy(), ref.numpy(), norm, what=f"tc dense n={n} K={K1}+{K2} mode={mode}")
 
 
-@pytest.mark.parametrize("n", [1, 127, 300, 4096])
+@pytest.mark.parametrize("n", [1, 127, 300, 4096, 50003])
 @pytest.mark.parametrize("N,K1,K2,acc", [(64, 64, 64, 1), (64, 64, 0, 0), (64, 64, 0, 1), (32, 16, 16, 0),
                                          (128, 64, 0, 0), (64, 4, 0, 0), (4, 16, 0, 0), (20, 8, 12, 1),
-                                         (128, 60, 68, 1)])
+                                         (128, 60, 68, 1), (64, 64, 64, 0), (32, 96, 32, 1), (128, 32, 0, 1)])
 def test_tc_backward_data_matches_fp64_product(n, N, K1, K2, acc):
     """[dX1 dX2] (+)= G W^T on the tensor cores, G rounded to BF16, against the FP64
     product of the rounded G and the BF16 W (plus the initial dX when accumulating)."""
+    if n == 50003 and (N % 32 or K1 % 32 or K2 % 32):
+        pytest.skip("the large case is for the pipelined shapes")
     g = torch.Generator().manual_seed(n * 7 + N + K1 + K2 + acc)
     G = torch.randn(n, N, generator=g).cuda()
     W = (torch.randn(K1 + K2, N, generator=g) * 0.2).to(torch.bfloat16).cuda()
@@ -166,3 +175,46 @@ def test_tc_kernels_reject_unaligned_or_unsupported_operands():
     with pytest.raises(abi.SpxError):
         abi.spx_dense_backward_weight_tc(n, X, K, None, 0, G, N, dW, None, ws[:16])   # workspace too small
     abi.spx_check_device()
+
+
+@pytest.mark.parametrize("n", [1, 300, 50003])
+def test_tc_pipelined_kernel_equals_the_staged_kernel_bitwise(n):
+    """The pipelined kernel (TMA ring, warp roles) and the stage-multiply-store kernel do the
+    same arithmetic: every forward mode and the data gradient, plain and accumulating, give
+    the same bits with the pipeline on and off."""
+    g = torch.Generator().manual_seed(n + 17)
+    H = 64
+    h = torch.randn(n, H, generator=g).cuda()
+    m = torch.randn(n, H, generator=g).cuda()
+    W = (torch.randn(2 * H, H, generator=g) * 0.2).to(torch.bfloat16).cuda()
+    Wh = (torch.randn(H, 2 * H, generator=g) * 0.2).to(torch.bfloat16).cuda()
+    b = torch.randn(H, generator=g).cuda()
+    G = torch.randn(n, H, generator=g).cuda()
+    init1, init2 = torch.randn(n, H, generator=g).cuda(), torch.randn(n, H, generator=g).cuda()
+
+    def run():
+        out = []
+        for mode in (0, 1, 2, 3):
+            Y, U = torch.empty(n, H, device="cuda"), torch.empty(n, H, device="cuda")
+            abi.spx_dense_forward_tc(n, h, H, m, H, W, b, H, mode, h, Y, U if mode == 2 else None)
+            out += [Y.clone()] + ([U.clone()] if mode == 2 else [])
+        P, Q = torch.empty(n, H, device="cuda"), torch.empty(n, H, device="cuda")
+        abi.spx_dense_forward_tc(n, h, H, None, 0, Wh, None, 2 * H, 4, None, P, Q)
+        out += [P, Q]
+        for acc in (0, 1):
+            d1, d2 = init1.clone(), init2.clone()
+            abi.spx_dense_backward_data_tc(n, G, H, W, H, H, d1, d2, acc)
+            out += [d1, d2]
+        torch.cuda.synchronize()
+        return [t.cpu() for t in out]
+
+    try:
+        abi.spx_tc_set_pipeline(True)
+        on = run()
+        abi.spx_tc_set_pipeline(False)
+        off = run()
+    finally:
+        abi.spx_tc_set_pipeline(True)
+    abi.spx_check_device()
+    for i, (a, c) in enumerate(zip(on, off)):
+        assert torch.equal(a.view(torch.int32), c.view(torch.int32)), i
