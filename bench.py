@@ -832,6 +832,96 @@ def spgemm_section():
     return out
 
 
+def network_section(n: int = 2 * 1024 * 1024):
+    """The network's dense layers on the tensor cores at n rows (hidden width 64; inputs
+    larger than L2), CUDA-event timed, each against the measured HBM bandwidth on its
+    algorithmic bytes per row: the training forward of a residual layer (reads X1 = h, X2 = E h,
+    writes Y and the pre-activation U), the inference forward (no U), both heads in one pass,
+    and the data gradient G W^T into two outputs, written and accumulated."""
+    import torch
+    from paper_2212_05159_gb300 import abi
+    H = 64
+    g = torch.Generator(device="cuda").manual_seed(5)
+    h = torch.randn(n, H, device="cuda", generator=g)
+    m = torch.randn(n, H, device="cuda", generator=g)
+    W = (torch.randn(2 * H, H, device="cuda", generator=g) * 0.2).to(torch.bfloat16)
+    Wh = (torch.randn(H, 2 * H, device="cuda", generator=g) * 0.2).to(torch.bfloat16)
+    b = torch.randn(H, device="cuda", generator=g)
+    Y, U = torch.empty(n, H, device="cuda"), torch.empty(n, H, device="cuda")
+    G = torch.randn(n, H, device="cuda", generator=g)
+    d1, d2 = torch.zeros(n, H, device="cuda"), torch.zeros(n, H, device="cuda")
+    hbm, src = measured_peaks()
+    cases = {
+        "forward_train_mode2": (lambda: abi.spx_dense_forward_tc(n, h, H, m, H, W, b, H, 2, h, Y, U),
+                                4 * 2 * H + 8 * H, "X1, X2 read; Y, U written"),
+        "forward_infer_mode3": (lambda: abi.spx_dense_forward_tc(n, h, H, m, H, W, b, H, 3, h, Y, None),
+                                4 * 2 * H + 4 * H, "X1, X2 read; Y written"),
+        "heads_mode4": (lambda: abi.spx_dense_forward_tc(n, h, H, None, 0, Wh, None, 2 * H, 4, None, Y, U),
+                        4 * H + 8 * H, "X read; both halves written"),
+        "data_gradient": (lambda: abi.spx_dense_backward_data_tc(n, G, H, W, H, H, d1, d2, 0),
+                          4 * H + 8 * H, "G read; dX1, dX2 written"),
+        "data_gradient_accumulate": (lambda: abi.spx_dense_backward_data_tc(n, G, H, W, H, H, d1, d2, 1),
+                                     4 * H + 16 * H, "G, old dX1, dX2 read; dX1, dX2 written"),
+    }
+    dW, db = torch.empty(2 * H, H, device="cuda"), torch.empty(H, device="cuda")
+    wws = abi.workspace(abi._size("spx_dense_backward_weight_tc_workspace_size", n, 2 * H, H), "cuda")
+    wgrad = lambda: abi.spx_dense_backward_weight_tc(n, h, H, m, H, G, H, dW, db, wws)  # noqa: E731
+    out = {"rows": n, "hidden": H, "peak_gbs": hbm, "peak_source": src}
+    ms = _ev_time(wgrad, reps=10)
+    bpr = 4 * (2 * H + H)
+    out["weight_gradient"] = {"bytes_per_row": bpr, "bytes_model": "X1, X2, G read (partials negligible)",
+                              "persistent": {"ms": ms, "gbs": bpr * n / (ms * 1e-3) / 1e9,
+                                             "frac": bpr * n / (ms * 1e-3) / 1e9 / hbm}}
+    for name, (fn, bpr, model) in cases.items():
+        r = {"bytes_per_row": bpr, "bytes_model": model}
+        for pipe in (True, False):
+            abi.spx_tc_set_pipeline(pipe)
+            ms = _ev_time(fn, reps=10)
+            gbs = bpr * n / (ms * 1e-3) / 1e9
+            r["pipelined" if pipe else "staged"] = {"ms": ms, "gbs": gbs, "frac": gbs / hbm}
+        abi.spx_tc_set_pipeline(True)
+        out[name] = r
+    abi.spx_check_device()
+    return out
+
+
+def pcg_case_section(nsys: int = 16, side: int = 256, seed: int = 5):
+    """Cost of one PCG iteration by preconditioner: nsys diffusion systems of side^2 (sigma 1),
+    one persistent launch each, Jacobi against M = L L^T applied from L's diagonals in shared
+    memory.  L is the untrained network's factor (D^-1/2 on the diagonal, zeros elsewhere on
+    tril(A)), so both take the same iterations and the time per iteration compares the
+    work of the two applies; timed with CUDA events (first launch after a warm-up)."""
+    import synth
+    import torch
+    from paper_2212_05159_gb300 import learned, solve
+    from paper_2212_05159_gb300.csr import CSR
+    mats = [synth.diffusion2d(side, 1.0, seed + i) for i in range(nsys)]
+    A, ptr = synth.block_diag(mats)
+    b = torch.from_numpy(synth.normal(A.m, seed=seed + 1)).cuda()
+    dA = CSR.from_host(A)
+    batch = solve.SystemBatch(dA, ptr)
+    G = learned.Graph(dA, "A")
+    G.features(dA.values)
+    L, _ = learned.MPNN(seed=0).forward(G, tensor_cores=True, inference=True)
+    F = solve.DiagonalFactor(batch, G.Lpat).fill(L)
+    maxit = 20 * side * side
+    out = {"systems": nsys, "side": side, "rows": A.m}
+    for name, kw in (("jacobi", {"pc": "jacobi"}), ("dia", {"pc": "dia", "dia": F})):
+        solve.cg(batch, b, tol=1e-8, maxit=maxit, **kw)                   # warm-up
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        _, it, st, _ = solve.cg(batch, b, tol=1e-8, maxit=maxit, **kw)
+        c.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(c)
+        itmax = int(it.max())
+        out[name] = {"ms": ms, "iters_max": itmax, "iters_total": int(it.sum()),
+                     "converged": int((st == 0).sum()), "us_per_iteration": 1e3 * ms / max(itmax, 1)}
+    out["dia_over_jacobi_per_iteration"] = out["dia"]["us_per_iteration"] / out["jacobi"]["us_per_iteration"]
+    return out
+
+
 def cg_section(args):
     """CG time to a true relative residual of 1e-8: the 256-system Jacobi batch (one persistent
     launch replayed from a CUDA graph) and learned vs Jacobi vs IC(0) on held-out 256^2 systems."""
@@ -897,12 +987,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=32)
+    ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "poisson3d"],
+                    help="matrix of the timed step: the n = 2^20 power-law matrix or the 3D Poisson 128^3 stencil")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="fixed launch parameters (the tuned choice for this workload) instead of autotuning")
-    ap.add_argument("--sections", default="step,extras,spgemm,cg,cpu",
-                    help="comma list of: step (always), extras, spgemm, cg, cpu")
+    ap.add_argument("--sections", default="step,extras,spgemm,network,pcgcase,cg,cpu",
+                    help="comma list of: step (always), extras, spgemm, network, pcgcase, cg, cpu")
     ap.add_argument("--train-steps", type=int, default=313,
                     help="training batches of 32 generated systems (313: the 10k-system training set)")
     ap.add_argument("--learned-patterns", default="A,A2",
@@ -919,7 +1011,7 @@ def main():
         return run_reference(args, ws, rank)
     secs = set(x.strip() for x in args.sections.split(","))
     if args.no_extras:
-        secs -= {"extras", "spgemm", "cg"}
+        secs -= {"extras", "spgemm", "network", "pcgcase", "cg"}
     if args.no_cpu:
         secs.discard("cpu")
     global NO_TUNE
@@ -933,7 +1025,7 @@ def main():
     args.warmup = max(args.warmup, 3)
     import paper_2212_05159_gb300  # noqa: F401  (fails loudly without the CUDA library)
 
-    W = Workload("powerlaw", k=args.k)
+    W = Workload(args.workload, k=args.k)
     clocks = NvmlClockSampler(index=local)
     if not clocks.ok:
         clocks = ClockSampler(index=local)
@@ -990,9 +1082,15 @@ def main():
                               "gather_probe": probe2, "per_launch_ms": per2,
                               "per_kernel_share": rep2["per_kernel_share"], "tuning": W.tuning}
         line["extras"] = extras
-    if ("spgemm" in secs or "cg" in secs) and rank == 0:
+    if ("spgemm" in secs or "network" in secs or "pcgcase" in secs or "cg" in secs) and rank == 0:
         del W
         torch.cuda.empty_cache()
+        if "network" in secs:
+            line["network_layers"] = network_section()
+            torch.cuda.empty_cache()
+        if "pcgcase" in secs:
+            line["pcg_iteration_cost"] = pcg_case_section()
+            torch.cuda.empty_cache()
         if "spgemm" in secs:
             line["spgemm"] = spgemm_section()
             line["spai"] = spai_section()
