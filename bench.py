@@ -78,7 +78,10 @@ def launch_bytes(m, n, nnz, k):
     return {"spmm": 4 * (m + 1) + 8 * nnz + 4 * n * k + 4 * m * k,
             "sddmm": 4 * (m + 1) + 8 * nnz + 4 * m * k + 4 * n * k,
             "gather": 12 * nnz,
-            "spmm_t": 4 * (n + 1) + 8 * nnz + 4 * m * k + 4 * n * k}
+            "spmm_t": 4 * (n + 1) + 8 * nnz + 4 * m * k + 4 * n * k,
+            # both gradients in one pass over A^T: A^T's pattern, perm and A's values read, G and
+            # X read, gX and gA written
+            "backward": 4 * (n + 1) + 16 * nnz + 4 * m * k + 8 * n * k}
 
 
 def gather_bytes(m, n, nnz, k):
@@ -86,7 +89,8 @@ def gather_bytes(m, n, nnz, k):
     return {"spmm": 4 * (m + 1) + 8 * nnz + 4 * nnz * k + 4 * m * k,
             "sddmm": 4 * (m + 1) + 8 * nnz + 4 * m * k + 4 * nnz * k,
             "gather": 12 * nnz,
-            "spmm_t": 4 * (n + 1) + 8 * nnz + 4 * nnz * k + 4 * n * k}
+            "spmm_t": 4 * (n + 1) + 8 * nnz + 4 * nnz * k + 4 * n * k,
+            "backward": 4 * (n + 1) + 16 * nnz + 4 * nnz * k + 8 * n * k}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -347,8 +351,33 @@ class Workload:
         per = {kk: ((2 if kk != "sddmm" else 1) if self.engine[kk][0] == "merge" else row_launches[kk])
                for kk in row_launches}
         self.launches = per["spmm"] + per["sddmm"] + 1 + per["spmm_t"]
+        # both gradients in one pass over A^T (spx_spmm_t_sddmm) or the three launches, by
+        # device timing on this pattern and width
+        self.abi = abi
+        self.KERNELS = ("spmm", "sddmm", "gather", "spmm_t")
+        self.backward = None
+        if k % 4 == 0 and 4 <= k <= 128:
+            self.s_ATpat = abi.csr_struct(A.n, A.m, t_ip, t_ix, None)
+            if NO_TUNE:
+                choice = ("fused", 0) if k >= 64 else None           # the measured choice on GB300
+            else:
+                sep_ms = _ev_time(lambda: [self.run_kernel(kk) for kk in ("sddmm", "gather", "spmm_t")], 5)
+                best = None
+                for v in (0, 1):
+                    self.backward = ("fused", v)
+                    t = _ev_time(lambda: self.run_kernel("backward"), 5)
+                    if best is None or t < best[0]:
+                        best = (t, v)
+                choice = ("fused", best[1]) if best[0] < sep_ms else None
+                self.backward_timing = {"separate_ms": sep_ms, "fused_ms": best[0]}
+            self.backward = choice
+            if choice is not None:
+                self.KERNELS = ("spmm", "backward")
+                self.launches = per["spmm"] + 1
         merge_desc = {kk: (f"merge: {v[4]} items per segment, variant {v[2]}" if v[0] == "merge" else "rows")
                       for kk, v in self.engine.items()}
+        merge_desc["backward"] = (f"fused: spx_spmm_t_sddmm, variant {self.backward[1]}" if self.backward
+                                  else "separate: sddmm, gather, spmm_t")
         self.tuning = {"engine": merge_desc,
                        "spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine,
                                 nparts(self.plan)],
@@ -398,20 +427,23 @@ class Workload:
                             plan=self.sddmm_plan)
         elif which == "gather":
             a.spx_gather_values(self.perm, b["v"], b["tv"])
+        elif which == "backward":
+            a.spx_spmm_t_sddmm(self.s_ATpat, self.perm, b["v"], b["G"], b["X"], b["gX"], b["gA"], plan=self.t_plan,
+                               variant=self.backward[1])
         else:
             if eng[0] == "merge":
                 a.spx_spmm_merge(b["sATv"], b["G"], b["gX"], eng[1], eng[3], variant=eng[2])
             else:
                 a.spx_spmm(b["sATv"], b["G"], b["gX"], 1.0, 0.0, self.t_plan, self.ws_tv)
 
-    KERNELS = ("spmm", "sddmm", "gather", "spmm_t")
     def cuda_kernel(self, launch):
         """The CUDA function a launch runs (spmm and spmm_t share one per engine)."""
         merge = self.engine.get(launch, ("rows",))[0] == "merge"
         return {"spmm": "spmm_merge_kernel" if merge else "spmm_kernel",
                 "sddmm": "sddmm_merge_kernel" if merge else "sddmm_rows_kernel",
                 "gather": "gather_values_kernel",
-                "spmm_t": "spmm_merge_kernel" if merge else "spmm_kernel"}[launch]
+                "spmm_t": "spmm_merge_kernel" if merge else "spmm_kernel",
+                "backward": "spmm_t_sddmm_kernel"}[launch]
 
 
 def time_workload(W, steps, warmup, ws):
@@ -495,7 +527,7 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
                                                                    KERNEL_SOURCE[dom])),
                 "algorithmic_bytes": d["bytes"] / nl, "bytes_model": "compulsory, per launch (mean of its launches)",
                 "gather_model_frac": d["gather_bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm}
-    if probe is not None and dom in ("spmm_kernel", "spmm_merge_kernel"):
+    if probe is not None and dom in ("spmm_kernel", "spmm_merge_kernel", "spmm_t_sddmm_kernel"):
         t_floor = sum(probe["A" if ln == "spmm" else "AT"]["ms"] for ln in d["launches"])
         roofline["gather_probe_ms"] = t_floor
         roofline["vs_gather_probe"] = d["ms"] / t_floor
@@ -507,7 +539,7 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
 
 KERNEL_SOURCE = {"spmm_kernel": "spmm.cu", "sddmm_rows_kernel": "sddmm.cu", "sddmm_kernel": "sddmm.cu",
                  "gather_values_kernel": "spmm.cu", "spmm_merge_kernel": "merge.cu",
-                 "sddmm_merge_kernel": "merge.cu"}
+                 "sddmm_merge_kernel": "merge.cu", "spmm_t_sddmm_kernel": "backward.cu"}
 
 
 def time_e2e(W, steps, warmup):

@@ -242,6 +242,27 @@ spx_status spx_spmm_t(const spx_csr* AT, const int32_t* perm, const float* G, in
                       const spx_rowplan* plan, void* workspace, size_t workspace_bytes,
                       void* stream);
 
+/* Both gradients of Y = A X in one pass over A^T (Table 1, SpDMM rows, w.r.t. A and X):
+ *   gX = alpha * A^T G + beta * gX,
+ *   gA[p] = scale * <G_i, X_j> for the entry a_ij stored at position p of A (SDDMM),
+ * exactly the products of spx_spmm_t and spx_sddmm, computed together: row j of A^T
+ * gathers the rows G_i of its entries once and uses each for both (X_j is read once per
+ * row), so the pass has one random gather stream instead of two.  A's values are read
+ * through perm, which also places each gA entry.  Deterministic (fixed-order sums).
+ * AT: the pattern of A^T from spx_csr_transpose (m = A.n rows, n = A.m columns; values
+ * unused); perm: device int32[nnz]; a_values: A's values in A's order (float32[nnz]).
+ * G: device float32 A.m x k (ldg); X: device float32 A.n x k (ldx), the forward's
+ * operand; gX: device float32 A.n x k (ldgx); gA: device float32[nnz] in A's order.
+ * k a multiple of 4 in 4..128; dense operands 16-byte aligned with ld % 4 == 0.
+ * plan: optional row plan of the transposed pattern (its row lists and order are used;
+ * column blocks and parts are not).  variant: 0 or 1, two launch shapes with the same
+ * result (1 requests every gathered row of a batch before using any; the faster one depends
+ * on k and the pattern, chosen by timing).  Other k: SPX_NOT_SUPPORTED (use the two calls). */
+spx_status spx_spmm_t_sddmm(const spx_csr* AT, const int32_t* perm, const float* a_values,
+                            const float* G, int64_t ldg, const float* X, int64_t ldx, int32_t k,
+                            float* gX, int64_t ldgx, float alpha, float beta, float* gA,
+                            float scale, const spx_rowplan* plan, int32_t variant, void* stream);
+
 /* ------------------------------------- SpSpMM / SpGEMM (Section 3.1.2, Table 1) */
 
 /* Workspace bytes of the SpGEMM calls for an m-row A (per-row counts, offsets and the

@@ -90,6 +90,7 @@ SIGNATURES = {
     "spx_csr_transpose": [_CSRP, _P, _P, _P, _P, _SZ, _P],
     "spx_spmm_t_workspace_size": [_CSRP, _I32, _PLANP, ctypes.POINTER(_SZ)],
     "spx_spmm_t": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P, _SZ, _P],
+    "spx_spmm_t_sddmm": [_CSRP, _P, _P, _P, _I64, _P, _I64, _I32, _P, _I64, _F, _F, _P, _F, _PLANP, _I32, _P],
     "spx_spmm_t_noalloc": [_CSRP, _P, _P, _I64, _I32, _P, _I64, _F, _F, _PLANP, _P],
     "spx_spgemm_workspace_size": [_I32, ctypes.POINTER(_SZ)],
     "spx_spgemm_analyse": [_CSRP, _CSRP, ctypes.POINTER(_I64), _P, _SZ, _P],
@@ -394,6 +395,19 @@ def spx_spmm_t(AT: spx_csr, perm, G, gX, alpha=1.0, beta=0.0, plan: spx_rowplan 
     _check(lib().spx_spmm_t(ctypes.byref(AT), ptr(perm), pg, ldg, G.shape[1], px, ldx, float(alpha),
                             float(beta), _planp(plan), *_wsargs(ws), _stream()), "spx_spmm_t")
     return gX
+
+
+def spx_spmm_t_sddmm(AT: spx_csr, perm, a_values, G, X, gX, gA, alpha=1.0, beta=0.0, scale=1.0,
+                     plan: spx_rowplan | None = None, variant: int = 0):
+    """gX = alpha A^T G + beta gX and gA = scale (G X^T) on A's pattern, in one pass."""
+    pg, ldg = _dense(G, "G")
+    pxx, ldx = _dense(X, "X")
+    px, ldgx = _dense(gX, "gX")
+    _check(lib().spx_spmm_t_sddmm(ctypes.byref(AT), ptr(perm), ptr(a_values), pg, ldg, pxx, ldx, G.shape[1], px,
+                                  ldgx, float(alpha), float(beta), ptr(gA), float(scale), _planp(plan), int(variant),
+                                  _stream()),
+           "spx_spmm_t_sddmm")
+    return gX, gA
 
 
 # ------------------------------------------------------------------ SpGEMM

@@ -26,6 +26,9 @@ class SpMM(torch.autograd.Function):
         values, X = ctx.saved_tensors
         A = ctx.A
         V = V.contiguous()
+        if ctx.needs_input_grad[0] and ctx.needs_input_grad[1]:
+            g_vals, g_X = ops.spmm_backward(A, V, X.contiguous(), values=values)   # one pass over A^T
+            return g_vals, g_X, None
         g_vals = ops.sddmm(A, V, X.contiguous()) if ctx.needs_input_grad[0] else None
         g_X = ops.spmm_t(A, V, values=values) if ctx.needs_input_grad[1] else None
         return g_vals, g_X, None

@@ -67,6 +67,26 @@ def spmm_t(A: CSR, G: torch.Tensor, values: torch.Tensor | None = None, out=None
     return gX2.squeeze(1) if vec else gX2
 
 
+def spmm_backward(A: CSR, G: torch.Tensor, X: torch.Tensor, values: torch.Tensor | None = None):
+    """(gA, gX) of Y = A X for the upstream gradient G: gA = (G X^T) on mask(A) and gX = A^T G
+    (Table 1).  Widths k that are multiples of 4 up to 128 (with aligned rows) take one pass
+    over A^T that gathers each row of G once for both (spx_spmm_t_sddmm); others the two
+    products apart."""
+    G2, vec = _as2d(G)
+    X2, _ = _as2d(X)
+    k = G2.shape[1]
+    aligned = all(t.is_contiguous() and t.data_ptr() % 16 == 0 for t in (G2, X2))
+    if k % 4 == 0 and 4 <= k <= 128 and aligned:
+        v = A.values if values is None else values
+        t_ip, t_ix, perm = A.transpose_pattern()
+        gX = torch.empty(A.n, k, dtype=torch.float32, device=G.device)
+        gA = torch.empty(A.nnz, dtype=torch.float32, device=G.device)
+        abi.spx_spmm_t_sddmm(abi.csr_struct(A.n, A.m, t_ip, t_ix, None), perm, v, G2, X2, gX, gA,
+                             plan=A.t_plan())
+        return gA, (gX.squeeze(1) if vec else gX)
+    return sddmm(A, G, X), spmm_t(A, G, values=values)
+
+
 class SpGEMMPlan:
     """Pattern of C = A B and the per-row classes, built once per (pattern A, pattern B)."""
 

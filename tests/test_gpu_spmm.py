@@ -152,13 +152,20 @@ def test_validate_rejects_bad_patterns():
         spx.CSR.from_host(oob).validate()
 
 
-@pytest.mark.parametrize("kind,k", [("powerlaw", 32), ("powerlaw", 128), ("poisson3d", 32)])
-def test_full_size_bench_configuration_sampled(kind, k):
+@pytest.mark.parametrize("kind,k,backward", [("powerlaw", 32, "tuned"), ("powerlaw", 128, "tuned"),
+                                             ("poisson3d", 32, "tuned"), ("powerlaw", 32, "fused"),
+                                             ("powerlaw", 32, "separate")])
+def test_full_size_bench_configuration_sampled(kind, k, backward):
     """The benchmark's own workloads (power-law n = 2^20 at k = 32 and 128, 3D Poisson 128^3 at
-    k = 32), built and autotuned exactly as bench.py does and run through its launch calls;
+    k = 32), built and autotuned exactly as bench.py does and run through its launch calls
+    (the backward as tuned, or forced to the fused pass or to the three separate launches);
     sampled rows of Y, gA and gX against the oracle computed on those rows alone."""
     import bench
     W = bench.Workload(kind, k=k)
+    if backward == "fused":
+        W.backward, W.KERNELS = ("fused", 0), ("spmm", "backward")
+    elif backward == "separate":
+        W.backward, W.KERNELS = None, ("spmm", "sddmm", "gather", "spmm_t")
     for kname in W.KERNELS:
         W.run_kernel(kname)
     torch.cuda.synchronize()
