@@ -589,18 +589,31 @@ spx_status spx_dia_analyse(const spx_csr* L, const int32_t* sys_ptr, int32_t nsy
 spx_status spx_dia_fill(const spx_csr* L, const int32_t* sys_ptr, int32_t nsys,
                         const int32_t* offsets, const int32_t* nd, void* values_bf16, void* stream);
 
-/* spx_cg_batched with M = L L^T, L in the diagonal form above.  Each block keeps its rows of
- * L (BF16) and of q = A p, z, r, p and w = L^T q in shared memory for the whole solve
- * (209 KB per 1024-thread block: 8 rows per thread, every system's rows must fit 8 per
- * thread per block of the cluster) and carries z = M r by z <- z - alpha M q: q is complete
- * over the cluster after the reduction that gives alpha, so M q needs no cluster barrier.
- * Rows of q beyond the block are read from the neighbouring blocks' shared memory (the
- * cluster's distributed shared memory), and the rows of L^T q that L reaches in the
- * previous block are recomputed locally; at the start and after every reliable update
- * z = M r is formed directly from the recomputed r.  The sums use L's BF16 values in
- * FP32.  A system whose offsets are unsupported, or whose halo max|off| exceeds a block's
- * rows, gets status SPX_NOT_SUPPORTED and relres -1.  Other arguments and results as in
- * spx_cg_batched (threads per block and cluster from spx_cg_set_launch). */
+/* M = L L^T from L's diagonal form (the offsets, counts and BF16 values above) by its lower
+ * diagonals: with s_d = -off_d, M_{i, i - o} = sum over pairs (d, e) with s_d - s_e = o of
+ * L_{i, i - s_d} L_{i - o, i - o - s_e}, summed in FP32 in (d, e) order (the products of BF16
+ * values are exact) and rounded to BF16.  m_offsets: device int32[nsys * 4], the distances
+ * o >= 0 ascending (0, then every positive s_d - s_e: at most 4 for 3 diagonals of L; for a
+ * 5-point grid of side N: 0, 1, N - 1, N); m_nd: device int32[nsys] (-1 where L's nd is -1);
+ * m_values_bf16: device BF16[4 * n], m_values[q * n + i] = M_{i, i - o_q}, 0 where row i - o_q
+ * lies outside the system.  n = rows of the batch.  Per value set of L; asynchronous. */
+spx_status spx_dia_square(const int32_t* sys_ptr, int32_t nsys, int32_t n, const int32_t* l_offsets,
+                          const int32_t* l_nd, const void* l_values_bf16, int32_t* m_offsets,
+                          int32_t* m_nd, void* m_values_bf16, void* stream);
+
+/* spx_cg_batched with a symmetric M given by its lower diagonals (spx_dia_square's output:
+ * dia_offsets int32[nsys * 4] distances, dia_nd int32[nsys], dia_values BF16[4 * n]), e.g.
+ * M = L L^T of Section 4.3.  Each block keeps its rows of M's diagonals (BF16) and of q = A p,
+ * z, r and p in shared memory for the whole solve (192 KB per 1024-thread block: 8 rows per
+ * thread, every system's rows must fit 8 per thread per block of the cluster) and applies M in
+ * one pass, (M x)_i = M_0[i] x_i + sum_{d>=1} (M_d[i] x_{i - o_d} + M_d[i + o_d] x_{i + o_d}),
+ * reading x (and M's rows) of the neighbouring blocks from their shared memory (the
+ * cluster's distributed shared memory).  It carries z = M r by z <- z - alpha M q: q is
+ * complete over the cluster after the reduction that gives alpha, so M q needs no cluster
+ * barrier; at the start and after every reliable update z = M r is formed directly from the
+ * recomputed r.  A system whose diagonals are unsupported, or whose halo max o_d exceeds a
+ * block's rows, gets status SPX_NOT_SUPPORTED and relres -1.  Other arguments and results as
+ * in spx_cg_batched (threads per block and cluster from spx_cg_set_launch). */
 spx_status spx_cg_batched_dia(const spx_csr* A, const int32_t* sys_ptr, int32_t nsys,
                               const int32_t* order, const float* b, double* x,
                               const int32_t* dia_offsets, const int32_t* dia_nd,

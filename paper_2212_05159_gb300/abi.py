@@ -107,6 +107,7 @@ SIGNATURES = {
     "spx_sddmm_merge": [_CSRP, _P, _I64, _P, _I64, _I32, _F, _P, ctypes.POINTER(spx_mergeplan), _I32, _P],
     "spx_dia_analyse": [_CSRP, _P, _I32, _P, _P, ctypes.POINTER(_I32), _P],
     "spx_dia_fill": [_CSRP, _P, _I32, _P, _P, _P, _P],
+    "spx_dia_square": [_P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P],
     "spx_cg_batched_dia": [_CSRP, _P, _I32, _P, _P, _P, _P, _P, _P, _D, _I32, _D, _P, _P, _P, _P, _SZ, _P],
     "spx_gather_probe": [_P, _I64, _I32, _P, _I64, _I32, _I32, _I32, _P, _I64, _P],
     "spx_csr_diagonal": [_CSRP, _P, _P, _P],
@@ -499,6 +500,7 @@ def spx_cg_batched(A: spx_csr, sys_ptr, nsys: int, order, b, x, pc_kind: int, di
 
 
 DIA_MAX = 3
+MDIA_MAX = 4
 
 
 def spx_dia_analyse(L: spx_csr, sys_ptr, nsys: int, device):
@@ -516,6 +518,19 @@ def spx_dia_fill(L: spx_csr, sys_ptr, nsys: int, offs, nd, out_bf16):
     _check(lib().spx_dia_fill(ctypes.byref(L), ptr(sys_ptr), int(nsys), ptr(offs), ptr(nd), ptr(out_bf16),
                               _stream()), "spx_dia_fill")
     return out_bf16
+
+
+def spx_dia_square(sys_ptr, nsys: int, n: int, l_offs, l_nd, l_vals_bf16, device, out=None):
+    """M = L L^T by its lower diagonals: (offsets int32[nsys * 4], counts int32[nsys],
+    values BF16[4 * n]), written into `out` (the same three tensors) when given."""
+    if out is None:
+        out = (torch.zeros(max(nsys, 1) * MDIA_MAX, dtype=torch.int32, device=device),
+               torch.zeros(max(nsys, 1), dtype=torch.int32, device=device),
+               torch.zeros(MDIA_MAX * max(n, 1), dtype=torch.bfloat16, device=device))
+    m_offs, m_nd, m_vals = out
+    _check(lib().spx_dia_square(ptr(sys_ptr), int(nsys), int(n), ptr(l_offs), ptr(l_nd), ptr(l_vals_bf16),
+                                ptr(m_offs), ptr(m_nd), ptr(m_vals), _stream()), "spx_dia_square")
+    return m_offs, m_nd, m_vals
 
 
 def spx_cg_batched_dia(A: spx_csr, sys_ptr, nsys: int, order, b, x, offs, nd, vals_bf16, tol: float, maxit: int,

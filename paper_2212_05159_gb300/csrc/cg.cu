@@ -25,8 +25,10 @@
 // in double-float (an FP32 pair with exact products, ~44 significant bits) and are
 // combined in double-float up to the last cross-block sum, which is converted to FP64.  Preconditioners: none, Jacobi (z = D^-1 r), the factored
 // approximate inverse M = L L^T of Section 4.3 (z = L (L^T r), two sparse products), and
-// an explicit sparse M (z = M r, one product; e.g. L L^T formed once by SpGEMM), and
-// IC(0) (z = (L L^T)^-1 r by two level-scheduled triangular solves).
+// an explicit sparse M (z = M r, one product; e.g. L L^T formed once by SpGEMM),
+// IC(0) (z = (L L^T)^-1 r by two level-scheduled triangular solves), and a symmetric M
+// given by at most four lower diagonals (e.g. L L^T of a factor on tril(A) of a 5-point
+// grid), kept in shared memory and applied in one pass (kind 5).
 //
 // Status per system: SPX_OK, SPX_MAXITER, SPX_BREAKDOWN (p^T A p <= 0 or r^T z <= 0),
 // SPX_NONFINITE.  No spin waits: only cluster / block barriers.
@@ -58,11 +60,13 @@ constexpr int CG_ROW2_W = 5;
 // threads the blocks that share an SM split the same budget).
 constexpr int CG_SMEM_ROWS_PER_THREAD = 8;
 constexpr int CG_SMEM_VECTORS = 6;
-// Kind 5 keeps q, z, r, p's own entries and w = L^T q in shared memory (5 vectors), a halo of
-// NT rows of w, and the block's rows of at most CG_DIA_MAX diagonals of L in BF16; x's FP32
-// partial stays in the workspace.  160 + 4 + 48 KB at 1024 threads.
+// Kind 5 keeps q, z, r and p's own entries in shared memory (4 vectors) and the block's rows of
+// the at most CG_MDIA_MAX lower diagonals of the symmetric M = L L^T in BF16; x's FP32 partial
+// stays in the workspace.  128 + 64 KB at 1024 threads.  L itself has at most CG_DIA_MAX
+// diagonals (spx_dia_analyse / spx_dia_fill); spx_dia_square forms M's.
 constexpr int CG_DIA_MAX = 3;
-constexpr int CG_DIA_VECTORS = 5;
+constexpr int CG_MDIA_MAX = 4;
+constexpr int CG_DIA_VECTORS = 4;
 
 struct CgArgs {
     int32_t nsys;
@@ -98,8 +102,9 @@ struct CgArgs {
     const int32_t* lev_ptr;   // IC(0): level l of a system = lev_rows[lev_ptr[l] .. lev_ptr[l+1])
     const int32_t* lev_rows;
     int32_t smem_rows;        // rows of a block's private vectors that fit in shared memory (0: none)
-    // diagonal-form factor (kind 5): L_{i, i + off[d]} = dia_val[d * n + i], per system
-    const int32_t* dia_off;   // [nsys * CG_DIA_MAX] offsets (<= 0), ascending |offset|
+    // kind 5: the symmetric M by its lower diagonals, M_{i, i - off[d]} = M_{i - off[d], i} =
+    // dia_val[d * n + i], per system
+    const int32_t* dia_off;   // [nsys * CG_MDIA_MAX] distances (>= 0), ascending, the first 0
     const int32_t* dia_nd;    // [nsys] diagonals per system
     const __nv_bfloat16* dia_val;
     int32_t n;                // rows of the batch
@@ -118,21 +123,18 @@ struct Vecs {
     float* po;        // the thread's own entries of p
     int off;
     bool sm;
-    // kind 5 only (shared memory): w = L^T x on the block's rows, w on the halo rows
-    // [lo - H, lo) of the previous block, and the block's rows of L's diagonals
-    float* w = nullptr;
-    float* halo = nullptr;
-    const __nv_bfloat16* ld = nullptr;
+    // kind 5 only (shared memory): the block's rows of M's lower diagonals
+    const __nv_bfloat16* md = nullptr;
     int cap = 0;
 };
 
-// A system's diagonal-form factor as a block sees it: L_{i, i + off[d]} for d < nd, halo
-// depth H = max |off[d]|, the system's rows [R0, R1), the block's rows [lo, hi) and the
+// A system's M as a block sees it: lower diagonals at distances off[d] (d < nd, off[0] = 0),
+// halo depth H = max off[d], the system's rows [R0, R1), the block's rows [lo, hi) and the
 // row count of a block (chunk; the next block's rows start at hi, the previous block's at
 // lo - chunk).
 struct DiaSys {
     int nd, H, R0, R1, lo, hi, chunk;
-    int off[CG_DIA_MAX];
+    int off[CG_MDIA_MAX];
     bool ok;
 };
 
@@ -358,67 +360,35 @@ __device__ __noinline__ void ic0_apply(const CgArgs& a, unsigned rank, int sid) 
     }
 }
 
-// Kind 5: the system's diagonals of L for the block's rows into shared memory (BF16).
+// Kind 5: the system's lower diagonals of M for the block's rows into shared memory (BF16).
 template <int NT>
 __device__ __forceinline__ void dia_load(const CgArgs& a, const Vecs& v, const DiaSys& ds) {
-    __nv_bfloat16* ld = const_cast<__nv_bfloat16*>(v.ld);
+    __nv_bfloat16* md = const_cast<__nv_bfloat16*>(v.md);
     for (int d = 0; d < ds.nd; ++d)
         for (int i = ds.lo + threadIdx.x; i < ds.hi; i += NT)
-            ld[d * v.cap + (i - ds.lo)] = a.dia_val[(size_t)d * a.n + i];
+            md[d * v.cap + (i - ds.lo)] = a.dia_val[(size_t)d * a.n + i];
 }
 
-// Kind 5: zs = scale * L (L^T xs) on the block's rows (accumulate: zs += ...), with xs
-// complete over the whole cluster (a cluster barrier since it was written).  xs and zs are
-// this block's shared-memory vectors (row i at [i - lo]).  With s_d = -off_d >= 0:
-//   w_i = (L^T x)_i = sum_d L_{i + s_d, i} x_{i + s_d},   (L w)_i = sum_d L_{i, i - s_d} w_{i - s_d}.
-// A row whose terms all lie in the block (i + H < hi for w, i - H >= lo for L w) reads only
-// shared memory; the block's last H rows read x from the next block's shared memory (the
-// same offset, through the cluster's distributed shared memory) and L from the global
-// diagonals, and w is formed again on the previous block's last H rows (the only rows
-// outside the block that L w reaches), so the block never waits for another block's w.
-// Every sum runs over the diagonals in a fixed order.
-// FUSED (the iteration's step, xs = q, scale = -alpha): the first pass also takes
-// x_p += alpha p (xp, po) and r -= alpha q on the row, the second adds <r, z> and <r, r> of
-// the updated row to dots -- the same operations as separate passes, one pass fewer each.
-template <int NT, int ND, bool FUSED>
-__device__ __forceinline__ void dia_apply_nd(cg::cluster_group& cl, unsigned rank, const __nv_bfloat16* __restrict__ gval,
-                                             int n, const float* xs, float* zs, float* w, float* halo,
-                                             const __nv_bfloat16* ld, int cap, int s0, int s1, int s2, int H, int R0,
-                                             int R1, int lo, int hi, int chunk, float scale, bool accumulate,
-                                             float* xp, const float* po, float* rs, DF (&dots)[2]) {
-    const int sd[3] = {s0, s1, s2};
+// Kind 5: zs = scale * M xs on the block's rows (accumulate: zs += ...), M symmetric from its
+// lower diagonals at distances o_d (o_0 = 0): with M_d[i] = M_{i, i - o_d},
+//   (M x)_i = M_0[i] x_i + sum_{d >= 1} M_d[i] x_{i - o_d} + sum_{d >= 1} M_d[i + o_d] x_{i + o_d},
+// summed in that order.  xs is complete over the whole cluster (a cluster barrier since it
+// was written); xs, zs and M's rows are this block's shared memory (row i at [i - lo]).  A
+// row whose reach [i - H, i + H] lies in the block reads only its own shared memory; the
+// other rows read x (and M's rows below them) of the adjacent blocks through distributed
+// shared memory (H <= chunk).  One pass, no barrier.
+// FUSED (the iteration's step, xs = q, scale = -alpha): the pass also takes x_p += alpha p
+// (xp, po) and r -= alpha q on the row, and adds <r, z> and <r, r> of the updated row to dots.
+template <int NT, int NM, bool FUSED>
+__device__ __forceinline__ void mdia_apply_nm(cg::cluster_group& cl, unsigned rank, const float* xs, float* zs,
+                                              const __nv_bfloat16* md, int cap, int o1, int o2, int o3, int H, int R0,
+                                              int R1, int lo, int hi, int chunk, float scale, bool accumulate,
+                                              float* xp, const float* po, float* rs, DF (&dots)[2]) {
+    const int od[4] = {0, o1, o2, o3};
     const float* xnext = hi < R1 ? cl.map_shared_rank(xs, rank + 1) : nullptr;
     const float* xprev = lo > R0 ? cl.map_shared_rank(xs, rank - 1) : nullptr;
+    const __nv_bfloat16* mnext = hi < R1 ? cl.map_shared_rank(md, rank + 1) : nullptr;
     const int lo_prev = lo - chunk;
-    // w_i on any row of the system within reach (general form: x and L anywhere)
-    auto wgeneral = [&](int i) -> float {
-        float t = 0.f;
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            const int j = i + sd[d];
-            if (j < R1) {
-                const bool own = j >= lo && j < hi;
-                const float lv = own ? __bfloat162float(ld[d * cap + (j - lo)])
-                                     : __bfloat162float(gval[(size_t)d * n + j]);
-                const float xv = own ? xs[j - lo] : (j >= hi ? xnext[j - hi] : xprev[j - lo_prev]);
-                t = fmaf(lv, xv, t);
-            }
-        }
-        return t;
-    };
-    // the halo row of this thread (if any; H <= NT): its terms are loaded first, so that the
-    // remote loads travel while the thread works on its own rows
-    const int hrow = (lo - H > R0 ? lo - H : R0) + (int)threadIdx.x;
-    float hl[ND], hx[ND];
-    const bool has_h = hrow < lo;
-#pragma unroll
-    for (int d = 0; d < ND; ++d) {
-        const int j = hrow + sd[d];
-        const bool ok = has_h && j < R1;
-        const bool own = j >= lo && j < hi;
-        hl[d] = !ok ? 0.f : own ? __bfloat162float(ld[d * cap + (j - lo)]) : __bfloat162float(gval[(size_t)d * n + j]);
-        hx[d] = !ok ? 0.f : own ? xs[j - lo] : (j >= hi ? xnext[j - hi] : xprev[j - lo_prev]);
-    }
     if constexpr (FUSED) {
         // x_p += alpha p on the thread's rows: x_p lives in global memory, so its loads are all
         // issued at once (scale = -alpha)
@@ -431,33 +401,26 @@ __device__ __forceinline__ void dia_apply_nd(cg::cluster_group& cl, unsigned ran
     for (int i = lo + threadIdx.x; i < hi; i += NT) {
         const int r = i - lo;
         if constexpr (FUSED) rs[r] = fmaf(scale, xs[r], rs[r]);  // r -= alpha q
-        float t = 0.f;
-        if (i + H < hi) {
+        float t = __bfloat162float(md[r]) * xs[r];
+        if (i - H >= lo && i + H < hi) {
 #pragma unroll
-            for (int d = 0; d < ND; ++d) t = fmaf(__bfloat162float(ld[d * cap + r + sd[d]]), xs[r + sd[d]], t);
-        } else {
-            t = wgeneral(i);
-        }
-        w[r] = t;
-    }
-    if (has_h) {
-        float t = 0.f;
+            for (int d = 1; d < NM; ++d) t = fmaf(__bfloat162float(md[d * cap + r]), xs[r - od[d]], t);
 #pragma unroll
-        for (int d = 0; d < ND; ++d) t = fmaf(hl[d], hx[d], t);
-        halo[hrow - (lo - H)] = t;
-    }
-    __syncthreads();
-    for (int i = lo + threadIdx.x; i < hi; i += NT) {
-        const int r = i - lo;
-        float t = 0.f;
-        if (i - H >= lo) {
-#pragma unroll
-            for (int d = 0; d < ND; ++d) t = fmaf(__bfloat162float(ld[d * cap + r]), w[r - sd[d]], t);
+            for (int d = 1; d < NM; ++d) t = fmaf(__bfloat162float(md[d * cap + r + od[d]]), xs[r + od[d]], t);
         } else {
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                const int j = i - sd[d];
-                if (j >= R0) t = fmaf(__bfloat162float(ld[d * cap + r]), j >= lo ? w[j - lo] : halo[j - (lo - H)], t);
+            for (int d = 1; d < NM; ++d) {
+                const int j = i - od[d];
+                if (j >= R0) t = fmaf(__bfloat162float(md[d * cap + r]), j >= lo ? xs[j - lo] : xprev[j - lo_prev], t);
+            }
+#pragma unroll
+            for (int d = 1; d < NM; ++d) {
+                const int j = i + od[d];
+                if (j < R1) {
+                    const bool own = j < hi;
+                    const float mv = __bfloat162float(own ? md[d * cap + (j - lo)] : mnext[d * cap + (j - hi)]);
+                    t = fmaf(mv, own ? xs[j - lo] : xnext[j - hi], t);
+                }
             }
         }
         const float zr = accumulate ? fmaf(scale, t, zs[r]) : scale * t;
@@ -471,21 +434,21 @@ __device__ __forceinline__ void dia_apply_nd(cg::cluster_group& cl, unsigned ran
 }
 
 template <int NT, bool FUSED>
-__device__ __forceinline__ void dia_apply(const __nv_bfloat16* gval, int n, cg::cluster_group& cl, unsigned rank,
-                                          const DiaSys& ds, const float* xs, float* zs, float* w, float* halo,
-                                          const __nv_bfloat16* ld, int cap, float scale, bool accumulate, float* xp,
-                                          const float* po, float* rs, DF (&dots)[2]) {
-    const int nd = ds.nd, s0 = -ds.off[0], s1 = -ds.off[1], s2 = -ds.off[2];
+__device__ __forceinline__ void mdia_apply(cg::cluster_group& cl, unsigned rank, const DiaSys& ds, const float* xs,
+                                           float* zs, const __nv_bfloat16* md, int cap, float scale, bool accumulate,
+                                           float* xp, const float* po, float* rs, DF (&dots)[2]) {
+    const int o1 = ds.off[1], o2 = ds.off[2], o3 = ds.off[3];
     const int H = ds.H, R0 = ds.R0, R1 = ds.R1, lo = ds.lo, hi = ds.hi, chunk = ds.chunk;
-    if (nd == 3)
-        dia_apply_nd<NT, 3, FUSED>(cl, rank, gval, n, xs, zs, w, halo, ld, cap, s0, s1, s2, H, R0, R1, lo, hi, chunk,
-                                   scale, accumulate, xp, po, rs, dots);
-    else if (nd == 2)
-        dia_apply_nd<NT, 2, FUSED>(cl, rank, gval, n, xs, zs, w, halo, ld, cap, s0, s1, s2, H, R0, R1, lo, hi, chunk,
-                                   scale, accumulate, xp, po, rs, dots);
-    else
-        dia_apply_nd<NT, 1, FUSED>(cl, rank, gval, n, xs, zs, w, halo, ld, cap, s0, s1, s2, H, R0, R1, lo, hi, chunk,
-                                   scale, accumulate, xp, po, rs, dots);
+#define SPX_MDIA(NMv)                                                                                          \
+    mdia_apply_nm<NT, NMv, FUSED>(cl, rank, xs, zs, md, cap, o1, o2, o3, H, R0, R1, lo, hi, chunk, scale,     \
+                                  accumulate, xp, po, rs, dots)
+    switch (ds.nd) {
+        case 4: SPX_MDIA(4); break;
+        case 3: SPX_MDIA(3); break;
+        case 2: SPX_MDIA(2); break;
+        default: SPX_MDIA(1); break;
+    }
+#undef SPX_MDIA
 }
 
 template <int NT, int PC>
@@ -532,12 +495,9 @@ template <int NT, int PC, bool SM>
 __device__ __forceinline__ Vecs make_vecs(const CgArgs& a, float* sv, int lo, int hi) {
     constexpr int cap = CG_SMEM_ROWS_PER_THREAD * NT;
     if constexpr (PC == 5) {
-        // [q | z | r | po | w] (cap floats each), halo (NT floats), then the BF16 diagonals
-        __nv_bfloat16* ld = reinterpret_cast<__nv_bfloat16*>(sv + CG_DIA_VECTORS * cap + NT);
+        // [q | z | r | po] (cap floats each), then M's BF16 diagonals (cap each)
         Vecs v{a.xp + lo, sv, sv + cap, sv + 2 * cap, nullptr, sv + 3 * cap, lo, true};
-        v.w = sv + 4 * cap;
-        v.halo = sv + CG_DIA_VECTORS * cap;
-        v.ld = ld;
+        v.md = reinterpret_cast<const __nv_bfloat16*>(sv + CG_DIA_VECTORS * cap);
         v.cap = cap;
         return v;
     } else if constexpr (SM) {
@@ -564,8 +524,7 @@ __device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& c
         if constexpr (PC == 5) {
             cl.sync();                                           // r (and L's rows) complete
             DF unused[2] = {{0.f, 0.f}, {0.f, 0.f}};
-            dia_apply<NT, false>(a.dia_val, a.n, cl, rank, ds, v.r, v.z, v.w, v.halo, v.ld, v.cap, 1.f, false,
-                                 nullptr, nullptr, nullptr, unused);
+            mdia_apply<NT, false>(cl, rank, ds, v.r, v.z, v.md, v.cap, 1.f, false, nullptr, nullptr, nullptr, unused);
         } else {
             apply_pc<NT, PC>(a, v, cl, lo, hi, rank, sid);
         }
@@ -709,8 +668,7 @@ __device__ __forceinline__ void pcg_system(const CgArgs& a, cg::cluster_group& c
             } else if constexpr (PC == 5) {
                 // x_p += alpha p; r -= alpha q; z -= alpha M q, with <r, z> and <r, r>: q = A p is
                 // complete over the cluster since the reduction above, so M q needs no barrier
-                dia_apply<NT, true>(a.dia_val, a.n, cl, rank, ds, v.q, v.z, v.w, v.halo, v.ld, v.cap, -alpha, true,
-                                    v.xp, v.po, v.r, v2n);
+                mdia_apply<NT, true>(cl, rank, ds, v.q, v.z, v.md, v.cap, -alpha, true, v.xp, v.po, v.r, v2n);
             } else {
                 float* __restrict__ XP = v.xp - v.off;
                 float* __restrict__ R = v.r - v.off;
@@ -878,9 +836,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
             if (t0) {
                 ds.nd = a.dia_nd[sid];
                 ds.H = 0;
-                for (int d = 0; d < CG_DIA_MAX; ++d) {
-                    ds.off[d] = d < ds.nd ? a.dia_off[sid * CG_DIA_MAX + d] : 0;
-                    if (d < ds.nd && -ds.off[d] > ds.H) ds.H = -ds.off[d];
+                bool offs_ok = true;
+                for (int d = 0; d < CG_MDIA_MAX; ++d) {
+                    ds.off[d] = d < ds.nd ? a.dia_off[sid * CG_MDIA_MAX + d] : 0;
+                    if (d < ds.nd && ds.off[d] > ds.H) ds.H = ds.off[d];
+                    if (d < ds.nd && (ds.off[d] < 0 || (d == 0) != (ds.off[d] == 0))) offs_ok = false;
                 }
                 ds.R0 = R0;
                 ds.R1 = R1;
@@ -888,8 +848,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) pcg_kernel(CgArgs a) {
                 ds.hi = hi;
                 ds.chunk = chunk;
                 // the block holds its rows in shared memory and reaches only the adjacent blocks
-                ds.ok = in_smem && ds.nd >= 1 && ds.nd <= CG_DIA_MAX && ds.H <= NT &&
-                        (ds.H <= chunk || (int)ncl == 1);
+                ds.ok = in_smem && offs_ok && ds.nd >= 1 && ds.nd <= CG_MDIA_MAX && (ds.H <= chunk || (int)ncl == 1);
             }
             __syncthreads();
             if (!ds.ok) {                                       // uniform across the cluster
@@ -1000,6 +959,70 @@ __global__ void dia_fill_kernel(int32_t n, int32_t nsys, const int32_t* __restri
     }
 }
 
+// M = L L^T by its lower diagonals.  With L's diagonals at distances s_d = -off_d (values
+// L_d[i] = L_{i, i - s_d}), M_{i, i - o} = sum over pairs (d, e) with s_d - s_e = o of
+// L_d[i] L_e[i - o] (the common column is k = i - s_d = (i - o) - s_e).  The distances are 0
+// and every positive s_d - s_e, ascending: at most CG_MDIA_MAX for CG_DIA_MAX diagonals.
+// One thread per system.
+__global__ void dia_square_offsets_kernel(int32_t nsys, const int32_t* __restrict__ l_offs,
+                                          const int32_t* __restrict__ l_nd, int32_t* __restrict__ m_offs,
+                                          int32_t* __restrict__ m_nd) {
+    const int sid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sid >= nsys) return;
+    const int c = l_nd[sid];
+    int o[CG_MDIA_MAX], cnt = 0;
+    if (c >= 1 && c <= CG_DIA_MAX) {
+        o[cnt++] = 0;
+        for (int d = 0; d < c; ++d)
+            for (int e = 0; e < c; ++e) {
+                const int dist = l_offs[sid * CG_DIA_MAX + e] - l_offs[sid * CG_DIA_MAX + d];   // s_d - s_e
+                if (dist <= 0) continue;
+                bool seen = false;
+                for (int q = 0; q < cnt; ++q) seen = seen || o[q] == dist;
+                if (!seen && cnt < CG_MDIA_MAX) o[cnt++] = dist;
+            }
+        for (int x = 1; x < cnt; ++x)                // insertion sort, ascending
+            for (int y = x; y > 0 && o[y] < o[y - 1]; --y) {
+                const int t = o[y];
+                o[y] = o[y - 1];
+                o[y - 1] = t;
+            }
+    }
+    m_nd[sid] = cnt > 0 ? cnt : -1;
+    for (int q = 0; q < CG_MDIA_MAX; ++q) m_offs[sid * CG_MDIA_MAX + q] = q < cnt ? o[q] : 0;
+}
+
+// values of M's diagonals, one thread per row: FP32 sums of the exact products of L's BF16
+// values in (d, e) order, rounded to BF16; zero where row i - o is outside the system.
+__global__ void dia_square_kernel(int32_t n, int32_t nsys, const int32_t* __restrict__ sys_ptr,
+                                  const int32_t* __restrict__ l_offs, const int32_t* __restrict__ l_nd,
+                                  const __nv_bfloat16* __restrict__ l_val, const int32_t* __restrict__ m_offs,
+                                  const int32_t* __restrict__ m_nd, __nv_bfloat16* __restrict__ m_val) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nsys;                       // the system s with sys_ptr[s] <= i < sys_ptr[s + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sys_ptr[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    const int c = l_nd[lo], cm = m_nd[lo];
+    const int64_t R0 = sys_ptr[lo];
+    for (int q = 0; q < CG_MDIA_MAX; ++q) {
+        float t = 0.f;
+        if (q < cm && c >= 1) {
+            const int o = m_offs[lo * CG_MDIA_MAX + q];
+            if (i - o >= R0)
+                for (int d = 0; d < c; ++d)
+                    for (int e = 0; e < c; ++e)
+                        if (l_offs[lo * CG_DIA_MAX + e] - l_offs[lo * CG_DIA_MAX + d] == o)
+                            t = fmaf(__bfloat162float(l_val[(int64_t)d * n + i]),
+                                     __bfloat162float(l_val[(int64_t)e * n + (i - o)]), t);
+        }
+        m_val[(int64_t)q * n + i] = __float2bfloat16(t);
+    }
+}
+
 // Launch shape of the batched PCG (threads per block, blocks per cluster); 0 = default.
 std::atomic<int> g_cg_threads{0};
 std::atomic<int> g_cg_cluster{0};
@@ -1028,8 +1051,7 @@ static spx_status launch_pcg(CgArgs& a, int pc_kind, cudaStream_t st) {
                            (g_cg_smem_vectors.load() != 0 && (pc_kind == 0 || pc_kind == 1 || pc_kind == 3));
     a.smem_rows = smem_vecs ? CG_SMEM_ROWS_PER_THREAD * nt : 0;
     const size_t smem = pc_kind == 5
-        ? (size_t)a.smem_rows * (CG_DIA_VECTORS * sizeof(float) + CG_DIA_MAX * sizeof(__nv_bfloat16)) +
-              (size_t)nt * sizeof(float)
+        ? (size_t)a.smem_rows * (CG_DIA_VECTORS * sizeof(float) + CG_MDIA_MAX * sizeof(__nv_bfloat16))
         : (size_t)a.smem_rows * CG_SMEM_VECTORS * sizeof(float);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(clusters * cl));
@@ -1227,6 +1249,24 @@ extern "C" spx_status spx_dia_fill(const spx_csr* L, const int32_t* sys_ptr, int
                                                                    L->values, offsets, nd,
                                                                    static_cast<__nv_bfloat16*>(values_bf16));
     SPX_CHECK_LAUNCH("spx_dia_fill");
+    return SPX_OK;
+}
+
+extern "C" spx_status spx_dia_square(const int32_t* sys_ptr, int32_t nsys, int32_t n, const int32_t* l_offsets,
+                                     const int32_t* l_nd, const void* l_values_bf16, int32_t* m_offsets,
+                                     int32_t* m_nd, void* m_values_bf16, void* stream) {
+    if (nsys < 0 || n < 0 ||
+        (nsys > 0 && (!sys_ptr || !l_offsets || !l_nd || !l_values_bf16 || !m_offsets || !m_nd || !m_values_bf16)))
+        return set_error(SPX_INVALID_ARG, "spx_dia_square: bad arguments");
+    if (nsys == 0) return SPX_OK;
+    cudaStream_t st = as_stream(stream);
+    dia_square_offsets_kernel<<<(unsigned)((nsys + 127) / 128), 128, 0, st>>>(nsys, l_offsets, l_nd, m_offsets, m_nd);
+    SPX_CHECK_LAUNCH("spx_dia_square offsets");
+    if (n == 0) return SPX_OK;
+    dia_square_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        n, nsys, sys_ptr, l_offsets, l_nd, static_cast<const __nv_bfloat16*>(l_values_bf16), m_offsets, m_nd,
+        static_cast<__nv_bfloat16*>(m_values_bf16));
+    SPX_CHECK_LAUNCH("spx_dia_square");
     return SPX_OK;
 }
 

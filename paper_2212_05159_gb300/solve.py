@@ -134,10 +134,11 @@ class IC0:
 
 class DiagonalFactor:
     """M = L L^T (Section 4.3) with L lower-triangular in diagonal form: per system at most
-    three diagonals L_{i, i + off} (off <= 0), the values in BF16.  The PCG keeps each
-    block's rows of L in shared memory for the whole solve and applies M with block
-    barriers only (spx_cg_batched_dia).  The analysis (offsets per system) depends on the
-    pattern; fill() takes new values of L on the same pattern."""
+    three diagonals L_{i, i + off} (off <= 0), the values in BF16.  fill() also forms M's
+    (at most four) lower diagonals (spx_dia_square); the PCG keeps each block's rows of them
+    in shared memory for the whole solve and applies M in one pass (spx_cg_batched_dia).
+    The analysis (offsets per system) depends on the pattern; fill() takes new values of L
+    on the same pattern."""
 
     def __init__(self, batch: SystemBatch, Lpat: CSR):
         self.batch = batch
@@ -145,6 +146,10 @@ class DiagonalFactor:
         self.offsets, self.nd, self.supported = abi.spx_dia_analyse(Lpat.struct(), batch.sys_ptr, batch.nsys,
                                                                     Lpat.device)
         self.values = torch.zeros(abi.DIA_MAX * max(Lpat.m, 1), dtype=torch.bfloat16, device=Lpat.device)
+        nsys = batch.nsys
+        self.m_offsets = torch.zeros(max(nsys, 1) * abi.MDIA_MAX, dtype=torch.int32, device=Lpat.device)
+        self.m_nd = torch.zeros(max(nsys, 1), dtype=torch.int32, device=Lpat.device)
+        self.m_values = torch.zeros(abi.MDIA_MAX * max(Lpat.m, 1), dtype=torch.bfloat16, device=Lpat.device)
 
     def rebind(self, batch: SystemBatch):
         if batch.A.m != self.batch.A.m or not np.array_equal(batch.sys_ptr_host, self.batch.sys_ptr_host):
@@ -155,6 +160,8 @@ class DiagonalFactor:
     def fill(self, L_values: torch.Tensor):
         abi.spx_dia_fill(self.Lpat.struct(L_values), self.batch.sys_ptr, self.batch.nsys, self.offsets, self.nd,
                          self.values)
+        abi.spx_dia_square(self.batch.sys_ptr, self.batch.nsys, self.Lpat.m, self.offsets, self.nd, self.values,
+                           self.Lpat.device, out=(self.m_offsets, self.m_nd, self.m_values))
         return self
 
 
@@ -177,7 +184,7 @@ def cg(batch: SystemBatch, b: torch.Tensor, pc: str = "jacobi", factor: Factor |
             raise ValueError("pc='dia' needs a DiagonalFactor")
         abi.spx_cg_set_launch(*batch.launch_for(kind))
         abi.spx_cg_batched_dia(A.struct(values), batch.sys_ptr, batch.nsys, batch.order, b.contiguous(), x,
-                               dia.offsets, dia.nd, dia.values, tol, maxit, delta, batch.iters, batch.status,
+                               dia.m_offsets, dia.m_nd, dia.m_values, tol, maxit, delta, batch.iters, batch.status,
                                batch.relres, batch.ws)
         return x, batch.iters, batch.status, batch.relres
     dinv = batch.dinv(values) if kind == 1 else None

@@ -1,8 +1,8 @@
-"""PCG with M = L L^T (Section 4.3), L in diagonal form in shared memory (spx_dia_analyse,
-spx_dia_fill, spx_cg_batched_dia), against the FP64 oracle's PCG with the same
-BF16-rounded factor: systems large enough that a cluster has several blocks (rows of q
-read from the neighbouring blocks, the halo of L^T q recomputed), and the unsupported
-cases reported per system."""
+"""PCG with M = L L^T (Section 4.3), L in diagonal form (spx_dia_analyse, spx_dia_fill), M's
+lower diagonals formed from it (spx_dia_square) and kept in shared memory by the PCG
+(spx_cg_batched_dia), against the FP64 oracle's PCG with the same BF16-rounded factor:
+systems large enough that a cluster has several blocks (rows of q and of M read from the
+neighbouring blocks), and the unsupported cases reported per system."""
 import numpy as np
 import pytest
 import torch
@@ -70,6 +70,38 @@ def test_analyse_and_fill_are_exact():
     for e in range(L.nnz):
         d = list(offs[sys_of[e], :nd[sys_of[e]]]).index(int(L.indices[e]) - int(rows[e]))
         ref[d, rows[e]] = L.values[e]
+    ref16 = torch.from_numpy(ref).to(torch.bfloat16).view(torch.int16).numpy()
+    np.testing.assert_array_equal(got, ref16)
+
+
+def test_square_forms_the_lower_diagonals_of_L_LT_exactly():
+    """M = L L^T from L's BF16 diagonals: the distances 0, 1, N - 1, N of a 5-point grid of side
+    N (fewer for tiny systems), and every value the FP32 sum, in (d, e) order, of the exact
+    products of L's BF16 values, rounded to BF16 -- bit for bit."""
+    sides = [1, 2, 7, 33]
+    A, ptr = _batch(sides, 4)
+    L = _factor(A, seed=6)
+    batch = solve.SystemBatch(spx.CSR.from_host(A), ptr)
+    dL = spx.CSR.from_host(L)
+    F = solve.DiagonalFactor(batch, dL).fill(dL.values)
+    loffs, lnd = host(F.offsets).reshape(-1, 3), host(F.nd)
+    moffs, mnd = host(F.m_offsets).reshape(-1, 4), host(F.m_nd)
+    Ld = host(F.values.float()).reshape(3, -1).astype(np.float32)
+    got = host(F.m_values.view(torch.int16)).reshape(4, -1)
+    ref = np.zeros((4, A.m), np.float32)
+    for s, side in enumerate(sides):
+        sd = [-int(o) for o in loffs[s, :lnd[s]]]
+        want = sorted({0} | {a - b for a in sd for b in sd if a > b})
+        assert mnd[s] == len(want) and list(moffs[s, :mnd[s]]) == want, (s, moffs[s], mnd[s])
+        for i in range(int(ptr[s]), int(ptr[s + 1])):
+            for q, o in enumerate(want):
+                t = np.float32(0.0)
+                if i - o >= ptr[s]:
+                    for d in range(lnd[s]):
+                        for e in range(lnd[s]):
+                            if sd[d] - sd[e] == o:
+                                t = np.float32(t + np.float32(Ld[d, i] * Ld[e, i - o]))
+                ref[q, i] = t
     ref16 = torch.from_numpy(ref).to(torch.bfloat16).view(torch.int16).numpy()
     np.testing.assert_array_equal(got, ref16)
 
