@@ -359,16 +359,17 @@ class Workload:
         if k % 4 == 0 and 4 <= k <= 128:
             self.s_ATpat = abi.csr_struct(A.n, A.m, t_ip, t_ix, None)
             if NO_TUNE:
-                choice = ("fused", 0) if k >= 64 else None           # the measured choice on GB300
+                choice = ("fused", 0, self.t_plan, "tuned") if k >= 64 else None   # the measured choice on GB300
             else:
                 sep_ms = _ev_time(lambda: [self.run_kernel(kk) for kk in ("sddmm", "gather", "spmm_t")], 5)
                 best = None
-                for v in (0, 1):
-                    self.backward = ("fused", v)
-                    t = _ev_time(lambda: self.run_kernel("backward"), 5)
-                    if best is None or t < best[0]:
-                        best = (t, v)
-                choice = ("fused", best[1]) if best[0] < sep_ms else None
+                for pname, pl in (("tuned", self.t_plan), ("default", self.dA.t_plan())):
+                    for v in (0, 1, 2, 3):
+                        self.backward = ("fused", v, pl, pname)
+                        t = _ev_time(lambda: self.run_kernel("backward"), 5)
+                        if best is None or t < best[0]:
+                            best = (t, v, pl, pname)
+                choice = ("fused", best[1], best[2], best[3]) if best[0] < sep_ms else None
                 self.backward_timing = {"separate_ms": sep_ms, "fused_ms": best[0]}
             self.backward = choice
             if choice is not None:
@@ -376,7 +377,8 @@ class Workload:
                 self.launches = per["spmm"] + 1
         merge_desc = {kk: (f"merge: {v[4]} items per segment, variant {v[2]}" if v[0] == "merge" else "rows")
                       for kk, v in self.engine.items()}
-        merge_desc["backward"] = (f"fused: spx_spmm_t_sddmm, variant {self.backward[1]}" if self.backward
+        merge_desc["backward"] = (f"fused: spx_spmm_t_sddmm, variant {self.backward[1]}, {self.backward[3]} plan"
+                                  if self.backward
                                   else "separate: sddmm, gather, spmm_t")
         self.tuning = {"engine": merge_desc,
                        "spmm": [self.plan.col_block, self.plan.rows_per_group, self.plan.engine,
@@ -428,7 +430,7 @@ class Workload:
         elif which == "gather":
             a.spx_gather_values(self.perm, b["v"], b["tv"])
         elif which == "backward":
-            a.spx_spmm_t_sddmm(self.s_ATpat, self.perm, b["v"], b["G"], b["X"], b["gX"], b["gA"], plan=self.t_plan,
+            a.spx_spmm_t_sddmm(self.s_ATpat, self.perm, b["v"], b["G"], b["X"], b["gX"], b["gA"], plan=self.backward[2],
                                variant=self.backward[1])
         else:
             if eng[0] == "merge":

@@ -252,7 +252,7 @@ extern "C" spx_status spx_spmm_t_sddmm(const spx_csr* AT, const int32_t* perm, c
                                        float alpha, float beta, float* gA, float scale, const spx_rowplan* plan,
                                        int32_t variant, void* stream) {
     const char* who = "spx_spmm_t_sddmm";
-    if (variant < 0 || variant > 1) return set_error(SPX_INVALID_ARG, "%s: variant %d (0 or 1)", who, variant);
+    if (variant < 0 || variant > 3) return set_error(SPX_INVALID_ARG, "%s: variant %d (0..3)", who, variant);
     SPX_TRY(check_csr(AT, false, who));
     if (k < 4 || k > 128 || k % 4 != 0)
         return set_error(SPX_NOT_SUPPORTED, "%s: k = %d (a multiple of 4 in 4..128)", who, k);
@@ -300,14 +300,17 @@ extern "C" spx_status spx_spmm_t_sddmm(const spx_csr* AT, const int32_t* perm, c
     (unsigned)grid, st, AT, perm, a_values, G, ldg, X, ldx, k, gX, ldgx, alpha, beta, gA, scale, rpg, threshold, \
         long_rows, n_long, long_blocks, med_rows, n_med, med_blocks, short_rows, n_short
     // 8-lane groups: variant 0 loads, shuffles and uses one row at a time (4 resident blocks),
-    // variant 1 requests the batch's rows first (3 resident blocks); 16-lane groups: 3 or 4
-    // resident blocks; 32-lane groups: one shape
+    // 1 requests the batch's rows first (3 resident blocks), 2 and 3 as 0 with 5 and 6 resident
+    // blocks (fewer registers); 16-lane groups: 3 or 4 resident blocks (2, 3: as 1); 32-lane
+    // groups: one shape
     if (lpr == 8) {
         if (variant == 0) fb_launch<8, false, 4>(SPX_FB_ARGS);
-        else fb_launch<8, true, 3>(SPX_FB_ARGS);
+        else if (variant == 1) fb_launch<8, true, 3>(SPX_FB_ARGS);
+        else if (variant == 2) fb_launch<8, false, 5>(SPX_FB_ARGS);
+        else fb_launch<8, false, 6>(SPX_FB_ARGS);
     } else if (lpr == 16) {
         if (variant == 0) fb_launch<16, false, 3>(SPX_FB_ARGS);
-        else fb_launch<16, false, 4>(SPX_FB_ARGS);
+        else fb_launch<16, false, 4>(SPX_FB_ARGS);          // variants 1..3
     } else {
         fb_launch<32, false, 3>(SPX_FB_ARGS);
     }

@@ -27,7 +27,7 @@ def _mats():
 
 @pytest.mark.parametrize("name", ["powerlaw", "ragged", "rect", "poisson"])
 @pytest.mark.parametrize("k", [4, 12, 32, 64, 100, 128])
-@pytest.mark.parametrize("use_plan,variant", [(True, 0), (False, 0), (True, 1)])
+@pytest.mark.parametrize("use_plan,variant", [(True, 0), (False, 0), (True, 1), (True, 2), (False, 3)])
 def test_fused_backward_matches_oracle(name, k, use_plan, variant):
     A = _mats()[name]
     dA = spx.CSR.from_host(A)
@@ -60,11 +60,11 @@ def test_fused_backward_is_deterministic_and_handles_degenerate_shapes():
     G = torch.from_numpy(synth.normal((A.m, k), seed=1)).cuda()
     X = torch.from_numpy(synth.normal((A.n, k), seed=2)).cuda()
     outs = []
-    for variant in (0, 0, 1, 1):
+    for variant in (0, 0, 1, 2, 3):
         gX, gA = torch.empty(A.n, k, device="cuda"), torch.empty(A.nnz, device="cuda")
         abi.spx_spmm_t_sddmm(AT, perm, dA.values, G, X, gX, gA, plan=dA.t_plan(), variant=variant)
         outs.append((gX.cpu(), gA.cpu()))
-    # the two launch shapes do the same arithmetic in the same order
+    # the launch shapes do the same arithmetic in the same order
     assert all(torch.equal(outs[0][0], o[0]) and torch.equal(outs[0][1], o[1]) for o in outs[1:])
     # no entries: gX = beta gX; one row; one column
     for B in (synth.CSR(7, 5, np.zeros(8, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32)),

@@ -163,7 +163,7 @@ def test_full_size_bench_configuration_sampled(kind, k, backward):
     import bench
     W = bench.Workload(kind, k=k)
     if backward == "fused":
-        W.backward, W.KERNELS = ("fused", 0), ("spmm", "backward")
+        W.backward, W.KERNELS = ("fused", 0, W.t_plan, "tuned"), ("spmm", "backward")
     elif backward == "separate":
         W.backward, W.KERNELS = None, ("spmm", "sddmm", "gather", "spmm_t")
     for kname in W.KERNELS:
