@@ -1138,11 +1138,41 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc,
                                 "single_thread": {"value": v1, "unit": "GB/s", "cores": 1, "sample": desc1}}
     if rank == 0:
+        line["summary"] = summarize(line)                 # last key: the short digest of the sections
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def summarize(line):
+    """The headline figures of every section in a few hundred bytes (printed last in the line)."""
+    r3 = lambda x: round(x, 3) if isinstance(x, float) else x  # noqa: E731
+    out = {"step_k32": {"ms": r3(line["ms_per_step"]), "frac": r3(line["step_frac_of_peak"]),
+                        "dominant": line["roofline"]["kernel"], "kernel_frac": r3(line["roofline"]["frac"]),
+                        "vs_gather_probe": r3(line["roofline"].get("vs_gather_probe")),
+                        "backward": line["tuning"]["engine"].get("backward")}}
+    for name, v in line.get("extras", {}).items():
+        key = "powerlaw_k128" if "k=128" in name else ("poisson3d_128" if "poisson" in name else name)
+        out[key] = {"ms": r3(v["ms_per_step"]), "frac": r3(v["frac_of_peak"]), "dominant": v["roofline"]["kernel"],
+                    "kernel_frac": r3(v["roofline"]["frac"]), "traffic": v["roofline"].get("traffic"),
+                    "backward": v["tuning"]["engine"].get("backward")}
+    if "spgemm" in line:
+        out["spgemm_symbolic_over_numeric"] = [r3(v["symbolic_over_numeric"]) for v in line["spgemm"].values()]
+    if "network_layers" in line:
+        out["tc_layers_frac"] = {k: r3(v["pipelined"]["frac"]) for k, v in line["network_layers"].items()
+                                 if isinstance(v, dict) and "pipelined" in v}
+    if "pcg_iteration_cost" in line:
+        out["pcg_us_per_iter"] = {k: r3(line["pcg_iteration_cost"][k]["us_per_iteration"]) for k in ("jacobi", "dia")}
+    ev = line.get("cg", {}).get("eval_256x256")
+    if ev:
+        out["pcg_1e-8_ms_per_system"] = {m: r3(v["ms_per_system"]) for m, v in ev.items()
+                                         if isinstance(v, dict) and "ms_per_system" in v}
+        out["learned_speedup_vs_jacobi"] = r3(ev.get("learned", {}).get("speedup_vs_jacobi"))
+    if "cpu_baseline" in line:
+        out["cpu_baseline_gbs"] = r3(line["cpu_baseline"]["value"])
+    return out
 
 
 if __name__ == "__main__":
