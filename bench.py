@@ -547,7 +547,7 @@ KERNEL_SOURCE = {"spmm_kernel": "spmm.cu", "sddmm_rows_kernel": "sddmm.cu", "sdd
 def time_e2e(W, steps, warmup):
     """The step end to end through host buffers: every step copies its inputs (A's values, X,
     G) from pinned host memory and its results (Y, gA, gX) back.  Streamed the way a user
-    feeds batches: two device buffer sets, copies in on one stream, the three products on a
+    feeds batches: three device buffer sets, copies in on one stream, the products on a
     second, copies out on a third, so step s + 1's inputs travel while step s computes and
     step s - 1's results travel back (the link is full duplex).  Returns (ms per step,
     H2D bytes per step, D2H bytes per step, ms per step with everything on one stream)."""
@@ -555,8 +555,10 @@ def time_e2e(W, steps, warmup):
     hv = torch.from_numpy(W.host.values).pin_memory()
     hX = W.X.cpu().pin_memory()
     hG = W.G.cpu().pin_memory()
+    nslots = 3
     slots = [W.buffers()]
-    slots.append(W.slot_like(slots[0]))
+    for _ in range(nslots - 1):
+        slots.append(W.slot_like(slots[0]))
     for sl in slots:
         # each slot's results land in host buffers of their own: consecutive steps' copies
         # back never share memory
@@ -595,14 +597,14 @@ def time_e2e(W, steps, warmup):
 
     s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     ev = lambda: torch.cuda.Event()  # noqa: E731
-    done_in = [ev(), ev()]
-    done_cmp = [ev(), ev()]
-    done_out = [ev(), ev()]
-    used = [False, False]
+    done_in = [ev() for _ in range(nslots)]
+    done_cmp = [ev() for _ in range(nslots)]
+    done_out = [ev() for _ in range(nslots)]
+    used = [False] * nslots
 
     def streamed(n):
         for step in range(n):
-            k = step % 2
+            k = step % nslots
             with torch.cuda.stream(s_in):
                 if used[k]:
                     s_in.wait_event(done_cmp[k])           # slot k's inputs consumed
@@ -619,9 +621,9 @@ def time_e2e(W, steps, warmup):
                 d2h(slots[k])
                 done_out[k].record(s_out)
             used[k] = True
-    streamed(max(warmup, 2))
+    streamed(max(warmup, nslots))
     torch.cuda.synchronize()
-    used[0] = used[1] = False
+    used[:] = [False] * nslots
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(s_in)
     streamed(steps)
@@ -1093,7 +1095,7 @@ def main():
         "gather_probe": probe,
         "e2e": {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "mode": "streamed: inputs, products and results on three streams, two buffer sets",
+                "mode": "streamed: inputs, products and results on three streams, three buffer sets",
                 "serial_ms_per_step": e2e_serial_ms, "streamed_results_equal_serial": e2e_same},
         "gpu_launches": W.launches_per_step() * args.steps,
         "clocks": clk,
