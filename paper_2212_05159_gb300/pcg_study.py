@@ -241,7 +241,7 @@ def evaluate(net: learned.MPNN, nsys: int = 128, per_batch: int = 64, side: int 
                   "analysis_ms": analysis_ms[m], "converged": res[m]["converged"],
                   "max_true_relres": res[m]["max_relres"]}
         if m in paths:
-            out[m]["apply"] = {"dia": "M = L L^T, L's diagonals in shared memory (spx_cg_batched_dia)",
+            out[m]["apply"] = {"dia": "M = L L^T by its diagonals in shared memory (spx_dia_square, spx_cg_batched_dia)",
                                "M": "explicit M = L L^T formed by SpGEMM, one gathered product"}[paths[m]]
     if "jacobi" in methods:
         for m in methods:
