@@ -504,6 +504,21 @@ def gather_probe(W, reps=5):
     return out
 
 
+def cusparse_yardstick(W, reps=10):
+    """Y = A X by torch's CSR product (cuSPARSE) on the same matrix and operand, timed for
+    context only: it is never on the library's path."""
+    import torch
+    import warnings
+    try:
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")                  # torch marks its CSR tensors as beta
+            A = torch.sparse_csr_tensor(W.dA.indptr, W.dA.indices, W.dA.values, size=(W.m, W.n))
+        ms = _ev_time(lambda: torch.sparse.mm(A, W.X), reps)
+    except (RuntimeError, TypeError, NotImplementedError) as e:        # a torch without it: say so
+        return {"unavailable": str(e).splitlines()[0][:120]}
+    return {"spmm_ms": ms, "what": "torch.sparse.mm(CSR, dense), cuSPARSE; context, not on the path"}
+
+
 def workload_report(W, ms, per, hbm, hbm_src, probe=None):
     """Roofline object of the dominant CUDA kernel of the step (the one with the largest share
     of the step time, summed over its launches) and per-launch figures."""
@@ -529,6 +544,15 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
                                                                    KERNEL_SOURCE[dom])),
                 "algorithmic_bytes": d["bytes"] / nl, "bytes_model": "compulsory, per launch (mean of its launches)",
                 "gather_model_frac": d["gather_bytes"] / (d["ms"] * 1e-3) / 1e9 / hbm}
+    # DRAM bytes of the profiled launch (the forward for the SpMM kernels, the fused backward)
+    # over that launch's live time: the measured DRAM rate, against the same peak
+    tr = roofline["traffic"]
+    prof_launch = "backward" if dom == "spmm_t_sddmm_kernel" else ("spmm" if "spmm" in d["launches"] else
+                                                                     d["launches"][0])
+    if tr and per.get(prof_launch):
+        roofline["traffic_gbs"] = tr / (per[prof_launch] * 1e-3) / 1e9
+        roofline["traffic_frac"] = roofline["traffic_gbs"] / hbm
+    roofline["frac_of_nominal"] = achieved / NOMINAL_HBM_GBS
     if probe is not None and dom in ("spmm_kernel", "spmm_merge_kernel", "spmm_t_sddmm_kernel"):
         t_floor = sum(probe["A" if ln == "spmm" else "AT"]["ms"] for ln in d["launches"])
         roofline["gather_probe_ms"] = t_floor
@@ -538,6 +562,8 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
             "per_launch_gbs_compulsory": {kk: lb[kk] / (per[kk] * 1e-3) / 1e9 for kk in per},
             "per_kernel_share": {kk: v["ms"] / ms for kk, v in by_kernel.items()}}
 
+
+NOMINAL_HBM_GBS = 7900.0          # GB300 HBM3e, nominal (context beside the measured copy peak)
 
 KERNEL_SOURCE = {"spmm_kernel": "spmm.cu", "sddmm_rows_kernel": "sddmm.cu", "sddmm_kernel": "sddmm.cu",
                  "gather_values_kernel": "spmm.cu", "spmm_merge_kernel": "merge.cu",
@@ -1075,6 +1101,10 @@ def main():
     hbm, hbm_src = measured_peaks()
     probe = gather_probe(W)
     rep = workload_report(W, ms, per, hbm, hbm_src, probe)
+    yard = cusparse_yardstick(W)
+    if "spmm_ms" in yard:
+        yard["ours_spmm_ms"] = per["spmm"]
+        yard["speedup"] = yard["spmm_ms"] / per["spmm"]
     e2e_ms, h2d, d2h, e2e_serial_ms, e2e_same = time_e2e(W, max(3, args.steps // 2), 2)
     e2e_ms = max_over_ranks(e2e_ms, ws)
     e2e_serial_ms = max_over_ranks(e2e_serial_ms, ws)
@@ -1093,6 +1123,7 @@ def main():
         "step_frac_of_peak": value / ws / hbm,
         "roofline": rep["roofline"],
         "gather_probe": probe,
+        "yardstick_cusparse": yard,
         "e2e": {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "mode": "streamed: inputs, products and results on three streams, three buffer sets",
@@ -1154,7 +1185,9 @@ def summarize(line):
     out = {"step_k32": {"ms": r3(line["ms_per_step"]), "frac": r3(line["step_frac_of_peak"]),
                         "dominant": line["roofline"]["kernel"], "kernel_frac": r3(line["roofline"]["frac"]),
                         "vs_gather_probe": r3(line["roofline"].get("vs_gather_probe")),
-                        "backward": line["tuning"]["engine"].get("backward")}}
+                        "backward": line["tuning"]["engine"].get("backward"),
+                        "traffic_frac": r3(line["roofline"].get("traffic_frac")),
+                        "cusparse_spmm_over_ours": r3(line.get("yardstick_cusparse", {}).get("speedup"))}}
     for name, v in line.get("extras", {}).items():
         key = "powerlaw_k128" if "k=128" in name else ("poisson3d_128" if "poisson" in name else name)
         out[key] = {"ms": r3(v["ms_per_step"]), "frac": r3(v["frac_of_peak"]), "dominant": v["roofline"]["kernel"],
