@@ -76,7 +76,9 @@ typedef struct spx_rowplan {
     int32_t engine;           /* gathers of the dense rows: 0 = loads into registers,
                                  1 = TMA-engine bulk copies into shared memory (needs k and
                                  the leading dimensions multiples of 4 and 16-byte aligned
-                                 operands; otherwise 0 is used) */
+                                 operands; otherwise 0 is used), 2 = loads into registers
+                                 with no batch prefetched ahead, for more resident warps
+                                 (one pass over all k, same conditions as 1; otherwise 0) */
     const int32_t* medium_rows; /* device int32[n_medium]: rows with medium_threshold < length
                                    <= threshold, one warp each (NULL / 0 = none) */
     int32_t n_medium;

@@ -271,6 +271,48 @@ __global__ void __launch_bounds__(SPMM_THREADS, SPMM_MIN_BLOCKS) spmm_kernel(
 }
 
 // ---------------------------------------------------------------------------------------
+// Short rows, lean (plan engine 2): a row's batches are loaded and gathered in turn, with no
+// batch held ahead, so fewer registers stay live and 8 blocks (64 warps) are resident per
+// SM.  Where every short row is one batch (a stencil's rows), the prefetch of the register
+// path has nothing to overlap and the extra warps keep more rows in flight instead.  Long
+// and medium rows still go to spmm_kernel's blocks and warps.  Same sums in the same order.
+template <int LPR, bool PERM>
+__global__ void __launch_bounds__(SPMM_THREADS, 8) spmm_lean_kernel(
+    int32_t m, const int32_t* __restrict__ indptr, const int32_t* __restrict__ indices, const float* __restrict__ vals,
+    const int32_t* __restrict__ perm, const float* __restrict__ X, int64_t ldx, int32_t col_end, float* __restrict__ Y,
+    int64_t ldy, float alpha, float beta, int32_t rows_per_group, int32_t threshold,
+    const int32_t* __restrict__ short_rows, int32_t n_short) {
+    constexpr int G = 32 / LPR;
+    constexpr int SLOTS = (BATCH + LPR - 1) / LPR;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LPR;
+    const int c = lane % LPR;
+    const unsigned gmask = LPR == 32 ? FULL : (((1u << LPR) - 1u) << (g * LPR));
+    const int col = c * 4;
+    const bool colok = col < col_end;
+    const uint64_t pol_stream = policy_evict_first();
+    const uint64_t pol_keep = policy_evict_last();
+    const int64_t wglobal = ((int64_t)blockIdx.x * SPMM_THREADS + threadIdx.x) >> 5;
+    const int64_t row0 = (wglobal * G + g) * rows_per_group;
+    const int64_t n_rows = short_rows ? (int64_t)n_short : (int64_t)m;
+    for (int p = 0; p < rows_per_group; ++p) {
+        const int64_t idx = row0 + p;
+        if (idx >= n_rows) break;
+        const int64_t row = short_rows ? (int64_t)short_rows[idx] : idx;
+        const int a = indptr[row], b = indptr[row + 1];
+        if (b - a > threshold) continue;            // a long-row block or a medium-row warp takes it
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int e = a; e < b; e += BATCH) {
+            int j[SLOTS];
+            float v[SLOTS];
+            load_batch<LPR, PERM>(j, v, e, b, c, indices, vals, perm, pol_stream);
+            gather_batch<4, LPR>(acc, j, v, gmask, colok, X, ldx, col, pol_keep);
+        }
+        if (colok) store_row<4>(Y + row * ldy + col, acc, alpha, beta);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Short rows through the TMA engine.  Each lane group keeps a ring of BK_DEPTH batch slots
 // in shared memory; for every batch (up to 8 entries of one row) the group's lanes issue
 // one cp.async.bulk row copy per entry (X row segment -> slot) counted on the slot's
@@ -577,6 +619,40 @@ spx_status launch_spmm(const spx_csr* A, const int32_t* perm, const float* vals,
     if (grid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
     if (use_slab) SPX_TRY(slab_repack(A->n, X, ldx, k, sh.cb, slab_ws, st));
     const int32_t parts = plan && plan->n_parts > 1 && plan->part_ptr ? plan->n_parts : 1;
+    const bool lean = vec4 && plan && plan->engine == 2 && sh.cb >= k && parts == 1 && !use_slab;
+    if (lean) {
+        const int64_t rows_per_lblock = (int64_t)SPMM_WARPS * G * sh.rpg;
+        const int64_t lgrid = (n_rows + rows_per_lblock - 1) / rows_per_lblock;
+        if (lgrid > INT_MAX) return set_error(SPX_INVALID_ARG, "%s: too many rows", who);
+        if (lgrid > 0) {
+#define SPX_LEAN_CASE(L)                                                                                       \
+    case L:                                                                                                    \
+        spmm_lean_kernel<L, PERM><<<(unsigned)lgrid, SPMM_THREADS, 0, st>>>(                                   \
+            A->m, A->indptr, A->indices, vals, perm, X, ldx, k, Y, ldy, alpha, beta, sh.rpg, threshold,        \
+            short_rows, n_short);                                                                              \
+        break;
+            switch (sh.lpr) {
+                SPX_LEAN_CASE(1)
+                SPX_LEAN_CASE(2)
+                SPX_LEAN_CASE(4)
+                SPX_LEAN_CASE(8)
+                SPX_LEAN_CASE(16)
+                SPX_LEAN_CASE(32)
+                default: return set_error(SPX_INVALID_ARG, "%s: lean lane count %d", who, sh.lpr);
+            }
+#undef SPX_LEAN_CASE
+            SPX_CHECK_LAUNCH(who);
+        }
+        if (long_blocks + med_blocks > 0) {
+            spx_status s2 = launch_lpr<4, PERM>(sh.lpr, (unsigned)(long_blocks + med_blocks), st, A, A->indptr,
+                                                A->indptr + 1, 0, perm, vals, X, ldx, 0, 0, k, Y, ldy, alpha, beta,
+                                                sh.rpg, threshold, long_rows, n_long, long_blocks, med_rows, n_med,
+                                                med_blocks, nullptr, 0);
+            if (s2 != SPX_OK) return s2;
+            SPX_CHECK_LAUNCH(who);
+        }
+        return SPX_OK;
+    }
     const bool bulk = !PERM && vec4 && plan && plan->engine == 1 && sh.cb % 4 == 0 && sh.lpr >= 2 &&
                       sh.lpr * 4 >= sh.cb && parts == 1;
     if (bulk) {

@@ -94,6 +94,8 @@ def tune_rows(A: CSR, k: int, transposed: bool = False, force: bool = False):
     best, best_ms, table = None, float("inf"), {}
     engines = (0, 1) if k % 4 == 0 else (0,)
     cands = [(cb, rpg, eng, 1) for cb in _col_blocks(k) for rpg in (1, 2, 4) for eng in engines]
+    if k % 4 == 0:                                      # lean short rows: one pass over all k
+        cands += [(k, rpg, 2, 1) for rpg in (1, 2, 4)]
     cands += [(cb, rpg, 0, np_) for cb in _col_blocks(k) for rpg in (1, 2, 4)
               for np_ in _part_counts(rows_in, min(cb, k)) if np_ > 1]
     for cb, rpg, eng, np_ in cands:
