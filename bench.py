@@ -363,8 +363,10 @@ class Workload:
             else:
                 sep_ms = _ev_time(lambda: [self.run_kernel(kk) for kk in ("sddmm", "gather", "spmm_t")], 5)
                 best = None
-                for pname, pl in (("tuned", self.t_plan), ("default", self.dA.t_plan())):
-                    for v in (0, 1, 2, 3):
+                plans = [("tuned", self.t_plan), ("default", self.dA.t_plan())]
+                plans += [(f"rows per group {r}", self.dA.t_plan().with_params(k, r, 0)) for r in (1, 4)]
+                for pname, pl in plans:
+                    for v in range(6):
                         self.backward = ("fused", v, pl, pname)
                         t = _ev_time(lambda: self.run_kernel("backward"), 5)
                         if best is None or t < best[0]:

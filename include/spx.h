@@ -257,10 +257,11 @@ spx_status spx_spmm_t(const spx_csr* AT, const int32_t* perm, const float* G, in
  * operand; gX: device float32 A.n x k (ldgx); gA: device float32[nnz] in A's order.
  * k a multiple of 4 in 4..128; dense operands 16-byte aligned with ld % 4 == 0.
  * plan: optional row plan of the transposed pattern (its row lists and order are used;
- * column blocks and parts are not).  variant: 0..3, launch shapes with the same result (1
+ * column blocks and parts are not).  variant: 0..5, launch shapes with the same result (1
  * requests every gathered row of a batch before using any; 2 and 3 keep more blocks
- * resident with fewer registers; the faster one depends on k and the pattern, chosen by
- * timing).  Other k: SPX_NOT_SUPPORTED (use the two calls). */
+ * resident with fewer registers; 4 and 5 also hold no batch ahead; the faster one depends
+ * on k and the pattern, chosen by timing).  Other k: SPX_NOT_SUPPORTED (use the two
+ * calls). */
 spx_status spx_spmm_t_sddmm(const spx_csr* AT, const int32_t* perm, const float* a_values,
                             const float* G, int64_t ldg, const float* X, int64_t ldx, int32_t k,
                             float* gX, int64_t ldgx, float alpha, float beta, float* gA,

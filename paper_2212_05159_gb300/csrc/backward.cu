@@ -122,8 +122,9 @@ __device__ __forceinline__ float4 fb_xrow(const float* __restrict__ X, int64_t l
 }
 
 // TWO: the batch's rows of G all requested before A's values are shuffled (more registers);
-// MINB: resident blocks per SM the register allocation must allow.
-template <int LPR, bool TWO, int MINB>
+// MINB: resident blocks per SM the register allocation must allow; LEAN: short rows without
+// the next batch held ahead.
+template <int LPR, bool TWO, int MINB, bool LEAN = false>
 __global__ void __launch_bounds__(FB_THREADS, MINB) spmm_t_sddmm_kernel(
     int32_t n, const int32_t* __restrict__ t_ptr, const int32_t* __restrict__ t_ix, const int32_t* __restrict__ perm,
     const float* __restrict__ vals, const float* __restrict__ G, int64_t ldg, const float* __restrict__ X,
@@ -218,23 +219,30 @@ __global__ void __launch_bounds__(FB_THREADS, MINB) spmm_t_sddmm_kernel(
         if (b - a > threshold) continue;            // a long-row block or a medium-row warp takes it
         const float4 xv = fb_xrow(X, ldx, row, col, colok);
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        FbEntry nxt = fb_load(t_ix, perm, vals, a + c, b, pol_stream);
-        for (int e = a; e < b; e += LPR) {
-            const FbEntry cur = nxt;
-            if (e + LPR < b) nxt = fb_load(t_ix, perm, vals, e + LPR + c, b, pol_stream);
-            fb_batch<LPR, TWO>(cur, gmask, colok, xv, G, ldg, col, acc, scale, gA, pol_keep);
+        if constexpr (LEAN) {
+            // no batch held ahead: fewer live registers, more resident warps
+            for (int e = a; e < b; e += LPR)
+                fb_batch<LPR, TWO>(fb_load(t_ix, perm, vals, e + c, b, pol_stream), gmask, colok, xv, G, ldg, col,
+                                   acc, scale, gA, pol_keep);
+        } else {
+            FbEntry nxt = fb_load(t_ix, perm, vals, a + c, b, pol_stream);
+            for (int e = a; e < b; e += LPR) {
+                const FbEntry cur = nxt;
+                if (e + LPR < b) nxt = fb_load(t_ix, perm, vals, e + LPR + c, b, pol_stream);
+                fb_batch<LPR, TWO>(cur, gmask, colok, xv, G, ldg, col, acc, scale, gA, pol_keep);
+            }
         }
         if (colok) fb_store(gX + row * ldgx + col, acc, alpha, beta);
     }
 }
 
-template <int LPR, bool TWO, int MINB>
+template <int LPR, bool TWO, int MINB, bool LEAN = false>
 void fb_launch(unsigned grid, cudaStream_t st, const spx_csr* AT, const int32_t* perm, const float* vals,
                const float* G, int64_t ldg, const float* X, int64_t ldx, int32_t k, float* gX, int64_t ldgx,
                float alpha, float beta, float* gA, float scale, int32_t rpg, int32_t threshold,
                const int32_t* long_rows, int32_t n_long, int32_t long_blocks, const int32_t* med_rows, int32_t n_med,
                int32_t med_blocks, const int32_t* short_rows, int32_t n_short) {
-    spmm_t_sddmm_kernel<LPR, TWO, MINB><<<grid, FB_THREADS, 0, st>>>(AT->m, AT->indptr, AT->indices, perm, vals, G, ldg, X, ldx,
+    spmm_t_sddmm_kernel<LPR, TWO, MINB, LEAN><<<grid, FB_THREADS, 0, st>>>(AT->m, AT->indptr, AT->indices, perm, vals, G, ldg, X, ldx,
                                                                     k, gX, ldgx, alpha, beta, gA, scale, rpg,
                                                                     threshold, long_rows, n_long, long_blocks,
                                                                     med_rows, n_med, med_blocks, short_rows, n_short);
@@ -252,7 +260,7 @@ extern "C" spx_status spx_spmm_t_sddmm(const spx_csr* AT, const int32_t* perm, c
                                        float alpha, float beta, float* gA, float scale, const spx_rowplan* plan,
                                        int32_t variant, void* stream) {
     const char* who = "spx_spmm_t_sddmm";
-    if (variant < 0 || variant > 3) return set_error(SPX_INVALID_ARG, "%s: variant %d (0..3)", who, variant);
+    if (variant < 0 || variant > 5) return set_error(SPX_INVALID_ARG, "%s: variant %d (0..5)", who, variant);
     SPX_TRY(check_csr(AT, false, who));
     if (k < 4 || k > 128 || k % 4 != 0)
         return set_error(SPX_NOT_SUPPORTED, "%s: k = %d (a multiple of 4 in 4..128)", who, k);
@@ -301,16 +309,18 @@ extern "C" spx_status spx_spmm_t_sddmm(const spx_csr* AT, const int32_t* perm, c
         long_rows, n_long, long_blocks, med_rows, n_med, med_blocks, short_rows, n_short
     // 8-lane groups: variant 0 loads, shuffles and uses one row at a time (4 resident blocks),
     // 1 requests the batch's rows first (3 resident blocks), 2 and 3 as 0 with 5 and 6 resident
-    // blocks (fewer registers); 16-lane groups: 3 or 4 resident blocks (2, 3: as 1); 32-lane
-    // groups: one shape
+    // blocks (fewer registers), 4 and 5 without a batch held ahead at 6 and 8; 16-lane groups:
+    // 3 or 4 resident blocks (2..5: as 1); 32-lane groups: one shape
     if (lpr == 8) {
         if (variant == 0) fb_launch<8, false, 4>(SPX_FB_ARGS);
         else if (variant == 1) fb_launch<8, true, 3>(SPX_FB_ARGS);
         else if (variant == 2) fb_launch<8, false, 5>(SPX_FB_ARGS);
-        else fb_launch<8, false, 6>(SPX_FB_ARGS);
+        else if (variant == 3) fb_launch<8, false, 6>(SPX_FB_ARGS);
+        else if (variant == 4) fb_launch<8, false, 6, true>(SPX_FB_ARGS);
+        else fb_launch<8, false, 8, true>(SPX_FB_ARGS);
     } else if (lpr == 16) {
         if (variant == 0) fb_launch<16, false, 3>(SPX_FB_ARGS);
-        else fb_launch<16, false, 4>(SPX_FB_ARGS);          // variants 1..3
+        else fb_launch<16, false, 4>(SPX_FB_ARGS);          // variants 1..5
     } else {
         fb_launch<32, false, 3>(SPX_FB_ARGS);
     }

@@ -27,7 +27,8 @@ def _mats():
 
 @pytest.mark.parametrize("name", ["powerlaw", "ragged", "rect", "poisson"])
 @pytest.mark.parametrize("k", [4, 12, 32, 64, 100, 128])
-@pytest.mark.parametrize("use_plan,variant", [(True, 0), (False, 0), (True, 1), (True, 2), (False, 3)])
+@pytest.mark.parametrize("use_plan,variant", [(True, 0), (False, 0), (True, 1), (True, 2), (False, 3),
+                                              (True, 4), (False, 5)])
 def test_fused_backward_matches_oracle(name, k, use_plan, variant):
     A = _mats()[name]
     dA = spx.CSR.from_host(A)
@@ -60,7 +61,7 @@ def test_fused_backward_is_deterministic_and_handles_degenerate_shapes():
     G = torch.from_numpy(synth.normal((A.m, k), seed=1)).cuda()
     X = torch.from_numpy(synth.normal((A.n, k), seed=2)).cuda()
     outs = []
-    for variant in (0, 0, 1, 2, 3):
+    for variant in (0, 0, 1, 2, 3, 4, 5):
         gX, gA = torch.empty(A.n, k, device="cuda"), torch.empty(A.nnz, device="cuda")
         abi.spx_spmm_t_sddmm(AT, perm, dA.values, G, X, gX, gA, plan=dA.t_plan(), variant=variant)
         outs.append((gX.cpu(), gA.cpu()))
