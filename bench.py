@@ -555,7 +555,7 @@ def workload_report(W, ms, per, hbm, hbm_src, probe=None):
         roofline["traffic_gbs"] = tr / (per[prof_launch] * 1e-3) / 1e9
         roofline["traffic_frac"] = roofline["traffic_gbs"] / hbm
     roofline["frac_of_nominal"] = achieved / NOMINAL_HBM_GBS
-    if probe is not None and dom in ("spmm_kernel", "spmm_merge_kernel", "spmm_t_sddmm_kernel"):
+    if probe is not None and dom in ("spmm_kernel", "spmm_merge_kernel"):   # one product per launch
         t_floor = sum(probe["A" if ln == "spmm" else "AT"]["ms"] for ln in d["launches"])
         roofline["gather_probe_ms"] = t_floor
         roofline["vs_gather_probe"] = d["ms"] / t_floor
