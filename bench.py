@@ -48,6 +48,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sparse fwd+bwd GB/s vs HBM peak"
 NO_TUNE = False
+BACKWARD = "tuned"       # the step's backward: "tuned" (by device timing), "fused" or "separate"
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -371,7 +372,8 @@ class Workload:
                         t = _ev_time(lambda: self.run_kernel("backward"), 5)
                         if best is None or t < best[0]:
                             best = (t, v, pl, pname)
-                choice = ("fused", best[1], best[2], best[3]) if best[0] < sep_ms else None
+                fused_wins = best[0] < sep_ms if BACKWARD == "tuned" else BACKWARD == "fused"
+                choice = ("fused", best[1], best[2], best[3]) if fused_wins else None
                 self.backward_timing = {"separate_ms": sep_ms, "fused_ms": best[0]}
             self.backward = choice
             if choice is not None:
@@ -1051,6 +1053,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=32)
+    ap.add_argument("--backward", default="tuned", choices=["tuned", "fused", "separate"],
+                    help="the step's backward: chosen by device timing (default), or forced (e.g. for profiling, "
+                         "where the timing that decides is itself perturbed)")
     ap.add_argument("--workload", default="powerlaw", choices=["powerlaw", "poisson3d"],
                     help="matrix of the timed step: the n = 2^20 power-law matrix or the 3D Poisson 128^3 stencil")
     ap.add_argument("--no-extras", action="store_true")
@@ -1078,8 +1083,9 @@ def main():
         secs -= {"extras", "spgemm", "network", "pcgcase", "cg"}
     if args.no_cpu:
         secs.discard("cpu")
-    global NO_TUNE
+    global NO_TUNE, BACKWARD
     NO_TUNE = args.no_tune
+    BACKWARD = args.backward
 
     import torch
     if ws > 1:
