@@ -423,66 +423,95 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_bwd_data_kernel(int64_t n
 // Weight gradient of the layer on the tensor cores: dW = [X1 X2]^T G (K x N) and db = the
 // column sums of G.  The reduction runs over the rows, so the operands are the transposes
 // of the row tiles: A (M = 128 rows of dW, the K inputs zero-padded to 128) holds X^T and
-// B (the MMA's N = N) holds G^T, both K-major over 128 rows of the tile.  Each thread
-// loads two rows of a 4-column piece (two float4, consecutive threads on consecutive
-// pieces) and stores four BF16 pairs (row r, r + 1) of the transposed operand.
+// B (the MMA's N = N) holds G^T, both K-major over 128 rows of the tile.  A thread item is
+// one 4-column piece of 8 consecutive rows (8 float4 loads, consecutive threads on
+// consecutive pieces of the same rows); its 32 values become four 16-byte core-matrix rows
+// of the transposed operand (one per column, the 8 rows' BF16 values side by side).  The
+// 8-row groups of the operands lie TW_SBO = 2064 bytes apart instead of 2048, so the 32
+// lanes' 16-byte stores fall evenly on the 8 slots of a 128-byte shared-memory window
+// (with 2048 they met two slots: a 16-way bank conflict); the MMA descriptors carry the
+// same stride.
 //
 // Two persistent CTAs per SM (one's loads in flight while the other converts) walk the row
 // tiles with a stride of the grid, each with two staging buffers in turn: while the tensor
 // cores run tile t's 8 MMAs (K = 16 rows each, the FP32 accumulator stays in tensor memory
-// across all of the CTA's tiles), the threads stage tile t + 1.  A buffer is restaged only after the mbarrier of the commit that read it has
-// completed (bounded wait).  db is summed in FP32 by the threads from the values they
-// load (each thread owns one 4-column piece of G).  Each CTA writes its partial (K + 1) x N
-// block (dW rows, then db) to the workspace; a second kernel adds the partials in block
-// order, so the result does not depend on timing.
+// across all of the CTA's tiles), the threads stage tile t + 1.  A buffer is restaged only
+// after the mbarrier of the commit that read it has completed (bounded wait).  db is summed
+// in FP32 by the threads from the values they load (each thread owns one 4-column piece of
+// G).  Each CTA writes its partial (K + 1) x N block (dW rows, then db) to the workspace; a
+// second kernel adds the partials in block order, so the result does not depend on timing.
 constexpr int TW_THREADS = 256;
 constexpr int TW_CTAS_PER_SM = 2;                               // two staging pipelines per SM
-constexpr int TW_BATCH = 8;                                    // row-pair items in flight per thread
-constexpr int TW_A = TC_M * TC_M * 2;                           // A buffer: 128 x 128 BF16
-__host__ __device__ constexpr int tw_buf_bytes(int N) { return TW_A + N * TC_M * 2; }
+constexpr int TW_SBO = (TC_M / 8) * 128 + 16;                   // 8-row group stride, padded
+constexpr int TW_A = (TC_M / 8) * TW_SBO;                       // A buffer: 128 x 128 BF16 (+ pads)
+__host__ __device__ constexpr int tw_buf_bytes(int N) { return TW_A + (N / 8) * TW_SBO; }
 
-// Stages rows [row0, row0 + 128) of the sources into the transposed operand: column c of
-// source s becomes operand row mbase_s + c.  nq1, nq2: 4-column pieces of the sources.
-// When sum != nullptr (only for a single source whose pieces divide TW_THREADS) the thread
-// adds the values of its piece into sum.
-__device__ __forceinline__ void stage_transposed(unsigned char* buf, const float* __restrict__ S1, int nq1,
-                                                 const float* __restrict__ S2, int nq2, int64_t row0, int64_t n,
-                                                 float4* sum) {
+// byte offset of element (operand row m, tile row k) in the padded transposed operands
+__device__ __forceinline__ uint32_t tw_off(int m, int k) {
+    return (uint32_t)((m >> 3) * TW_SBO + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2);
+}
+
+// Item t of a tile over the sources S1 (nq1 pieces) then S2 (nq2): rows row0 + 8 o .. + 7 of
+// piece q, o = t / (nq1 + nq2); rows past n read as zero.
+__device__ __forceinline__ void tw_item_load(float4 (&v)[8], int t, const float* __restrict__ S1, int nq1,
+                                             const float* __restrict__ S2, int nq2, int64_t row0, int64_t n) {
     const int nq = nq1 + nq2;
-    const int total = (TC_M / 2) * nq;                          // (row pair, piece) items
-    for (int t0 = threadIdx.x; t0 < total; t0 += TW_BATCH * TW_THREADS) {
-        float4 lo[TW_BATCH], hi[TW_BATCH];
+    const int o = t / nq, q = t - o * nq;
+    const bool first = q < nq1;
+    const float* src = first ? S1 + 4 * q : S2 + 4 * (q - nq1);
+    const int64_t step = first ? 4 * nq1 : 4 * nq2;
+    const int64_t r0 = row0 + 8 * o;
 #pragma unroll
-        for (int u = 0; u < TW_BATCH; ++u) {
-            const int t = t0 + u * TW_THREADS;
-            lo[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            hi[u] = lo[u];
-            if (t < total) {
-                const int p = t / nq, q = t - p * nq;
-                const int64_t r = row0 + 2 * p;
-                const float* src = q < nq1 ? S1 + r * (4 * nq1) + 4 * q : S2 + r * (4 * nq2) + 4 * (q - nq1);
-                const int64_t step = q < nq1 ? 4 * nq1 : 4 * nq2;
-                if (r < n) lo[u] = __ldcs(reinterpret_cast<const float4*>(src));
-                if (r + 1 < n) hi[u] = __ldcs(reinterpret_cast<const float4*>(src + step));
-            }
-        }
+    for (int r = 0; r < 8; ++r)
+        v[r] = r0 + r < n ? __ldcs(reinterpret_cast<const float4*>(src + (r0 + r) * step))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The item's four columns as four 16-byte operand rows (operand row 4 q + i, tile rows 8 o ..)
+__device__ __forceinline__ void tw_item_store(unsigned char* buf, const float4 (&v)[8], int t, int nq) {
+    const int o = t / nq, q = t - o * nq;
+    const int m = 4 * q, k = 8 * o;
+    *reinterpret_cast<uint4*>(buf + tw_off(m + 0, k)) =
+        make_uint4(pack_bf16x2(v[0].x, v[1].x), pack_bf16x2(v[2].x, v[3].x), pack_bf16x2(v[4].x, v[5].x),
+                   pack_bf16x2(v[6].x, v[7].x));
+    *reinterpret_cast<uint4*>(buf + tw_off(m + 1, k)) =
+        make_uint4(pack_bf16x2(v[0].y, v[1].y), pack_bf16x2(v[2].y, v[3].y), pack_bf16x2(v[4].y, v[5].y),
+                   pack_bf16x2(v[6].y, v[7].y));
+    *reinterpret_cast<uint4*>(buf + tw_off(m + 2, k)) =
+        make_uint4(pack_bf16x2(v[0].z, v[1].z), pack_bf16x2(v[2].z, v[3].z), pack_bf16x2(v[4].z, v[5].z),
+                   pack_bf16x2(v[6].z, v[7].z));
+    *reinterpret_cast<uint4*>(buf + tw_off(m + 3, k)) =
+        make_uint4(pack_bf16x2(v[0].w, v[1].w), pack_bf16x2(v[2].w, v[3].w), pack_bf16x2(v[4].w, v[5].w),
+                   pack_bf16x2(v[6].w, v[7].w));
+}
+
+// Stages the tile's rows into A (X1, X2) and B (G): per round two A items and one B item a
+// thread, all 24 loads issued before any store.  Thread x owns G's piece x mod N/4 (N / 4
+// divides the block), whose values it adds into db.
+__device__ __forceinline__ void tw_stage(unsigned char* sA, unsigned char* sB, const float* __restrict__ X1, int nq1,
+                                         const float* __restrict__ X2, int nq2, const float* __restrict__ G, int nqb,
+                                         int64_t row0, int64_t n, float4& db) {
+    const int totA = (TC_M / 8) * (nq1 + nq2), totB = (TC_M / 8) * nqb;
+    const int rounds_a = (totA + 2 * TW_THREADS - 1) / (2 * TW_THREADS);
+    const int rounds_b = (totB + TW_THREADS - 1) / TW_THREADS;
+    const int rounds = rounds_a > rounds_b ? rounds_a : rounds_b;
+    for (int rd = 0; rd < rounds; ++rd) {
+        float4 va[2][8], vb[8];
+        const int ta0 = threadIdx.x + 2 * TW_THREADS * rd, ta1 = ta0 + TW_THREADS;
+        const int tb = threadIdx.x + TW_THREADS * rd;
+        if (ta0 < totA) tw_item_load(va[0], ta0, X1, nq1, X2, nq2, row0, n);
+        if (ta1 < totA) tw_item_load(va[1], ta1, X1, nq1, X2, nq2, row0, n);
+        if (tb < totB) tw_item_load(vb, tb, G, nqb, nullptr, 0, row0, n);
+        if (ta0 < totA) tw_item_store(sA, va[0], ta0, nq1 + nq2);
+        if (ta1 < totA) tw_item_store(sA, va[1], ta1, nq1 + nq2);
+        if (tb < totB) {
+            tw_item_store(sB, vb, tb, nqb);
 #pragma unroll
-        for (int u = 0; u < TW_BATCH; ++u) {
-            const int t = t0 + u * TW_THREADS;
-            if (t < total) {
-                const int p = t / nq, q = t - p * nq;
-                const int m = 4 * q;                            // operand row of the piece's first column
-                const int kr = 2 * p;
-                *reinterpret_cast<uint32_t*>(buf + core_off(m + 0, kr, TC_M)) = pack_bf16x2(lo[u].x, hi[u].x);
-                *reinterpret_cast<uint32_t*>(buf + core_off(m + 1, kr, TC_M)) = pack_bf16x2(lo[u].y, hi[u].y);
-                *reinterpret_cast<uint32_t*>(buf + core_off(m + 2, kr, TC_M)) = pack_bf16x2(lo[u].z, hi[u].z);
-                *reinterpret_cast<uint32_t*>(buf + core_off(m + 3, kr, TC_M)) = pack_bf16x2(lo[u].w, hi[u].w);
-                if (sum) {
-                    sum->x += lo[u].x + hi[u].x;
-                    sum->y += lo[u].y + hi[u].y;
-                    sum->z += lo[u].z + hi[u].z;
-                    sum->w += lo[u].w + hi[u].w;
-                }
+            for (int r = 0; r < 8; ++r) {
+                db.x += vb[r].x;
+                db.y += vb[r].y;
+                db.z += vb[r].z;
+                db.w += vb[r].w;
             }
         }
     }
@@ -508,7 +537,7 @@ __global__ void __launch_bounds__(TW_THREADS, TW_CTAS_PER_SM) dense_tc_bwd_weigh
         for (int t = threadIdx.x; t < 2 * zq; t += TW_THREADS) {
             const int b = t / zq, z = t - b * zq;
             const int m = K + z / (TC_M / 8), k8 = (z % (TC_M / 8)) * 8;
-            *reinterpret_cast<uint4*>(smem + b * bufb + core_off(m, k8, TC_M)) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(smem + b * bufb + tw_off(m, k8)) = make_uint4(0u, 0u, 0u, 0u);
         }
     }
     if (threadIdx.x == 0) {
@@ -527,7 +556,7 @@ __global__ void __launch_bounds__(TW_THREADS, TW_CTAS_PER_SM) dense_tc_bwd_weigh
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
     const uint32_t idesc = instr_desc(TC_M, N);
-    const uint32_t sbo = (uint32_t)(TC_M >> 3) * 128u;
+    const uint32_t sbo = (uint32_t)TW_SBO;
 
     float4 dbs = make_float4(0.f, 0.f, 0.f, 0.f);
     bool failed = false;
@@ -545,8 +574,7 @@ __global__ void __launch_bounds__(TW_THREADS, TW_CTAS_PER_SM) dense_tc_bwd_weigh
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
         const int64_t row0 = tile * TC_M;
-        stage_transposed(sA, X1, K1 >> 2, X2, K2 >> 2, row0, n, nullptr);
-        stage_transposed(sB, G, N >> 2, nullptr, 0, row0, n, &dbs);
+        tw_stage(sA, sB, X1, K1 >> 2, X2, K2 >> 2, G, N >> 2, row0, n, dbs);
         fence_proxy_async();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
