@@ -887,6 +887,16 @@ def spgemm_section():
         bwd_bytes = (4 * (m + 1) + 8 * nA + 8 * P + 4 * (m + 1) + 8 * nC + 4 * nA) + \
                     (4 * (B.m + 1) + 8 * nA + 4 * nA + 8 * nB + 8 * P + 4 * nB)
         hbm, _ = measured_peaks()
+        # The numeric phase reads B's rows once per product from L2 (B is 15-21 MB): its bound is
+        # the L2 gather rate, measured here by the gather probe on A's column stream over an
+        # L2-resident operand of B's row count with 64-byte rows (B's rows hold 7-8 (column,
+        # value) pairs, 56-64 bytes)
+        xl2 = torch.randn(B.m, 16, device="cuda")
+        pbuf = torch.empty(16 * 256 * torch.cuda.get_device_properties(0).multi_processor_count, device="cuda")
+        probe_ms = min(_ev_time(lambda: abi.spx_gather_probe(dA.indices, B.m, xl2, u, bps, pbuf))
+                       for u, bps in ((1, 8), (2, 8), (4, 4)))
+        probe_bytes = 4 * nA + 64 * nA
+        del xl2, pbuf
         out[name] = {"m": m, "nnz_A": nA, "nnz_B": nB, "nnz_C": nC, "products": P,
                      "symbolic_ms_host_timed": sym_ms, "symbolic_ms_device": sym_dev_ms,
                      "symbolic_device_timing": "analyse + symbolic + fill without read-backs, CUDA events",
@@ -894,7 +904,11 @@ def spgemm_section():
                      "numeric_gbs": num_bytes / (num_ms * 1e-3) / 1e9,
                      "backward_gbs": bwd_bytes / (bwd_ms * 1e-3) / 1e9,
                      "numeric_frac_of_peak": num_bytes / (num_ms * 1e-3) / 1e9 / hbm,
-                     "bytes_model": "A, B rows per product (index+value), C pattern and values once"}
+                     "bytes_model": "A, B rows per product (index+value), C pattern and values once",
+                     "l2_gather_probe": {"ms": probe_ms, "gbs": probe_bytes / (probe_ms * 1e-3) / 1e9,
+                                         "what": "spx_gather_probe on A's column stream, 64-byte rows of an "
+                                                 "L2-resident operand with B's row count"},
+                     "numeric_over_l2_probe": num_ms / probe_ms}
     return out
 
 
@@ -1203,9 +1217,13 @@ def summarize(line):
                     "backward": v["tuning"]["engine"].get("backward")}
     if "spgemm" in line:
         out["spgemm_symbolic_over_numeric"] = [r3(v["symbolic_over_numeric"]) for v in line["spgemm"].values()]
+        out["spgemm_numeric_over_l2_probe"] = [r3(v.get("numeric_over_l2_probe")) for v in line["spgemm"].values()]
     if "network_layers" in line:
         out["tc_layers_frac"] = {k: r3(v["pipelined"]["frac"]) for k, v in line["network_layers"].items()
                                  if isinstance(v, dict) and "pipelined" in v}
+        wg = line["network_layers"].get("weight_gradient", {}).get("persistent")
+        if wg:
+            out["tc_layers_frac"]["weight_gradient"] = r3(wg["frac"])
     if "pcg_iteration_cost" in line:
         out["pcg_us_per_iter"] = {k: r3(line["pcg_iteration_cost"][k]["us_per_iteration"]) for k in ("jacobi", "dia")}
     ev = line.get("cg", {}).get("eval_256x256")

@@ -15,7 +15,10 @@
 //             shared bitmap of the column space (chunked), which yields the columns already
 //             sorted.  mask(C) is structural: no numerical-zero dropping.
 //   fill      copies the unique columns into C_indices (8 lanes per row).
-//   numeric   per row, C_ij = sum over k in A_i of A_ik B_kj.  Rows with at most 128
+//   numeric   per row, C_ij = sum over k in A_i of A_ik B_kj.  Rows of at most 8 entries of
+//             A and 64 columns of C: one 8-lane group each (four rows per warp), every B_k's
+//             first 8 entries loaded at once, products placed by binary search in C's row and
+//             summed over A's entries in order.  Other rows with at most 128
 //             columns: four 8-lane groups, group g takes the entries k = g, g+4, ... of A_i
 //             (in A's order) into a private slice of the row's accumulator (the four slices
 //             fit the space one wide row needs), its lanes over B_k's columns (distinct within
@@ -377,18 +380,110 @@ __device__ __forceinline__ int lower_bound_i32(const int* __restrict__ a, int n,
     return lo;
 }
 
-__global__ void __launch_bounds__(NUM_WARPS * 32) numeric_warp_kernel(
+// Small rows: at most SG_A entries of A, at most SG_C columns of C and at most WARP_CAP
+// products.  One 8-lane group per row, so a warp keeps four rows in flight.  Lane e loads A's
+// entry e and B_k's bounds, then lane w the first 8 entries of every B_k (entry w of each),
+// so a row costs four dependent round trips (its bounds; A's entries and C's columns; B's
+// bounds; B's entries).  Every product's place in C's row comes from a binary search over
+// C's columns in shared memory, all searches before any sum; the sums then run over A's
+// entries in order, one fixed-order FMA per product into the group's accumulator (the
+// columns of one B_k are distinct, so the lanes never collide).  numeric_warp_kernel
+// skips these rows.
+constexpr int SG_THREADS = 256;
+constexpr int SG_A = 8;                // A entries per small row
+constexpr int SG_C = 64;               // C columns per small row
+
+__device__ __forceinline__ bool small_row(int na, int nc, int p) {
+    return na <= SG_A && nc <= SG_C && p <= WARP_CAP;
+}
+
+__global__ void __launch_bounds__(SG_THREADS, 5) numeric_group_kernel(
     int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const float* __restrict__ a_val,
     const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_idx, const float* __restrict__ b_val,
     const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx, const int32_t* __restrict__ prod,
     float* __restrict__ c_val) {
-    __shared__ int cols_all[NUM_WARPS][WARP_CAP];
-    __shared__ float acc_all[NUM_WARPS][WARP_CAP];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t row = (int64_t)blockIdx.x * NUM_WARPS + warp;
-    if (row >= m || prod[row] > WARP_CAP) return;
-    int* cols = cols_all[warp];
-    float* acc = acc_all[warp];
+    // each group's rows padded by 8 words: the four groups of a warp start 8 banks apart, so
+    // their searches and sums at equal offsets do not meet in one bank
+    __shared__ int scol[SG_THREADS / GRP][SG_C + 8];
+    __shared__ float sacc[SG_THREADS / GRP][SG_C + 8];
+    const int lane = threadIdx.x & 31;
+    const int gid = threadIdx.x / GRP;
+    const int w = lane % GRP;
+    const unsigned gmask = ((1u << GRP) - 1u) << ((lane / GRP) * GRP);
+    const int64_t row = (int64_t)blockIdx.x * (SG_THREADS / GRP) + gid;
+    if (row >= m) return;                                  // the whole group leaves
+    const int a0 = a_ptr[row], na = a_ptr[row + 1] - a0;
+    const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
+    if (!small_row(na, nc, prod[row])) return;
+    int* cols = scol[gid];
+    float* acc = sacc[gid];
+    int k = -1;
+    float av = 0.f;
+    if (w < na) {
+        k = a_idx[a0 + w];
+        av = a_val[a0 + w];
+    }
+    {                                                      // C's columns: all loads in flight at once
+        int cv[SG_C / GRP];
+#pragma unroll
+        for (int q = 0; q < SG_C / GRP; ++q) cv[q] = w + q * GRP < nc ? c_idx[c0 + w + q * GRP] : 0;
+#pragma unroll
+        for (int q = 0; q < SG_C / GRP; ++q)
+            if (w + q * GRP < nc) {
+                cols[w + q * GRP] = cv[q];
+                acc[w + q * GRP] = 0.f;
+            }
+    }
+    int bs = 0, be = 0;
+    if (k >= 0) {
+        bs = b_ptr[k];
+        be = b_ptr[k + 1];
+    }
+    int jt[SG_A];
+    float vt[SG_A];
+#pragma unroll
+    for (int t = 0; t < SG_A; ++t) {
+        const int s_t = __shfl_sync(gmask, bs, t, GRP), e_t = __shfl_sync(gmask, be, t, GRP);
+        jt[t] = -1;
+        vt[t] = 0.f;
+        if (t < na && s_t + w < e_t) {
+            jt[t] = b_idx[s_t + w];
+            vt[t] = b_val[s_t + w];
+        }
+    }
+    __syncwarp(gmask);                                     // C's columns visible to the group
+    int pos[SG_A];
+#pragma unroll
+    for (int t = 0; t < SG_A; ++t) pos[t] = jt[t] >= 0 ? lower_bound_i32(cols, nc, jt[t]) : 0;
+#pragma unroll
+    for (int t = 0; t < SG_A; ++t) {
+        if (t < na) {                                      // group-uniform
+            const float a_t = __shfl_sync(gmask, av, t, GRP);
+            const int s_t = __shfl_sync(gmask, bs, t, GRP), e_t = __shfl_sync(gmask, be, t, GRP);
+            if (jt[t] >= 0) acc[pos[t]] = fmaf(a_t, vt[t], acc[pos[t]]);
+            __syncwarp(gmask);
+            for (int f0 = s_t + GRP; f0 < e_t; f0 += GRP) {    // the rest of a longer B_k
+                const int f = f0 + w;
+                if (f < e_t) {
+                    const int p2 = lower_bound_i32(cols, nc, b_idx[f]);
+                    acc[p2] = fmaf(a_t, b_val[f], acc[p2]);
+                }
+                __syncwarp(gmask);
+            }
+        }
+    }
+    __syncwarp(gmask);
+#pragma unroll
+    for (int q = 0; q < SG_C / GRP; ++q)
+        if (w + q * GRP < nc) c_val[c0 + w + q * GRP] = acc[w + q * GRP];
+}
+
+// One row, one warp (rows of C wider than numeric_group_kernel takes, up to WARP_CAP products).
+__device__ __forceinline__ void numeric_warp_row(
+    int64_t row, int lane, int* __restrict__ cols, float* __restrict__ acc, const int32_t* __restrict__ a_ptr,
+    const int32_t* __restrict__ a_idx, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const float* __restrict__ b_val, const int32_t* __restrict__ c_ptr,
+    const int32_t* __restrict__ c_idx, float* __restrict__ c_val) {
     const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
     const int a0 = a_ptr[row], a1 = a_ptr[row + 1];
     if (nc * NGRP <= WARP_CAP) {
@@ -416,6 +511,7 @@ __global__ void __launch_bounds__(NUM_WARPS * 32) numeric_warp_kernel(
             for (int q = 1; q < NGRP; ++q) sum += acc[q * nc + t];
             c_val[c0 + t] = sum;
         }
+        __syncwarp();                               // cols / acc free for the warp's next row
         return;
     }
     // wider rows: the whole warp on one k at a time, one accumulator
@@ -434,6 +530,36 @@ __global__ void __launch_bounds__(NUM_WARPS * 32) numeric_warp_kernel(
         __syncwarp();
     }
     for (int t = lane; t < nc; t += 32) c_val[c0 + t] = acc[t];
+    __syncwarp();
+}
+
+// The rows neither numeric_group_kernel (small rows) nor numeric_big_kernel (more than
+// WARP_CAP products) takes: each warp checks 32 rows at once (lane r row base + r), then
+// runs the ones that are its, one at a time.  Grid-strided over the rows.
+__global__ void __launch_bounds__(NUM_WARPS * 32) numeric_warp_kernel(
+    int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const float* __restrict__ a_val,
+    const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_idx, const float* __restrict__ b_val,
+    const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx, const int32_t* __restrict__ prod,
+    float* __restrict__ c_val) {
+    __shared__ int cols_all[NUM_WARPS][WARP_CAP];
+    __shared__ float acc_all[NUM_WARPS][WARP_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * NUM_WARPS;
+    for (int64_t base = ((int64_t)blockIdx.x * NUM_WARPS + warp) * 32; base < m; base += nw * 32) {
+        const int64_t r = base + lane;
+        bool mine = false;
+        if (r < m) {
+            const int p = prod[r];
+            mine = p <= WARP_CAP && !small_row(a_ptr[r + 1] - a_ptr[r], c_ptr[r + 1] - c_ptr[r], p);
+        }
+        unsigned todo = __ballot_sync(FULL, mine);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            numeric_warp_row(base + b, lane, cols_all[warp], acc_all[warp], a_ptr, a_idx, a_val, b_ptr, b_idx, b_val,
+                             c_ptr, c_idx, c_val);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(BIG_THREADS) numeric_big_kernel(
@@ -655,7 +781,13 @@ extern "C" spx_status spx_spgemm_numeric(const spx_csr* A, const spx_csr* B, con
     if (A->m == 0) return SPX_OK;
     cudaStream_t st = as_stream(stream);
     const char* w = static_cast<const char*>(ws);
-    numeric_warp_kernel<<<(unsigned)((A->m + NUM_WARPS - 1) / NUM_WARPS), NUM_WARPS * 32, 0, st>>>(
+    numeric_group_kernel<<<(unsigned)((A->m + SG_THREADS / GRP - 1) / (SG_THREADS / GRP)), SG_THREADS, 0, st>>>(
+        A->m, A->indptr, A->indices, A->values, B->indptr, B->indices, B->values, C->indptr, C->indices,
+        (const int32_t*)(w + L.prod), c_values);
+    SPX_CHECK_LAUNCH("spgemm numeric small rows");
+    const int64_t wblocks = ((int64_t)A->m + 32 * NUM_WARPS - 1) / (32 * NUM_WARPS);
+    const int64_t wcap = (int64_t)num_sms() * 16;
+    numeric_warp_kernel<<<(unsigned)(wblocks < wcap ? wblocks : wcap), NUM_WARPS * 32, 0, st>>>(
         A->m, A->indptr, A->indices, A->values, B->indptr, B->indices, B->values, C->indptr, C->indices,
         (const int32_t*)(w + L.prod), c_values);
     SPX_CHECK_LAUNCH("spgemm numeric");
