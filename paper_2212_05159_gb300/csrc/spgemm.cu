@@ -24,7 +24,13 @@
 //             fit the space one wide row needs), its lanes over B_k's columns (distinct within
 //             a k, so lanes never collide); the slices are added in group order.  Wider rows:
 //             the whole warp on one k at a time.  Every sum has a fixed order.
-// Reverse (8-lane groups as well, four stored entries of the output in flight per warp):
+// Reverse.  Small rows (at most 8 entries of A and 64 columns of C for gA; at most 32 entries in
+// A^T_k and 8 in B_k for gB, when C's rows average at most 32 columns) take one 8-lane group per
+// row, four rows per warp: gA with C_i
+// staged in shared memory and lane w owning A's entry w; gB with lane w owning A^T_k's entry
+// w and every column of B_k looked up in C_i by binary searches that advance together, then
+// a fixed butterfly over the group.  Other rows (8-lane groups as well, four stored entries
+// of the output in flight per warp):
 //   gA[(i,k)] = sum_{j in B_k} V[i,j] B[k,j]: one warp per row i, C_i's columns and V's
 //             values staged in shared memory; a group per stored (i,k), its lanes over
 //             B_k's entries (binary search of j in C_i), then a fixed shuffle tree.
@@ -593,7 +599,76 @@ __device__ __forceinline__ float group_sum(float v, unsigned gmask) {
     return v;
 }
 
-// gA[(i,k)] = sum_{f in B_k} V[i, B_idx[f]] * B_val[f]   (V on C's pattern)
+// gA on small rows (at most SG_A entries of A and SG_C columns of C): one 8-lane group per row
+// i, C_i's columns and V's values staged in shared memory (padded per group as in
+// numeric_group_kernel); lane w owns A's entry w, loads the first 8 entries of its B_k at
+// once, places each column in C_i by a binary search in shared memory (all searches before
+// the sum) and adds V[i, j] B[k, j] in B_k's order.  grad_a_kernel skips these rows.
+__global__ void __launch_bounds__(SG_THREADS, 5) grad_a_group_kernel(
+    int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const float* __restrict__ b_val, const int32_t* __restrict__ c_ptr,
+    const int32_t* __restrict__ c_idx, const float* __restrict__ gc, float* __restrict__ ga) {
+    __shared__ int scol[SG_THREADS / GRP][SG_C + 8];
+    __shared__ float sv[SG_THREADS / GRP][SG_C + 8];
+    const int lane = threadIdx.x & 31;
+    const int gid = threadIdx.x / GRP;
+    const int w = lane % GRP;
+    const unsigned gmask = ((1u << GRP) - 1u) << ((lane / GRP) * GRP);
+    const int64_t row = (int64_t)blockIdx.x * (SG_THREADS / GRP) + gid;
+    if (row >= m) return;                                  // the whole group leaves
+    const int a0 = a_ptr[row], na = a_ptr[row + 1] - a0;
+    const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
+    if (na > SG_A || nc > SG_C) return;
+    int* cols = scol[gid];
+    float* v = sv[gid];
+    {
+        int cv[SG_C / GRP];
+        float vv[SG_C / GRP];
+#pragma unroll
+        for (int q = 0; q < SG_C / GRP; ++q) {
+            const bool in = w + q * GRP < nc;
+            cv[q] = in ? c_idx[c0 + w + q * GRP] : 0;
+            vv[q] = in ? gc[c0 + w + q * GRP] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < SG_C / GRP; ++q)
+            if (w + q * GRP < nc) {
+                cols[w + q * GRP] = cv[q];
+                v[w + q * GRP] = vv[q];
+            }
+    }
+    int bs = 0, be = 0;
+    if (w < na) {
+        const int k = a_idx[a0 + w];
+        bs = b_ptr[k];
+        be = b_ptr[k + 1];
+    }
+    int jt[GRP];
+    float bt[GRP];
+#pragma unroll
+    for (int q = 0; q < GRP; ++q) {
+        jt[q] = bs + q < be ? b_idx[bs + q] : -1;
+        bt[q] = bs + q < be ? b_val[bs + q] : 0.f;
+    }
+    __syncwarp(gmask);                                     // the staged row visible to the group
+    int pos[GRP];
+#pragma unroll
+    for (int q = 0; q < GRP; ++q) pos[q] = jt[q] >= 0 ? lower_bound_i32(cols, nc, jt[q]) : nc;
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < GRP; ++q)
+        if (pos[q] < nc && cols[pos[q]] == jt[q]) sum = fmaf(v[pos[q]], bt[q], sum);
+    for (int f = bs + GRP; f < be; ++f) {                  // the rest of a longer B_k
+        const int j = b_idx[f];
+        const int p = lower_bound_i32(cols, nc, j);
+        if (p < nc && cols[p] == j) sum = fmaf(v[p], b_val[f], sum);
+    }
+    if (w < na) ga[a0 + w] = sum;
+}
+
+// gA[(i,k)] = sum_{f in B_k} V[i, B_idx[f]] * B_val[f]   (V on C's pattern), the rows
+// grad_a_group_kernel does not take: each warp checks 32 rows at once and runs its own, one at
+// a time (grid-strided).
 __global__ void __launch_bounds__(NUM_WARPS * 32) grad_a_kernel(
     int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
     const int32_t* __restrict__ b_idx, const float* __restrict__ b_val, const int32_t* __restrict__ c_ptr,
@@ -603,38 +678,125 @@ __global__ void __launch_bounds__(NUM_WARPS * 32) grad_a_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane / GRP, w = lane % GRP;
     const unsigned gmask = ((1u << GRP) - 1u) << (g * GRP);
-    const int64_t row = (int64_t)blockIdx.x * NUM_WARPS + warp;
-    if (row >= m) return;
-    const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
-    const bool staged = nc <= WARP_CAP;
-    const int* cols = staged ? cols_all[warp] : c_idx + c0;
-    const float* v = staged ? v_all[warp] : gc + c0;
-    if (staged) {
-        for (int t = lane; t < nc; t += 32) {
-            cols_all[warp][t] = c_idx[c0 + t];
-            v_all[warp][t] = gc[c0 + t];
-        }
-    }
-    __syncwarp();
-    const int a0 = a_ptr[row], a1 = a_ptr[row + 1];
-    // the groups take the row's entries round-robin; every lane of a group runs the same trips
-    for (int e0 = a0; e0 < a1; e0 += NGRP) {
-        const int e = e0 + g;
-        float s = 0.f;
-        if (e < a1) {
-            const int k = a_idx[e];
-            for (int f = b_ptr[k] + w; f < b_ptr[k + 1]; f += GRP) {
-                const int j = b_idx[f];
-                const int pos = lower_bound_i32(cols, nc, j);
-                if (pos < nc && cols[pos] == j) s = fmaf(v[pos], b_val[f], s);
+    const int64_t nw = (int64_t)gridDim.x * NUM_WARPS;
+    for (int64_t base = ((int64_t)blockIdx.x * NUM_WARPS + warp) * 32; base < m; base += nw * 32) {
+        const int64_t r = base + lane;
+        const bool mine = r < m && (a_ptr[r + 1] - a_ptr[r] > SG_A || c_ptr[r + 1] - c_ptr[r] > SG_C);
+        unsigned todo = __ballot_sync(FULL, mine);
+        while (todo) {
+            const int bb = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t row = base + bb;
+            const int c0 = c_ptr[row], nc = c_ptr[row + 1] - c0;
+            const bool staged = nc <= WARP_CAP;
+            const int* cols = staged ? cols_all[warp] : c_idx + c0;
+            const float* v = staged ? v_all[warp] : gc + c0;
+            if (staged) {
+                for (int t = lane; t < nc; t += 32) {
+                    cols_all[warp][t] = c_idx[c0 + t];
+                    v_all[warp][t] = gc[c0 + t];
+                }
             }
+            __syncwarp();
+            const int a0 = a_ptr[row], a1 = a_ptr[row + 1];
+            // the groups take the row's entries round-robin; every lane of a group runs the same trips
+            for (int e0 = a0; e0 < a1; e0 += NGRP) {
+                const int e = e0 + g;
+                float s = 0.f;
+                if (e < a1) {
+                    const int k = a_idx[e];
+                    for (int f = b_ptr[k] + w; f < b_ptr[k + 1]; f += GRP) {
+                        const int j = b_idx[f];
+                        const int pos = lower_bound_i32(cols, nc, j);
+                        if (pos < nc && cols[pos] == j) s = fmaf(v[pos], b_val[f], s);
+                    }
+                }
+                s = group_sum(s, gmask);
+                if (e < a1 && w == 0) ga[e] = s;
+            }
+            __syncwarp();                                  // the staged row is free again
         }
-        s = group_sum(s, gmask);
-        if (e < a1 && w == 0) ga[e] = s;
     }
 }
 
-// gB[(k,j)] = sum_{i in A^T_k} A[i,k] * V[i,j]: a group per stored (k,j), lanes over A^T_k
+// gB on small rows (|A^T_k| <= SG_AT and |B_k| <= 8): one 8-lane group per row k of B.  In
+// round r lane w owns A^T_k's entry 8 r + w (row i of A and A[i,k]) and looks every column j
+// of B_k up in C_i at once: the binary searches of all j advance together, one level per
+// step, so a round costs the depth of one search in dependent loads rather than one search
+// per j.  The lane's terms A[i,k] V[i,j] are added per j over the rounds in order, then over
+// the group by a butterfly that leaves j's sum in lane j (a fixed order).  grad_b_kernel
+// skips these rows.
+constexpr int SG_AT = 4 * GRP;         // A^T_k entries per small row of B
+
+__global__ void __launch_bounds__(SG_THREADS, 4) grad_b_group_kernel(
+    int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
+    const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx,
+    const float* __restrict__ gc, float* __restrict__ gb) {
+    const int lane = threadIdx.x & 31;
+    const int w = lane % GRP;
+    const unsigned gmask = ((1u << GRP) - 1u) << ((lane / GRP) * GRP);
+    const int64_t k = (int64_t)blockIdx.x * (SG_THREADS / GRP) + threadIdx.x / GRP;
+    if (k >= kb) return;                                   // the whole group leaves
+    const int ia = at_ptr[k], ni = at_ptr[k + 1] - ia;
+    const int f0 = b_ptr[k], nf = b_ptr[k + 1] - f0;
+    if (ni > SG_AT || nf > GRP) return;
+    const int jm = w < nf ? b_idx[f0 + w] : -1;
+    int jq[GRP];
+    float P[GRP];
+#pragma unroll
+    for (int q = 0; q < GRP; ++q) {
+        jq[q] = __shfl_sync(gmask, jm, q, GRP);
+        P[q] = 0.f;
+    }
+    for (int r0 = 0; r0 < ni; r0 += GRP) {                 // group-uniform rounds
+        const int t = r0 + w;
+        int i = -1;
+        float aik = 0.f;
+        if (t < ni) {
+            i = at_idx[ia + t];
+            aik = a_val[a_perm[ia + t]];
+        }
+        int c0 = 0, nc = 0;
+        if (i >= 0) {
+            c0 = c_ptr[i];
+            nc = c_ptr[i + 1] - c0;
+        }
+        int lo[GRP];
+#pragma unroll
+        for (int q = 0; q < GRP; ++q) lo[q] = 0;
+        // lower bounds of all jq in c_idx[c0, c0 + nc), one level per step for all of them
+        for (int n = nc; n > 1;) {
+            const int half = n >> 1;
+#pragma unroll
+            for (int q = 0; q < GRP; ++q)
+                if (q < nf && c_idx[c0 + lo[q] + half - 1] < jq[q]) lo[q] += half;
+            n -= half;
+        }
+#pragma unroll
+        for (int q = 0; q < GRP; ++q) {
+            if (q < nf && nc > 0) {
+                int p = lo[q];
+                if (c_idx[c0 + p] < jq[q]) ++p;
+                if (p < nc && c_idx[c0 + p] == jq[q]) P[q] = fmaf(aik, gc[c0 + p], P[q]);
+            }
+        }
+    }
+    for (int h = GRP / 2, cnt = GRP / 2; h >= 1; h >>= 1, cnt >>= 1) {
+        const bool upper = (w & h) != 0;
+#pragma unroll
+        for (int q = 0; q < cnt; ++q) {
+            const float send = upper ? P[q] : P[q + cnt];
+            const float keep = upper ? P[q + cnt] : P[q];
+            P[q] = keep + __shfl_xor_sync(gmask, send, h, GRP);
+        }
+    }
+    if (w < nf) gb[f0 + w] = P[0];
+}
+
+// gB[(k,j)] = sum_{i in A^T_k} A[i,k] * V[i,j]: a group per stored (k,j), its lanes over
+// A^T_k (binary search of j in C_i), one warp per row k of B.  When grad_b_group_kernel runs
+// first (skip_small), its rows are left alone.
 __global__ void __launch_bounds__(256) grad_b_kernel(
     int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
     const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
@@ -662,6 +824,47 @@ __global__ void __launch_bounds__(256) grad_b_kernel(
         }
         s = group_sum(s, gmask);
         if (f < f1 && w == 0) gb[f] = s;
+    }
+}
+
+// The same per row, for the rows grad_b_group_kernel does not take: each warp checks 32 rows
+// of B at once and runs its own one at a time (grid-strided).
+__global__ void __launch_bounds__(256) grad_b_rest_kernel(
+    int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
+    const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx,
+    const float* __restrict__ gc, float* __restrict__ gb) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane / GRP, w = lane % GRP;
+    const unsigned gmask = ((1u << GRP) - 1u) << (g * GRP);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < kb; base += nw * 32) {
+        const int64_t r = base + lane;
+        const bool mine = r < kb && (at_ptr[r + 1] - at_ptr[r] > SG_AT || b_ptr[r + 1] - b_ptr[r] > GRP);
+        unsigned todo = __ballot_sync(FULL, mine);
+        while (todo) {
+            const int bb = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t k = base + bb;
+            const int ia = at_ptr[k], ib = at_ptr[k + 1];
+            const int f1 = b_ptr[k + 1];
+            for (int fs = b_ptr[k]; fs < f1; fs += NGRP) {
+                const int f = fs + g;
+                float s = 0.f;
+                if (f < f1) {
+                    const int j = b_idx[f];
+                    for (int t = ia + w; t < ib; t += GRP) {
+                        const int i = at_idx[t];
+                        const float aik = a_val[a_perm[t]];
+                        const int c0 = c_ptr[i], nc = c_ptr[i + 1] - c0;
+                        const int pos = lower_bound_i32(c_idx + c0, nc, j);
+                        if (pos < nc && c_idx[c0 + pos] == j) s = fmaf(aik, gc[c0 + pos], s);
+                    }
+                }
+                s = group_sum(s, gmask);
+                if (f < f1 && w == 0) gb[f] = s;
+            }
+        }
     }
 }
 
@@ -808,17 +1011,38 @@ extern "C" spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, co
     cudaStream_t st = as_stream(stream);
     if (ga && A->m > 0) {
         if (B->nnz > 0 && !B->values) return set_error(SPX_INVALID_ARG, "spx_spgemm_backward: B values needed");
-        grad_a_kernel<<<(unsigned)((A->m + NUM_WARPS - 1) / NUM_WARPS), NUM_WARPS * 32, 0, st>>>(
+        grad_a_group_kernel<<<(unsigned)((A->m + SG_THREADS / GRP - 1) / (SG_THREADS / GRP)), SG_THREADS, 0, st>>>(
+            A->m, A->indptr, A->indices, B->indptr, B->indices, B->values, C->indptr, C->indices, gc, ga);
+        SPX_CHECK_LAUNCH("spgemm grad_a small rows");
+        const int64_t wb = ((int64_t)A->m + 32 * NUM_WARPS - 1) / (32 * NUM_WARPS);
+        const int64_t cap = (int64_t)num_sms() * 16;
+        grad_a_kernel<<<(unsigned)(wb < cap ? wb : cap), NUM_WARPS * 32, 0, st>>>(
             A->m, A->indptr, A->indices, B->indptr, B->indices, B->values, C->indptr, C->indices, gc, ga);
         SPX_CHECK_LAUNCH("spgemm grad_a");
     }
     if (gb && B->m > 0) {
         if (!at_indptr || (A->nnz > 0 && (!at_indices || !a_perm || !A->values)))
             return set_error(SPX_INVALID_ARG, "spx_spgemm_backward: grad B needs A's transpose and values");
-        int64_t threads = (int64_t)B->m * 32;
-        grad_b_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-            B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices, C->indptr, C->indices, gc, gb);
-        SPX_CHECK_LAUNCH("spgemm grad_b");
+        // The group kernel's searches run one lane per row of C: measured faster where C's rows
+        // are short (3D Poisson 64^3 squared, 24 columns: 141 -> 120 us) and slower where they
+        // are long (random 8 per row squared, 64 columns: 297 -> 388 us, the warp kernel's four
+        // groups searching one row of C together share its sectors).  Chosen by C's mean row.
+        if (C->nnz <= 32 * (int64_t)C->m) {
+            grad_b_group_kernel<<<(unsigned)((B->m + SG_THREADS / GRP - 1) / (SG_THREADS / GRP)), SG_THREADS, 0,
+                                  st>>>(B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices,
+                                        C->indptr, C->indices, gc, gb);
+            SPX_CHECK_LAUNCH("spgemm grad_b small rows");
+            const int64_t wb = ((int64_t)B->m + 32 * 8 - 1) / (32 * 8);
+            const int64_t cap = (int64_t)num_sms() * 8;
+            grad_b_rest_kernel<<<(unsigned)(wb < cap ? wb : cap), 256, 0, st>>>(
+                B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices, C->indptr, C->indices, gc, gb);
+            SPX_CHECK_LAUNCH("spgemm grad_b");
+        } else {
+            const int64_t threads = (int64_t)B->m * 32;
+            grad_b_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+                B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices, C->indptr, C->indices, gc, gb);
+            SPX_CHECK_LAUNCH("spgemm grad_b");
+        }
     }
     return SPX_OK;
 }
