@@ -4,7 +4,8 @@
 //
 // Forward, expand / sort / compress per row (the ESC scheme the paper follows):
 //   analyse   products P_i = sum_{k in A_i} |B_k|, their prefix sums, and the list of
-//             "big" rows (P_i > WARP_CAP);
+//             "big" rows (P_i > WARP_CAP, appended by an atomic counter: their order in
+//             the list varies, no result depends on it);
 //   symbolic  per row: expand the P_i product columns, sort, keep the unique ones; the
 //             sorted unique columns go to a products-sized scratch at offset Pptr[i] and
 //             their count to row_nnz[i]; C_indptr = scan(row_nnz).  One warp per row:
@@ -59,7 +60,7 @@ constexpr int BITMAP_WORDS = 8192;     // 32 KB shared bitmap: 262144 columns pe
 inline size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct GemmLayout {
-    size_t prod, pptr, row_nnz, flags, big_pos, big_rows, scan64, scan32, total;
+    size_t prod, pptr, row_nnz, big_pos, big_rows, scan64, scan32, total;
 };
 
 GemmLayout gemm_layout(int32_t m) {
@@ -68,7 +69,6 @@ GemmLayout gemm_layout(int32_t m) {
     L.prod = o;     o = al(o + 4 * (size_t)m);
     L.pptr = o;     o = al(o + 8 * ((size_t)m + 1));
     L.row_nnz = o;  o = al(o + 4 * (size_t)m);
-    L.flags = o;    o = al(o + 4 * (size_t)m);
     L.big_pos = o;  o = al(o + 4 * ((size_t)m + 1));
     L.big_rows = o; o = al(o + 4 * ((size_t)m + 1));
     L.scan64 = o;   o = al(o + scan_workspace_bytes<int64_t>(m));
@@ -78,9 +78,12 @@ GemmLayout gemm_layout(int32_t m) {
 }
 
 // ------------------------------------------------------------------ analyse
+// Products per row, and the rows with more than WARP_CAP of them appended to big_rows (their
+// order in the list varies from run to run; each is computed whole by one block, so no result
+// depends on it).  *n_big must be zero before the launch.
 __global__ void products_kernel(int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx,
                                 const int32_t* __restrict__ b_ptr, int32_t* __restrict__ prod,
-                                int32_t* __restrict__ big) {
+                                int32_t* __restrict__ big_rows, int32_t* __restrict__ n_big) {
     // 8 lanes per row
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t row = t >> 3;
@@ -97,14 +100,8 @@ __global__ void products_kernel(int32_t m, const int32_t* __restrict__ a_ptr, co
     if (row < m && sub == 0) {
         const int32_t p = s > INT_MAX ? INT_MAX : (int32_t)s;
         prod[row] = p;
-        big[row] = p > WARP_CAP ? 1 : 0;
+        if (p > WARP_CAP) big_rows[atomicAdd(n_big, 1)] = (int32_t)row;
     }
-}
-
-__global__ void compact_kernel(int32_t m, const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
-                               int32_t* __restrict__ out) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < m && flags[i]) out[pos[i]] = (int32_t)i;
 }
 
 // ------------------------------------------------------------------ symbolic (warp rows)
@@ -898,21 +895,16 @@ extern "C" spx_status spx_spgemm_analyse(const spx_csr* A, const spx_csr* B, int
     char* w = static_cast<char*>(ws);
     int32_t* prod = (int32_t*)(w + L.prod);
     int64_t* pptr = (int64_t*)(w + L.pptr);
-    int32_t* flags = (int32_t*)(w + L.flags);
-    int32_t* bpos = (int32_t*)(w + L.big_pos);
+    int32_t* n_big = (int32_t*)(w + L.big_pos) + A->m;     // the count the big-row kernels read
     int32_t* brows = (int32_t*)(w + L.big_rows);
+    SPX_CUDA(cudaMemsetAsync(n_big, 0, sizeof(int32_t), st), "spx_spgemm_analyse clear");
     if (A->m > 0) {
         int64_t threads = (int64_t)A->m * 8;
         products_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A->m, A->indptr, A->indices, B->indptr,
-                                                                           prod, flags);
+                                                                           prod, brows, n_big);
         SPX_CHECK_LAUNCH("spgemm products");
     }
     SPX_TRY((scan_counts<int32_t, int64_t>(prod, pptr, A->m, (int64_t*)(w + L.scan64), st)));
-    SPX_TRY((scan_counts<int32_t, int32_t>(flags, bpos, A->m, (int32_t*)(w + L.scan32), st)));
-    if (A->m > 0) {
-        compact_kernel<<<(unsigned)((A->m + 255) / 256), 256, 0, st>>>(A->m, flags, bpos, brows);
-        SPX_CHECK_LAUNCH("spgemm compact");
-    }
     if (products_host) {
         SPX_CUDA(cudaMemcpyAsync(products_host, pptr + A->m, sizeof(int64_t), cudaMemcpyDeviceToHost, st),
                  "spx_spgemm_analyse copy");
