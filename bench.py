@@ -243,18 +243,22 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- traffic
 def ncu_traffic(kernel_tag, src_file):
-    """dram bytes per launch from a committed ncu summary, if it matches the source."""
+    """dram bytes per launch from a committed ncu summary, if it matches the kernel's source and
+    the shared device header (common.cuh: the hinted loads every kernel uses)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     m_h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
-    if not m_b or not m_h:
+    m_c = re.search(r"header_sha256:\s*([0-9a-f]+)", txt)
+    if not m_b or not m_h or not m_c:
         return None
-    with open(src_file, "rb") as fh:
-        if hashlib.sha256(fh.read()).hexdigest() != m_h.group(1):
-            return None                      # kernel changed since the counters were taken
+    header = os.path.join(os.path.dirname(src_file), "common.cuh")
+    for f, want in ((src_file, m_h.group(1)), (header, m_c.group(1))):
+        with open(f, "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != want:
+                return None                  # kernel changed since the counters were taken
     return float(m_b.group(1))
 
 
