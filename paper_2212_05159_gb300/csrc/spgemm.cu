@@ -25,13 +25,13 @@
 //             fit the space one wide row needs), its lanes over B_k's columns (distinct within
 //             a k, so lanes never collide); the slices are added in group order.  Wider rows:
 //             the whole warp on one k at a time.  Every sum has a fixed order.
-// Reverse.  Small rows (at most 8 entries of A and 64 columns of C for gA; at most 32 entries in
-// A^T_k and 8 in B_k for gB, when C's rows average at most 32 columns) take one 8-lane group per
-// row, four rows per warp: gA with C_i
-// staged in shared memory and lane w owning A's entry w; gB with lane w owning A^T_k's entry
-// w and every column of B_k looked up in C_i by binary searches that advance together, then
-// a fixed butterfly over the group.  Other rows (8-lane groups as well, four stored entries
-// of the output in flight per warp):
+// Reverse.  Small rows take one 8-lane group per row, four rows per warp: for gA rows of at
+// most 8 entries of A and 64 columns of C, C_i staged in shared memory and lane w owning A's
+// entry w; for gB (when C's rows average at most 32 columns) rows of B with at most 32 entries
+// in A^T_k and 8 in B_k, lane w owning A^T_k's entries w, w + 8, ... and every column of B_k
+// looked up in C_i by binary searches that advance together, then a fixed butterfly over the
+// group.  Other rows (8-lane groups as well, four stored entries of the output in flight per
+// warp):
 //   gA[(i,k)] = sum_{j in B_k} V[i,j] B[k,j]: one warp per row i, C_i's columns and V's
 //             values staged in shared memory; a group per stored (i,k), its lanes over
 //             B_k's entries (binary search of j in C_i), then a fixed shuffle tree.
