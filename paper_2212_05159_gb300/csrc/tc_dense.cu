@@ -435,7 +435,8 @@ __global__ void __launch_bounds__(TC_THREADS) dense_tc_bwd_data_kernel(int64_t n
 // Two persistent CTAs per SM (one's loads in flight while the other converts) walk the row
 // tiles with a stride of the grid, each with two staging buffers in turn: while the tensor
 // cores run tile t's 8 MMAs (K = 16 rows each, the FP32 accumulator stays in tensor memory
-// across all of the CTA's tiles), the threads stage tile t + 1.  A buffer is restaged only
+// across all of the CTA's tiles), the threads stage tile t + 1 (for N <= 64 with its loads
+// already in flight: PIPE, below).  A buffer is restaged only
 // after the mbarrier of the commit that read it has completed (bounded wait).  db is summed
 // in FP32 by the threads from the values they load (each thread owns one 4-column piece of
 // G).  Each CTA writes its partial (K + 1) x N block (dW rows, then db) to the workspace; a
@@ -517,6 +518,7 @@ __device__ __forceinline__ void tw_stage(unsigned char* sA, unsigned char* sB, c
     }
 }
 
+template <bool PIPE>
 __global__ void __launch_bounds__(TW_THREADS, TW_CTAS_PER_SM) dense_tc_bwd_weight_kernel(int64_t n, const float* __restrict__ X1,
                                                                             int K1, const float* __restrict__ X2,
                                                                             int K2, const float* __restrict__ G, int N,
@@ -561,6 +563,20 @@ __global__ void __launch_bounds__(TW_THREADS, TW_CTAS_PER_SM) dense_tc_bwd_weigh
     float4 dbs = make_float4(0.f, 0.f, 0.f, 0.f);
     bool failed = false;
     int it = 0;
+    // When a tile is one round of items a thread (N <= 64), the stage is software-pipelined:
+    // each item's registers take the next tile's load as soon as the item is stored, so the
+    // loads stay in flight through the barrier and the MMA issue (the next tile's loads need
+    // registers only; its buffer is written after the wait below).
+    const int nq1 = K1 >> 2, nq2 = K2 >> 2, nqb = N >> 2;
+    const int totA = (TC_M / 8) * (nq1 + nq2), totB = (TC_M / 8) * nqb;
+    const int ta0 = threadIdx.x, ta1 = threadIdx.x + TW_THREADS, tb = threadIdx.x;
+    float4 va0[8], va1[8], vb[8];
+    if (PIPE && (int64_t)blockIdx.x < tiles) {
+        const int64_t r0 = (int64_t)blockIdx.x * TC_M;
+        if (ta0 < totA) tw_item_load(va0, ta0, X1, nq1, X2, nq2, r0, n);
+        if (ta1 < totA) tw_item_load(va1, ta1, X1, nq1, X2, nq2, r0, n);
+        if (tb < totB) tw_item_load(vb, tb, G, nqb, nullptr, 0, r0, n);
+    }
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
         const int b = it & 1;
         unsigned char* sA = smem + b * bufb;
@@ -574,7 +590,31 @@ __global__ void __launch_bounds__(TW_THREADS, TW_CTAS_PER_SM) dense_tc_bwd_weigh
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
         const int64_t row0 = tile * TC_M;
-        tw_stage(sA, sB, X1, K1 >> 2, X2, K2 >> 2, G, N >> 2, row0, n, dbs);
+        if constexpr (PIPE) {
+            const int64_t nrow0 = (tile + gridDim.x) * TC_M;
+            const bool more = tile + gridDim.x < tiles;
+            if (ta0 < totA) {
+                tw_item_store(sA, va0, ta0, nq1 + nq2);
+                if (more) tw_item_load(va0, ta0, X1, nq1, X2, nq2, nrow0, n);
+            }
+            if (ta1 < totA) {
+                tw_item_store(sA, va1, ta1, nq1 + nq2);
+                if (more) tw_item_load(va1, ta1, X1, nq1, X2, nq2, nrow0, n);
+            }
+            if (tb < totB) {
+                tw_item_store(sB, vb, tb, nqb);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    dbs.x += vb[r].x;
+                    dbs.y += vb[r].y;
+                    dbs.z += vb[r].z;
+                    dbs.w += vb[r].w;
+                }
+                if (more) tw_item_load(vb, tb, G, nqb, nullptr, 0, nrow0, n);
+            }
+        } else {
+            tw_stage(sA, sB, X1, nq1, X2, nq2, G, nqb, row0, n, dbs);
+        }
         fence_proxy_async();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -800,12 +840,20 @@ extern "C" spx_status spx_dense_backward_weight_tc(int64_t n, const float* X1, i
     }
     const int64_t tiles = (n + TC_M - 1) / TC_M;
     const int parts = (int)(tiles < TW_CTAS_PER_SM * num_sms() ? tiles : TW_CTAS_PER_SM * num_sms());
-    static std::atomic<unsigned long long> attr_done{0};
-    SPX_TRY(ensure_smem_attr(dense_tc_bwd_weight_kernel, 2 * tw_buf_bytes(TC_NMAX), attr_done,
+    static std::atomic<unsigned long long> attr_done{0}, attr_done_pipe{0};
+    SPX_TRY(ensure_smem_attr(dense_tc_bwd_weight_kernel<false>, 2 * tw_buf_bytes(TC_NMAX), attr_done,
+                             "spx_dense_backward_weight_tc attribute"));
+    SPX_TRY(ensure_smem_attr(dense_tc_bwd_weight_kernel<true>, 2 * tw_buf_bytes(TC_NMAX), attr_done_pipe,
                              "spx_dense_backward_weight_tc attribute"));
     float* partial = static_cast<float*>(ws);
-    dense_tc_bwd_weight_kernel<<<(unsigned)parts, TW_THREADS, 2 * tw_buf_bytes(N), st>>>(n, X1, K1, X2, K2, G, N,
-                                                                                       partial, device_error_word());
+    // a tile of one round of items a thread (K <= 128 always; N <= 64): the pipelined stage
+    const bool pipe = (TC_M / 8) * (N / 4) <= TW_THREADS && (TC_M / 8) * (K / 4) <= 2 * TW_THREADS;
+    if (pipe)
+        dense_tc_bwd_weight_kernel<true><<<(unsigned)parts, TW_THREADS, 2 * tw_buf_bytes(N), st>>>(
+            n, X1, K1, X2, K2, G, N, partial, device_error_word());
+    else
+        dense_tc_bwd_weight_kernel<false><<<(unsigned)parts, TW_THREADS, 2 * tw_buf_bytes(N), st>>>(
+            n, X1, K1, X2, K2, G, N, partial, device_error_word());
     SPX_CHECK_LAUNCH("spx_dense_backward_weight_tc");
     const int outs = (K + 1) * N;
     tc_wgrad_reduce_kernel<<<(unsigned)((outs + 31) / 32), 256, 0, st>>>(parts, K, N, partial, dW, db);
