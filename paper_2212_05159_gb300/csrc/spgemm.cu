@@ -25,12 +25,9 @@
 //             fit the space one wide row needs), its lanes over B_k's columns (distinct within
 //             a k, so lanes never collide); the slices are added in group order.  Wider rows:
 //             the whole warp on one k at a time.  Every sum has a fixed order.
-// Reverse.  Small rows take one 8-lane group per row, four rows per warp: for gA rows of at
-// most 8 entries of A and 64 columns of C, C_i staged in shared memory and lane w owning A's
-// entry w; for gB (when C's rows average at most 32 columns) rows of B with at most 32 entries
-// in A^T_k and 8 in B_k, lane w owning A^T_k's entries w, w + 8, ... and every column of B_k
-// looked up in C_i by binary searches that advance together, then a fixed butterfly over the
-// group.  Other rows (8-lane groups as well, four stored entries of the output in flight per
+// Reverse.  gA on small rows (at most 8 entries of A and 64 columns of C): one 8-lane group per
+// row, four rows per warp, C_i staged in shared memory and lane w owning A's entry w.  Other
+// rows of gA, and gB (8-lane groups as well, four stored entries of the output in flight per
 // warp):
 //   gA[(i,k)] = sum_{j in B_k} V[i,j] B[k,j]: one warp per row i, C_i's columns and V's
 //             values staged in shared memory; a group per stored (i,k), its lanes over
@@ -38,7 +35,9 @@
 //   gB[(k,j)] = sum_{i in A^T_k} A[i,k] V[i,j]: the "SpGEMM on the columns of A" of
 //             Section 3.1.2 -- one warp per row k of B over the transposed pattern of A; a
 //             group per stored (k,j), its lanes over A^T_k (binary search of j in C_i),
-//             then a fixed shuffle tree.
+//             then a fixed shuffle tree; when A^T_k and B_k have at most 8 entries, a lane's
+//             entry of A^T_k and C_i's bounds are loaded once and both rounds of B_k search
+//             together.
 // All integer work is exact; every floating-point sum has a fixed order.
 #include <limits.h>
 
@@ -716,97 +715,58 @@ __global__ void __launch_bounds__(NUM_WARPS * 32) grad_a_kernel(
     }
 }
 
-// gB on small rows (|A^T_k| <= SG_AT and |B_k| <= 8): one 8-lane group per row k of B.  In
-// round r lane w owns A^T_k's entry 8 r + w (row i of A and A[i,k]) and looks every column j
-// of B_k up in C_i at once: the binary searches of all j advance together, one level per
-// step, so a round costs the depth of one search in dependent loads rather than one search
-// per j.  The lane's terms A[i,k] V[i,j] are added per j over the rounds in order, then over
-// the group by a butterfly that leaves j's sum in lane j (a fixed order).  grad_b_kernel
-// skips these rows.
-constexpr int SG_AT = 4 * GRP;         // A^T_k entries per small row of B
-
-__global__ void __launch_bounds__(SG_THREADS, 4) grad_b_group_kernel(
-    int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
-    const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
-    const int32_t* __restrict__ b_idx, const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx,
-    const float* __restrict__ gc, float* __restrict__ gb) {
-    const int lane = threadIdx.x & 31;
-    const int w = lane % GRP;
-    const unsigned gmask = ((1u << GRP) - 1u) << ((lane / GRP) * GRP);
-    const int64_t k = (int64_t)blockIdx.x * (SG_THREADS / GRP) + threadIdx.x / GRP;
-    if (k >= kb) return;                                   // the whole group leaves
-    const int ia = at_ptr[k], ni = at_ptr[k + 1] - ia;
-    const int f0 = b_ptr[k], nf = b_ptr[k + 1] - f0;
-    if (ni > SG_AT || nf > GRP) return;
-    const int jm = w < nf ? b_idx[f0 + w] : -1;
-    int jq[GRP];
-    float P[GRP];
-#pragma unroll
-    for (int q = 0; q < GRP; ++q) {
-        jq[q] = __shfl_sync(gmask, jm, q, GRP);
-        P[q] = 0.f;
-    }
-    for (int r0 = 0; r0 < ni; r0 += GRP) {                 // group-uniform rounds
-        const int t = r0 + w;
-        int i = -1;
-        float aik = 0.f;
-        if (t < ni) {
-            i = at_idx[ia + t];
-            aik = a_val[a_perm[ia + t]];
-        }
+// gB[(k,j)] = sum_{i in A^T_k} A[i,k] * V[i,j] for one row k of B, one warp: a group per stored
+// (k,j), its lanes over A^T_k (binary search of j in C_i), then a fixed shuffle tree.  When
+// A^T_k fits one entry per lane and B_k two rounds of the four groups (both at most 8), each
+// lane loads its entry of A^T_k, A's value and C_i's bounds once and the two rounds' searches
+// advance together; the sums are the same (one term per lane, the same tree).
+__device__ __forceinline__ void grad_b_row(int64_t k, int g, int w, unsigned gmask, const int32_t* __restrict__ at_ptr,
+                                           const int32_t* __restrict__ at_idx, const int32_t* __restrict__ a_perm,
+                                           const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
+                                           const int32_t* __restrict__ b_idx, const int32_t* __restrict__ c_ptr,
+                                           const int32_t* __restrict__ c_idx, const float* __restrict__ gc,
+                                           float* __restrict__ gb) {
+    const int ia = at_ptr[k], ib = at_ptr[k + 1];
+    const int fb = b_ptr[k], f1 = b_ptr[k + 1];
+    if (ib - ia <= GRP && f1 - fb <= 2 * NGRP) {
+        const int t = ia + w;
         int c0 = 0, nc = 0;
-        if (i >= 0) {
+        float aik = 0.f;
+        if (t < ib) {
+            const int i = at_idx[t];
+            aik = a_val[a_perm[t]];
             c0 = c_ptr[i];
             nc = c_ptr[i + 1] - c0;
         }
-        int lo[GRP];
-#pragma unroll
-        for (int q = 0; q < GRP; ++q) lo[q] = 0;
-        // lower bounds of all jq in c_idx[c0, c0 + nc), one level per step for all of them
-        for (int n = nc; n > 1;) {
+        const int fa = fb + g, fz = fb + g + NGRP;
+        const int ja = fa < f1 ? b_idx[fa] : -1, jz = fz < f1 ? b_idx[fz] : -1;
+        int la = 0, lz = 0;
+        for (int n = nc; n > 1;) {                         // both lower bounds, one level per step
             const int half = n >> 1;
-#pragma unroll
-            for (int q = 0; q < GRP; ++q)
-                if (q < nf && c_idx[c0 + lo[q] + half - 1] < jq[q]) lo[q] += half;
+            if (ja >= 0 && c_idx[c0 + la + half - 1] < ja) la += half;
+            if (jz >= 0 && c_idx[c0 + lz + half - 1] < jz) lz += half;
             n -= half;
         }
-#pragma unroll
-        for (int q = 0; q < GRP; ++q) {
-            if (q < nf && nc > 0) {
-                int p = lo[q];
-                if (c_idx[c0 + p] < jq[q]) ++p;
-                if (p < nc && c_idx[c0 + p] == jq[q]) P[q] = fmaf(aik, gc[c0 + p], P[q]);
+        float sa = 0.f, sz = 0.f;
+        if (nc > 0) {
+            if (ja >= 0) {
+                const int p = la + (c_idx[c0 + la] < ja ? 1 : 0);
+                if (p < nc && c_idx[c0 + p] == ja) sa = fmaf(aik, gc[c0 + p], 0.f);
+            }
+            if (jz >= 0) {
+                const int p = lz + (c_idx[c0 + lz] < jz ? 1 : 0);
+                if (p < nc && c_idx[c0 + p] == jz) sz = fmaf(aik, gc[c0 + p], 0.f);
             }
         }
-    }
-    for (int h = GRP / 2, cnt = GRP / 2; h >= 1; h >>= 1, cnt >>= 1) {
-        const bool upper = (w & h) != 0;
-#pragma unroll
-        for (int q = 0; q < cnt; ++q) {
-            const float send = upper ? P[q] : P[q + cnt];
-            const float keep = upper ? P[q + cnt] : P[q];
-            P[q] = keep + __shfl_xor_sync(gmask, send, h, GRP);
+        sa = group_sum(sa, gmask);
+        sz = group_sum(sz, gmask);
+        if (w == 0) {
+            if (fa < f1) gb[fa] = sa;
+            if (fz < f1) gb[fz] = sz;
         }
+        return;
     }
-    if (w < nf) gb[f0 + w] = P[0];
-}
-
-// gB[(k,j)] = sum_{i in A^T_k} A[i,k] * V[i,j]: a group per stored (k,j), its lanes over
-// A^T_k (binary search of j in C_i), one warp per row k of B.  When grad_b_group_kernel runs
-// first (skip_small), its rows are left alone.
-__global__ void __launch_bounds__(256) grad_b_kernel(
-    int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
-    const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
-    const int32_t* __restrict__ b_idx, const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx,
-    const float* __restrict__ gc, float* __restrict__ gb) {
-    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int g = lane / GRP, w = lane % GRP;
-    const unsigned gmask = ((1u << GRP) - 1u) << (g * GRP);
-    if (k >= kb) return;
-    const int ia = at_ptr[k], ib = at_ptr[k + 1];
-    const int f1 = b_ptr[k + 1];
-    for (int f0 = b_ptr[k]; f0 < f1; f0 += NGRP) {
+    for (int f0 = fb; f0 < f1; f0 += NGRP) {
         const int f = f0 + g;
         float s = 0.f;
         if (f < f1) {
@@ -824,45 +784,18 @@ __global__ void __launch_bounds__(256) grad_b_kernel(
     }
 }
 
-// The same per row, for the rows grad_b_group_kernel does not take: each warp checks 32 rows
-// of B at once and runs its own one at a time (grid-strided).
-__global__ void __launch_bounds__(256) grad_b_rest_kernel(
+// gB on every row of B, one warp per row.
+__global__ void __launch_bounds__(256) grad_b_kernel(
     int32_t kb, const int32_t* __restrict__ at_ptr, const int32_t* __restrict__ at_idx,
     const int32_t* __restrict__ a_perm, const float* __restrict__ a_val, const int32_t* __restrict__ b_ptr,
     const int32_t* __restrict__ b_idx, const int32_t* __restrict__ c_ptr, const int32_t* __restrict__ c_idx,
     const float* __restrict__ gc, float* __restrict__ gb) {
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const int g = lane / GRP, w = lane % GRP;
     const unsigned gmask = ((1u << GRP) - 1u) << (g * GRP);
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < kb; base += nw * 32) {
-        const int64_t r = base + lane;
-        const bool mine = r < kb && (at_ptr[r + 1] - at_ptr[r] > SG_AT || b_ptr[r + 1] - b_ptr[r] > GRP);
-        unsigned todo = __ballot_sync(FULL, mine);
-        while (todo) {
-            const int bb = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t k = base + bb;
-            const int ia = at_ptr[k], ib = at_ptr[k + 1];
-            const int f1 = b_ptr[k + 1];
-            for (int fs = b_ptr[k]; fs < f1; fs += NGRP) {
-                const int f = fs + g;
-                float s = 0.f;
-                if (f < f1) {
-                    const int j = b_idx[f];
-                    for (int t = ia + w; t < ib; t += GRP) {
-                        const int i = at_idx[t];
-                        const float aik = a_val[a_perm[t]];
-                        const int c0 = c_ptr[i], nc = c_ptr[i + 1] - c0;
-                        const int pos = lower_bound_i32(c_idx + c0, nc, j);
-                        if (pos < nc && c_idx[c0 + pos] == j) s = fmaf(aik, gc[c0 + pos], s);
-                    }
-                }
-                s = group_sum(s, gmask);
-                if (f < f1 && w == 0) gb[f] = s;
-            }
-        }
-    }
+    if (k >= kb) return;
+    grad_b_row(k, g, w, gmask, at_ptr, at_idx, a_perm, a_val, b_ptr, b_idx, c_ptr, c_idx, gc, gb);
 }
 
 int big_grid() { return num_sms() * 2; }
@@ -1015,26 +948,10 @@ extern "C" spx_status spx_spgemm_backward(const spx_csr* A, const spx_csr* B, co
     if (gb && B->m > 0) {
         if (!at_indptr || (A->nnz > 0 && (!at_indices || !a_perm || !A->values)))
             return set_error(SPX_INVALID_ARG, "spx_spgemm_backward: grad B needs A's transpose and values");
-        // The group kernel's searches run one lane per row of C: measured faster where C's rows
-        // are short (3D Poisson 64^3 squared, 24 columns: 141 -> 120 us) and slower where they
-        // are long (random 8 per row squared, 64 columns: 297 -> 388 us, the warp kernel's four
-        // groups searching one row of C together share its sectors).  Chosen by C's mean row.
-        if (C->nnz <= 32 * (int64_t)C->m) {
-            grad_b_group_kernel<<<(unsigned)((B->m + SG_THREADS / GRP - 1) / (SG_THREADS / GRP)), SG_THREADS, 0,
-                                  st>>>(B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices,
-                                        C->indptr, C->indices, gc, gb);
-            SPX_CHECK_LAUNCH("spgemm grad_b small rows");
-            const int64_t wb = ((int64_t)B->m + 32 * 8 - 1) / (32 * 8);
-            const int64_t cap = (int64_t)num_sms() * 8;
-            grad_b_rest_kernel<<<(unsigned)(wb < cap ? wb : cap), 256, 0, st>>>(
-                B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices, C->indptr, C->indices, gc, gb);
-            SPX_CHECK_LAUNCH("spgemm grad_b");
-        } else {
-            const int64_t threads = (int64_t)B->m * 32;
-            grad_b_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-                B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices, C->indptr, C->indices, gc, gb);
-            SPX_CHECK_LAUNCH("spgemm grad_b");
-        }
+        const int64_t threads = (int64_t)B->m * 32;
+        grad_b_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+            B->m, at_indptr, at_indices, a_perm, A->values, B->indptr, B->indices, C->indptr, C->indices, gc, gb);
+        SPX_CHECK_LAUNCH("spgemm grad_b");
     }
     return SPX_OK;
 }

@@ -1,9 +1,8 @@
 """SpGEMM (Section 3.1.2, Table 1) on matrices built to sit on both sides of the limits where
-the library switches kernels: rows of A with 8 / 9 entries and rows of C with 64 / 65 columns
-(the small-row kernels of the numeric phase and of gA), columns of A with 32 / 33 entries and
-rows of B with 8 / 9 entries (the small-row kernel of gB), and C's mean row length on both
-sides of 32 columns (which gB kernel runs).  Pattern bit-exact; values and both gradients
-within 1e-5 normalised of the FP64 oracle."""
+the library switches paths: rows of A with 8 / 9 entries and rows of C with 64 / 65 columns
+(the small-row kernels of the numeric phase and of gA), columns of A with 8 / 9 and more
+entries and rows of B with 8 / 9 entries (gB's one-round path), with C's rows short and long.
+Pattern bit-exact; values and both gradients within 1e-5 normalised of the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -61,8 +60,8 @@ def wide_rows_pair():
 
 def deep_columns_pair():
     """Rows of A with one or two entries (C's rows stay short: mean below 32 columns) whose
-    columns are chosen so that some columns of A hold exactly 8, 32, 33 and 40 entries; rows of
-    B with 8 or 9 overlapping columns."""
+    columns are chosen so that some columns of A hold exactly 8, 32, 33 and 40 entries (and
+    the others about 9); rows of B with 8 or 9 overlapping columns."""
     rng = np.random.default_rng(7)
     nb, ncol_b = 600, 500
     m = 4000
