@@ -161,6 +161,24 @@ class CSR:
             return plan.C.with_values(autograd.SpGEMM.apply(self.values, other.values, plan))
         return autograd.spmm(self, other)
 
+    def __add__(self, other):
+        """A + B for a CSR B of the same shape (Section 3.1.4): the union pattern, differentiable
+        in both value arrays (dA = V masked to A, dB = V masked to B).  The pattern is analysed on
+        every call -- keep an ops.SpAddPlan to reuse it."""
+        return self._add(other, 1.0)
+
+    def __sub__(self, other):
+        """A - B, as A + (-1) B."""
+        return self._add(other, -1.0)
+
+    def _add(self, other, beta: float):
+        if not isinstance(other, CSR):
+            return NotImplemented
+        from . import autograd
+        from .ops import SpAddPlan
+        plan = SpAddPlan(self, other)
+        return plan.C.with_values(autograd.SpAdd.apply(self.values, other.values, plan, 1.0, beta))
+
     @property
     def T(self) -> "CSR":
         """A^T: the cached transposed pattern with A's values gathered through its

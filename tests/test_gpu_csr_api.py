@@ -1,6 +1,6 @@
-"""The CSR class's operator syntax (A @ X, A @ B, A.T, A.diagonal()) on the library's
-kernels, against the FP64 oracle, and its gradients against dense FP64 autograd on tiny
-inputs (Section 3.1: gradients of sparse values live on the input's pattern)."""
+"""The CSR class's operator syntax (A @ X, A @ B, A + B, A - B, A.T, A.diagonal()) on the
+library's kernels, against the FP64 oracle, and its gradients against dense FP64 autograd on
+tiny inputs (Section 3.1: gradients of sparse values live on the input's pattern)."""
 import numpy as np
 import pytest
 import torch
@@ -122,3 +122,55 @@ def test_composed_expression_gradients_match_dense_autograd():
     assert abs(float(loss.detach()) - float(lossd.detach())) <= 1e-5 * max(1.0, abs(float(lossd.detach())))
     assert np.abs(host(v.grad) - gd).max() <= 1e-4 * np.abs(gd).max()
     assert np.abs(host(x.grad) - xd.grad.numpy()).max() <= 1e-4 * np.abs(xd.grad.numpy()).max()
+
+
+@pytest.mark.parametrize("op", ["+", "-"])
+def test_add_and_sub_on_the_union_pattern(op):
+    """A + B and A - B for two patterns that overlap in part (and rows empty in one of them):
+    the union pattern bit-exact, values and both value gradients against the oracle."""
+    from oracle.spadd import spadd as o_spadd, spadd_backward as o_spadd_bwd
+    A = synth.empty_rows_csr(400, 300, seed=21, max_len=15)
+    B = synth.empty_rows_csr(400, 300, seed=22, max_len=15)
+    beta = 1.0 if op == "+" else -1.0
+    dA, dB = spx.CSR.from_host(A), spx.CSR.from_host(B)
+    va = dA.values.clone().requires_grad_(True)
+    vb = dB.values.clone().requires_grad_(True)
+    C = dA.with_values(va) + dB.with_values(vb) if op == "+" else dA.with_values(va) - dB.with_values(vb)
+    ip, ix, vals = o_spadd(A, B, 1.0, beta)
+    np.testing.assert_array_equal(host(C.indptr), ip)
+    np.testing.assert_array_equal(host(C.indices), ix)
+    _, _, norm = o_spadd(synth.CSR(A.m, A.n, A.indptr, A.indices, np.abs(A.values)),
+                         synth.CSR(B.m, B.n, B.indptr, B.indices, np.abs(B.values)), 1.0, 1.0)
+    assert_close_normalised(host(C.values), vals, norm, what=f"A {op} B")
+    gc = synth.normal(ix.size, seed=23)
+    (C.values * dev(gc)).sum().backward()
+    ga, gb = o_spadd_bwd(A, B, ip, ix, gc, 1.0, beta)
+    np.testing.assert_array_equal(host(va.grad), ga.astype(np.float32))
+    np.testing.assert_array_equal(host(vb.grad), gb.astype(np.float32))
+
+
+def test_sum_of_sparse_terms_gradients_match_dense_autograd():
+    """loss = sum(w * ((A - B) @ x + (A + B).T @ x)) through +, -, @ and .T, against dense FP64
+    autograd on the same matrices."""
+    A = synth.poisson2d(5)
+    B = synth.with_values(synth.random_k_per_row(A.m, 3, seed=24, ncols=A.n), synth.normal(A.m * 3, seed=25))
+    dA, dB = spx.CSR.from_host(A), spx.CSR.from_host(B)
+    va = dA.values.clone().requires_grad_(True)
+    vb = dB.values.clone().requires_grad_(True)
+    xh = synth.normal(A.n, seed=26)
+    w = synth.normal(A.n, seed=27)
+    x = dev(xh)
+    SA, SB = dA.with_values(va), dB.with_values(vb)
+    loss = ((((SA - SB) @ x) + ((SA + SB).T @ x)) * dev(w)).sum()
+    loss.backward()
+    Da = torch.tensor(_dense(A), requires_grad=True)
+    Db = torch.tensor(_dense(B), requires_grad=True)
+    xd = torch.tensor(xh.astype(np.float64))
+    lossd = ((((Da - Db) @ xd) + ((Da + Db).t() @ xd)) * torch.tensor(w.astype(np.float64))).sum()
+    lossd.backward()
+    ra = np.repeat(np.arange(A.m), np.diff(A.indptr))
+    rb = np.repeat(np.arange(B.m), np.diff(B.indptr))
+    ga, gb = Da.grad.numpy()[ra, A.indices], Db.grad.numpy()[rb, B.indices]
+    assert abs(float(loss.detach()) - float(lossd.detach())) <= 1e-5 * max(1.0, abs(float(lossd.detach())))
+    assert np.abs(host(va.grad) - ga).max() <= 1e-5 * max(1.0, np.abs(ga).max())
+    assert np.abs(host(vb.grad) - gb).max() <= 1e-5 * max(1.0, np.abs(gb).max())
