@@ -11,7 +11,8 @@ arrive as float32 (what the GPU consumes) and are promoted exactly to float64.
 
 Submodules: ``pcg_unrolled`` (the unrolled-PCG loss of Section 4.3 and its reverse),
 ``mpnn`` (the learned-preconditioner network), ``spai`` (Section 4.6: SPAI by gradient
-descent and the static-pattern SPAI).
+descent and the static-pattern SPAI), ``spadd`` and ``sptrsv`` (sparse add and the
+triangular solve with their gradients), ``adam`` (the optimiser that trains the network).
 
 Parity pins: every function here is checked by ``tests/test_oracle_*.py`` against
 dense linear algebra, closed forms of the model problems, finite differences or
