@@ -794,13 +794,22 @@ spx_status spx_edge_backward(const spx_csr* Lpat, const int32_t* lt_indptr,
                              float* gparams, void* workspace, size_t workspace_bytes,
                              void* stream);
 
-/* One Adam step on `count` float32 parameters (step >= 1 is the step number); when
- * params_bf16 is non-NULL the updated values are also written there as BF16. */
+/* One step of Adam (Kingma and Ba, ICLR 2015, Algorithm 1), the optimiser the paper trains
+ * its examples with (Section 4.1's Jacobi weights, Section 4.5's GCN), on `count` float32
+ * parameters.  For every t in [0, count), with c1 = 1 - beta1^step and c2 = 1 - beta2^step
+ * (formed in double on the host, then rounded to float):
+ *   m[t] = beta1 m[t] + (1 - beta1) g[t],   v[t] = beta2 v[t] + (1 - beta2) g[t]^2,
+ *   params[t] -= lr (m[t] / c1) / (sqrt(v[t] / c2) + eps)
+ * in float32 arithmetic.  params, m, v (device float32[count], updated in place; m and v
+ * zero before step 1) and grads (device float32[count]) belong to the caller; step >= 1 is
+ * the step number.  When params_bf16 (device bf16[count]) is non-NULL the updated
+ * parameters are also written there, rounded to nearest even.  SPX_INVALID_ARG for
+ * count < 0, step < 1 or a NULL array with count > 0.  Asynchronous on `stream`. */
 spx_status spx_adam_step(int64_t count, float* params, const float* grads, float* m, float* v,
                          int32_t step, float lr, float beta1, float beta2, float eps,
                          void* params_bf16, void* stream);
 
-/* dst[t] = (bf16) src[t]. */
+/* dst[t] = src[t] rounded to BF16 (nearest, ties to even); device arrays of count. */
 spx_status spx_to_bf16(int64_t count, const float* src, void* dst, void* stream);
 
 /* ---------------------------------------- IC(0) baseline (Section 3.1.5 solves) */

@@ -606,8 +606,10 @@ extern "C" spx_status spx_adam_step(int64_t count, float* params, const float* g
     if (count < 0 || step < 1 || (count > 0 && (!params || !grads || !m || !v)))
         return set_error(SPX_INVALID_ARG, "spx_adam_step: bad arguments");
     if (count == 0) return SPX_OK;
-    const float c1 = 1.f - powf(beta1, (float)step);
-    const float c2 = 1.f - powf(beta2, (float)step);
+    // Bias corrections in double on the host, rounded once: 1 - beta2^t is small for small t,
+    // so a float power would carry its rounding error into every update at 1/(1 - beta2^t).
+    const float c1 = (float)(1.0 - pow((double)beta1, (double)step));
+    const float c2 = (float)(1.0 - pow((double)beta2, (double)step));
     adam_kernel<<<grid1(count, 256), 256, 0, as_stream(stream)>>>(count, params, grads, m, v, lr, beta1, beta2, eps, c1,
                                                                    c2, static_cast<__nv_bfloat16*>(params_bf16));
     SPX_CHECK_LAUNCH("spx_adam_step");
