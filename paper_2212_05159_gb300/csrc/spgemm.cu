@@ -8,13 +8,15 @@
 //             the list varies, no result depends on it);
 //   symbolic  per row: expand the P_i product columns, sort, keep the unique ones; the
 //             sorted unique columns go to a products-sized scratch at offset Pptr[i] and
-//             their count to row_nnz[i]; C_indptr = scan(row_nnz).  One warp per row:
-//             rows of at most 64 products fetch them straight into registers (two per
-//             lane) and sort them there with a bitonic network over shuffles, skipping its
-//             first levels when B's rows can be laid out as aligned sorted runs; rows of
-//             65..512 products sort in shared memory; a big row takes a whole block and a
-//             shared bitmap of the column space (chunked), which yields the columns already
-//             sorted.  mask(C) is structural: no numerical-zero dropping.
+//             their count to row_nnz[i]; C_indptr = scan(row_nnz).  Rows of at most 8
+//             entries of A and 64 products: one 8-lane group each (four rows per warp),
+//             the products in eight registers per lane, sorted by a bitonic network whose
+//             short strides stay in a lane and long ones are shuffles, its first levels
+//             skipped when B's rows can be laid out as aligned sorted runs.  Other rows of
+//             at most 64 products: one warp, two registers per lane, the same network;
+//             rows of 65..512 products sort in shared memory; a big row takes a whole block
+//             and a shared bitmap of the column space (chunked), which yields the columns
+//             already sorted.  mask(C) is structural: no numerical-zero dropping.
 //   fill      copies the unique columns into C_indices (8 lanes per row).
 //   numeric   per row, C_ij = sum over k in A_i of A_ik B_kj.  Rows of at most 8 entries of
 //             A and 64 columns of C: one 8-lane group each (four rows per warp), every B_k's
@@ -156,17 +158,162 @@ __device__ __forceinline__ void warp_bitonic_sort_regs(int (&v)[NS], int lane, i
     }
 }
 
-// Sorted unique product columns of row i -> tmp + pptr[i]; count -> row_nnz[i].
-__global__ void __launch_bounds__(SYM_WARPS * 32) symbolic_warp_kernel(
+// ------------------------------------------------------------------ symbolic (small rows)
+// Rows with at most SYG_A entries of A and at most SYG_P products: one 8-lane group per row,
+// so a warp keeps four rows in flight.  A row's 64 slots are laid out lane-major (slot
+// i = 8 c + s is register s of lane c): the bitonic network's strides 1..4 compare registers
+// of one lane, strides 8..32 exchange register s with lane c ^ (stride / 8) by a shuffle.  When
+// the aligned-run layout fits (|A_i| R <= 64, R the smallest power of two >= every |B_k|),
+// entry e's columns fill slots [e R, e R + R), ascending for even e and reversed (pads first)
+// for odd e, and the levels up to R are skipped; with R = 8 a lane's run is its own registers.
+// Otherwise the products are packed in entry order and sorted in full.  The first of each
+// run is kept, in order.  symbolic_warp_kernel skips these rows.
+constexpr int SYG_THREADS = 256;
+constexpr int SYG_A = GRP;             // entries of A per small row: one per lane of the group
+constexpr int SYG_P = 8 * GRP;         // products per small row: eight registers per lane
+
+__device__ __forceinline__ bool small_symbolic_row(int na, int p) { return na <= SYG_A && p <= SYG_P; }
+
+__global__ void __launch_bounds__(SYG_THREADS) symbolic_group_kernel(
     int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
     const int32_t* __restrict__ b_idx, const int32_t* __restrict__ prod, const int64_t* __restrict__ pptr,
     int32_t* __restrict__ tmp, int32_t* __restrict__ row_nnz) {
-    __shared__ int keys_all[SYM_WARPS][WARP_CAP];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t row = (int64_t)blockIdx.x * SYM_WARPS + warp;
-    if (row >= m) return;
+    const int lane = threadIdx.x & 31;
+    const int c = lane % GRP;
+    const unsigned gmask = ((1u << GRP) - 1u) << ((lane / GRP) * GRP);
+    const int64_t row = ((int64_t)blockIdx.x * SYG_THREADS + threadIdx.x) / GRP;
+    if (row >= m) return;                                  // the whole group leaves
     const int P = prod[row];
-    if (P > WARP_CAP) return;                       // a big-row block takes it
+    const int a0 = a_ptr[row], nA = a_ptr[row + 1] - a0;
+    if (!small_symbolic_row(nA, P)) return;                // group-uniform
+    int32_t* out = tmp + pptr[row];                        // loaded now, off the row's chain
+    int b0 = 0, len = 0;
+    if (c < nA) {
+        const int k = a_idx[a0 + c];
+        b0 = b_ptr[k];
+        len = b_ptr[k + 1] - b0;
+    }
+    int lmax = len;
+#pragma unroll
+    for (int o = 1; o < GRP; o <<= 1) lmax = max(lmax, __shfl_xor_sync(gmask, lmax, o, GRP));
+    int R = 1;
+    while (R < lmax) R <<= 1;
+    int v[8];
+    int start;
+    if (R == 8) {                                          // entry c's run is lane c's registers
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            int key = INT_MAX;
+            if ((c & 1) == 0) {
+                if (s < len) key = b_idx[b0 + s];
+            } else {
+                const int q = s - (8 - len);                   // descending: pads first
+                if (q >= 0) key = b_idx[b0 + len - 1 - q];
+            }
+            v[s] = key;                                        // lanes c >= nA have len 0: pads
+        }
+        start = 16;
+    } else if (nA * R <= SYG_P) {
+        const int lg = __ffs(R) - 1;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int i = 8 * c + s;
+            const int e = i >> lg, pos = i & (R - 1);
+            const int bb = __shfl_sync(gmask, b0, e & (GRP - 1), GRP);
+            const int ll = __shfl_sync(gmask, len, e & (GRP - 1), GRP);
+            int key = INT_MAX;
+            if (e < nA) {
+                if ((e & 1) == 0) {
+                    if (pos < ll) key = b_idx[bb + pos];
+                } else {
+                    const int q = pos - (R - ll);              // descending: pads first
+                    if (q >= 0) key = b_idx[bb + ll - 1 - q];
+                }
+            }
+            v[s] = key;
+        }
+        start = 2 * R;
+    } else {
+        // packed: product t lies in the entry whose inclusive scan of the lengths first exceeds t
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < GRP; o <<= 1) {
+            const int y = __shfl_up_sync(gmask, incl, o, GRP);
+            if (c >= o) incl += y;
+        }
+        const int excl = incl - len;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int t = 8 * c + s;
+            int e = 0;                                       // lanes with incl <= t
+#pragma unroll
+            for (int step = GRP / 2; step >= 1; step >>= 1) {
+                const int cc = __shfl_sync(gmask, incl, e + step - 1, GRP);
+                if (cc <= t) e += step;
+            }
+            e = min(e, GRP - 1);
+            const int src = __shfl_sync(gmask, b0, e, GRP) + t - __shfl_sync(gmask, excl, e, GRP);
+            v[s] = t < P ? b_idx[src] : INT_MAX;
+        }
+        start = 2;
+    }
+#pragma unroll
+    for (int size = 2; size <= SYG_P; size <<= 1) {
+        if (size < start) continue;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 8) {                               // partner: register s of lane c ^ (stride / 8)
+                const int lm = stride >> 3;
+                const bool lower = (c & lm) == 0;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const bool up = ((8 * c + s) & size) == 0;
+                    const int p = __shfl_xor_sync(gmask, v[s], lm, GRP);
+                    v[s] = (lower == up) ? min(v[s], p) : max(v[s], p);
+                }
+            } else {                                         // both keys in this lane
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    if (s & stride) continue;
+                    const bool up = ((8 * c + s) & size) == 0;
+                    const int a = v[s], b = v[s | stride];
+                    v[s] = up ? min(a, b) : max(a, b);
+                    v[s | stride] = up ? max(a, b) : min(a, b);
+                }
+            }
+        }
+    }
+    // the first of each run among the P real keys (pads, INT_MAX, sort last)
+    const int prev7 = __shfl_up_sync(gmask, v[7], 1, GRP);
+    unsigned keep = 0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int i = 8 * c + s;
+        const int prev = s ? v[s - 1] : prev7;
+        if (i < P && (i == 0 || v[s] != prev)) keep |= 1u << s;
+    }
+    const int cnt = __popc(keep);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < GRP; o <<= 1) {
+        const int y = __shfl_up_sync(gmask, incl, o, GRP);
+        if (c >= o) incl += y;
+    }
+    out += incl - cnt;
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+        if (keep & (1u << s)) *out++ = v[s];
+    if (c == GRP - 1) row_nnz[row] = incl;
+}
+
+// ------------------------------------------------------------------ symbolic (other warp rows)
+// Sorted unique product columns of row i -> tmp + pptr[i]; count -> row_nnz[i].
+__device__ __forceinline__ void symbolic_warp_row(
+    int64_t row, int lane, int* keys, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx,
+    const int32_t* __restrict__ b_ptr, const int32_t* __restrict__ b_idx, const int32_t* __restrict__ prod,
+    const int64_t* __restrict__ pptr, int32_t* __restrict__ tmp, int32_t* __restrict__ row_nnz) {
+    __syncwarp();                                   // the previous row's reads of keys are done
+    const int P = prod[row];
     const int a0 = a_ptr[row], nA = a_ptr[row + 1] - a0;
     int32_t* out = tmp + pptr[row];
     if (P <= 64 && nA <= 32) {
@@ -257,7 +404,6 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) symbolic_warp_kernel(
         if (lane == 0) row_nnz[row] = base;
         return;
     }
-    int* keys = keys_all[warp];
     // expand
     int pos = 0;
     for (int e = a0; e < a0 + nA; ++e) {
@@ -282,6 +428,32 @@ __global__ void __launch_bounds__(SYM_WARPS * 32) symbolic_warp_kernel(
         base += __popc(bal);
     }
     if (lane == 0) row_nnz[row] = base;
+}
+
+// The rows neither symbolic_group_kernel (small rows) nor symbolic_big_kernel (more than
+// WARP_CAP products) takes: each warp checks 32 rows at once (lane r: row base + r), then runs
+// the ones that are its, one at a time.  Grid-strided over the rows.
+__global__ void __launch_bounds__(SYM_WARPS * 32) symbolic_warp_kernel(
+    int32_t m, const int32_t* __restrict__ a_ptr, const int32_t* __restrict__ a_idx, const int32_t* __restrict__ b_ptr,
+    const int32_t* __restrict__ b_idx, const int32_t* __restrict__ prod, const int64_t* __restrict__ pptr,
+    int32_t* __restrict__ tmp, int32_t* __restrict__ row_nnz) {
+    __shared__ int keys_all[SYM_WARPS][WARP_CAP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * SYM_WARPS;
+    for (int64_t base = ((int64_t)blockIdx.x * SYM_WARPS + warp) * 32; base < m; base += nw * 32) {
+        const int64_t r = base + lane;
+        bool mine = false;
+        if (r < m) {
+            const int p = prod[r];
+            mine = p <= WARP_CAP && !small_symbolic_row(a_ptr[r + 1] - a_ptr[r], p);
+        }
+        unsigned todo = __ballot_sync(FULL, mine);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            symbolic_warp_row(base + b, lane, keys_all[warp], a_ptr, a_idx, b_ptr, b_idx, prod, pptr, tmp, row_nnz);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ symbolic (big rows)
@@ -862,7 +1034,13 @@ extern "C" spx_status spx_spgemm_symbolic(const spx_csr* A, const spx_csr* B, in
                          (long long)products * 4);
     int32_t* row_nnz = (int32_t*)(w + L.row_nnz);
     if (A->m > 0) {
-        symbolic_warp_kernel<<<(unsigned)((A->m + SYM_WARPS - 1) / SYM_WARPS), SYM_WARPS * 32, 0, st>>>(
+        symbolic_group_kernel<<<(unsigned)((A->m + SYG_THREADS / GRP - 1) / (SYG_THREADS / GRP)), SYG_THREADS, 0,
+                                st>>>(A->m, A->indptr, A->indices, B->indptr, B->indices,
+                                      (const int32_t*)(w + L.prod), pptr, (int32_t*)tmp, row_nnz);
+        SPX_CHECK_LAUNCH("spgemm symbolic small rows");
+        const int64_t wblocks = ((int64_t)A->m + 32 * SYM_WARPS - 1) / (32 * SYM_WARPS);
+        const int64_t wcap = (int64_t)num_sms() * 8;
+        symbolic_warp_kernel<<<(unsigned)(wblocks < wcap ? wblocks : wcap), SYM_WARPS * 32, 0, st>>>(
             A->m, A->indptr, A->indices, B->indptr, B->indices, (const int32_t*)(w + L.prod), pptr, (int32_t*)tmp,
             row_nnz);
         SPX_CHECK_LAUNCH("spgemm symbolic");

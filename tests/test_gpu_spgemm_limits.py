@@ -83,7 +83,39 @@ def deep_columns_pair():
     return A, B
 
 
-PAIRS = {"wide_rows": wide_rows_pair, "deep_columns": deep_columns_pair}
+def group_layouts_pair():
+    """Rows of A that put the symbolic phase's 8-lane groups in each of their layouts: one entry
+    whose B row has 1, 33 or 64 columns (runs of 1 and 64 slots), two entries of 17..32 columns
+    (runs of 32), eight of exactly 8 (a lane's registers each, 64 products), five with one row
+    of 9..16 columns (packed: 5 x 16 > 64 slots), eight of mixed lengths summing to 64 and 65
+    (packed at the product limit, and one past it), empty rows of A and of B; B's rows overlap
+    heavily, so most products repeat a column."""
+    rng = np.random.default_rng(11)
+    ncol = 200
+    lens = [0, 1, 8, 8, 8, 8, 8, 8, 8, 8, 9, 12, 16, 17, 25, 32, 33, 40, 64, 3, 2, 5, 7, 4, 6, 15, 1, 0]
+    nb = len(lens)
+    B = csr_from_rows([sorted(rng.choice(ncol, L, replace=False).tolist()) for L in lens], ncol, seed=12)
+    by_len = {}
+    for k, L in enumerate(lens):
+        by_len.setdefault(L, []).append(k)
+    eights = by_len[8]
+    templates = [
+        [], [by_len[1][0]], [by_len[33][0]], [by_len[64][0]], [by_len[0][0]], [by_len[0][0], by_len[0][1]],
+        [by_len[17][0], by_len[32][0]], [by_len[25][0], by_len[17][0]],
+        eights,                                                       # 8 x 8 = 64, runs of 8
+        [by_len[12][0], by_len[1][0], by_len[2][0], by_len[3][0], by_len[4][0]],        # packed, 22 products
+        [by_len[16][0], by_len[15][0], by_len[9][0], by_len[8][0], by_len[7][0],
+         by_len[5][0], by_len[3][0], by_len[1][0]],                  # packed, 64 products
+        [by_len[16][0], by_len[15][0], by_len[9][0], by_len[8][0], by_len[7][0],
+         by_len[6][0], by_len[3][0], by_len[1][0]],                  # 65 products: the warp path
+        [by_len[40][0], by_len[8][0], by_len[8][1]],                 # 56 products, R = 64: packed
+    ]
+    rows = [sorted(set(templates[i % len(templates)])) for i in range(3 * len(templates))]
+    A = csr_from_rows(rows, nb, seed=13)
+    return A, B
+
+
+PAIRS = {"wide_rows": wide_rows_pair, "deep_columns": deep_columns_pair, "group_layouts": group_layouts_pair}
 
 
 @pytest.fixture(scope="module", params=list(PAIRS))
@@ -101,6 +133,12 @@ def test_the_matrices_reach_the_limits(pair):
     if name == "wide_rows":
         assert {64, 65} <= set(c_len[a_len == 8].tolist()) and (a_len == 9).any()
         assert c_len.mean() > 32
+    elif name == "group_layouts":
+        b_len = np.diff(B.indptr.astype(np.int64))
+        prods = np.array([b_len[A.indices[A.indptr[i]:A.indptr[i + 1]]].sum() for i in range(A.m)])
+        assert {0, 1, 22, 33, 49, 56, 64, 65} <= set(prods.tolist())
+        assert (prods[a_len == 8] == 64).any() and (prods[a_len == 8] == 65).any()
+        assert (c_len < prods).any()                  # repeated columns to merge
     else:
         assert {8, 32, 33, 40} <= set(at_len.tolist()) and {8, 9} <= set(np.diff(B.indptr).tolist())
         assert c_len.mean() <= 32
