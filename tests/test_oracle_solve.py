@@ -1,7 +1,8 @@
 """Pins for the oracle's PCG, preconditioners, IC(0), triangular solves and the
 sparse-solve adjoint (CPU only).
 
-* PCG against a dense LAPACK solve on tiny SPD systems;
+* PCG against a dense LAPACK solve on tiny SPD systems, and against the closed-form inverse
+  of A_N (the discrete Green's function) with plain and Jacobi preconditioning;
 * one-iteration convergence on an eigenvector right-hand side of A_N / 2D Poisson
   (Section 4 model problems);
 * IC(0) of the tridiagonal A_N is its exact Cholesky factor (no fill), so IC(0)-PCG
@@ -179,3 +180,24 @@ def test_solve_adjoint_finite_differences(orc):
         Am[rows[e], A.indices[e]] -= h
         fd = (g @ np.linalg.solve(Ap, b) - g @ np.linalg.solve(Am, b)) / (2 * h)
         assert abs(fd - ga[e]) < 1e-4 * (1 + abs(ga[e]))
+
+
+@pytest.mark.parametrize("N", [1, 2, 17, 64])
+def test_a_n_solve_is_the_discrete_green_function(orc, N):
+    """A_N (Section 4's 1D model problem) has the closed-form inverse
+    (A_N^-1)_ij = min(i, j) (N + 1 - max(i, j)) / (N + 1), i, j = 1..N (the discrete Green's
+    function); CG reaches it within N iterations (A_N has N distinct eigenvalues)."""
+    A = synth.poisson1d(N)
+    i = np.arange(1, N + 1)
+    G = np.minimum.outer(i, i) * (N + 1 - np.maximum.outer(i, i)) / (N + 1)
+    rng = np.random.default_rng(N)
+    b = rng.normal(size=N)
+    x, st, it = orc.pcg(A, b, tol=1e-13)
+    assert st == 0 and it <= N
+    np.testing.assert_allclose(x, G @ b, rtol=1e-10, atol=1e-12 * np.abs(G @ b).max())
+    for j in (0, N - 1, N // 2):                       # columns of the inverse
+        e = np.zeros(N)
+        e[j] = 1.0
+        xj, st, _ = orc.pcg(A, e, tol=1e-13, pc="jacobi")
+        assert st == 0
+        np.testing.assert_allclose(xj, G[:, j], rtol=1e-10, atol=1e-13)
